@@ -1,0 +1,272 @@
+"""Euler operator, boundary conditions, RK stages, patch exchange, Δt, sums (oracle).
+
+Test infrastructure: only the test suite, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` may use this module.
+
+Follows:
+  * Eq. (1)-(3): 2D Euler equations in conservative form, e = (rho, rho u,
+    rho v, E), E = p/(gamma-1) + rho |u|^2 / 2;
+  * Algorithm 5 / §5 item 1: the operator in parameter space built from FC
+    derivatives and the Jacobian of the inverse patch map.  Reading used here:
+    conservative contravariant form
+        L(e) = -(1/J) [ d/dq1 (y_q2 f - x_q2 g) + d/dq2 (-y_q1 f + x_q1 g) ],
+    J = x_q1 y_q2 - x_q2 y_q1, with the metrics obtained by the same FC
+    derivative of the grid coordinates; on Cartesian patches this is
+    L(e) = -(df/dx + dg/dy) with FC derivatives at the physical spacings;
+  * artificial viscosity term (reading; the paper's form is in Part I):
+    d_t e + div f = div(mu grad e), folded into the fluxes as
+    f - mu de/dx, g - mu de/dy (Cartesian patches);
+  * §5 item 4 / Algorithm 1: explicit four-stage Runge-Kutta (classical RK4
+    coefficients, reading of "SSPRK-4"), boundary conditions enforced after
+    every stage, exchange of fringe values after every stage;
+  * §3.3: n_f-point fringes of internal sides receive values from donor points
+    of other patches that are not themselves receivers; coincident grids copy;
+  * Δt (reading of I-(31)): CFL * min over points of h_k / (|U_k| + c |grad q_k|)
+    with U_k the contravariant velocity along parameter direction k.
+"""
+import numpy as np
+
+from paper_2506_19370_gb300 import inputs as I
+from . import fcgram
+
+RK4_A = (0.5, 0.5, 1.0)          # e_{s+1} = e_n + a_s dt k_s
+RK4_B = (1.0 / 6.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 6.0)
+
+
+def pressure(e, gamma):
+    rho, mx, my, E = e
+    return (gamma - 1.0) * (E - 0.5 * (mx * mx + my * my) / rho)
+
+
+def fluxes(e, gamma):
+    """Physical fluxes f (x) and g (y) of Eq. (1)."""
+    rho, mx, my, E = e
+    u = mx / rho
+    v = my / rho
+    p = pressure(e, gamma)
+    f = np.stack([mx, mx * u + p, my * u, (E + p) * u])
+    g = np.stack([my, mx * v, my * v + p, (E + p) * v])
+    return f, g
+
+
+class PatchGeom:
+    """Per-patch quantities the operator needs: spacings and metrics."""
+
+    def __init__(self, patch, d, C):
+        self.patch = patch
+        self.n1, self.n2 = patch.n1, patch.n2
+        self.h1 = 1.0 / (patch.n1 - 1)
+        self.h2 = 1.0 / (patch.n2 - 1)
+        if patch.cartesian:
+            x0, x1, y0, y1 = patch.box
+            self.hx = (x1 - x0) / (patch.n1 - 1)
+            self.hy = (y1 - y0) / (patch.n2 - 1)
+            self.x_q1 = np.full((self.n2, self.n1), x1 - x0)
+            self.y_q2 = np.full((self.n2, self.n1), y1 - y0)
+            self.x_q2 = np.zeros((self.n2, self.n1))
+            self.y_q1 = np.zeros((self.n2, self.n1))
+        else:
+            X, Y = patch.coords()
+            self.x_q1 = fcgram.fc_derivative_axis(X, self.h1, d, C, axis=1)
+            self.x_q2 = fcgram.fc_derivative_axis(X, self.h2, d, C, axis=0)
+            self.y_q1 = fcgram.fc_derivative_axis(Y, self.h1, d, C, axis=1)
+            self.y_q2 = fcgram.fc_derivative_axis(Y, self.h2, d, C, axis=0)
+        self.J = self.x_q1 * self.y_q2 - self.x_q2 * self.y_q1
+
+
+def rhs(e, geom, d, C, gamma, mu=None):
+    """L(e) on one patch (Algorithm 5, operator evaluation); e is (4, n2, n1)."""
+    e = np.asarray(e, dtype=np.float64)
+    f, g = fluxes(e, gamma)
+    if geom.patch.cartesian:
+        if mu is not None:
+            f = f - mu * fcgram.fc_derivative_axis(e, geom.hx, d, C, axis=2)
+            g = g - mu * fcgram.fc_derivative_axis(e, geom.hy, d, C, axis=1)
+        return -(fcgram.fc_derivative_axis(f, geom.hx, d, C, axis=2)
+                 + fcgram.fc_derivative_axis(g, geom.hy, d, C, axis=1))
+    if mu is not None:
+        raise NotImplementedError("artificial viscosity on curvilinear patches")
+    F1 = geom.y_q2 * f - geom.x_q2 * g
+    F2 = -geom.y_q1 * f + geom.x_q1 * g
+    div = (fcgram.fc_derivative_axis(F1, geom.h1, d, C, axis=2)
+           + fcgram.fc_derivative_axis(F2, geom.h2, d, C, axis=1))
+    return -div / geom.J
+
+
+def _side_index(side, n1, n2):
+    if side == 0:
+        return (slice(None), slice(None), 0)
+    if side == 1:
+        return (slice(None), slice(None), n1 - 1)
+    if side == 2:
+        return (slice(None), 0, slice(None))
+    return (slice(None), n2 - 1, slice(None))
+
+
+def apply_bc(e, geom, inst):
+    """Boundary conditions of one patch, sides in the order left, right, bottom, top.
+
+    Wall: normal momentum removed (Cartesian: the normal component is set to
+    zero); inflow: the prescribed conserved state; outflow: energy recomputed
+    for the prescribed pressure.  Acts in place on e (4, n2, n1).
+    """
+    n1, n2 = geom.n1, geom.n2
+    gamma = inst.gamma
+    for side, code in enumerate(geom.patch.bc):
+        idx = _side_index(side, n1, n2)
+        if code == I.BC_WALL:
+            if geom.patch.cartesian:
+                comp = 1 if side < 2 else 2
+                e[(comp,) + idx[1:]] = 0.0
+            else:
+                if side < 2:
+                    nx, ny = geom.y_q2[idx[1:]], -geom.x_q2[idx[1:]]
+                else:
+                    nx, ny = -geom.y_q1[idx[1:]], geom.x_q1[idx[1:]]
+                nn = np.sqrt(nx * nx + ny * ny)
+                nx, ny = nx / nn, ny / nn
+                mn = e[(1,) + idx[1:]] * nx + e[(2,) + idx[1:]] * ny
+                e[(1,) + idx[1:]] -= mn * nx
+                e[(2,) + idx[1:]] -= mn * ny
+        elif code == I.BC_INFLOW:
+            for c in range(4):
+                e[(c,) + idx[1:]] = inst.inflow[c]
+        elif code == I.BC_OUTFLOW:
+            rho = e[(0,) + idx[1:]]
+            mx = e[(1,) + idx[1:]]
+            my = e[(2,) + idx[1:]]
+            e[(3,) + idx[1:]] = inst.p_out / (gamma - 1.0) + 0.5 * (mx * mx + my * my) / rho
+    return e
+
+
+def receiver_mask(patch, n_f):
+    """Points within n_f points of an internal side (the n_f-point fringe, §3.3)."""
+    m = np.zeros((patch.n2, patch.n1), dtype=bool)
+    b = patch.bc
+    if b[0] == I.BC_INTERNAL:
+        m[:, :n_f] = True
+    if b[1] == I.BC_INTERNAL:
+        m[:, patch.n1 - n_f:] = True
+    if b[2] == I.BC_INTERNAL:
+        m[:n_f, :] = True
+    if b[3] == I.BC_INTERNAL:
+        m[patch.n2 - n_f:, :] = True
+    return m
+
+
+def fringe_map(patches, n_f=5):
+    """Donor for every fringe point: rows (dst patch, j, i, src patch, j', i').
+
+    Coincident Cartesian grids only: the donor is the lowest-numbered other
+    patch holding a grid point at the same location outside its own fringe.
+    """
+    masks = [receiver_mask(p, n_f) for p in patches]
+    rows = []
+    for p, pt in enumerate(patches):
+        if not pt.cartesian and masks[p].any():
+            raise NotImplementedError("exchange on curvilinear patches")
+        X, Y = pt.coords()
+        for j, i in zip(*np.nonzero(masks[p])):
+            x, y = X[j, i], Y[j, i]
+            found = None
+            for q, qt in enumerate(patches):
+                if q == p:
+                    continue
+                x0, x1, y0, y1 = qt.box
+                hx = (x1 - x0) / (qt.n1 - 1)
+                hy = (y1 - y0) / (qt.n2 - 1)
+                fi = (x - x0) / hx
+                fj = (y - y0) / hy
+                ii, jj = int(round(fi)), int(round(fj))
+                if abs(fi - ii) > 1e-6 or abs(fj - jj) > 1e-6:
+                    continue
+                if not (0 <= ii < qt.n1 and 0 <= jj < qt.n2):
+                    continue
+                if masks[q][jj, ii]:
+                    continue
+                found = (q, jj, ii)
+                break
+            if found is None:
+                raise ValueError(f"no donor for patch {p} point ({j},{i})")
+            rows.append((p, j, i) + found)
+    return np.array(rows, dtype=np.int64).reshape(-1, 6)
+
+
+def exchange(state, fmap):
+    """Copy donor values into every fringe point (all four fields)."""
+    for p, j, i, q, jj, ii in fmap:
+        state[p][:, j, i] = state[q][:, jj, ii]
+    return state
+
+
+def time_step(state, geoms, gamma, cfl):
+    """Δt = CFL * min over all points of min_k h_k / (|U_k| + c |grad q_k|)."""
+    best = np.inf
+    for e, g in zip(state, geoms):
+        rho, mx, my, E = e
+        u, v = mx / rho, my / rho
+        c = np.sqrt(gamma * pressure(e, gamma) / rho)
+        # grad q1 = (y_q2, -x_q2)/J, grad q2 = (-y_q1, x_q1)/J
+        U1 = (g.y_q2 * u - g.x_q2 * v) / g.J
+        U2 = (-g.y_q1 * u + g.x_q1 * v) / g.J
+        n1 = np.sqrt(g.y_q2 ** 2 + g.x_q2 ** 2) / np.abs(g.J)
+        n2 = np.sqrt(g.y_q1 ** 2 + g.x_q1 ** 2) / np.abs(g.J)
+        best = min(best, np.min(g.h1 / (np.abs(U1) + c * n1)), np.min(g.h2 / (np.abs(U2) + c * n2)))
+    return cfl * best
+
+
+def max_wave_speed(state, gamma):
+    return max(float(np.max(np.sqrt(e[1] ** 2 + e[2] ** 2) / e[0]
+                            + np.sqrt(gamma * pressure(e, gamma) / e[0]))) for e in state)
+
+
+class Solver:
+    """Multi-patch FC-SDNN stepping on one instance (Algorithms 1 and 5)."""
+
+    def __init__(self, inst, d=5, C=25, n_f=5, cfl=0.5):
+        self.inst = inst
+        self.d, self.C, self.n_f, self.cfl = d, C, n_f, cfl
+        self.geoms = [PatchGeom(p, d, C) for p in inst.patches]
+        self.fmap = fringe_map(inst.patches, n_f)
+
+    def rhs_all(self, state, mu=None):
+        return [rhs(e, g, self.d, self.C, self.inst.gamma, None if mu is None else mu[k])
+                for k, (e, g) in enumerate(zip(state, self.geoms))]
+
+    def stage(self, s, dt, e_n, e_s, acc, mu=None):
+        """One RK4 stage: returns (e_out, acc); BCs then exchange on e_out."""
+        k = self.rhs_all(e_s, mu)
+        out, acc_new = [], []
+        for p in range(len(e_n)):
+            if s == 0:
+                a = e_n[p] + (RK4_B[0] * dt) * k[p]
+            elif s < 3:
+                a = acc[p] + (RK4_B[s] * dt) * k[p]
+            else:
+                a = None
+            o = e_n[p] + (RK4_A[s] * dt) * k[p] if s < 3 else acc[p] + (RK4_B[3] * dt) * k[p]
+            apply_bc(o, self.geoms[p], self.inst)
+            out.append(o)
+            acc_new.append(a)
+        exchange(out, self.fmap)
+        return out, acc_new
+
+    def step(self, state, dt, mu=None):
+        e_n = [e.copy() for e in state]
+        e_s, acc = e_n, None
+        for s in range(4):
+            e_s, acc = self.stage(s, dt, e_n, e_s, acc, mu)
+        return e_s
+
+    def dt(self, state):
+        return time_step(state, self.geoms, self.inst.gamma, self.cfl)
+
+    def conservation_sums(self, state):
+        """Per patch: FC quadrature of each conserved field times |J| (4 sums)."""
+        out = []
+        for e, g in zip(state, self.geoms):
+            W1 = fcgram.fc_quadrature_weights(g.n1, self.d, self.C)
+            W2 = fcgram.fc_quadrature_weights(g.n2, self.d, self.C)
+            w = np.outer(W2, W1) * np.abs(g.J)
+            out.append(np.array([np.sum(w * e[c]) for c in range(4)]))
+        return np.array(out)

@@ -1,0 +1,219 @@
+"""Seeded synthetic inputs: patch layouts, initial data and classifier windows.
+
+This module is the one piece shared by the CUDA path and the CPU oracle.  It
+holds no step of the FC-SDNN method: it only lays out patches, samples initial
+conditions and draws labelled training windows from seeded generators.
+
+Workloads (shapes follow the paper's problems, §7):
+  * ``vortex_instance``: one Cartesian patch on [0,1]^2 with an isentropic
+    vortex advected by a uniform flow (single-patch accuracy case);
+  * ``sod_instance``: the shock tube on [0,1] x [0,0.1] split into overlapping
+    Cartesian patches, Sod data (§7 energy-conservation test uses the same
+    states), reflecting walls;
+  * ``mach_shock_state`` / ``mach_flow_state``: the Mach-M initial states of §7
+    (Eq. for the Mach-M flow and the Mach-M shock);
+  * ``classifier_windows``: labelled 16-point windows of seeded smooth, C1,
+    kink and jump profiles for training the smoothness classifier.
+"""
+from dataclasses import dataclass, field
+from typing import List, Optional, Sequence
+
+import numpy as np
+
+GAMMA = 1.4
+SEED = 2506
+
+# boundary-condition codes, one per patch side (left i=0, right i=n1-1,
+# bottom j=0, top j=n2-1); they match the FCS_BC_* values of the C ABI
+BC_INTERNAL = 0   # side lies inside the domain: values come from donors
+BC_WALL = 1       # slip / reflecting wall: normal momentum set to zero
+BC_INFLOW = 2     # Dirichlet: all four conserved variables prescribed
+BC_OUTFLOW = 3    # pressure prescribed, energy recomputed
+BC_FREE = 4       # nothing imposed (supersonic outflow)
+
+
+@dataclass
+class Patch:
+    """One logically rectangular patch with an n1 x n2 grid (i along q1).
+
+    Cartesian patches carry their box; curvilinear ones carry the physical
+    coordinates x[j, i], y[j, i] of every grid point.
+    """
+    n1: int
+    n2: int
+    bc: Sequence[int]
+    box: Optional[Sequence[float]] = None          # (x0, x1, y0, y1)
+    x: Optional[np.ndarray] = None
+    y: Optional[np.ndarray] = None
+
+    @property
+    def cartesian(self):
+        return self.box is not None
+
+    def coords(self):
+        if self.cartesian:
+            x0, x1, y0, y1 = self.box
+            xs = x0 + (x1 - x0) * np.arange(self.n1) / (self.n1 - 1)
+            ys = y0 + (y1 - y0) * np.arange(self.n2) / (self.n2 - 1)
+            return np.meshgrid(xs, ys)
+        return self.x, self.y
+
+
+@dataclass
+class Instance:
+    """One flow problem: patches, gas constant, boundary data, initial state."""
+    patches: List[Patch]
+    state: List[np.ndarray]                       # per patch (4, n2, n1), conserved
+    gamma: float = GAMMA
+    inflow: Sequence[float] = (1.0, 1.0, 0.0, 2.5)  # conserved inflow state
+    p_out: float = 1.0
+    name: str = ""
+    meta: dict = field(default_factory=dict)
+
+
+def conserved(rho, u, v, p, gamma=GAMMA):
+    """(rho, rho u, rho v, E) from primitives, E = p/(gamma-1) + rho|u|^2/2 (Eq. 2)."""
+    rho, u, v, p = np.broadcast_arrays(*(np.asarray(a, dtype=np.float64) for a in (rho, u, v, p)))
+    return np.stack([rho, rho * u, rho * v, p / (gamma - 1.0) + 0.5 * rho * (u * u + v * v)])
+
+
+def vortex_primitives(x, y, t, eps=5.0, R=0.05, x0=0.5, y0=0.5, u0=1.0, v0=0.0, gamma=GAMMA):
+    """Isentropic vortex of strength eps and radius R advected by (u0, v0).
+
+    Standard form: with (xb, yb) = ((x - x0 - u0 t)/R, (y - y0 - v0 t)/R) and
+    r2 = xb^2 + yb^2, du = -eps/(2 pi) e^{(1-r2)/2} yb, dv = eps/(2 pi)
+    e^{(1-r2)/2} xb, T = 1 - (gamma-1) eps^2/(8 gamma pi^2) e^{1-r2},
+    rho = T^{1/(gamma-1)}, p = rho^gamma (free stream rho = p = 1).
+    """
+    xb = (x - x0 - u0 * t) / R
+    yb = (y - y0 - v0 * t) / R
+    r2 = xb * xb + yb * yb
+    g = np.exp(0.5 * (1.0 - r2))
+    u = u0 - eps / (2 * np.pi) * g * yb
+    v = v0 + eps / (2 * np.pi) * g * xb
+    T = 1.0 - (gamma - 1.0) * eps * eps / (8.0 * gamma * np.pi ** 2) * g * g
+    rho = T ** (1.0 / (gamma - 1.0))
+    p = rho ** gamma
+    return rho, u, v, p
+
+
+def vortex_instance(n=101, eps=5.0, R=0.05):
+    """Single Cartesian patch [0,1]^2, n x n points, vortex at (0.5, 0.5)."""
+    patch = Patch(n, n, (BC_INFLOW, BC_OUTFLOW, BC_WALL, BC_WALL), box=(0.0, 1.0, 0.0, 1.0))
+    X, Y = patch.coords()
+    e = conserved(*vortex_primitives(X, Y, 0.0, eps=eps, R=R))
+    inflow = tuple(float(a) for a in conserved(1.0, 1.0, 0.0, 1.0))
+    return Instance([patch], [e], inflow=inflow, p_out=1.0, name=f"vortex_{n}x{n}",
+                    meta=dict(eps=eps, R=R))
+
+
+def sod_layout(npatch=8, n1=160, n2=40, overlap=10, length=1.0, height=0.1):
+    """Overlapping Cartesian patches along x covering [0,length] x [0,height].
+
+    Neighbouring patches share `overlap` grid columns; the global x grid has
+    npatch*n1 - (npatch-1)*overlap points.
+    """
+    nx = npatch * n1 - (npatch - 1) * overlap
+    hx = length / (nx - 1)
+    patches = []
+    for p in range(npatch):
+        i0 = p * (n1 - overlap)
+        bc = [BC_INTERNAL, BC_INTERNAL, BC_WALL, BC_WALL]
+        if p == 0:
+            bc[0] = BC_WALL
+        if p == npatch - 1:
+            bc[1] = BC_WALL
+        patches.append(Patch(n1, n2, tuple(bc), box=(i0 * hx, (i0 + n1 - 1) * hx, 0.0, height)))
+    return patches
+
+
+def sod_instance(npatch=8, n1=160, n2=40, overlap=10, x_jump=0.5, height=0.1, perturb=0.0, seed=SEED):
+    """Sod shock tube (rho,u,p) = (1,0,1) | (0.125,0,0.1), jump at x_jump.
+
+    `perturb` adds a seeded relative perturbation to the density (used to make
+    batched instances distinct).
+    """
+    patches = sod_layout(npatch, n1, n2, overlap, 1.0, height)
+    rng = np.random.default_rng(seed)
+    state = []
+    for pt in patches:
+        X, Y = pt.coords()
+        left = X < x_jump
+        rho = np.where(left, 1.0, 0.125)
+        p = np.where(left, 1.0, 0.1)
+        if perturb:
+            rho = rho * (1.0 + perturb * rng.uniform(-1.0, 1.0))
+        state.append(conserved(rho, 0.0 * X, 0.0 * X, p))
+    return Instance(patches, state, inflow=(1.0, 0.0, 0.0, 2.5), p_out=0.1, name="sod",
+                    meta=dict(x_jump=x_jump))
+
+
+def annulus_patch(n1=48, n2=32, r0=0.5, r1=1.0, th0=0.3, th1=1.4, bc=(BC_FREE,) * 4):
+    """Curvilinear polar patch: q1 -> angle in [th0, th1], q2 -> radius in [r0, r1]."""
+    q1 = np.arange(n1) / (n1 - 1)
+    q2 = np.arange(n2) / (n2 - 1)
+    Q1, Q2 = np.meshgrid(q1, q2)
+    th = th0 + (th1 - th0) * Q1
+    r = r0 + (r1 - r0) * Q2
+    return Patch(n1, n2, tuple(bc), x=r * np.cos(th), y=r * np.sin(th))
+
+
+def mach_flow_state(M, gamma=GAMMA):
+    """Uniform Mach-M flow (rho, u, v, p) = (1.4, M, 0, 1) of §7 (sound speed 1)."""
+    return (1.4, float(M), 0.0, 1.0)
+
+
+def mach_shock_state(M, gamma=GAMMA):
+    """Post-shock state of a Mach-M shock into (1.4, 0, 0, 1), as printed in §7.
+
+    rho = (gamma+1) M^2 / ((gamma-1) M^2 + 2), u = (zeta-1)/(gamma M), p = zeta,
+    zeta = (2 gamma M^2 - gamma + 1)/(gamma + 1).
+    """
+    zeta = (2 * gamma * M * M - gamma + 1) / (gamma + 1)
+    rho = (gamma + 1) * M * M / ((gamma - 1) * M * M + 2)
+    return (rho, (zeta - 1) / (gamma * M), 0.0, zeta)
+
+
+def random_state(patch, rng, amp=0.05):
+    """Smooth seeded perturbation of a uniform state (for parity tests)."""
+    X, Y = patch.coords()
+    k = rng.uniform(1.0, 4.0, size=(4, 2))
+    ph = rng.uniform(0, 2 * np.pi, size=4)
+    base = (1.0, 0.3, -0.2, 1.0)
+    prim = [base[c] * (1 + amp * np.sin(k[c, 0] * X + k[c, 1] * Y + ph[c])) if c in (0, 3)
+            else base[c] + amp * np.sin(k[c, 0] * X + k[c, 1] * Y + ph[c]) for c in range(4)]
+    return conserved(*prim)
+
+
+# --------------------------------------------------------------------------
+# classifier training windows
+# --------------------------------------------------------------------------
+WINDOW = 16
+CLASS_JUMP, CLASS_KINK, CLASS_C1, CLASS_SMOOTH = 1, 2, 3, 4
+
+
+def classifier_windows(count, seed=SEED, window=WINDOW):
+    """Seeded labelled windows of raw profile samples (count, window), labels 1..4.
+
+    Each window samples s(x) + A * feature(x - x0) on x = 0..window-1, with s a
+    random smooth function (sine + linear + constant) and the feature a jump
+    (label 1), a kink |x| (label 2), a one-sided square (x)_+^2 (label 3) or
+    nothing (label 4), located at a random x0 inside the window.
+    """
+    rng = np.random.default_rng(seed)
+    x = np.arange(window, dtype=np.float64)
+    lab = rng.integers(1, 5, size=count)
+    amp_s = rng.uniform(0.0, 1.0, size=(count, 1))
+    om = rng.uniform(0.0, 0.35, size=(count, 1))
+    ph = rng.uniform(0.0, 2 * np.pi, size=(count, 1))
+    slope = rng.uniform(-0.2, 0.2, size=(count, 1))
+    off = rng.uniform(-1.0, 1.0, size=(count, 1))
+    A = rng.uniform(0.3, 2.0, size=(count, 1)) * rng.choice([-1.0, 1.0], size=(count, 1))
+    x0 = rng.uniform(3.0, window - 4.0, size=(count, 1))
+    s = amp_s * np.sin(om * x + ph) + slope * x + off
+    t = x - x0
+    feat = np.zeros((count, window))
+    feat = np.where(lab[:, None] == CLASS_JUMP, (t >= 0).astype(np.float64), feat)
+    feat = np.where(lab[:, None] == CLASS_KINK, np.abs(t) / window * 4.0, feat)
+    feat = np.where(lab[:, None] == CLASS_C1, np.maximum(t, 0.0) ** 2 / window ** 2 * 8.0, feat)
+    return s + A * feat, lab.astype(np.int8)

@@ -1,0 +1,120 @@
+"""Pins of the oracle's FC-Gram continuation and FC derivative (paper §2)."""
+import mpmath as mp
+import numpy as np
+import pytest
+
+from oracle import fcgram
+
+
+@pytest.mark.parametrize("d", [2, 5])
+def test_gram_basis_orthonormal_and_consistent(d):
+    Q, Rinv = fcgram.gram_basis(d)
+    q = np.array(Q.tolist(), dtype=float)
+    assert np.allclose(q.T @ q, np.eye(d), atol=1e-15)
+    # the polynomial form reproduces the tabulated values at the matching points
+    with mp.workdps(40):
+        for k in range(d):
+            for m in range(d):
+                v = fcgram._gram_poly(Rinv, d, k, mp.mpf(m))
+                assert abs(v - Q[m, k]) < mp.mpf("1e-35")
+    # p_k has degree k: its k-th finite difference is nonzero, (k+1)-th vanishes
+    with mp.workdps(40):
+        for k in range(d):
+            vals = [fcgram._gram_poly(Rinv, d, k, mp.mpf(s) / 3) for s in range(3 * d)]
+            diffs = vals
+            for _ in range(k):
+                diffs = [b - a for a, b in zip(diffs, diffs[1:])]
+            assert min(abs(float(x)) for x in diffs) > 1e-6
+            diffs = [b - a for a, b in zip(diffs, diffs[1:])]
+            assert max(abs(float(x)) for x in diffs) < 1e-25
+
+
+@pytest.mark.parametrize("d,C", [(5, 25), (2, 25), (5, 26)])
+def test_blend_fit_matches_and_vanishes(d, C):
+    # the blend-to-zero reproduces each Gram polynomial on the matching region
+    # and vanishes on the zero region to far below FP64 derivative accuracy
+    _, resid = fcgram.blend_fit(d, C)
+    assert resid < 2e-12
+
+
+def test_fft_matches_naive_dft():
+    rng = np.random.default_rng(0)
+    f = np.sin(np.linspace(0, 2, 101)) + 0.1 * rng.standard_normal(101)
+    y = fcgram.continue_lines(f, 5, 25)
+    Y = np.fft.fft(y)
+    assert np.abs(Y - fcgram.naive_dft(y)).max() < 1e-13 * np.abs(Y).max() * y.size
+
+
+def _errors(fn, dfn, Ns, d, C, order=1):
+    errs = []
+    for N in Ns:
+        x = np.linspace(0.0, 1.0, N)
+        errs.append(np.abs(fcgram.fc_derivative(fn(x), 1.0 / (N - 1), d, C, order) - dfn(x)).max())
+    return np.array(errs)
+
+
+@pytest.mark.parametrize("fn,dfn", [
+    (lambda x: np.sin(3 * x + 1), lambda x: 3 * np.cos(3 * x + 1)),
+    (lambda x: np.exp(x) * np.cos(5 * x), lambda x: np.exp(x) * (np.cos(5 * x) - 5 * np.sin(5 * x))),
+])
+def test_first_derivative_converges_at_fc_gram_order(fn, dfn):
+    # FC-Gram of degree d: observed order >= d - 1 (d = 5)
+    Ns = [25, 50, 100, 200]
+    e = _errors(fn, dfn, Ns, 5, 25)
+    order = np.log2(e[:-1] / e[1:])
+    assert e[-1] < 2e-6
+    assert np.all(order > 3.5), order
+
+
+def test_second_derivative_converges():
+    fn = lambda x: np.sin(3 * x + 1)
+    d2 = lambda x: -9 * np.sin(3 * x + 1)
+    e = _errors(fn, d2, [50, 100, 200], 5, 25, order=2)
+    assert np.all(np.log2(e[:-1] / e[1:]) > 2.5), e
+
+
+def test_low_degree_polynomial_derivative():
+    # polynomials of degree < d are continued smoothly: derivative close to exact
+    N = 101
+    x = np.linspace(0, 1, N)
+    f = 1 + 2 * x - 3 * x ** 2 + 0.5 * x ** 3 - x ** 4
+    df = 2 - 6 * x + 1.5 * x ** 2 - 4 * x ** 3
+    err = np.abs(fcgram.fc_derivative(f, 1 / (N - 1), 5, 25) - df).max()
+    assert err < 1e-7
+
+
+@pytest.mark.parametrize("N", [101, 57])
+def test_spectral_integral_identity(N):
+    # integral over [0,1] of the derivative of the FC expansion = f(1) - f(0):
+    # pins the wavenumber scaling (period beta = n h) and that the expansion
+    # interpolates the data; exact up to rounding for odd N
+    rng = np.random.default_rng(N)
+    x = np.linspace(0, 1, N)
+    f = np.sin(2.3 * x + rng.uniform()) + 0.3 * x ** 2
+    h = 1 / (N - 1)
+    y = fcgram.continue_lines(f, 5, 25)
+    n = y.size
+    Y = np.fft.fft(y)
+    I = fcgram.spectral_integral_weights(n, h, N)
+    integral = np.sum(Y * fcgram.spectral_multiplier(n, h, 1) * I).real / n
+    assert abs(integral - (f[-1] - f[0])) < 1e-12
+
+
+def test_quadrature_weights():
+    N = 101
+    W = fcgram.fc_quadrature_weights(N, 5, 25)
+    assert abs(W.sum() - 1.0) < 1e-12
+    x = np.linspace(0, 1, N)
+    exact = (np.cos(1.0) - np.cos(4.0)) / 3.0
+    assert abs(W @ np.sin(3 * x + 1) - exact) < 1e-9
+
+
+def test_tables_reflection():
+    A_R, A_L = fcgram.continuation_tables(5, 25)
+    assert A_R.shape == (25, 5)
+    assert np.array_equal(A_L, A_R[::-1, ::-1])
+    # a constant line: the continuation is mirror-symmetric and the FC
+    # derivative on the data points vanishes up to the fit residual
+    c = fcgram.continue_lines(np.full(40, 3.0), 5, 25)
+    assert np.abs(c[40:] - c[40:][::-1]).max() < 5e-12
+    assert np.abs(fcgram.fc_derivative(np.full(40, 3.0), 1 / 39, 5, 25)).max() < 5e-9
