@@ -1,0 +1,347 @@
+"""Benchmark: FC-SDNN grid-point-stage updates per second on one GB300.
+
+Workload (one "step" = one full time step of the hot path): a batch of
+independent Sod shock-tube instances, each on [0,1] x [0,0.1] split into 8
+overlapping Cartesian patches of 160 x 40 points (overlap 10), seeded
+perturbations of the Sod states; per step: proxy + windows + classifier MLP,
+artificial viscosity assembly, CFL time step, four Runge-Kutta stages (FC
+derivatives of fluxes and viscous fluxes, operator, stage update, boundary
+conditions), each followed by the fringe exchange.  Inputs are synthetic.
+
+Prints one JSON line (see --help).  --impl reference times the FP64 CPU
+oracle on a bounded sample of the same workload on the host cores.
+"""
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "FC-SDNN grid-point-stage updates/s on 1 GB300, batched FP32 vs plain FP64, at set error"
+UNIT = "pt-stage/s"
+L2_BYTES = 129 * 2 ** 20
+FALLBACK_HBM = 6800.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--dtype", default="f32", choices=["f32", "f64"])
+    ap.add_argument("--instances", type=int, default=128)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def workload(instances):
+    from paper_2506_19370_gb300 import inputs as I
+    return [I.sod_instance(perturb=0.01, seed=I.SEED + k) for k in range(instances)]
+
+
+def config(args, points):
+    return {"workload": f"Sod shock tube, 8 overlapping Cartesian patches of 160x40 points (overlap 10) per "
+                        f"instance, x {args.instances} independent instances; SDNN classifier + artificial "
+                        f"viscosity + CFL dt + 4 RK stages + exchange per step",
+            "instances": args.instances, "points_per_instance": points // args.instances, "points": points,
+            "d": 5, "C": "25, raised per line to a 7-smooth FFT length (185->189, 65->70)",
+            "classifier": "16-32-32-4 MLP, seeded weights", "l2": "flushed (256 MiB write) between timed steps",
+            "parallelism": f"replicas x{args.gpus}" if args.gpus > 1 else "1 GPU"}
+
+
+# ---------------------------------------------------------------- CPU oracle
+def cpu_baseline(seconds, dist_note=None):
+    """Time the oracle (single-threaded numpy) on whole steps of one instance."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    code = (
+        "import time, json, sys; sys.path.insert(0, %r)\n"
+        "from oracle import euler, sdnn\n"
+        "from paper_2506_19370_gb300 import inputs as I\n"
+        "inst = I.sod_instance(perturb=0.01)\n"
+        "s = euler.Solver(inst, c_policy=1)\n"
+        "params = sdnn.init_params(0)\n"
+        "st = [e.copy() for e in inst.state]\n"
+        "def step(st):\n"
+        "    taus = [sdnn.classify_patch(params, e, inst.gamma)[0] for e in st]\n"
+        "    mu = sdnn.av_assemble(s, st, taus)\n"
+        "    dt = s.dt(st)\n"
+        "    return s.step(st, dt, mu)\n"
+        "st = step(st)\n"
+        "t0 = time.perf_counter(); n = 0\n"
+        "while time.perf_counter() - t0 < %f or n < 2:\n"
+        "    st = step(st); n += 1\n"
+        "el = time.perf_counter() - t0\n"
+        "pts = sum(p.n1 * p.n2 for p in inst.patches)\n"
+        "print(json.dumps({'steps': n, 'seconds': el, 'points': pts}))\n"
+    ) % (ROOT, seconds)
+    r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True)
+    if r.returncode != 0:
+        return {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": "failed: " + r.stderr[-300:]}
+    res = json.loads(r.stdout.strip().splitlines()[-1])
+    val = res["points"] * 4 * res["steps"] / res["seconds"]
+    return {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{res['steps']} full steps (classifier, viscosity, dt, 4 stages, exchange) of one Sod "
+                      f"instance ({res['points']} points) in {res['seconds']:.1f} s, FP64 numpy, 1 thread",
+            "seconds": res["seconds"]}
+
+
+def run_reference(args):
+    import torch  # noqa: F401  (rank bookkeeping only)
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    per = max(args.cpu_seconds / max(args.steps, 1), 2.0)
+    vals, secs = [], 0.0
+    base = None
+    for _ in range(args.steps):
+        b = cpu_baseline(per)
+        if b["value"] is None:
+            print(json.dumps({"impl": "reference", "unavailable": b["sample"]}))
+            return
+        vals.append(b["value"])
+        secs += b["seconds"]
+        base = b
+    pts = 51200
+    value = sum(vals) / len(vals)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1000.0 * pts * 4 / value, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config(args, pts * args.instances), "impl": "reference",
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": base["sample"]},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm = [float(r[0]) for r in self.rows if len(r) >= 8 and r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if len(r) >= 8 and r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in self.rows if len(r) >= 8 for k in range(4) if r[4 + k] == "Active"})
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(sm)}
+
+
+def measured_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("fcs_device.cuh", "fcs_kernels.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2506_19370_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(per_launch_points):
+    """DRAM bytes per launch of the stage operator from the committed ncu summary,
+    scaled to this launch's points; None if the kernels changed since."""
+    p = os.path.join(ROOT, "profiles", "rk_stage_traffic.json")
+    try:
+        d = json.load(open(p))
+    except Exception:
+        return None
+    if d.get("kernel_source_hash") != kernel_source_hash():
+        return None
+    return d["dram_bytes_per_point_stage"] * per_launch_points
+
+
+# ---------------------------------------------------------------- GPU arm
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_2506_19370_gb300 import fcsdnn
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dtype = fcsdnn.F64 if args.dtype == "f64" else fcsdnn.F32
+    insts = workload(args.instances)
+    ctx = fcsdnn.Context(insts[0], d=5, C=25, dtype=dtype, instances=args.instances, c_policy=1)
+    from paper_2506_19370_gb300.inputs import SEED
+    rng = np.random.default_rng(SEED)
+    # seeded classifier weights (He-uniform), drawn here to keep the oracle out of the GPU arm
+    w = []
+    for shape in ((32, 16), (32,), (32, 32), (32,), (4, 32), (4,)):
+        if len(shape) == 2:
+            lim = np.sqrt(6.0 / shape[1])
+            w.append(rng.uniform(-lim, lim, size=shape).ravel())
+        else:
+            w.append(np.zeros(shape))
+    ctx.set_weights(np.concatenate(w).astype(np.float32))
+    host = ctx.pack_state([i.state for i in insts])
+    e = ctx.to_device(host)
+    points = args.instances * sum(p.n1 * p.n2 for p in insts[0].patches)
+    tau = ctx.new_scalar(torch.int8)
+    mu = ctx.new_scalar()
+    dtd = torch.zeros(args.instances, dtype=torch.float64, device=dev)
+    S = ctx.new_state()
+    A = ctx.new_state()
+    flush = torch.empty(256 * 2 ** 20 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.Stream(device=dev)
+    torch.cuda.synchronize()
+    launches = {"n": 0}
+
+    def step(ev=None):
+        # the same sequence as fcs_step, call by call, so the stage operator can be timed
+        ctx.classify(e, tau, None, stream)
+        ctx.av_assemble(e, tau, mu, stream)
+        ctx.time_step(e, dtd, stream)
+        launches["n"] += 2 + 7 + 3
+        for s in range(4):
+            es = e if s == 0 else S
+            out = e if s == 3 else S
+            if ev is not None:
+                ev[s][0].record(stream)
+            ctx.rk_stage(s, 0.0, e, es, A, out, mu=mu, dt_dev=dtd, stream=stream)
+            if ev is not None:
+                ev[s][1].record(stream)
+            ctx.patch_exchange(out, 4, stream)
+            launches["n"] += 3
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step()
+    stream.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = ClockSampler(local)
+    clk.start()
+    time.sleep(0.3)
+    step_ms, stage_ms = [], []
+    launches["n"] = 0
+    with torch.cuda.stream(stream):
+        for _ in range(args.steps):
+            flush.fill_(1.0)
+            t0 = torch.cuda.Event(enable_timing=True)
+            t1 = torch.cuda.Event(enable_timing=True)
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(4)]
+            t0.record(stream)
+            step(ev)
+            t1.record(stream)
+            stream.synchronize()
+            step_ms.append(t0.elapsed_time(t1))
+            stage_ms += [a.elapsed_time(b) for a, b in ev]
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    rc, flags = ctx.status()
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = t.item()
+    value = world * points * 4 * args.steps / (total_ms / 1000.0)
+
+    # end to end through the C ABI: pinned host state in, step (graph), state out
+    pinned = torch.from_numpy(host).pin_memory()
+    out_host = torch.empty_like(pinned).pin_memory()
+    ctx.step_graph(e, dt_dev=dtd, use_av=True, stream=stream)   # capture outside the timed region
+    stream.synchronize()
+    e2e_ms = 0.0
+    with torch.cuda.stream(stream):
+        for _ in range(max(3, args.steps // 2)):
+            flush.fill_(1.0)
+            stream.synchronize()
+            t0 = time.perf_counter()
+            e.copy_(pinned, non_blocking=True)
+            ctx.step_graph(e, dt_dev=dtd, use_av=True, stream=stream)
+            out_host.copy_(e, non_blocking=True)
+            stream.synchronize()
+            e2e_ms += 1000.0 * (time.perf_counter() - t0)
+    n_e2e = max(3, args.steps // 2)
+    e2e_val = world * points * 4 * n_e2e / (e2e_ms / 1000.0)
+    nbytes = e.numel() * e.element_size()
+
+    # roofline of the stage operator (flux passes + stage update): algorithmic
+    # bytes per point-stage averaged over the 4 stages (state reads/writes,
+    # accumulator, viscosity), see the design notes
+    ts = 8 if dtype == fcsdnn.F64 else 4
+    # elements per point: stage 0 reads e_n, writes acc and out (12); stages 1-2
+    # read e_s, e_n, acc, write acc, out (20); stage 3 reads e_s, acc, writes
+    # out (12); every stage reads mu (1): mean 17 elements per point-stage
+    alg_bytes_pt = ts * 17
+    stage_avg_ms = sum(stage_ms) / len(stage_ms)
+    achieved = alg_bytes_pt * points / (stage_avg_ms / 1000.0) / 1e9
+    peak, peak_kind = measured_peak()
+    traffic = recorded_traffic(points)
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
+                "config": config(args, points),
+                "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
+                        "note": "pinned host state -> device, one graph-captured step, state -> host"},
+                "gpu_launches": launches["n"],
+                "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                             "frac": achieved / peak, "traffic": traffic, "peak_source": peak_kind,
+                             "kernel": "rk_stage (flux pass along q1 + flux pass along q2 with stage update)",
+                             "alg_bytes_per_point_stage": alg_bytes_pt, "stage_ms": stage_avg_ms},
+                "clocks": clocks, "status": rc}
+        if not args.no_cpu_baseline and world == 1:
+            line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

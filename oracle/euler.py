@@ -52,8 +52,11 @@ def fluxes(e, gamma):
 class PatchGeom:
     """Per-patch quantities the operator needs: spacings and metrics."""
 
-    def __init__(self, patch, d, C):
+    def __init__(self, patch, d, C, c_policy=0):
         self.patch = patch
+        # continuation length per direction (lines along q1 have n1 points)
+        self.C1 = fcgram.smooth_c(patch.n1, C) if c_policy else C
+        self.C2 = fcgram.smooth_c(patch.n2, C) if c_policy else C
         self.n1, self.n2 = patch.n1, patch.n2
         self.h1 = 1.0 / (patch.n1 - 1)
         self.h2 = 1.0 / (patch.n2 - 1)
@@ -67,10 +70,10 @@ class PatchGeom:
             self.y_q1 = np.zeros((self.n2, self.n1))
         else:
             X, Y = patch.coords()
-            self.x_q1 = fcgram.fc_derivative_axis(X, self.h1, d, C, axis=1)
-            self.x_q2 = fcgram.fc_derivative_axis(X, self.h2, d, C, axis=0)
-            self.y_q1 = fcgram.fc_derivative_axis(Y, self.h1, d, C, axis=1)
-            self.y_q2 = fcgram.fc_derivative_axis(Y, self.h2, d, C, axis=0)
+            self.x_q1 = fcgram.fc_derivative_axis(X, self.h1, d, self.C1, axis=1)
+            self.x_q2 = fcgram.fc_derivative_axis(X, self.h2, d, self.C2, axis=0)
+            self.y_q1 = fcgram.fc_derivative_axis(Y, self.h1, d, self.C1, axis=1)
+            self.y_q2 = fcgram.fc_derivative_axis(Y, self.h2, d, self.C2, axis=0)
         self.J = self.x_q1 * self.y_q2 - self.x_q2 * self.y_q1
 
 
@@ -78,18 +81,19 @@ def rhs(e, geom, d, C, gamma, mu=None):
     """L(e) on one patch (Algorithm 5, operator evaluation); e is (4, n2, n1)."""
     e = np.asarray(e, dtype=np.float64)
     f, g = fluxes(e, gamma)
+    C1, C2 = geom.C1, geom.C2
     if geom.patch.cartesian:
         if mu is not None:
-            f = f - mu * fcgram.fc_derivative_axis(e, geom.hx, d, C, axis=2)
-            g = g - mu * fcgram.fc_derivative_axis(e, geom.hy, d, C, axis=1)
-        return -(fcgram.fc_derivative_axis(f, geom.hx, d, C, axis=2)
-                 + fcgram.fc_derivative_axis(g, geom.hy, d, C, axis=1))
+            f = f - mu * fcgram.fc_derivative_axis(e, geom.hx, d, C1, axis=2)
+            g = g - mu * fcgram.fc_derivative_axis(e, geom.hy, d, C2, axis=1)
+        return -(fcgram.fc_derivative_axis(f, geom.hx, d, C1, axis=2)
+                 + fcgram.fc_derivative_axis(g, geom.hy, d, C2, axis=1))
     if mu is not None:
         raise NotImplementedError("artificial viscosity on curvilinear patches")
     F1 = geom.y_q2 * f - geom.x_q2 * g
     F2 = -geom.y_q1 * f + geom.x_q1 * g
-    div = (fcgram.fc_derivative_axis(F1, geom.h1, d, C, axis=2)
-           + fcgram.fc_derivative_axis(F2, geom.h2, d, C, axis=1))
+    div = (fcgram.fc_derivative_axis(F1, geom.h1, d, C1, axis=2)
+           + fcgram.fc_derivative_axis(F2, geom.h2, d, C2, axis=1))
     return -div / geom.J
 
 
@@ -223,10 +227,10 @@ def max_wave_speed(state, gamma):
 class Solver:
     """Multi-patch FC-SDNN stepping on one instance (Algorithms 1 and 5)."""
 
-    def __init__(self, inst, d=5, C=25, n_f=5, cfl=0.5):
+    def __init__(self, inst, d=5, C=25, n_f=5, cfl=0.5, c_policy=0):
         self.inst = inst
         self.d, self.C, self.n_f, self.cfl = d, C, n_f, cfl
-        self.geoms = [PatchGeom(p, d, C) for p in inst.patches]
+        self.geoms = [PatchGeom(p, d, C, c_policy) for p in inst.patches]
         self.fmap = fringe_map(inst.patches, n_f)
 
     def rhs_all(self, state, mu=None):
@@ -265,8 +269,8 @@ class Solver:
         """Per patch: FC quadrature of each conserved field times |J| (4 sums)."""
         out = []
         for e, g in zip(state, self.geoms):
-            W1 = fcgram.fc_quadrature_weights(g.n1, self.d, self.C)
-            W2 = fcgram.fc_quadrature_weights(g.n2, self.d, self.C)
+            W1 = fcgram.fc_quadrature_weights(g.n1, self.d, g.C1)
+            W2 = fcgram.fc_quadrature_weights(g.n2, self.d, g.C2)
             w = np.outer(W2, W1) * np.abs(g.J)
             out.append(np.array([np.sum(w * e[c]) for c in range(4)]))
         return np.array(out)

@@ -44,6 +44,23 @@ LAMBDA = "1e-14"
 DIGITS = 40
 
 
+def smooth_c(N, C):
+    """Smallest C' in [C, C+16] with N + C' a product of 2, 3, 5 and 7.
+
+    FFT-length policy (a choice of this implementation, not of the paper):
+    the continuation length of a line may be raised so that its FFT length
+    has only small prime factors.  Returns C if no such C' exists.
+    """
+    for c in range(C, C + 17):
+        m = N + c
+        for q in (2, 3, 5, 7):
+            while m % q == 0:
+                m //= q
+        if m == 1:
+            return c
+    return C
+
+
 def fit_params(d, C):
     """Period P (index units) and highest mode K of the blend-to-zero fit."""
     P = 2 * C + 4 * d - 1

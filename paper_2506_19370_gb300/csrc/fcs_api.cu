@@ -1,0 +1,882 @@
+// C ABI of the FC-SDNN stage library: context setup and the entry points
+// declared in include/fcsdnn.h.  Device code lives in fcs_kernels.cuh.
+#include <cmath>
+#include <complex>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <vector>
+
+#include "../../include/fcsdnn.h"
+#include "fcs_internal.h"
+#include "fcs_kernels.cuh"
+
+using namespace fcs;
+
+namespace {
+
+constexpr int kNParams = 1732;
+constexpr int kIndC = 26;   // continuation length of the indicator (16 + 26 = 42 = 2 * 3 * 7)
+constexpr int kIndD = 5;
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+struct HostPlan {
+  PlanDev dev;
+  std::vector<double> tab;  // C x d
+};
+
+}  // namespace
+
+struct fcs_ctx {
+  fcs_options opt{};
+  int d = 0, C = 0, npatch = 0;
+  size_t tsize = 4;  // sizeof(T)
+  std::vector<PatchDev> patches;
+  std::vector<HostPlan> plans;
+  std::map<int, int> plan_of_len;  // line length -> plan index
+  std::vector<int64_t> state_off, scalar_off, window_off;
+  size_t sstride = 0, qstride = 0, nwin = 0;
+  int nlines0 = 0, nlines1 = 0, npairs0 = 0, npairs1 = 0, nent = 0;
+  int nmax = 0, nfmax = 0;
+  CtxDev dev{};
+  std::vector<void*> allocs;
+  // device arrays
+  int4* pairs0 = nullptr;
+  int4* pairs1 = nullptr;
+  int4* fringe_ent = nullptr;
+  double* wq = nullptr;
+  int2* woff = nullptr;
+  double* bump = nullptr;
+  void* R = nullptr;     // x-pass partial operator (state-sized)
+  void* S = nullptr;     // stage buffer
+  void* A = nullptr;     // Runge-Kutta accumulator
+  void* av0 = nullptr;   // viscosity scratch (scalar-sized)
+  void* av1 = nullptr;
+  void* mu = nullptr;    // viscosity of the step
+  signed char* tau = nullptr;
+  signed char* tau_w = nullptr;
+  unsigned long long* dtbest = nullptr;
+  double* dt_internal = nullptr;
+  float* Wm = nullptr;   // FP32 master weights
+  float* Am = nullptr;   // Adam moments
+  float* Av = nullptr;
+  float* grad = nullptr;
+  __nv_bfloat16* Wb = nullptr;
+  float* bias = nullptr;
+  double* W64 = nullptr;
+  float* acts = nullptr;
+  float* loss_s = nullptr;
+  int adam_t = 0;
+  // graph of fcs_step
+  cudaGraphExec_t gexec = nullptr;
+  cudaGraph_t graph = nullptr;
+  void* g_e = nullptr;
+  double g_dt = 0.0;
+  double* g_dtdev = nullptr;
+  int g_av = -1;
+  cudaStream_t g_stream = nullptr;
+};
+
+namespace {
+
+int cuda_err(cudaError_t e) {
+  if (e == cudaSuccess) return FCS_OK;
+  std::fprintf(stderr, "fcsdnn: CUDA error %s\n", cudaGetErrorString(e));
+  return FCS_ECUDA;
+}
+
+#define FCS_CUDA(x)                        \
+  do {                                     \
+    int _rc = cuda_err((x));               \
+    if (_rc != FCS_OK) return _rc;         \
+  } while (0)
+
+template <typename P>
+int dalloc(fcs_ctx* c, P** out, size_t bytes) {
+  void* p = nullptr;
+  if (bytes == 0) bytes = 16;
+  if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return FCS_ENOMEM;
+  }
+  cudaMemset(p, 0, bytes);
+  c->allocs.push_back(p);
+  *out = static_cast<P*>(p);
+  return FCS_OK;
+}
+
+template <typename P>
+int upload(fcs_ctx* c, P** out, const void* src, size_t bytes) {
+  int rc = dalloc(c, out, bytes);
+  if (rc) return rc;
+  if (bytes) FCS_CUDA(cudaMemcpy(*out, src, bytes, cudaMemcpyHostToDevice));
+  return FCS_OK;
+}
+
+bool factor_radices(int n, std::vector<int>* rad) {
+  rad->clear();
+  int m = n;
+  while (m % 8 == 0) { rad->push_back(8); m /= 8; }
+  while (m % 4 == 0) { rad->push_back(4); m /= 4; }
+  while (m % 2 == 0) { rad->push_back(2); m /= 2; }
+  for (int p : {3, 5, 7})
+    while (m % p == 0) { rad->push_back(p); m /= p; }
+  return m == 1 && (int)rad->size() <= kMaxStages;
+}
+
+bool smooth7(int n) {
+  for (int p : {2, 3, 5, 7})
+    while (n % p == 0) n /= p;
+  return n == 1;
+}
+
+int choose_c(const fcs_options& o, int C, int N) {
+  if (o.c_policy == 0) return C;
+  for (int c = C; c <= C + 16; ++c)
+    if (smooth7(N + c)) return c;
+  return C;
+}
+
+// Host FP64 FC quadrature weights of a line of N points (integral over
+// [0, 1] of the FC expansion), folded onto the data points.
+std::vector<double> quad_weights(int N, int C, int d, const std::vector<double>& AR) {
+  const int n = N + C;
+  const double h = 1.0 / (N - 1), beta = n * h, PI = 3.14159265358979323846;
+  std::vector<std::complex<double>> I(n);
+  for (int k = 0; k < n; ++k) {
+    const int kk = (2 * k <= n) ? k : k - n;
+    if (kk == 0) I[k] = 1.0;
+    else {
+      const double th = 2 * PI * kk / beta;
+      I[k] = (std::exp(std::complex<double>(0, th)) - 1.0) / std::complex<double>(0, th);
+    }
+  }
+  if (n % 2 == 0) I[n / 2] = 0.0;
+  std::vector<double> w(n);
+  for (int j = 0; j < n; ++j) {
+    std::complex<double> s = 0;
+    for (int k = 0; k < n; ++k) s += std::exp(std::complex<double>(0, -2 * PI * (double)((long long)j * k % n) / n)) * I[k];
+    w[j] = s.real() / n;
+  }
+  std::vector<double> W(w.begin(), w.begin() + N);
+  for (int c = 0; c < C; ++c)
+    for (int m = 0; m < d; ++m) {
+      W[N - d + m] += AR[c * d + m] * w[N + c];           // right blend acts on the last d values
+      W[m] += AR[(C - 1 - c) * d + (d - 1 - m)] * w[N + c];  // reflected left blend on the first d
+    }
+  return W;
+}
+
+int get_plan(fcs_ctx* c, int N, int C, int d) {
+  const int key = N * 4096 + C * 16 + d;
+  auto it = c->plan_of_len.find(key);
+  if (it != c->plan_of_len.end()) return it->second;
+  HostPlan hp{};
+  hp.dev.N = N;
+  hp.dev.C = C;
+  hp.dev.n = N + C;
+  std::vector<int> rad;
+  if (!factor_radices(N + C, &rad)) return FCS_EUNSUPPORTED;
+  hp.dev.nst = (int)rad.size();
+  for (int s = 0; s < hp.dev.nst; ++s) hp.dev.radix[s] = rad[s];
+  hp.tab.resize((size_t)C * d);
+  if (build_table(d, C, hp.tab.data()) != 0) return FCS_EINVAL;
+  c->plans.push_back(hp);
+  const int idx = (int)c->plans.size() - 1;
+  c->plan_of_len[key] = idx;
+  return idx;
+}
+
+template <typename T>
+size_t flux_smem(const fcs_ctx* c) { return kWarps * flux_warp_bytes<T>(c->nmax, c->nfmax); }
+template <typename T>
+size_t deriv_smem(const fcs_ctx* c) { return (size_t)kWarps * 2 * c->nfmax * sizeof(Cx<T>); }
+
+int grid_for(long long work, int per_block) {
+  long long g = (work + per_block - 1) / per_block;
+  if (g < 1) g = 1;
+  if (g > 152 * 32) g = 152 * 32;
+  return (int)g;
+}
+
+template <typename T>
+int set_smem_attrs(const fcs_ctx* c) {
+  const int fs = (int)flux_smem<T>(c), ds = (int)deriv_smem<T>(c);
+  FCS_CUDA(cudaFuncSetAttribute(k_flux<T, 0, MODE_X>, cudaFuncAttributeMaxDynamicSharedMemorySize, fs));
+  FCS_CUDA(cudaFuncSetAttribute(k_flux<T, 1, MODE_RHS>, cudaFuncAttributeMaxDynamicSharedMemorySize, fs));
+  FCS_CUDA(cudaFuncSetAttribute(k_flux<T, 1, MODE_RK>, cudaFuncAttributeMaxDynamicSharedMemorySize, fs));
+  FCS_CUDA(cudaFuncSetAttribute(k_fc_deriv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, ds));
+  return FCS_OK;
+}
+
+template <typename T>
+int launch_deriv(fcs_ctx* c, const void* in, void* out, int dir, int order, cudaStream_t s) {
+  const int np = dir == 0 ? c->npairs0 : c->npairs1;
+  const int4* pr = dir == 0 ? c->pairs0 : c->pairs1;
+  const long long work = (long long)c->opt.instances * np;
+  k_fc_deriv<T><<<grid_for(work, kWarps), kWarps * 32, deriv_smem<T>(c), s>>>(
+      c->dev, dir, order, pr, np, static_cast<const T*>(in), static_cast<T*>(out));
+  return cuda_err(cudaGetLastError());
+}
+
+template <typename T>
+int launch_flux(fcs_ctx* c, const void* e, const void* mu, int mode, StageArgs<T> st, cudaStream_t s) {
+  const size_t sm = flux_smem<T>(c);
+  const long long w0 = (long long)c->opt.instances * c->nlines0;
+  const long long w1 = (long long)c->opt.instances * c->nlines1;
+  const T* ep = static_cast<const T*>(e);
+  const T* mp = static_cast<const T*>(mu);
+  T* R = static_cast<T*>(c->R);
+  k_flux<T, 0, MODE_X><<<grid_for(w0, kWarps), kWarps * 32, sm, s>>>(c->dev, ep, mp, R, st);
+  FCS_CUDA(cudaGetLastError());
+  if (mode == MODE_RHS)
+    k_flux<T, 1, MODE_RHS><<<grid_for(w1, kWarps), kWarps * 32, sm, s>>>(c->dev, ep, mp, R, st);
+  else
+    k_flux<T, 1, MODE_RK><<<grid_for(w1, kWarps), kWarps * 32, sm, s>>>(c->dev, ep, mp, R, st);
+  return cuda_err(cudaGetLastError());
+}
+
+cudaStream_t as_stream(void* s) { return static_cast<cudaStream_t>(s); }
+
+}  // namespace
+
+namespace {
+template <typename T>
+int av_impl(fcs_ctx* c, const void* e, const int8_t* tau, void* mu, cudaStream_t s) {
+  const long long np = (long long)c->opt.instances * c->qstride;
+  const int g = grid_for(np, 256), r = c->opt.av_radius;
+  T* a0 = static_cast<T*>(c->av0);
+  T* a1 = static_cast<T*>(c->av1);
+  T* m = static_cast<T*>(mu);
+  k_av_speed<T><<<g, 256, 0, s>>>(c->dev, static_cast<const T*>(e), a0);
+  k_av_prelim<T><<<g, 256, 0, s>>>(c->dev, a0, reinterpret_cast<const signed char*>(tau), T(c->opt.c_mu), a1);
+  k_av_boxmax<T><<<g, 256, 0, s>>>(c->dev, a1, a0, r, 0);
+  k_av_boxmax<T><<<g, 256, 0, s>>>(c->dev, a0, a1, r, 1);
+  k_av_bump<T><<<g, 256, 0, s>>>(c->dev, a1, a0, c->bump, r, 0);
+  k_av_bump<T><<<g, 256, 0, s>>>(c->dev, a0, m, c->bump, r, 1);
+  FCS_CUDA(cudaGetLastError());
+  return patch_exchange(c, mu, 1, s);
+}
+}  // namespace
+
+namespace {
+int train_forward_backward(fcs_ctx* c, const float* x, const int8_t* lab, int B, float* loss, cudaStream_t s) {
+  k_train_sample<<<(B + 127) / 128, 128, 0, s>>>(x, reinterpret_cast<const signed char*>(lab), B, c->Wm, c->acts,
+                                                 c->loss_s);
+  k_train_grad<<<(kNParams + 127) / 128, 128, 0, s>>>(c->acts, B, c->grad);
+  k_train_loss<<<1, 256, 0, s>>>(c->loss_s, B, loss);
+  return cuda_err(cudaGetLastError());
+}
+}  // namespace
+
+// =====================================================================
+extern "C" {
+
+void fcs_default_options(fcs_options* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->gamma = 1.4;
+  o->cfl = 0.5;
+  o->n_f = 5;
+  o->dtype = FCS_F32;
+  o->instances = 1;
+  o->inflow[0] = 1.0;
+  o->inflow[1] = 1.0;
+  o->inflow[2] = 0.0;
+  o->inflow[3] = 3.0;
+  o->p_out = 1.0;
+  o->c_mu = 1.0;
+  o->av_radius = 4;
+  o->c_policy = 0;
+  o->train_batch_max = 4096;
+}
+
+const char* fcs_strerror(int code) {
+  switch (code) {
+    case FCS_OK: return "ok";
+    case FCS_EINVAL: return "invalid argument";
+    case FCS_EOVERLAP: return "fringe point without a donor outside the donor's own fringe";
+    case FCS_EUNSUPPORTED: return "unsupported configuration";
+    case FCS_ECUDA: return "CUDA runtime error";
+    case FCS_ENOMEM: return "device allocation failed";
+    case FCS_ENONFINITE: return "non-finite value in the state";
+    case FCS_ENEGATIVE: return "non-positive density or pressure";
+    default: return "unknown error";
+  }
+}
+
+int fcs_build_table(int d, int C, double* A_R_host) {
+  if (!A_R_host) return FCS_EINVAL;
+  return build_table(d, C, A_R_host) == 0 ? FCS_OK : FCS_EINVAL;
+}
+
+int fcs_line_c(const fcs_ctx* ctx, int N) {
+  if (!ctx) return FCS_EINVAL;
+  return choose_c(ctx->opt, ctx->C, N);
+}
+
+void fc_destroy(fcs_ctx* c) {
+  if (!c) return;
+  if (c->gexec) cudaGraphExecDestroy(c->gexec);
+  if (c->graph) cudaGraphDestroy(c->graph);
+  for (void* p : c->allocs) cudaFree(p);
+  delete c;
+}
+
+int fc_setup(fcs_ctx** out, int d, int C, const fcs_patch_desc* pd, int npatch, const fcs_options* opt) {
+  if (!out) return FCS_EINVAL;
+  *out = nullptr;
+  if (!pd || npatch <= 0 || d < 2 || d > 12 || C < 2 || C > 64) return FCS_EINVAL;
+  fcs_options o;
+  if (opt) o = *opt;
+  else fcs_default_options(&o);
+  if (o.instances < 1 || (o.dtype != FCS_F32 && o.dtype != FCS_F64) || o.n_f < 1 || o.gamma <= 1.0 ||
+      o.av_radius < 0 || o.av_radius > 32 || o.train_batch_max < 1)
+    return FCS_EINVAL;
+  for (int p = 0; p < npatch; ++p) {
+    const fcs_patch_desc& q = pd[p];
+    if (q.n1 < 16 || q.n2 < 16 || q.n1 > 256 || q.n2 > 256) return FCS_EINVAL;
+    for (int s = 0; s < 4; ++s)
+      if (q.bc[s] < 0 || q.bc[s] > 4) return FCS_EINVAL;
+    if (q.cartesian) {
+      if (!(q.box[1] > q.box[0]) || !(q.box[3] > q.box[2])) return FCS_EINVAL;
+    } else {
+      if (!q.x || !q.y) return FCS_EINVAL;
+      for (int s = 0; s < 4; ++s)
+        if (q.bc[s] == FCS_BC_INTERNAL) return FCS_EUNSUPPORTED;
+    }
+    if (2 * o.n_f >= q.n1 || 2 * o.n_f >= q.n2) return FCS_EINVAL;
+  }
+  fcs_ctx* c = new fcs_ctx();
+  c->opt = o;
+  c->d = d;
+  c->C = C;
+  c->npatch = npatch;
+  c->tsize = o.dtype == FCS_F64 ? 8 : 4;
+  auto fail = [&](int rc) {
+    fc_destroy(c);
+    return rc;
+  };
+
+  // ---- plans, layout, patch descriptors
+  size_t soff = 0, qoff = 0, woff_ = 0;
+  const size_t align = 64;
+  std::vector<LineRef> l0, l1;
+  std::vector<int4> p0, p1, wins;
+  for (int p = 0; p < npatch; ++p) {
+    const fcs_patch_desc& q = pd[p];
+    PatchDev P{};
+    P.n1 = q.n1;
+    P.n2 = q.n2;
+    P.cart = q.cartesian ? 1 : 0;
+    for (int s = 0; s < 4; ++s) P.bc[s] = q.bc[s];
+    for (int dir = 0; dir < 2; ++dir) {
+      const int N = dir == 0 ? q.n1 : q.n2;
+      const int pi = get_plan(c, N, choose_c(o, C, N), d);
+      if (pi < 0) return fail(pi);
+      P.plan[dir] = pi;
+      c->nmax = std::max(c->nmax, N);
+      c->nfmax = std::max(c->nfmax, c->plans[pi].dev.n);
+    }
+    P.soff = (long long)soff;
+    P.qoff = (long long)qoff;
+    c->state_off.push_back((int64_t)soff);
+    c->scalar_off.push_back((int64_t)qoff);
+    soff += ((size_t)4 * q.n1 * q.n2 + align - 1) / align * align;
+    qoff += ((size_t)q.n1 * q.n2 + align - 1) / align * align;
+    if (q.cartesian) {
+      P.hx = (q.box[1] - q.box[0]) / (q.n1 - 1);
+      P.hy = (q.box[3] - q.box[2]) / (q.n2 - 1);
+      P.hmax = std::max(P.hx, P.hy);
+    } else {
+      P.hx = 1.0 / (q.n1 - 1);
+      P.hy = 1.0 / (q.n2 - 1);
+      double hm = 0;
+      for (int j = 0; j < q.n2; ++j)
+        for (int i = 0; i < q.n1; ++i) {
+          const long long k = (long long)j * q.n1 + i;
+          if (i + 1 < q.n1) hm = std::max(hm, std::hypot(q.x[k + 1] - q.x[k], q.y[k + 1] - q.y[k]));
+          if (j + 1 < q.n2) hm = std::max(hm, std::hypot(q.x[k + q.n1] - q.x[k], q.y[k + q.n1] - q.y[k]));
+        }
+      P.hmax = hm;
+    }
+    // windows: x-lines (j outer) then y-lines (i outer)
+    auto starts = [](int N) {
+      std::vector<int> s;
+      for (int a = 0; a + 16 <= N; a += 16) s.push_back(a);
+      if (s.back() + 16 < N) s.push_back(N - 16);
+      return s;
+    };
+    const std::vector<int> sx = starts(q.n1), sy = starts(q.n2);
+    P.wpl_x = (int)sx.size();
+    P.wpl_y = (int)sy.size();
+    P.wx_off = (int)woff_;
+    c->window_off.push_back((int64_t)woff_);
+    for (int j = 0; j < q.n2; ++j)
+      for (int s : sx) wins.push_back(make_int4(p, 0, j, s));
+    P.wy_off = (int)(woff_ + (size_t)q.n2 * sx.size());
+    for (int i = 0; i < q.n1; ++i)
+      for (int s : sy) wins.push_back(make_int4(p, 1, i, s));
+    woff_ = wins.size();
+    for (int j = 0; j < q.n2; ++j) l0.push_back({p, j});
+    for (int i = 0; i < q.n1; ++i) l1.push_back({p, i});
+    for (int j = 0; j < q.n2; j += 2) p0.push_back(make_int4(p, j, j + 1 < q.n2 ? j + 1 : -1, 0));
+    for (int i = 0; i < q.n1; i += 2) p1.push_back(make_int4(p, i, i + 1 < q.n1 ? i + 1 : -1, 0));
+    c->patches.push_back(P);
+  }
+  // indicator plan (degree 5, C = 26 on 16-point windows)
+  const int ind = get_plan(c, 16, kIndC, kIndD);
+  if (ind < 0) return fail(ind);
+  c->sstride = soff;
+  c->qstride = qoff;
+  c->nwin = wins.size();
+  c->nlines0 = (int)l0.size();
+  c->nlines1 = (int)l1.size();
+  c->npairs0 = (int)p0.size();
+  c->npairs1 = (int)p1.size();
+
+  // ---- fringe map (§3.3): receivers within n_f points of an internal side;
+  // donor = lowest-numbered other Cartesian patch holding the same grid point
+  // outside its own fringe
+  std::vector<unsigned char> fringe(qoff, 0);
+  auto is_recv = [&](int p, int i, int j) {
+    const fcs_patch_desc& q = pd[p];
+    return (q.bc[0] == FCS_BC_INTERNAL && i < o.n_f) || (q.bc[1] == FCS_BC_INTERNAL && i >= q.n1 - o.n_f) ||
+           (q.bc[2] == FCS_BC_INTERNAL && j < o.n_f) || (q.bc[3] == FCS_BC_INTERNAL && j >= q.n2 - o.n_f);
+  };
+  std::vector<int4> ent;
+  for (int p = 0; p < npatch; ++p) {
+    const fcs_patch_desc& q = pd[p];
+    for (int j = 0; j < q.n2; ++j)
+      for (int i = 0; i < q.n1; ++i) {
+        if (!is_recv(p, i, j)) continue;
+        fringe[c->scalar_off[p] + (long long)j * q.n1 + i] = 1;
+        const double x = q.box[0] + (q.box[1] - q.box[0]) * i / (q.n1 - 1);
+        const double y = q.box[2] + (q.box[3] - q.box[2]) * j / (q.n2 - 1);
+        int found = -1, fi = 0, fj = 0;
+        for (int r = 0; r < npatch && found < 0; ++r) {
+          if (r == p || !pd[r].cartesian) continue;
+          const fcs_patch_desc& s = pd[r];
+          const double hx = (s.box[1] - s.box[0]) / (s.n1 - 1), hy = (s.box[3] - s.box[2]) / (s.n2 - 1);
+          const double ui = (x - s.box[0]) / hx, uj = (y - s.box[2]) / hy;
+          const long long ii = std::llround(ui), jj = std::llround(uj);
+          if (std::fabs(ui - ii) > 1e-6 || std::fabs(uj - jj) > 1e-6) continue;
+          if (ii < 0 || ii >= s.n1 || jj < 0 || jj >= s.n2) continue;
+          if (is_recv(r, (int)ii, (int)jj)) continue;
+          found = r;
+          fi = (int)ii;
+          fj = (int)jj;
+        }
+        if (found < 0) return fail(FCS_EOVERLAP);
+        ent.push_back(make_int4(p, j * q.n1 + i, found, fj * pd[found].n1 + fi));
+      }
+  }
+  c->nent = (int)ent.size();
+
+  // ---- device tables
+  std::vector<double> tab64;
+  std::vector<float> thi, tlo;
+  std::vector<double2> tw64;
+  std::vector<float2> tw32;
+  std::vector<PlanDev> plans;
+  for (HostPlan& hp : c->plans) {
+    hp.dev.tab_off = (int)tab64.size();
+    for (double v : hp.tab) {
+      float a, b;
+      split_float(v, &a, &b);
+      tab64.push_back(v);
+      thi.push_back(a);
+      tlo.push_back(b);
+    }
+    hp.dev.tw_off = (int)tw64.size();
+    std::vector<double> re(hp.dev.n), im(hp.dev.n);
+    twiddles(hp.dev.n, re.data(), im.data());
+    for (int k = 0; k < hp.dev.n; ++k) {
+      tw64.push_back(make_double2(re[k], im[k]));
+      tw32.push_back(make_float2((float)re[k], (float)im[k]));
+    }
+    plans.push_back(hp.dev);
+  }
+  // quadrature weights per patch
+  std::vector<double> wq;
+  std::vector<int2> wo;
+  for (int p = 0; p < npatch; ++p) {
+    int2 w2;
+    for (int dir = 0; dir < 2; ++dir) {
+      const HostPlan& hp = c->plans[c->patches[p].plan[dir]];
+      std::vector<double> W = quad_weights(hp.dev.N, hp.dev.C, d, hp.tab);
+      (dir == 0 ? w2.x : w2.y) = (int)wq.size();
+      wq.insert(wq.end(), W.begin(), W.end());
+    }
+    wo.push_back(w2);
+  }
+  std::vector<double> bump(2 * o.av_radius + 1);
+  for (int k = -o.av_radius; k <= o.av_radius; ++k) {
+    const double t = k / (o.av_radius + 1.0);
+    bump[k + o.av_radius] = std::exp(1.0 - 1.0 / (1.0 - t * t));
+  }
+
+  int rc;
+  CtxDev& D = c->dev;
+  PatchDev* dpatch;
+  PlanDev* dplan;
+  double *dtab64, *dW64;
+  float *dthi, *dtlo;
+  double2* dtw64;
+  float2* dtw32;
+  LineRef *dl0, *dl1;
+  int4* dwin;
+  unsigned char* dfr;
+  int* dstatus;
+  if ((rc = upload(c, &dpatch, c->patches.data(), c->patches.size() * sizeof(PatchDev))) ||
+      (rc = upload(c, &dplan, plans.data(), plans.size() * sizeof(PlanDev))) ||
+      (rc = upload(c, &dtab64, tab64.data(), tab64.size() * 8)) ||
+      (rc = upload(c, &dthi, thi.data(), thi.size() * 4)) || (rc = upload(c, &dtlo, tlo.data(), tlo.size() * 4)) ||
+      (rc = upload(c, &dtw64, tw64.data(), tw64.size() * sizeof(double2))) ||
+      (rc = upload(c, &dtw32, tw32.data(), tw32.size() * sizeof(float2))) ||
+      (rc = upload(c, &dl0, l0.data(), l0.size() * sizeof(LineRef))) ||
+      (rc = upload(c, &dl1, l1.data(), l1.size() * sizeof(LineRef))) ||
+      (rc = upload(c, &c->pairs0, p0.data(), p0.size() * sizeof(int4))) ||
+      (rc = upload(c, &c->pairs1, p1.data(), p1.size() * sizeof(int4))) ||
+      (rc = upload(c, &dwin, wins.data(), wins.size() * sizeof(int4))) ||
+      (rc = upload(c, &dfr, fringe.data(), fringe.size())) ||
+      (rc = upload(c, &c->fringe_ent, ent.data(), ent.size() * sizeof(int4))) ||
+      (rc = upload(c, &c->wq, wq.data(), wq.size() * 8)) || (rc = upload(c, &c->woff, wo.data(), wo.size() * sizeof(int2))) ||
+      (rc = upload(c, &c->bump, bump.data(), bump.size() * 8)) || (rc = dalloc(c, &dstatus, 16)))
+    return fail(rc);
+  const size_t I = (size_t)o.instances, ts = c->tsize;
+  double *m64;
+  float* m32;
+  if ((rc = dalloc(c, &c->R, I * c->sstride * ts)) || (rc = dalloc(c, &c->S, I * c->sstride * ts)) ||
+      (rc = dalloc(c, &c->A, I * c->sstride * ts)) || (rc = dalloc(c, &c->av0, I * c->qstride * ts)) ||
+      (rc = dalloc(c, &c->av1, I * c->qstride * ts)) || (rc = dalloc(c, &c->mu, I * c->qstride * ts)) ||
+      (rc = dalloc(c, &c->tau, I * c->qstride)) || (rc = dalloc(c, &c->tau_w, I * c->nwin)) ||
+      (rc = dalloc(c, &c->dtbest, I * 8)) || (rc = dalloc(c, &c->dt_internal, I * 8)) ||
+      (rc = dalloc(c, &c->Wm, kNParams * 4)) || (rc = dalloc(c, &c->Am, kNParams * 4)) ||
+      (rc = dalloc(c, &c->Av, kNParams * 4)) || (rc = dalloc(c, &c->grad, kNParams * 4)) ||
+      (rc = dalloc(c, &c->Wb, 1664 * 2)) || (rc = dalloc(c, &c->bias, 68 * 4)) ||
+      (rc = dalloc(c, &dW64, kNParams * 8)) || (rc = dalloc(c, &c->acts, (size_t)o.train_batch_max * kActs * 4)) ||
+      (rc = dalloc(c, &c->loss_s, (size_t)o.train_batch_max * 4)) || (rc = dalloc(c, &m64, 5 * c->qstride * 8)) ||
+      (rc = dalloc(c, &m32, 5 * c->qstride * 4)))
+    return fail(rc);
+  c->W64 = dW64;
+  D.patches = dpatch;
+  D.plans = dplan;
+  D.tab64 = dtab64;
+  D.tabhi = dthi;
+  D.tablo = dtlo;
+  D.tw64 = dtw64;
+  D.tw32 = dtw32;
+  D.lines0 = dl0;
+  D.lines1 = dl1;
+  D.windows = dwin;
+  D.metrics64 = m64;
+  D.metrics32 = m32;
+  D.fringe = dfr;
+  D.status = dstatus;
+  D.npatch = npatch;
+  D.nlines0 = c->nlines0;
+  D.nlines1 = c->nlines1;
+  D.nwin = (int)c->nwin;
+  D.instances = o.instances;
+  D.d = d;
+  D.sstride = (long long)c->sstride;
+  D.qstride = (long long)c->qstride;
+  D.gamma = o.gamma;
+  for (int k = 0; k < 4; ++k) D.inflow[k] = o.inflow[k];
+  D.p_out = o.p_out;
+  D.ind_plan = ind;
+  D.nmax = c->nmax;
+  D.nfmax = c->nfmax;
+  if ((rc = set_smem_attrs<float>(c)) || (rc = set_smem_attrs<double>(c))) return fail(rc);
+
+  // ---- metrics of curvilinear patches: FP64 FC derivatives of x and y
+  bool curvi = false;
+  for (int p = 0; p < npatch; ++p) curvi |= !pd[p].cartesian;
+  if (curvi) {
+    std::vector<double> X(c->qstride, 0.0), Y(c->qstride, 0.0);
+    for (int p = 0; p < npatch; ++p) {
+      const fcs_patch_desc& q = pd[p];
+      for (int j = 0; j < q.n2; ++j)
+        for (int i = 0; i < q.n1; ++i) {
+          const long long k = (long long)j * q.n1 + i;
+          double xv, yv;
+          if (q.cartesian) {
+            xv = q.box[0] + (q.box[1] - q.box[0]) * i / (q.n1 - 1);
+            yv = q.box[2] + (q.box[3] - q.box[2]) * j / (q.n2 - 1);
+          } else {
+            xv = q.x[k];
+            yv = q.y[k];
+          }
+          X[c->scalar_off[p] + k] = xv;
+          Y[c->scalar_off[p] + k] = yv;
+        }
+    }
+    double *dX, *dY;
+    if ((rc = upload(c, &dX, X.data(), X.size() * 8)) || (rc = upload(c, &dY, Y.data(), Y.size() * 8))) return fail(rc);
+    // run with one instance: the geometry is shared by all instances
+    CtxDev saved = D;
+    D.instances = 1;
+    const size_t Q = c->qstride;
+    if ((rc = launch_deriv<double>(c, dX, m64 + 0 * Q, 0, 1, 0)) || (rc = launch_deriv<double>(c, dX, m64 + 1 * Q, 1, 1, 0)) ||
+        (rc = launch_deriv<double>(c, dY, m64 + 2 * Q, 0, 1, 0)) || (rc = launch_deriv<double>(c, dY, m64 + 3 * Q, 1, 1, 0)))
+      return fail(rc);
+    D = saved;
+    std::vector<double> Mh(5 * Q);
+    if (cudaMemcpy(Mh.data(), m64, 4 * Q * 8, cudaMemcpyDeviceToHost) != cudaSuccess) return fail(FCS_ECUDA);
+    for (size_t k = 0; k < Q; ++k) Mh[4 * Q + k] = Mh[k] * Mh[3 * Q + k] - Mh[Q + k] * Mh[2 * Q + k];
+    std::vector<float> Mf(Mh.begin(), Mh.end());
+    if (cudaMemcpy(m64, Mh.data(), 5 * Q * 8, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(m32, Mf.data(), 5 * Q * 4, cudaMemcpyHostToDevice) != cudaSuccess)
+      return fail(FCS_ECUDA);
+  }
+  if (cudaDeviceSynchronize() != cudaSuccess) return fail(FCS_ECUDA);
+  *out = c;
+  return FCS_OK;
+}
+
+int fcs_get_layout(const fcs_ctx* c, fcs_layout* o) {
+  if (!c || !o) return FCS_EINVAL;
+  o->instances = c->opt.instances;
+  o->npatch = c->npatch;
+  o->dtype = c->opt.dtype;
+  o->d = c->d;
+  o->state_elems = c->sstride;
+  o->scalar_elems = c->qstride;
+  o->windows = c->nwin;
+  o->state_off = c->state_off.data();
+  o->scalar_off = c->scalar_off.data();
+  o->window_off = c->window_off.data();
+  return FCS_OK;
+}
+
+int fc_derivative(fcs_ctx* c, const void* in, void* out, int dir, int order, void* stream) {
+  if (!c || !in || !out || in == out || (dir != 0 && dir != 1) || (order != 1 && order != 2)) return FCS_EINVAL;
+  if (c->opt.dtype == FCS_F64) return launch_deriv<double>(c, in, out, dir, order, as_stream(stream));
+  return launch_deriv<float>(c, in, out, dir, order, as_stream(stream));
+}
+
+int euler_rhs(fcs_ctx* c, const void* e, const void* mu, void* rhs, void* stream) {
+  if (!c || !e || !rhs || e == rhs) return FCS_EINVAL;
+  if (c->opt.dtype == FCS_F64) {
+    StageArgs<double> st{0, 0.0, nullptr, nullptr, nullptr, static_cast<double*>(rhs)};
+    return launch_flux<double>(c, e, mu, MODE_RHS, st, as_stream(stream));
+  }
+  StageArgs<float> st{0, 0.f, nullptr, nullptr, nullptr, static_cast<float*>(rhs)};
+  return launch_flux<float>(c, e, mu, MODE_RHS, st, as_stream(stream));
+}
+
+int rk_stage(fcs_ctx* c, int stage, double dt, const double* dt_dev, const void* e_n, const void* e_s, void* acc,
+             void* out, const void* mu, void* stream) {
+  if (!c || stage < 0 || stage > 3 || !e_n || !e_s || !acc || !out) return FCS_EINVAL;
+  if (stage == 0 && e_s != e_n) return FCS_EINVAL;
+  if (out == e_n && stage != 3) return FCS_EINVAL;
+  if (out == acc) return FCS_EINVAL;
+  if (c->opt.dtype == FCS_F64) {
+    StageArgs<double> st{stage, dt, dt_dev, static_cast<const double*>(e_n), static_cast<double*>(acc),
+                         static_cast<double*>(out)};
+    return launch_flux<double>(c, e_s, mu, MODE_RK, st, as_stream(stream));
+  }
+  StageArgs<float> st{stage, (float)dt, dt_dev, static_cast<const float*>(e_n), static_cast<float*>(acc),
+                      static_cast<float*>(out)};
+  return launch_flux<float>(c, e_s, mu, MODE_RK, st, as_stream(stream));
+}
+
+int patch_exchange(fcs_ctx* c, void* field, int nfields, void* stream) {
+  if (!c || !field || (nfields != 1 && nfields != 4)) return FCS_EINVAL;
+  if (c->nent == 0) return FCS_OK;
+  const long long work = (long long)c->opt.instances * c->nent * nfields;
+  if (c->opt.dtype == FCS_F64)
+    k_exchange<double><<<grid_for(work, 256), 256, 0, as_stream(stream)>>>(c->dev, c->fringe_ent, c->nent,
+                                                                           static_cast<double*>(field), nfields);
+  else
+    k_exchange<float><<<grid_for(work, 256), 256, 0, as_stream(stream)>>>(c->dev, c->fringe_ent, c->nent,
+                                                                         static_cast<float*>(field), nfields);
+  return cuda_err(cudaGetLastError());
+}
+
+int fcs_time_step(fcs_ctx* c, const void* e, double* dt_dev, void* stream) {
+  if (!c || !e || !dt_dev) return FCS_EINVAL;
+  cudaStream_t s = as_stream(stream);
+  const int I = c->opt.instances;
+  k_dt_init<<<(I + 127) / 128, 128, 0, s>>>(c->dtbest, I);
+  const long long work = (long long)I * c->qstride;
+  if (c->opt.dtype == FCS_F64)
+    k_dt<double><<<grid_for(work, 256), 256, 0, s>>>(c->dev, static_cast<const double*>(e), c->dtbest);
+  else
+    k_dt<float><<<grid_for(work, 256), 256, 0, s>>>(c->dev, static_cast<const float*>(e), c->dtbest);
+  k_dt_final<<<(I + 127) / 128, 128, 0, s>>>(c->dtbest, dt_dev, c->opt.cfl, I);
+  return cuda_err(cudaGetLastError());
+}
+
+int fcs_conservation_sums(fcs_ctx* c, const void* e, double* sums, void* stream) {
+  if (!c || !e || !sums) return FCS_EINVAL;
+  const int blocks = c->opt.instances * c->npatch;
+  if (c->opt.dtype == FCS_F64)
+    k_sums<double><<<blocks, 256, 0, as_stream(stream)>>>(c->dev, static_cast<const double*>(e), c->wq, c->woff, sums);
+  else
+    k_sums<float><<<blocks, 256, 0, as_stream(stream)>>>(c->dev, static_cast<const float*>(e), c->wq, c->woff, sums);
+  return cuda_err(cudaGetLastError());
+}
+
+int sdnn_set_weights(fcs_ctx* c, const float* w, size_t n) {
+  if (!c || !w || n != (size_t)kNParams) return FCS_EINVAL;
+  std::vector<__nv_bfloat16> wb(1664);
+  std::vector<float> bias(68);
+  std::vector<double> w64(kNParams);
+  for (int t = 0; t < kNParams; ++t) {
+    w64[t] = w[t];
+    if (t < 512) wb[t] = __float2bfloat16_rn(w[t]);
+    else if (t < 544) bias[t - 512] = w[t];
+    else if (t < 1568) wb[512 + t - 544] = __float2bfloat16_rn(w[t]);
+    else if (t < 1600) bias[32 + t - 1568] = w[t];
+    else if (t < 1728) wb[1536 + t - 1600] = __float2bfloat16_rn(w[t]);
+    else bias[64 + t - 1728] = w[t];
+  }
+  FCS_CUDA(cudaMemcpy(c->Wm, w, kNParams * 4, cudaMemcpyHostToDevice));
+  FCS_CUDA(cudaMemcpy(c->Wb, wb.data(), 1664 * 2, cudaMemcpyHostToDevice));
+  FCS_CUDA(cudaMemcpy(c->bias, bias.data(), 68 * 4, cudaMemcpyHostToDevice));
+  FCS_CUDA(cudaMemcpy(c->W64, w64.data(), kNParams * 8, cudaMemcpyHostToDevice));
+  FCS_CUDA(cudaMemset(c->Am, 0, kNParams * 4));
+  FCS_CUDA(cudaMemset(c->Av, 0, kNParams * 4));
+  c->adam_t = 0;
+  return FCS_OK;
+}
+
+int sdnn_get_weights(fcs_ctx* c, float* w, size_t n) {
+  if (!c || !w || n != (size_t)kNParams) return FCS_EINVAL;
+  FCS_CUDA(cudaDeviceSynchronize());
+  FCS_CUDA(cudaMemcpy(w, c->Wm, kNParams * 4, cudaMemcpyDeviceToHost));
+  return FCS_OK;
+}
+
+int sdnn_classify(fcs_ctx* c, const void* e, int8_t* tau, void* logits, void* stream) {
+  if (!c || !e || !tau) return FCS_EINVAL;
+  cudaStream_t s = as_stream(stream);
+  const long long nw = (long long)c->opt.instances * c->nwin;
+  if (c->opt.dtype == FCS_F64) {
+    k_mlp64<double><<<grid_for(nw, 128), 128, 0, s>>>(c->dev, static_cast<const double*>(e), c->W64, c->tau_w,
+                                                      static_cast<double*>(logits));
+  } else {
+    const long long groups = (nw + 15) / 16;
+    k_mlp_bf16<<<grid_for(groups, 4), 128, 0, s>>>(c->dev, static_cast<const float*>(e), c->Wb, c->bias, c->tau_w,
+                                                    static_cast<float*>(logits));
+  }
+  FCS_CUDA(cudaGetLastError());
+  const long long np = (long long)c->opt.instances * c->qstride;
+  k_tau_gather<<<grid_for(np, 256), 256, 0, s>>>(c->dev, c->tau_w, reinterpret_cast<signed char*>(tau));
+  return cuda_err(cudaGetLastError());
+}
+
+int sdnn_indicator(fcs_ctx* c, const void* e, int8_t* tau, void* s_out, void* stream) {
+  if (!c || !e || !tau) return FCS_EINVAL;
+  cudaStream_t s = as_stream(stream);
+  const long long nw = (long long)c->opt.instances * c->nwin;
+  if (c->opt.dtype == FCS_F64)
+    k_indicator<double><<<grid_for(nw, 128), 128, 0, s>>>(c->dev, static_cast<const double*>(e), c->tau_w,
+                                                          static_cast<double*>(s_out));
+  else
+    k_indicator<float><<<grid_for(nw, 128), 128, 0, s>>>(c->dev, static_cast<const float*>(e), c->tau_w,
+                                                         static_cast<float*>(s_out));
+  FCS_CUDA(cudaGetLastError());
+  const long long np = (long long)c->opt.instances * c->qstride;
+  k_tau_gather<<<grid_for(np, 256), 256, 0, s>>>(c->dev, c->tau_w, reinterpret_cast<signed char*>(tau));
+  return cuda_err(cudaGetLastError());
+}
+
+
+int av_assemble(fcs_ctx* c, const void* e, const int8_t* tau, void* mu, void* stream) {
+  if (!c || !e || !tau || !mu) return FCS_EINVAL;
+  if (c->opt.dtype == FCS_F64) return av_impl<double>(c, e, tau, mu, as_stream(stream));
+  return av_impl<float>(c, e, tau, mu, as_stream(stream));
+}
+
+
+int sdnn_gradient(fcs_ctx* c, const float* x, const int8_t* lab, int B, float* loss, float* grad, void* stream) {
+  if (!c || !x || !lab || !grad || B < 1 || B > c->opt.train_batch_max) return FCS_EINVAL;
+  cudaStream_t s = as_stream(stream);
+  int rc = train_forward_backward(c, x, lab, B, loss, s);
+  if (rc) return rc;
+  return cuda_err(cudaMemcpyAsync(grad, c->grad, kNParams * 4, cudaMemcpyDeviceToDevice, s));
+}
+
+int sdnn_train_step(fcs_ctx* c, const float* x, const int8_t* lab, int B, float lr, float* loss, void* stream) {
+  if (!c || !x || !lab || B < 1 || B > c->opt.train_batch_max) return FCS_EINVAL;
+  cudaStream_t s = as_stream(stream);
+  int rc = train_forward_backward(c, x, lab, B, loss, s);
+  if (rc) return rc;
+  c->adam_t += 1;
+  const float b1c = 1.f - std::pow(0.9f, (float)c->adam_t), b2c = 1.f - std::pow(0.999f, (float)c->adam_t);
+  k_adam<<<(kNParams + 127) / 128, 128, 0, s>>>(c->Wm, c->Am, c->Av, c->grad, lr, b1c, b2c, c->Wb, c->bias, c->W64);
+  return cuda_err(cudaGetLastError());
+}
+
+int fcs_step(fcs_ctx* c, void* e, double dt, double* dt_dev, int use_av, void* stream) {
+  if (!c || !e) return FCS_EINVAL;
+  if (!(dt > 0.0) && !dt_dev) return FCS_EINVAL;
+  int rc;
+  const void* mu = nullptr;
+  if (use_av) {
+    if ((rc = sdnn_classify(c, e, reinterpret_cast<int8_t*>(c->tau), nullptr, stream))) return rc;
+    if ((rc = av_assemble(c, e, reinterpret_cast<int8_t*>(c->tau), c->mu, stream))) return rc;
+    mu = c->mu;
+  }
+  const double* dtd = nullptr;
+  if (!(dt > 0.0)) {
+    if ((rc = fcs_time_step(c, e, dt_dev, stream))) return rc;
+    dtd = dt_dev;
+  }
+  for (int s = 0; s < 4; ++s) {
+    const void* es = s == 0 ? e : c->S;
+    void* out = s == 3 ? e : c->S;
+    if ((rc = rk_stage(c, s, dt, dtd, e, es, c->A, out, mu, stream))) return rc;
+    if ((rc = patch_exchange(c, out, 4, stream))) return rc;
+  }
+  return FCS_OK;
+}
+
+int fcs_step_graph(fcs_ctx* c, void* e, double dt, double* dt_dev, int use_av, void* stream) {
+  if (!c || !e || !stream) return FCS_EINVAL;
+  cudaStream_t s = as_stream(stream);
+  if (!c->gexec || c->g_e != e || c->g_dt != dt || c->g_dtdev != dt_dev || c->g_av != use_av || c->g_stream != s) {
+    if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    if (c->graph) cudaGraphDestroy(c->graph);
+    c->gexec = nullptr;
+    c->graph = nullptr;
+    FCS_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    int rc = fcs_step(c, e, dt, dt_dev, use_av, stream);
+    cudaGraph_t g = nullptr;
+    cudaError_t ce = cudaStreamEndCapture(s, &g);
+    if (rc) {
+      if (g) cudaGraphDestroy(g);
+      return rc;
+    }
+    FCS_CUDA(ce);
+    c->graph = g;
+    FCS_CUDA(cudaGraphInstantiate(&c->gexec, g, 0));
+    c->g_e = e;
+    c->g_dt = dt;
+    c->g_dtdev = dt_dev;
+    c->g_av = use_av;
+    c->g_stream = s;
+  }
+  return cuda_err(cudaGraphLaunch(c->gexec, s));
+}
+
+int fcs_status(fcs_ctx* c, int* flags) {
+  if (!c) return FCS_EINVAL;
+  FCS_CUDA(cudaDeviceSynchronize());
+  int f = 0;
+  FCS_CUDA(cudaMemcpy(&f, c->dev.status, sizeof(int), cudaMemcpyDeviceToHost));
+  FCS_CUDA(cudaMemset(c->dev.status, 0, sizeof(int)));
+  if (flags) *flags = f;
+  if (f & 1) return FCS_ENONFINITE;
+  if (f & 2) return FCS_ENEGATIVE;
+  return FCS_OK;
+}
+
+}  // extern "C"

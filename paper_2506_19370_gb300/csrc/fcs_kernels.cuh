@@ -1,0 +1,948 @@
+// Kernels of the FC-SDNN stage library (included once, by fcs_api.cu).
+#pragma once
+
+#include <cuda_bf16.h>
+
+#include "fcs_device.cuh"
+
+namespace fcs {
+
+// ============================================================ FC derivative
+// One warp per pair of lines of one patch (two real lines -> one complex FFT).
+template <typename T>
+__global__ void __launch_bounds__(kWarps * 32) k_fc_deriv(CtxDev c, int dir, int order, const int4* __restrict__ pairs,
+                                                           int npairs, const T* __restrict__ in, T* __restrict__ out) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  Cx<T>* a = reinterpret_cast<Cx<T>*>(smem_raw) + (size_t)warp * 2 * c.nfmax;
+  Cx<T>* b = a + c.nfmax;
+  const long long total = (long long)c.instances * npairs;
+  for (long long w = (long long)blockIdx.x * kWarps + warp; w < total; w += (long long)gridDim.x * kWarps) {
+    const int inst = (int)(w / npairs);
+    const int4 pr = pairs[w % npairs];
+    const PatchDev P = c.patches[pr.x];
+    const PlanDev pl = c.plans[P.plan[dir]];
+    const int N = pl.N;
+    const long long stride = dir == 0 ? 1 : P.n1;
+    const long long la = dir == 0 ? (long long)pr.y * P.n1 : pr.y;
+    const long long lb = pr.z < 0 ? -1 : (dir == 0 ? (long long)pr.z * P.n1 : pr.z);
+    const T* src = in + inst * c.qstride + P.qoff;
+    T* dst = out + inst * c.qstride + P.qoff;
+    for (int t = lane; t < N; t += 32) {
+      const T va = src[la + t * stride];
+      const T vb = lb >= 0 ? src[lb + t * stride] : T(0);
+      a[t] = {va, vb};
+    }
+    __syncwarp();
+    const T h = T(1) / T(N - 1);
+    Cx<T>* r = fc_deriv_pair<T>(a, b, c, pl, c.d, h, order, lane);
+    for (int t = lane; t < N; t += 32) {
+      dst[la + t * stride] = r[t].x;
+      if (lb >= 0) dst[lb + t * stride] = r[t].y;
+    }
+    __syncwarp();
+  }
+}
+
+// ============================================================ Euler operator
+// Per-warp shared layout of the flux passes: E[4][nmax], W[4][nmax], M[nmax],
+// then two complex buffers of nfmax.
+template <typename T>
+__host__ __device__ inline size_t flux_warp_bytes(int nmax, int nfmax) {
+  size_t r = (size_t)9 * nmax * sizeof(T);
+  r = (r + 15) & ~size_t(15);
+  return r + (size_t)2 * nfmax * sizeof(Cx<T>);
+}
+
+enum { MODE_X = 0, MODE_RHS = 1, MODE_RK = 2 };
+
+template <typename T>
+struct StageArgs {
+  int stage;
+  T dt;
+  const double* dt_dev;
+  const T* e_n;
+  T* acc;
+  T* out;
+};
+
+// Apply the boundary conditions of the sides the point lies on, in the order
+// left, right, bottom, top (paper §5 item 4: enforced at every stage).
+template <typename T>
+__device__ __forceinline__ void apply_bc(const CtxDev& c, const PatchDev& P, int i, int j, long long q, T* v) {
+  const T gm1 = T(c.gamma - 1.0);
+  const bool on[4] = {i == 0, i == P.n1 - 1, j == 0, j == P.n2 - 1};
+#pragma unroll
+  for (int s = 0; s < 4; ++s) {
+    if (!on[s]) continue;
+    const int code = P.bc[s];
+    if (code == 1) {  // wall
+      if (P.cart) {
+        v[s < 2 ? 1 : 2] = T(0);
+      } else {
+        const T* M = metrics<T>(c);
+        const long long qs = c.qstride;
+        T nx, ny;
+        if (s < 2) {
+          nx = M[3 * qs + q];
+          ny = -M[1 * qs + q];
+        } else {
+          nx = -M[2 * qs + q];
+          ny = M[0 * qs + q];
+        }
+        const T nn = sqrt(nx * nx + ny * ny);
+        nx /= nn;
+        ny /= nn;
+        const T mn = v[1] * nx + v[2] * ny;
+        v[1] -= mn * nx;
+        v[2] -= mn * ny;
+      }
+    } else if (code == 2) {  // inflow
+      v[0] = T(c.inflow[0]);
+      v[1] = T(c.inflow[1]);
+      v[2] = T(c.inflow[2]);
+      v[3] = T(c.inflow[3]);
+    } else if (code == 3) {  // outflow pressure
+      v[3] = T(c.p_out) / gm1 + T(0.5) * (v[1] * v[1] + v[2] * v[2]) / v[0];
+    }
+  }
+}
+
+// Flux pass along direction DIR.  DIR 0 (rows): R = -d/dq1 F1 with
+// F1 = y_q2 f - x_q2 g (Cartesian: f, derivative at the physical spacing).
+// DIR 1 (columns): L = (R - d/dq2 F2) / J with F2 = -y_q1 f + x_q1 g
+// (Cartesian: g, J = 1); MODE_RHS writes L, MODE_RK applies the stage.
+// With mu, Cartesian fluxes carry the viscous part: f - mu de/dx, g - mu de/dy.
+template <typename T, int DIR, int MODE>
+__global__ void __launch_bounds__(kWarps * 32) k_flux(CtxDev c, const T* __restrict__ e, const T* __restrict__ mu,
+                                                       T* R, StageArgs<T> st) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nmax = c.nmax;
+  unsigned char* base = smem_raw + (size_t)warp * flux_warp_bytes<T>(nmax, c.nfmax);
+  T* E = reinterpret_cast<T*>(base);
+  T* W = E + 4 * nmax;
+  T* M = W + 4 * nmax;
+  Cx<T>* ba = reinterpret_cast<Cx<T>*>(base + (((size_t)9 * nmax * sizeof(T) + 15) & ~size_t(15)));
+  Cx<T>* bb = ba + c.nfmax;
+  const int nl = DIR == 0 ? c.nlines0 : c.nlines1;
+  const LineRef* L = DIR == 0 ? c.lines0 : c.lines1;
+  const T gam = T(c.gamma), gm1 = T(c.gamma - 1.0);
+  const long long total = (long long)c.instances * nl;
+  for (long long w = (long long)blockIdx.x * kWarps + warp; w < total; w += (long long)gridDim.x * kWarps) {
+    const int inst = (int)(w / nl);
+    const LineRef lr = L[w % nl];
+    const PatchDev P = c.patches[lr.patch];
+    const PlanDev pl = c.plans[P.plan[DIR]];
+    const int N = pl.N;
+    const long long np = (long long)P.n1 * P.n2;
+    const long long stride = DIR == 0 ? 1 : P.n1;
+    const long long l0 = DIR == 0 ? (long long)lr.line * P.n1 : lr.line;
+    const T* es = e + inst * c.sstride + P.soff + l0;
+    const T h = T(DIR == 0 ? P.hx : P.hy);
+    const bool visc = (mu != nullptr) && P.cart;
+    for (int t = lane; t < N; t += 32) {
+#pragma unroll
+      for (int f = 0; f < 4; ++f) E[f * nmax + t] = es[f * np + t * stride];
+      if (visc) M[t] = mu[inst * c.qstride + P.qoff + l0 + t * stride];
+    }
+    __syncwarp();
+    if (visc) {  // W = d e / dx (or dy) for the four fields
+#pragma unroll
+      for (int pr = 0; pr < 2; ++pr) {
+        for (int t = lane; t < N; t += 32) ba[t] = {E[(2 * pr) * nmax + t], E[(2 * pr + 1) * nmax + t]};
+        __syncwarp();
+        Cx<T>* r = fc_deriv_pair<T>(ba, bb, c, pl, c.d, h, 1, lane);
+        for (int t = lane; t < N; t += 32) {
+          W[(2 * pr) * nmax + t] = r[t].x;
+          W[(2 * pr + 1) * nmax + t] = r[t].y;
+        }
+        __syncwarp();
+      }
+    }
+    // flux combination F = a f + b g (W)
+    const T* Mt = metrics<T>(c);
+    for (int t = lane; t < N; t += 32) {
+      const T rho = E[t], mx = E[nmax + t], my = E[2 * nmax + t], En = E[3 * nmax + t];
+      const T u = mx / rho, v = my / rho;
+      const T p = pressure<T>(rho, mx, my, En, gm1);
+      T fl[4];
+      if (P.cart) {
+        if (DIR == 0) {
+          fl[0] = mx; fl[1] = mx * u + p; fl[2] = my * u; fl[3] = (En + p) * u;
+        } else {
+          fl[0] = my; fl[1] = mx * v; fl[2] = my * v + p; fl[3] = (En + p) * v;
+        }
+        if (visc) {
+#pragma unroll
+          for (int f = 0; f < 4; ++f) fl[f] -= M[t] * W[f * nmax + t];
+        }
+      } else {
+        const long long q = P.qoff + l0 + t * stride;
+        T ca, cb;
+        if (DIR == 0) {
+          ca = Mt[3 * c.qstride + q];   // y_q2
+          cb = -Mt[1 * c.qstride + q];  // -x_q2
+        } else {
+          ca = -Mt[2 * c.qstride + q];  // -y_q1
+          cb = Mt[0 * c.qstride + q];   // x_q1
+        }
+        const T f0 = mx, f1 = mx * u + p, f2 = my * u, f3 = (En + p) * u;
+        const T g0 = my, g1 = mx * v, g2 = my * v + p, g3 = (En + p) * v;
+        fl[0] = ca * f0 + cb * g0;
+        fl[1] = ca * f1 + cb * g1;
+        fl[2] = ca * f2 + cb * g2;
+        fl[3] = ca * f3 + cb * g3;
+      }
+#pragma unroll
+      for (int f = 0; f < 4; ++f) W[f * nmax + t] = fl[f];
+    }
+    __syncwarp();
+    // derivatives of the two flux pairs; results of pair 0 parked in W[0..1]
+    const long long base_s = inst * c.sstride + P.soff + l0;
+#pragma unroll
+    for (int pr = 0; pr < 2; ++pr) {
+      for (int t = lane; t < N; t += 32) ba[t] = {W[(2 * pr) * nmax + t], W[(2 * pr + 1) * nmax + t]};
+      __syncwarp();
+      Cx<T>* r = fc_deriv_pair<T>(ba, bb, c, pl, c.d, h, 1, lane);
+      if (MODE == MODE_X) {
+        for (int t = lane; t < N; t += 32) {
+          R[base_s + (2 * pr) * np + t * stride] = -r[t].x;
+          R[base_s + (2 * pr + 1) * np + t * stride] = -r[t].y;
+        }
+      } else {
+        for (int t = lane; t < N; t += 32) {
+          W[(2 * pr) * nmax + t] = r[t].x;
+          W[(2 * pr + 1) * nmax + t] = r[t].y;
+        }
+      }
+      __syncwarp();
+    }
+    if (MODE == MODE_X) continue;
+    const T dtv = st.dt_dev ? T(st.dt_dev[inst]) : st.dt;
+    for (int t = lane; t < N; t += 32) {
+      const long long off = base_s + t * stride;
+      const long long q = P.qoff + l0 + t * stride;
+      const T invJ = P.cart ? T(1) : T(1) / Mt[4 * c.qstride + q];
+      T k[4];
+#pragma unroll
+      for (int f = 0; f < 4; ++f) k[f] = (R[off + f * np] - W[f * nmax + t]) * invJ;
+      if (MODE == MODE_RHS) {
+#pragma unroll
+        for (int f = 0; f < 4; ++f) st.out[off + f * np] = k[f];
+        continue;
+      }
+      T v[4];
+      const int s = st.stage;
+      if (s == 0) {
+#pragma unroll
+        for (int f = 0; f < 4; ++f) {
+          const T en = st.e_n[off + f * np];
+          st.acc[off + f * np] = en + (dtv / T(6)) * k[f];
+          v[f] = en + (dtv / T(2)) * k[f];
+        }
+      } else if (s < 3) {
+        const T b = s == 1 ? dtv / T(3) : dtv / T(3);
+        const T a = s == 1 ? dtv / T(2) : dtv;
+#pragma unroll
+        for (int f = 0; f < 4; ++f) {
+          st.acc[off + f * np] = st.acc[off + f * np] + b * k[f];
+          v[f] = st.e_n[off + f * np] + a * k[f];
+        }
+      } else {
+#pragma unroll
+        for (int f = 0; f < 4; ++f) v[f] = st.acc[off + f * np] + (dtv / T(6)) * k[f];
+      }
+      const int i = DIR == 0 ? t : lr.line;
+      const int j = DIR == 0 ? lr.line : t;
+      apply_bc<T>(c, P, i, j, q, v);
+      const T pr_ = pressure<T>(v[0], v[1], v[2], v[3], gm1);
+      int flag = 0;
+      if (!(isfinite(v[0]) && isfinite(v[1]) && isfinite(v[2]) && isfinite(v[3]))) flag |= 1;
+      else if (!(v[0] > T(0)) || !(pr_ > T(0))) flag |= 2;
+      if (flag) atomicOr(c.status, flag);
+#pragma unroll
+      for (int f = 0; f < 4; ++f) st.out[off + f * np] = v[f];
+    }
+    __syncwarp();
+  }
+  (void)gam;
+}
+
+// ============================================================ exchange
+// entries: (dst patch, dst point, src patch, src point) of one instance.
+template <typename T>
+__global__ void k_exchange(CtxDev c, const int4* __restrict__ ent, int nent, T* field, int nfields) {
+  const long long total = (long long)c.instances * nent * nfields;
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x) {
+    const int f = (int)(t % nfields);
+    const long long r = t / nfields;
+    const int inst = (int)(r / nent);
+    const int4 x = ent[r % nent];
+    const PatchDev& Pd = c.patches[x.x];
+    const PatchDev& Ps = c.patches[x.z];
+    if (nfields == 4) {
+      const long long pd = (long long)Pd.n1 * Pd.n2, ps = (long long)Ps.n1 * Ps.n2;
+      field[inst * c.sstride + Pd.soff + f * pd + x.y] = field[inst * c.sstride + Ps.soff + f * ps + x.w];
+    } else {
+      field[inst * c.qstride + Pd.qoff + x.y] = field[inst * c.qstride + Ps.qoff + x.w];
+    }
+  }
+}
+
+// ============================================================ point helpers
+__device__ __forceinline__ int find_patch(const CtxDev& c, long long q) {
+  int lo = 0, hi = c.npatch - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (c.patches[mid].qoff <= q) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+// ============================================================ time step
+template <typename T>
+__global__ void k_dt(CtxDev c, const T* __restrict__ e, unsigned long long* best) {
+  const long long per = c.qstride;
+  const long long total = (long long)c.instances * per;
+  const T gam = T(c.gamma), gm1 = T(c.gamma - 1.0);
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x) {
+    const int inst = (int)(t / per);
+    const long long q = t % per;
+    const int p = find_patch(c, q);
+    const PatchDev P = c.patches[p];
+    const long long np = (long long)P.n1 * P.n2;
+    const long long lq = q - P.qoff;
+    if (lq >= np) continue;
+    const T* es = e + inst * c.sstride + P.soff + lq;
+    const double rho = es[0], mx = es[np], my = es[2 * np], En = es[3 * np];
+    const double pr = (c.gamma - 1.0) * (En - 0.5 * (mx * mx + my * my) / rho);
+    const double u = mx / rho, v = my / rho;
+    const double cs = sqrt(c.gamma * pr / rho);
+    double x_q1, x_q2, y_q1, y_q2, J, h1, h2;
+    if (P.cart) {
+      x_q1 = P.hx * (P.n1 - 1); y_q2 = P.hy * (P.n2 - 1); x_q2 = 0; y_q1 = 0;
+      J = x_q1 * y_q2;
+      h1 = 1.0 / (P.n1 - 1); h2 = 1.0 / (P.n2 - 1);
+    } else {
+      x_q1 = c.metrics64[q]; x_q2 = c.metrics64[c.qstride + q];
+      y_q1 = c.metrics64[2 * c.qstride + q]; y_q2 = c.metrics64[3 * c.qstride + q];
+      J = c.metrics64[4 * c.qstride + q];
+      h1 = P.hx; h2 = P.hy;
+    }
+    const double U1 = (y_q2 * u - x_q2 * v) / J, U2 = (-y_q1 * u + x_q1 * v) / J;
+    const double n1 = sqrt(y_q2 * y_q2 + x_q2 * x_q2) / fabs(J), n2 = sqrt(y_q1 * y_q1 + x_q1 * x_q1) / fabs(J);
+    double r = fmin(h1 / (fabs(U1) + cs * n1), h2 / (fabs(U2) + cs * n2));
+    if (!(r > 0.0)) r = 0.0;
+    atomicMin(best + inst, (unsigned long long)__double_as_longlong(r));
+  }
+  (void)gam; (void)gm1;
+}
+
+__global__ void k_dt_init(unsigned long long* best, int n) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n) best[t] = 0x7ff0000000000000ULL;  // +Inf
+}
+
+__global__ void k_dt_final(const unsigned long long* best, double* dt, double cfl, int n) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n) dt[t] = cfl * __longlong_as_double((long long)best[t]);
+}
+
+// ============================================================ conservation sums
+// one block per (instance, patch); quadrature weights w1 (per patch, n1) and
+// w2 (n2) at offsets wq1[p], wq2[p] of wq.
+template <typename T>
+__global__ void k_sums(CtxDev c, const T* __restrict__ e, const double* __restrict__ wq, const int2* __restrict__ woff,
+                       double* sums) {
+  const int p = blockIdx.x % c.npatch;
+  const int inst = blockIdx.x / c.npatch;
+  const PatchDev P = c.patches[p];
+  const long long np = (long long)P.n1 * P.n2;
+  const T* es = e + inst * c.sstride + P.soff;
+  const int2 wo = woff[p];
+  double acc[4] = {0, 0, 0, 0};
+  int flag = 0;
+  const double gm1 = c.gamma - 1.0;
+  for (long long t = threadIdx.x; t < np; t += blockDim.x) {
+    const int i = (int)(t % P.n1), j = (int)(t / P.n1);
+    double J;
+    if (P.cart) J = (P.hx * (P.n1 - 1)) * (P.hy * (P.n2 - 1));
+    else J = c.metrics64[4 * c.qstride + P.qoff + t];
+    const double w = wq[wo.x + i] * wq[wo.y + j] * fabs(J);
+    double v[4];
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+      v[f] = (double)es[f * np + t];
+      acc[f] += w * v[f];
+    }
+    if (!(isfinite(v[0]) && isfinite(v[1]) && isfinite(v[2]) && isfinite(v[3]))) flag |= 1;
+    else if (!(v[0] > 0.0) || !(gm1 * (v[3] - 0.5 * (v[1] * v[1] + v[2] * v[2]) / v[0]) > 0.0)) flag |= 2;
+  }
+  __shared__ double red[4][256];
+#pragma unroll
+  for (int f = 0; f < 4; ++f) red[f][threadIdx.x] = acc[f];
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) {
+#pragma unroll
+      for (int f = 0; f < 4; ++f) red[f][threadIdx.x] += red[f][threadIdx.x + s];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x < 4) sums[((long long)inst * c.npatch + p) * 4 + threadIdx.x] = red[threadIdx.x][0];
+  if (flag) atomicOr(c.status, flag);
+}
+
+// ============================================================ classifier
+// Window w of instance inst: proxy values Phi = |u| sqrt(rho/(gamma p)).
+template <typename T>
+__device__ __forceinline__ void window_point(const CtxDev& c, int4 wd, int t, long long* so, long long* np_) {
+  const PatchDev& P = c.patches[wd.x];
+  const long long ji = wd.y == 0 ? (long long)wd.z * P.n1 + wd.w + t : (long long)(wd.w + t) * P.n1 + wd.z;
+  *so = P.soff + ji;
+  *np_ = (long long)P.n1 * P.n2;
+}
+
+template <typename T>
+__device__ __forceinline__ T proxy_at(const CtxDev& c, const T* e, long long inst, int4 wd, int t) {
+  long long so, np;
+  window_point<T>(c, wd, t, &so, &np);
+  const T* es = e + inst * c.sstride + so;
+  const T rho = es[0], mx = es[np], my = es[2 * np], En = es[3 * np];
+  const T p = pressure<T>(rho, mx, my, En, T(c.gamma - 1.0));
+  return sqrt(mx * mx + my * my) / rho * sqrt(rho / (T(c.gamma) * p));
+}
+
+struct MlpW64 {
+  const double* w;  // 1732 doubles, layout of sdnn_set_weights
+};
+
+// FP64 classifier: one thread per window.
+template <typename T>
+__global__ void k_mlp64(CtxDev c, const T* __restrict__ e, const double* __restrict__ W, signed char* tau_w,
+                        T* logits) {
+  const long long total = (long long)c.instances * c.nwin;
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x) {
+    const long long inst = t / c.nwin;
+    const int4 wd = c.windows[t % c.nwin];
+    double x[16];
+    double mn = 1e300, mxv = -1e300, sum = 0.0, amax = 0.0;
+    for (int k = 0; k < 16; ++k) {
+      x[k] = (double)proxy_at<T>(c, e, inst, wd, k);
+      mn = fmin(mn, x[k]);
+      mxv = fmax(mxv, x[k]);
+      sum += x[k];
+      amax = fmax(amax, fabs(x[k]));
+    }
+    const double mean = sum / 16.0;
+    const bool flat = (mxv - mn) <= 1e-8 * amax;
+    double z[4] = {0, 0, 0, 0};
+    if (!flat) {
+      const double rng = mxv - mn;
+      for (int k = 0; k < 16; ++k) x[k] = (x[k] - mean) / rng;
+      double h1[32], h2[32];
+      const double* W1 = W;
+      const double* b1 = W + 512;
+      const double* W2 = W + 544;
+      const double* b2 = W + 1568;
+      const double* W3 = W + 1600;
+      const double* b3 = W + 1728;
+      for (int o = 0; o < 32; ++o) {
+        double s = 0.0;
+        for (int k = 0; k < 16; ++k) s = fma(W1[o * 16 + k], x[k], s);
+        h1[o] = fmax(s + b1[o], 0.0);
+      }
+      for (int o = 0; o < 32; ++o) {
+        double s = 0.0;
+        for (int k = 0; k < 32; ++k) s = fma(W2[o * 32 + k], h1[k], s);
+        h2[o] = fmax(s + b2[o], 0.0);
+      }
+      for (int o = 0; o < 4; ++o) {
+        double s = 0.0;
+        for (int k = 0; k < 32; ++k) s = fma(W3[o * 32 + k], h2[k], s);
+        z[o] = s + b3[o];
+      }
+    }
+    int best = 0;
+    for (int o = 1; o < 4; ++o)
+      if (z[o] > z[best]) best = o;
+    tau_w[t] = flat ? 4 : (signed char)(best + 1);
+    if (logits)
+      for (int o = 0; o < 4; ++o) logits[t * 4 + o] = (T)z[o];
+  }
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+  __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<uint32_t*>(&v);
+}
+
+__device__ __forceinline__ void mma_bf16(float* d, const uint32_t* a, uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// BF16 tensor-core classifier (FP32 contexts): one warp per 16 windows,
+// m16n8k16 MMAs with FP32 accumulation; hidden activations are rounded to
+// BF16 between layers.  Weights (bf16, [out][in]; W3 padded to 8 rows) and
+// FP32 biases are staged in shared memory.
+__global__ void __launch_bounds__(128) k_mlp_bf16(CtxDev c, const float* __restrict__ e,
+                                                  const __nv_bfloat16* __restrict__ Wb, const float* __restrict__ bias,
+                                                  signed char* tau_w, float* logits) {
+  __shared__ __align__(16) __nv_bfloat16 sW1[32 * 16];
+  __shared__ __align__(16) __nv_bfloat16 sW2[32 * 32];
+  __shared__ __align__(16) __nv_bfloat16 sW3[8 * 32];
+  __shared__ float sb[68];
+  __shared__ float X[4][16][17];
+  __shared__ float Lg[4][16][4];
+  __shared__ int Fl[4][16];
+  for (int t = threadIdx.x; t < 512; t += blockDim.x) sW1[t] = Wb[t];
+  for (int t = threadIdx.x; t < 1024; t += blockDim.x) sW2[t] = Wb[512 + t];
+  for (int t = threadIdx.x; t < 256; t += blockDim.x) sW3[t] = t < 128 ? Wb[1536 + t] : __float2bfloat16(0.f);
+  for (int t = threadIdx.x; t < 68; t += blockDim.x) sb[t] = bias[t];
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int g = lane >> 2, tg = lane & 3;
+  const long long total = (long long)c.instances * c.nwin;
+  const long long ngroups = (total + 15) / 16;
+  for (long long grp = (long long)blockIdx.x * 4 + warp; grp < ngroups; grp += (long long)gridDim.x * 4) {
+    // proxies of 16 windows x 16 points
+    for (int k = lane; k < 256; k += 32) {
+      const int r = k >> 4, t = k & 15;
+      const long long wid = grp * 16 + r;
+      float v = 0.f;
+      if (wid < total) v = proxy_at<float>(c, e, wid / c.nwin, c.windows[wid % c.nwin], t);
+      X[warp][r][t] = v;
+    }
+    __syncwarp();
+    if (lane < 16) {
+      float mn = X[warp][lane][0], mx = mn, sum = 0.f, amax = 0.f;
+      for (int t = 0; t < 16; ++t) {
+        const float v = X[warp][lane][t];
+        mn = fminf(mn, v);
+        mx = fmaxf(mx, v);
+        sum += v;
+        amax = fmaxf(amax, fabsf(v));
+      }
+      const float mean = sum / 16.f;
+      const bool flat = (mx - mn) <= 1e-8f * amax;
+      Fl[warp][lane] = flat;
+      const float rng = flat ? 1.f : (mx - mn);
+      for (int t = 0; t < 16; ++t) X[warp][lane][t] = flat ? 0.f : (X[warp][lane][t] - mean) / rng;
+    }
+    __syncwarp();
+    uint32_t a[4];
+    a[0] = pack_bf16(X[warp][g][2 * tg], X[warp][g][2 * tg + 1]);
+    a[1] = pack_bf16(X[warp][g + 8][2 * tg], X[warp][g + 8][2 * tg + 1]);
+    a[2] = pack_bf16(X[warp][g][2 * tg + 8], X[warp][g][2 * tg + 9]);
+    a[3] = pack_bf16(X[warp][g + 8][2 * tg + 8], X[warp][g + 8][2 * tg + 9]);
+    float h[4][4];
+#pragma unroll
+    for (int nt = 0; nt < 4; ++nt) {
+      h[nt][0] = h[nt][1] = h[nt][2] = h[nt][3] = 0.f;
+      const __nv_bfloat16* wr = sW1 + (nt * 8 + g) * 16;
+      const uint32_t b0 = *reinterpret_cast<const uint32_t*>(wr + 2 * tg);
+      const uint32_t b1 = *reinterpret_cast<const uint32_t*>(wr + 2 * tg + 8);
+      mma_bf16(h[nt], a, b0, b1);
+      const float bb0 = sb[nt * 8 + 2 * tg], bb1 = sb[nt * 8 + 2 * tg + 1];
+      h[nt][0] = fmaxf(h[nt][0] + bb0, 0.f);
+      h[nt][1] = fmaxf(h[nt][1] + bb1, 0.f);
+      h[nt][2] = fmaxf(h[nt][2] + bb0, 0.f);
+      h[nt][3] = fmaxf(h[nt][3] + bb1, 0.f);
+    }
+    // layer 2: K = 32 (two k-tiles made of accumulator tiles 2kt, 2kt+1)
+    float h2[4][4];
+#pragma unroll
+    for (int nt = 0; nt < 4; ++nt) h2[nt][0] = h2[nt][1] = h2[nt][2] = h2[nt][3] = 0.f;
+#pragma unroll
+    for (int kt = 0; kt < 2; ++kt) {
+      uint32_t a2[4];
+      a2[0] = pack_bf16(h[2 * kt][0], h[2 * kt][1]);
+      a2[1] = pack_bf16(h[2 * kt][2], h[2 * kt][3]);
+      a2[2] = pack_bf16(h[2 * kt + 1][0], h[2 * kt + 1][1]);
+      a2[3] = pack_bf16(h[2 * kt + 1][2], h[2 * kt + 1][3]);
+#pragma unroll
+      for (int nt = 0; nt < 4; ++nt) {
+        const __nv_bfloat16* wr = sW2 + (nt * 8 + g) * 32 + kt * 16;
+        const uint32_t b0 = *reinterpret_cast<const uint32_t*>(wr + 2 * tg);
+        const uint32_t b1 = *reinterpret_cast<const uint32_t*>(wr + 2 * tg + 8);
+        mma_bf16(h2[nt], a2, b0, b1);
+      }
+    }
+#pragma unroll
+    for (int nt = 0; nt < 4; ++nt) {
+      const float bb0 = sb[32 + nt * 8 + 2 * tg], bb1 = sb[32 + nt * 8 + 2 * tg + 1];
+      h2[nt][0] = fmaxf(h2[nt][0] + bb0, 0.f);
+      h2[nt][1] = fmaxf(h2[nt][1] + bb1, 0.f);
+      h2[nt][2] = fmaxf(h2[nt][2] + bb0, 0.f);
+      h2[nt][3] = fmaxf(h2[nt][3] + bb1, 0.f);
+    }
+    float z[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int kt = 0; kt < 2; ++kt) {
+      uint32_t a3[4];
+      a3[0] = pack_bf16(h2[2 * kt][0], h2[2 * kt][1]);
+      a3[1] = pack_bf16(h2[2 * kt][2], h2[2 * kt][3]);
+      a3[2] = pack_bf16(h2[2 * kt + 1][0], h2[2 * kt + 1][1]);
+      a3[3] = pack_bf16(h2[2 * kt + 1][2], h2[2 * kt + 1][3]);
+      const __nv_bfloat16* wr = sW3 + g * 32 + kt * 16;
+      const uint32_t b0 = *reinterpret_cast<const uint32_t*>(wr + 2 * tg);
+      const uint32_t b1 = *reinterpret_cast<const uint32_t*>(wr + 2 * tg + 8);
+      mma_bf16(z, a3, b0, b1);
+    }
+    if (tg < 2) {
+      Lg[warp][g][2 * tg] = z[0] + sb[64 + 2 * tg];
+      Lg[warp][g][2 * tg + 1] = z[1] + sb[64 + 2 * tg + 1];
+      Lg[warp][g + 8][2 * tg] = z[2] + sb[64 + 2 * tg];
+      Lg[warp][g + 8][2 * tg + 1] = z[3] + sb[64 + 2 * tg + 1];
+    }
+    __syncwarp();
+    if (lane < 16) {
+      const long long wid = grp * 16 + lane;
+      if (wid < total) {
+        const bool flat = Fl[warp][lane];
+        int best = 0;
+        for (int o = 1; o < 4; ++o)
+          if (Lg[warp][lane][o] > Lg[warp][lane][best]) best = o;
+        tau_w[wid] = flat ? 4 : (signed char)(best + 1);
+        if (logits)
+          for (int o = 0; o < 4; ++o) logits[wid * 4 + o] = flat ? 0.f : Lg[warp][lane][o];
+      }
+    }
+    __syncwarp();
+  }
+}
+
+// Point tau = minimum over the windows (both directions) that cover it.
+__global__ void k_tau_gather(CtxDev c, const signed char* __restrict__ tau_w, signed char* tau) {
+  const long long per = c.qstride;
+  const long long total = (long long)c.instances * per;
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x) {
+    const long long inst = t / per;
+    const long long q = t % per;
+    const int p = find_patch(c, q);
+    const PatchDev P = c.patches[p];
+    const long long lq = q - P.qoff;
+    if (lq >= (long long)P.n1 * P.n2) continue;
+    const int i = (int)(lq % P.n1), j = (int)(lq / P.n1);
+    const signed char* tw = tau_w + inst * c.nwin;
+    int best = 4;
+    // x-windows of row j: regular windows k with 16k <= i < 16k+16, plus the right-aligned one
+    {
+      const int nw = P.wpl_x, base = P.wx_off + j * nw;
+      const int k = i / 16;
+      if (k < nw && 16 * k + 16 <= P.n1) best = min(best, (int)tw[base + k]);
+      if (P.n1 % 16 != 0 && i >= P.n1 - 16) best = min(best, (int)tw[base + nw - 1]);
+    }
+    {
+      const int nw = P.wpl_y, base = P.wy_off + i * nw;
+      const int k = j / 16;
+      if (k < nw && 16 * k + 16 <= P.n2) best = min(best, (int)tw[base + k]);
+      if (P.n2 % 16 != 0 && j >= P.n2 - 16) best = min(best, (int)tw[base + nw - 1]);
+    }
+    tau[t] = (signed char)best;
+  }
+}
+
+// ============================================================ indicator
+// Coefficient-decay estimate per window (thread per window): FC continuation
+// of the raw proxy window (n = 16 + 26 = 42), |Y_k| for k = 1..20 by direct
+// DFT, band RMS of modes 2..5 and 11..20 floored at 1e-6 of the peak.
+template <typename T>
+__global__ void k_indicator(CtxDev c, const T* __restrict__ e, signed char* tau_w, T* s_out) {
+  const PlanDev pl = c.plans[c.ind_plan];
+  const int n = pl.n;  // 42
+  const long long total = (long long)c.instances * c.nwin;
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x) {
+    const long long inst = t / c.nwin;
+    const int4 wd = c.windows[t % c.nwin];
+    Cx<T> y[48];
+    T amax = 0;
+    for (int k = 0; k < 16; ++k) {
+      const T v = proxy_at<T>(c, e, inst, wd, k);
+      y[k] = {v, T(0)};
+      amax = fmax(amax, fabs(v));
+    }
+    // continuation with the (5, 26) table, single real line
+    for (int q = 0; q < pl.C; ++q) {
+      double s = 0.0;
+      const double* tr = c.tab64 + pl.tab_off + q * 5;
+      const double* tl = c.tab64 + pl.tab_off + (pl.C - 1 - q) * 5;
+      if (sizeof(T) == 8) {
+        for (int m = 0; m < 5; ++m) s = fma(tr[m], (double)y[16 - 5 + m].x, fma(tl[m], (double)y[4 - m].x, s));
+        y[16 + q] = {T(s), T(0)};
+      } else {
+        Dot2 a{0.f, 0.f};
+        const float* hi = c.tabhi + pl.tab_off;
+        const float* lo = c.tablo + pl.tab_off;
+        for (int m = 0; m < 5; ++m) {
+          a.add(hi[q * 5 + m], lo[q * 5 + m], (float)y[16 - 5 + m].x);
+          a.add(hi[(pl.C - 1 - q) * 5 + m], lo[(pl.C - 1 - q) * 5 + m], (float)y[4 - m].x);
+        }
+        y[16 + q] = {T(a.get()), T(0)};
+      }
+    }
+    T A[21];
+    T peak = 0;
+    for (int k = 1; k <= 20; ++k) {
+      T re = 0, im = 0;
+      for (int j = 0; j < n; ++j) {
+        const Cx<T> w = twid<T>(c, pl.tw_off + (j * k) % n);
+        re += y[j].x * w.x;
+        im += y[j].x * w.y;
+      }
+      A[k] = sqrt(re * re + im * im);
+      peak = fmax(peak, A[k]);
+    }
+    const T tiny = sizeof(T) == 8 ? T(1e-300) : T(1e-30);
+    const bool flat = peak <= T(1e-8) * fmax(amax, tiny) * T(n);
+    T s = T(INFINITY);
+    signed char tau = 4;
+    if (!flat) {
+      const T fl = T(1e-6) * peak;
+      T lo = 0, hi = 0;
+      for (int k = 2; k <= 5; ++k) { const T a = fmax(A[k], fl); lo += a * a; }
+      for (int k = 11; k <= 20; ++k) { const T a = fmax(A[k], fl); hi += a * a; }
+      lo = sqrt(lo / T(4));
+      hi = sqrt(hi / T(10));
+      s = log(lo / hi) / log(T(15.5) / T(3.5));
+      tau = s < T(2.7) ? 1 : (s < T(4.4) ? 2 : 4);
+    }
+    tau_w[t] = tau;
+    if (s_out) s_out[t] = s;
+  }
+}
+
+// ============================================================ viscosity
+// (a) wave speed |u| + c per point
+template <typename T>
+__global__ void k_av_speed(CtxDev c, const T* __restrict__ e, T* S) {
+  const long long per = c.qstride, total = (long long)c.instances * per;
+  const T gm1 = T(c.gamma - 1.0), gam = T(c.gamma);
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x) {
+    const long long inst = t / per, q = t % per;
+    const PatchDev P = c.patches[find_patch(c, q)];
+    const long long np = (long long)P.n1 * P.n2, lq = q - P.qoff;
+    if (lq >= np) continue;
+    const T* es = e + inst * c.sstride + P.soff + lq;
+    const T rho = es[0], mx = es[np], my = es[2 * np], En = es[3 * np];
+    const T p = pressure<T>(rho, mx, my, En, gm1);
+    S[t] = sqrt(mx * mx + my * my) / rho + sqrt(gam * p / rho);
+  }
+}
+
+// (b) preliminary viscosity: c_mu h_max max_{3x3}(S) w(tau), zero on fringes
+template <typename T>
+__global__ void k_av_prelim(CtxDev c, const T* __restrict__ S, const signed char* __restrict__ tau, T cmu, T* M) {
+  const long long per = c.qstride, total = (long long)c.instances * per;
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x) {
+    const long long inst = t / per, q = t % per;
+    const PatchDev P = c.patches[find_patch(c, q)];
+    const long long np = (long long)P.n1 * P.n2, lq = q - P.qoff;
+    if (lq >= np) continue;
+    const int i = (int)(lq % P.n1), j = (int)(lq / P.n1);
+    const int tv = tau[t];
+    T w = tv == 1 ? T(1) : (tv == 2 ? T(0.5) : T(0));
+    if (c.fringe[q]) w = T(0);
+    T m = 0;
+    if (w != T(0)) {
+      const T* Sp = S + inst * per + P.qoff;
+      for (int dj = -1; dj <= 1; ++dj) {
+        const int jj = j + dj;
+        if (jj < 0 || jj >= P.n2) continue;
+        for (int di = -1; di <= 1; ++di) {
+          const int ii = i + di;
+          if (ii < 0 || ii >= P.n1) continue;
+          m = fmax(m, Sp[(long long)jj * P.n1 + ii]);
+        }
+      }
+    }
+    M[t] = cmu * T(P.hmax) * m * w;
+  }
+}
+
+// (c) box maximum of radius r along i (dir 0) or j (dir 1)
+template <typename T>
+__global__ void k_av_boxmax(CtxDev c, const T* __restrict__ in, T* out, int r, int dir) {
+  const long long per = c.qstride, total = (long long)c.instances * per;
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x) {
+    const long long inst = t / per, q = t % per;
+    const PatchDev P = c.patches[find_patch(c, q)];
+    const long long np = (long long)P.n1 * P.n2, lq = q - P.qoff;
+    if (lq >= np) continue;
+    const int i = (int)(lq % P.n1), j = (int)(lq / P.n1);
+    const T* ip = in + inst * per + P.qoff;
+    T m = ip[lq];
+    for (int k = -r; k <= r; ++k) {
+      const int ii = dir == 0 ? i + k : i, jj = dir == 0 ? j : j + k;
+      if (ii < 0 || ii >= P.n1 || jj < 0 || jj >= P.n2) continue;
+      m = fmax(m, ip[(long long)jj * P.n1 + ii]);
+    }
+    out[t] = m;
+  }
+}
+
+// (d) normalised bump average of radius r, b(x) = exp(1 - 1/(1 - x^2)), x = k/(r+1)
+template <typename T>
+__global__ void k_av_bump(CtxDev c, const T* __restrict__ in, T* out, const double* __restrict__ bw, int r, int dir) {
+  const long long per = c.qstride, total = (long long)c.instances * per;
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x) {
+    const long long inst = t / per, q = t % per;
+    const PatchDev P = c.patches[find_patch(c, q)];
+    const long long np = (long long)P.n1 * P.n2, lq = q - P.qoff;
+    if (lq >= np) continue;
+    const int i = (int)(lq % P.n1), j = (int)(lq / P.n1);
+    const T* ip = in + inst * per + P.qoff;
+    T num = 0, den = 0;
+    for (int k = -r; k <= r; ++k) {
+      const int ii = dir == 0 ? i + k : i, jj = dir == 0 ? j : j + k;
+      if (ii < 0 || ii >= P.n1 || jj < 0 || jj >= P.n2) continue;
+      const T b = T(bw[k + r]);
+      num += b * ip[(long long)jj * P.n1 + ii];
+      den += b;
+    }
+    out[t] = num / den;
+  }
+}
+
+// ============================================================ training
+constexpr int kActs = 148;  // per sample: x 16, h1 32, h2 32, dz1 32, dz2 32, dz3 4
+
+__device__ __forceinline__ float bfr(float v) { return __bfloat162float(__float2bfloat16_rn(v)); }
+
+// forward + backward of one sample per thread; weights rounded to bf16.
+__global__ void k_train_sample(const float* __restrict__ x, const signed char* __restrict__ lab, int B,
+                               const float* __restrict__ Wm, float* acts, float* loss_s) {
+  __shared__ float sW[1732];
+  for (int t = threadIdx.x; t < 1732; t += blockDim.x) {
+    const bool isb = (t >= 512 && t < 544) || (t >= 1568 && t < 1600) || t >= 1728;
+    sW[t] = isb ? Wm[t] : bfr(Wm[t]);
+  }
+  __syncthreads();
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= B) return;
+  const float* W1 = sW;
+  const float* b1 = sW + 512;
+  const float* W2 = sW + 544;
+  const float* b2 = sW + 1568;
+  const float* W3 = sW + 1600;
+  const float* b3 = sW + 1728;
+  float xv[16];
+  float mn = x[s * 16], mx = mn, sum = 0.f, amax = 0.f;
+  for (int k = 0; k < 16; ++k) {
+    xv[k] = x[s * 16 + k];
+    mn = fminf(mn, xv[k]);
+    mx = fmaxf(mx, xv[k]);
+    sum += xv[k];
+    amax = fmaxf(amax, fabsf(xv[k]));
+  }
+  const bool flat = (mx - mn) <= 1e-8f * amax;
+  const float mean = sum / 16.f, rng = flat ? 1.f : mx - mn;
+  for (int k = 0; k < 16; ++k) xv[k] = bfr(flat ? 0.f : (xv[k] - mean) / rng);
+  float h1[32], h2[32], z[4];
+  for (int o = 0; o < 32; ++o) {
+    float a = b1[o];
+    for (int k = 0; k < 16; ++k) a = fmaf(W1[o * 16 + k], xv[k], a);
+    h1[o] = a;  // pre-activation kept for the mask
+  }
+  for (int o = 0; o < 32; ++o) {
+    float a = b2[o];
+    for (int k = 0; k < 32; ++k) a = fmaf(W2[o * 32 + k], fmaxf(h1[k], 0.f), a);
+    h2[o] = a;
+  }
+  for (int o = 0; o < 4; ++o) {
+    float a = b3[o];
+    for (int k = 0; k < 32; ++k) a = fmaf(W3[o * 32 + k], fmaxf(h2[k], 0.f), a);
+    z[o] = a;
+  }
+  const float zm = fmaxf(fmaxf(z[0], z[1]), fmaxf(z[2], z[3]));
+  float ez[4], se = 0.f;
+  for (int o = 0; o < 4; ++o) {
+    ez[o] = expf(z[o] - zm);
+    se += ez[o];
+  }
+  const int y = lab[s] - 1;
+  loss_s[s] = -(z[y] - zm - logf(se));
+  float dz3[4];
+  for (int o = 0; o < 4; ++o) dz3[o] = (ez[o] / se - (o == y ? 1.f : 0.f)) / (float)B;
+  float dz2[32], dz1[32];
+  for (int k = 0; k < 32; ++k) {
+    float a = 0.f;
+    for (int o = 0; o < 4; ++o) a = fmaf(dz3[o], W3[o * 32 + k], a);
+    dz2[k] = h2[k] > 0.f ? a : 0.f;
+  }
+  for (int k = 0; k < 32; ++k) {
+    float a = 0.f;
+    for (int o = 0; o < 32; ++o) a = fmaf(dz2[o], W2[o * 32 + k], a);
+    dz1[k] = h1[k] > 0.f ? a : 0.f;
+  }
+  float* A = acts + (long long)s * kActs;
+  for (int k = 0; k < 16; ++k) A[k] = xv[k];
+  for (int k = 0; k < 32; ++k) {
+    A[16 + k] = fmaxf(h1[k], 0.f);
+    A[48 + k] = fmaxf(h2[k], 0.f);
+    A[80 + k] = dz1[k];
+    A[112 + k] = dz2[k];
+  }
+  for (int o = 0; o < 4; ++o) A[144 + o] = dz3[o];
+}
+
+// gradient of every parameter: fixed-order FP64 sum over the batch
+__global__ void k_train_grad(const float* __restrict__ acts, int B, float* grad) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 1732) return;
+  int dz, in;  // column of dz and of the input in the activation record (in < 0: bias)
+  if (t < 512) { dz = 80 + t / 16; in = t % 16; }
+  else if (t < 544) { dz = 80 + (t - 512); in = -1; }
+  else if (t < 1568) { dz = 112 + (t - 544) / 32; in = 16 + (t - 544) % 32; }
+  else if (t < 1600) { dz = 112 + (t - 1568); in = -1; }
+  else if (t < 1728) { dz = 144 + (t - 1600) / 32; in = 48 + (t - 1600) % 32; }
+  else { dz = 144 + (t - 1728); in = -1; }
+  double a = 0.0;
+  for (int s = 0; s < B; ++s) {
+    const float* A = acts + (long long)s * kActs;
+    a += (double)A[dz] * (in >= 0 ? (double)A[in] : 1.0);
+  }
+  grad[t] = (float)a;
+}
+
+__global__ void k_train_loss(const float* __restrict__ loss_s, int B, float* loss) {
+  __shared__ double red[256];
+  double a = 0.0;
+  for (int s = threadIdx.x; s < B; s += blockDim.x) a += loss_s[s];
+  red[threadIdx.x] = a;
+  __syncthreads();
+  for (int k = blockDim.x / 2; k > 0; k >>= 1) {
+    if (threadIdx.x < k) red[threadIdx.x] += red[threadIdx.x + k];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0 && loss) *loss = (float)(red[0] / B);
+}
+
+__global__ void k_adam(float* W, float* m, float* v, const float* __restrict__ g, float lr, float b1c, float b2c,
+                       __nv_bfloat16* Wb, float* bias, double* W64) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 1732) return;
+  const float gv = g[t];
+  const float mm = 0.9f * m[t] + 0.1f * gv;
+  const float vv = 0.999f * v[t] + 0.001f * gv * gv;
+  m[t] = mm;
+  v[t] = vv;
+  const float w = W[t] - lr * (mm / b1c) / (sqrtf(vv / b2c) + 1e-8f);
+  W[t] = w;
+  // refresh the inference copies
+  if (t < 512) Wb[t] = __float2bfloat16_rn(w);
+  else if (t < 544) bias[t - 512] = w;
+  else if (t < 1568) Wb[512 + t - 544] = __float2bfloat16_rn(w);
+  else if (t < 1600) bias[32 + t - 1568] = w;
+  else if (t < 1728) Wb[1536 + t - 1600] = __float2bfloat16_rn(w);
+  else bias[64 + t - 1728] = w;
+  W64[t] = (double)w;
+}
+
+}  // namespace fcs

@@ -1,0 +1,49 @@
+"""Shared helpers of the GPU parity tests (seeded inputs, context builders)."""
+import numpy as np
+
+from paper_2506_19370_gb300 import inputs as I
+
+LAYOUTS = ("vortex", "sod", "annulus")
+
+
+def layout(name):
+    """(instance, C policy) of a parity layout."""
+    if name == "vortex":
+        return I.vortex_instance(101), 0
+    if name == "sod":
+        return I.sod_instance(), 1
+    if name == "annulus":
+        p = I.annulus_patch(48, 40)
+        X, _ = p.coords()
+        e = I.conserved(1.4 + 0.0 * X, 2.0, 0.5, 1.0)
+        return I.Instance([p], [e], name="annulus"), 0
+    if name == "split":
+        # two overlapping Cartesian patches in y and two in x (4 patches, corners)
+        pts = [I.Patch(40, 36, (I.BC_WALL, I.BC_INTERNAL, I.BC_WALL, I.BC_INTERNAL), box=(0, 39 / 60, 0, 35 / 60)),
+               I.Patch(36, 36, (I.BC_INTERNAL, I.BC_WALL, I.BC_WALL, I.BC_INTERNAL), box=(29 / 60, 1, 0, 35 / 60)),
+               I.Patch(40, 36, (I.BC_WALL, I.BC_INTERNAL, I.BC_INTERNAL, I.BC_WALL), box=(0, 39 / 60, 25 / 60, 1)),
+               I.Patch(36, 36, (I.BC_INTERNAL, I.BC_WALL, I.BC_INTERNAL, I.BC_WALL), box=(29 / 60, 1, 25 / 60, 1))]
+        rng = np.random.default_rng(7)
+        return I.Instance(pts, [I.random_state(p, rng) for p in pts], name="split"), 0
+    raise KeyError(name)
+
+
+def random_fields(inst, seed):
+    rng = np.random.default_rng(seed)
+    out = []
+    for p in inst.patches:
+        X, Y = p.coords()
+        a, b, c = rng.uniform(1, 4, 3)
+        out.append(np.sin(a * X + 0.3) * np.cos(b * Y - c) + 0.2 * X * Y + 1.5)
+    return out
+
+
+def random_states(inst, seed):
+    rng = np.random.default_rng(seed)
+    return [I.random_state(p, rng) for p in inst.patches]
+
+
+def rel_err(a, b):
+    a = np.concatenate([np.ravel(x) for x in a])
+    b = np.concatenate([np.ravel(x) for x in b])
+    return float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
