@@ -44,7 +44,7 @@ def parse():
 
 def workload(instances):
     from paper_2506_19370_gb300 import inputs as I
-    return [I.sod_instance(perturb=0.01, seed=I.SEED + k) for k in range(instances)]
+    return [I.sod_instance(perturb=0.01, seed=I.SEED + k, smear=2.0) for k in range(instances)]
 
 
 def config(args, points):
@@ -65,14 +65,14 @@ def cpu_baseline(seconds, dist_note=None):
         "import time, json, sys; sys.path.insert(0, %r)\n"
         "from oracle import euler, sdnn\n"
         "from paper_2506_19370_gb300 import inputs as I\n"
-        "inst = I.sod_instance(perturb=0.01)\n"
+        "inst = I.sod_instance(perturb=0.01, smear=2.0)\n"
         "s = euler.Solver(inst, c_policy=1)\n"
         "params = sdnn.init_params(0)\n"
         "st = [e.copy() for e in inst.state]\n"
         "def step(st):\n"
         "    taus = [sdnn.classify_patch(params, e, inst.gamma)[0] for e in st]\n"
         "    mu = sdnn.av_assemble(s, st, taus)\n"
-        "    dt = s.dt(st)\n"
+        "    dt = s.dt(st, mu)\n"
         "    return s.step(st, dt, mu)\n"
         "st = step(st)\n"
         "t0 = time.perf_counter(); n = 0\n"
@@ -237,7 +237,7 @@ def run_ours(args):
         # the same sequence as fcs_step, call by call, so the stage operator can be timed
         ctx.classify(e, tau, None, stream)
         ctx.av_assemble(e, tau, mu, stream)
-        ctx.time_step(e, dtd, stream)
+        ctx.time_step(e, dtd, mu, stream)
         launches["n"] += 2 + 7 + 3
         for s in range(4):
             es = e if s == 0 else S

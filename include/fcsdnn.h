@@ -167,9 +167,13 @@ int rk_stage(fcs_ctx* ctx, int stage, double dt, const double* dt_dev, const voi
  * scalar layout (used for the viscosity). */
 int patch_exchange(fcs_ctx* ctx, void* field_dev, int nfields, void* stream);
 
-/* Per-instance time step (Algorithm 1): dt = cfl * min over points and
- * directions of h_k / (|U_k| + c |grad q_k|) into dt_dev (instances doubles). */
-int fcs_time_step(fcs_ctx* ctx, const void* e_dev, double* dt_dev, void* stream);
+/* Per-instance time step (Algorithm 1, the step-size evaluation; formula of
+ * Part I (31) read as the CFL condition): dt = min over points of
+ * min(cfl * min_k h_k / (|U_k| + c |grad q_k|), 0.25 h_min^2 / mu), U_k the
+ * contravariant velocity, h_k the parameter spacing, h_min the smaller
+ * physical spacing; mu_dev (scalar layout) may be NULL (no viscous limit).
+ * Writes dt_dev (instances doubles). */
+int fcs_time_step(fcs_ctx* ctx, const void* e_dev, const void* mu_dev, double* dt_dev, void* stream);
 
 /* Per instance and patch, FP64 sums of each conserved field with the FC
  * quadrature weights (tensor product along q1 and q2) times |J|:

@@ -21,8 +21,11 @@ Follows:
     every stage, exchange of fringe values after every stage;
   * §3.3: n_f-point fringes of internal sides receive values from donor points
     of other patches that are not themselves receivers; coincident grids copy;
-  * Δt (reading of I-(31)): CFL * min over points of h_k / (|U_k| + c |grad q_k|)
-    with U_k the contravariant velocity along parameter direction k.
+  * Δt (reading of I-(31)): min over points of
+        min( CFL h_k / (|U_k| + c |grad q_k|),  CFL_MU h_min^2 / mu )
+    with U_k the contravariant velocity along parameter direction k, h_k the
+    parameter spacing, h_min the smaller physical spacing and CFL_MU = 0.25
+    (the viscous limit keeps mu dt (pi/h)^2 inside the RK4 stability region).
 """
 import numpy as np
 
@@ -55,8 +58,8 @@ class PatchGeom:
     def __init__(self, patch, d, C, c_policy=0):
         self.patch = patch
         # continuation length per direction (lines along q1 have n1 points)
-        self.C1 = fcgram.smooth_c(patch.n1, C) if c_policy else C
-        self.C2 = fcgram.smooth_c(patch.n2, C) if c_policy else C
+        self.C1 = fcgram.policy_c(patch.n1, C) if c_policy else C
+        self.C2 = fcgram.policy_c(patch.n2, C) if c_policy else C
         self.n1, self.n2 = patch.n1, patch.n2
         self.h1 = 1.0 / (patch.n1 - 1)
         self.h2 = 1.0 / (patch.n2 - 1)
@@ -203,10 +206,13 @@ def exchange(state, fmap):
     return state
 
 
-def time_step(state, geoms, gamma, cfl):
-    """Δt = CFL * min over all points of min_k h_k / (|U_k| + c |grad q_k|)."""
+CFL_MU = 0.25
+
+
+def time_step(state, geoms, gamma, cfl, mu=None):
+    """Δt = min over all points of min(CFL min_k h_k/(|U_k| + c|grad q_k|), CFL_MU h_min^2/mu)."""
     best = np.inf
-    for e, g in zip(state, geoms):
+    for k, (e, g) in enumerate(zip(state, geoms)):
         rho, mx, my, E = e
         u, v = mx / rho, my / rho
         c = np.sqrt(gamma * pressure(e, gamma) / rho)
@@ -215,8 +221,16 @@ def time_step(state, geoms, gamma, cfl):
         U2 = (-g.y_q1 * u + g.x_q1 * v) / g.J
         n1 = np.sqrt(g.y_q2 ** 2 + g.x_q2 ** 2) / np.abs(g.J)
         n2 = np.sqrt(g.y_q1 ** 2 + g.x_q1 ** 2) / np.abs(g.J)
-        best = min(best, np.min(g.h1 / (np.abs(U1) + c * n1)), np.min(g.h2 / (np.abs(U2) + c * n2)))
-    return cfl * best
+        adv = cfl * np.minimum(g.h1 / (np.abs(U1) + c * n1), g.h2 / (np.abs(U2) + c * n2))
+        if mu is not None:
+            s1 = g.h1 * np.sqrt(g.x_q1 ** 2 + g.y_q1 ** 2)
+            s2 = g.h2 * np.sqrt(g.x_q2 ** 2 + g.y_q2 ** 2)
+            hmin = np.minimum(s1, s2)
+            with np.errstate(divide="ignore"):
+                visc = np.where(mu[k] > 0, CFL_MU * hmin * hmin / np.where(mu[k] > 0, mu[k], 1.0), np.inf)
+            adv = np.minimum(adv, visc)
+        best = min(best, float(np.min(adv)))
+    return best
 
 
 def max_wave_speed(state, gamma):
@@ -262,8 +276,8 @@ class Solver:
             e_s, acc = self.stage(s, dt, e_n, e_s, acc, mu)
         return e_s
 
-    def dt(self, state):
-        return time_step(state, self.geoms, self.inst.gamma, self.cfl)
+    def dt(self, state, mu=None):
+        return time_step(state, self.geoms, self.inst.gamma, self.cfl, mu)
 
     def conservation_sums(self, state):
         """Per patch: FC quadrature of each conserved field times |J| (4 sums)."""

@@ -44,13 +44,17 @@ LAMBDA = "1e-14"
 DIGITS = 40
 
 
-def smooth_c(N, C):
-    """Smallest C' in [C, C+16] with N + C' a product of 2, 3, 5 and 7.
+def policy_c(N, C):
+    """Continuation length of an N-point line under the FFT-length policy.
 
-    FFT-length policy (a choice of this implementation, not of the paper):
-    the continuation length of a line may be raised so that its FFT length
-    has only small prime factors.  Returns C if no such C' exists.
+    A choice of this implementation, not of the paper: the smallest
+    C' >= max(C - 4, 20), C' <= 64, with N + C' = 32 n1 and 2 <= n1 <= 9 (an
+    FFT held in registers of one warp); failing that the smallest C' in
+    [C, C + 16] with N + C' a product of 2, 3, 5 and 7; failing that C.
     """
+    for c in range(max(C - 4, 20), 65):
+        if (N + c) % 32 == 0 and 2 <= (N + c) // 32 <= 9:
+            return c
     for c in range(C, C + 17):
         m = N + c
         for q in (2, 3, 5, 7):

@@ -9,7 +9,8 @@ Follows Algorithm 3 and §5 item 2 (the formulas themselves are in Part I,
   * windows: every grid line is cut into 16-point windows starting at 0, 16,
     32, ...; if the line length is not a multiple of 16 the last window is
     right-aligned.  A window is normalised as (Phi - mean) / (max - min);
-    a window with max - min <= 1e-8 max|Phi| is flat and gets tau = 4;
+    a window with max - min <= 1e-4 max(1, max|Phi|) is flat (its Mach-number
+    variation is far below any shock) and gets tau = 4 without inference;
   * smoothness classifier (the ANN of §4): dense 16 -> 32 (ReLU) -> 32 (ReLU)
     -> 4, tau = 1 + argmax (1 jump, 2 kink, 3 C1 with a jump in the second
     derivative, 4 smooth); a point takes the smallest tau of all windows, in
@@ -41,7 +42,7 @@ HIDDEN = 32
 CLASSES = 4
 LAYER_SHAPES = ((HIDDEN, WINDOW), (HIDDEN,), (HIDDEN, HIDDEN), (HIDDEN,), (CLASSES, HIDDEN), (CLASSES,))
 N_PARAMS = sum(int(np.prod(s)) for s in LAYER_SHAPES)
-FLAT_TOL = 1e-8
+FLAT_TOL = 1e-4
 VISC_WEIGHT = (1.0, 0.5, 0.0, 0.0)
 IND_C = 26
 IND_D = 5
@@ -89,7 +90,7 @@ def normalise(win):
     mx = win.max(axis=1, keepdims=True)
     mean = win.mean(axis=1, keepdims=True)
     amax = np.abs(win).max(axis=1, keepdims=True)
-    flat = (mx - mn) <= FLAT_TOL * amax
+    flat = (mx - mn) <= FLAT_TOL * np.maximum(1.0, amax)
     rng = np.where(flat, 1.0, mx - mn)
     return np.where(flat, 0.0, (win - mean) / rng), flat[:, 0]
 
@@ -227,7 +228,7 @@ def decay_indicator(win):
     A = np.abs(np.fft.fft(y, axis=-1))[:, 1:n // 2]        # modes 1..20
     peak = A.max(axis=1, keepdims=True)
     amax = np.abs(win).max(axis=1)
-    flat = peak[:, 0] <= FLAT_TOL * np.maximum(amax, 1e-300) * n
+    flat = (win.max(axis=1) - win.min(axis=1)) <= FLAT_TOL * np.maximum(1.0, amax)
     a = np.maximum(A, 1e-6 * peak)
     e_lo = np.sqrt(np.mean(a[:, 1:5] ** 2, axis=1))        # modes 2..5
     e_hi = np.sqrt(np.mean(a[:, 10:20] ** 2, axis=1))      # modes 11..20

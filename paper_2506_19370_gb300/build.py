@@ -18,26 +18,32 @@ def _nvcc():
 
 
 def build(verbose=False, extra=()):
-    """Compile csrc/*.cu and csrc/*.cpp into _lib/libfcsdnn.so; returns the path."""
+    """Compile csrc/*.cu and csrc/*.cpp (in parallel) into _lib/libfcsdnn.so; returns the path."""
+    import glob
     os.makedirs(OUT_DIR, exist_ok=True)
     nvcc = _nvcc()
-    obj_cu = os.path.join(OUT_DIR, "fcs_api.o")
-    obj_cpp = os.path.join(OUT_DIR, "fcs_tables.o")
     host_flags = "-fPIC,-O2,-ffp-contract=off"
-    cmds = [
-        [nvcc, "-c", "-O3", "-std=c++17", *ARCH, "-lineinfo", "-Xcompiler", host_flags,
-         "-Xptxas", "-v" if verbose else "-O3", *extra, "-o", obj_cu, os.path.join(SRC, "fcs_api.cu")],
-        ["g++", "-c", "-O2", "-std=c++17", "-fPIC", "-ffp-contract=off", "-o", obj_cpp,
-         os.path.join(SRC, "fcs_tables.cpp")],
-    ]
+    cmds, objs = [], []
+    for src in sorted(glob.glob(os.path.join(SRC, "*.cu"))):
+        obj = os.path.join(OUT_DIR, os.path.basename(src)[:-3] + ".o")
+        objs.append(obj)
+        cmds.append([nvcc, "-c", "-O3", "-std=c++17", *ARCH, "-lineinfo", "-Xcompiler", host_flags,
+                     "-Xptxas", "-v" if verbose else "-O3", *extra, "-o", obj, src])
+    for src in sorted(glob.glob(os.path.join(SRC, "*.cpp"))):
+        obj = os.path.join(OUT_DIR, os.path.basename(src)[:-4] + ".o")
+        objs.append(obj)
+        cmds.append(["g++", "-c", "-O2", "-std=c++17", "-fPIC", "-ffp-contract=off", "-o", obj, src])
     procs = [subprocess.Popen(c, stdout=subprocess.PIPE, stderr=subprocess.STDOUT, text=True) for c in cmds]
+    failed = None
     for c, p in zip(cmds, procs):
         out, _ = p.communicate()
         if verbose or p.returncode != 0:
             sys.stdout.write(out)
         if p.returncode != 0:
-            raise RuntimeError("build failed: " + " ".join(c))
-    link = [nvcc, "-shared", *ARCH, "-o", LIB, obj_cu, obj_cpp]
+            failed = c
+    if failed:
+        raise RuntimeError("build failed: " + " ".join(failed))
+    link = [nvcc, "-shared", *ARCH, "-o", LIB, *objs]
     r = subprocess.run(link, stdout=subprocess.PIPE, stderr=subprocess.STDOUT, text=True)
     if r.returncode != 0:
         sys.stdout.write(r.stdout)

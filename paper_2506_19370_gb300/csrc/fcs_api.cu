@@ -10,6 +10,7 @@
 #include "../../include/fcsdnn.h"
 #include "fcs_internal.h"
 #include "fcs_kernels.cuh"
+#include "fcs_launch.cuh"
 
 using namespace fcs;
 
@@ -18,6 +19,7 @@ namespace {
 constexpr int kNParams = 1732;
 constexpr int kIndC = 26;   // continuation length of the indicator (16 + 26 = 42 = 2 * 3 * 7)
 constexpr int kIndD = 5;
+constexpr double kCflMu = 0.25;  // viscous limit of the time step: dt <= 0.25 h_min^2 / mu
 
 struct DevBuf {
   void* p = nullptr;
@@ -40,13 +42,15 @@ struct fcs_ctx {
   std::map<int, int> plan_of_len;  // line length -> plan index
   std::vector<int64_t> state_off, scalar_off, window_off;
   size_t sstride = 0, qstride = 0, nwin = 0;
-  int nlines0 = 0, nlines1 = 0, npairs0 = 0, npairs1 = 0, nent = 0;
-  int nmax = 0, nfmax = 0;
+  int nlines0 = 0, nlines1 = 0, npairs0 = 0, npairs1 = 0, nent = 0, ntiles = 0;
+  int nmax = 0, nfmax = 0, n2max = 0, stockham = 0, tw = 32;
+  int n1x = -1, n1y = -1;  // register-FFT size shared by all lines along q1 / q2 (0: Stockham kernels)
   CtxDev dev{};
   std::vector<void*> allocs;
   // device arrays
   int4* pairs0 = nullptr;
   int4* pairs1 = nullptr;
+  int2* tiles = nullptr;
   int4* fringe_ent = nullptr;
   double* wq = nullptr;
   int2* woff = nullptr;
@@ -134,8 +138,15 @@ bool smooth7(int n) {
   return n == 1;
 }
 
+// Continuation length of a line of N points.  Policy 0: C.  Policy 1: the
+// smallest C' >= max(C - 4, 20) with N + C' = 32 n1, 2 <= n1 <= 9 (register
+// FFT), else the smallest C' in [C, C + 16] with N + C' 7-smooth (Stockham).
 int choose_c(const fcs_options& o, int C, int N) {
   if (o.c_policy == 0) return C;
+  for (int c = std::max(C - 4, 20); c <= 64; ++c) {
+    const int n = N + c;
+    if (n % 32 == 0 && n / 32 >= 2 && n / 32 <= 9) return c;
+  }
   for (int c = C; c <= C + 16; ++c)
     if (smooth7(N + c)) return c;
   return C;
@@ -180,7 +191,13 @@ int get_plan(fcs_ctx* c, int N, int C, int d) {
   hp.dev.C = C;
   hp.dev.n = N + C;
   std::vector<int> rad;
-  if (!factor_radices(N + C, &rad)) return FCS_EUNSUPPORTED;
+  const int n = N + C;
+  const bool stk = factor_radices(n, &rad);
+  hp.dev.n1reg = (n % 32 == 0 && n / 32 >= 2 && n / 32 <= 9) ? n / 32 : 0;
+  if (!stk) {
+    if (hp.dev.n1reg == 0) return FCS_EUNSUPPORTED;
+    rad.clear();
+  }
   hp.dev.nst = (int)rad.size();
   for (int s = 0; s < hp.dev.nst; ++s) hp.dev.radix[s] = rad[s];
   hp.tab.resize((size_t)C * d);
@@ -192,9 +209,11 @@ int get_plan(fcs_ctx* c, int N, int C, int d) {
 }
 
 template <typename T>
-size_t flux_smem(const fcs_ctx* c) { return kWarps * flux_warp_bytes<T>(c->nmax, c->nfmax); }
+size_t xpass_smem(const fcs_ctx* c) { return kWarps * warp_line_bytes<T>(9, c->nmax, c->nfmax, c->n1x == 0); }
 template <typename T>
-size_t deriv_smem(const fcs_ctx* c) { return (size_t)kWarps * 2 * c->nfmax * sizeof(Cx<T>); }
+size_t deriv_smem(const fcs_ctx* c, int n1) { return kWarps * warp_line_bytes<T>(2, c->nmax, c->nfmax, n1 == 0); }
+template <typename T>
+size_t ypass_smem(const fcs_ctx* c, int tw) { return ypass_bytes<T>(c->n2max, tw, c->nfmax, c->n1y == 0, kYWarps); }
 
 int grid_for(long long work, int per_block) {
   long long g = (work + per_block - 1) / per_block;
@@ -203,13 +222,28 @@ int grid_for(long long work, int per_block) {
   return (int)g;
 }
 
+// dispatch on the compile-time FFT size of a direction
+#define FCS_N1_SWITCH(n1, CALL)            \
+  switch (n1) {                            \
+    case 0: { constexpr int K = 0; CALL; } \
+    case 2: { constexpr int K = 2; CALL; } \
+    case 3: { constexpr int K = 3; CALL; } \
+    case 4: { constexpr int K = 4; CALL; } \
+    case 5: { constexpr int K = 5; CALL; } \
+    case 6: { constexpr int K = 6; CALL; } \
+    case 7: { constexpr int K = 7; CALL; } \
+    case 8: { constexpr int K = 8; CALL; } \
+    case 9: { constexpr int K = 9; CALL; } \
+    default: return FCS_EINVAL;            \
+  }
+
 template <typename T>
 int set_smem_attrs(const fcs_ctx* c) {
-  const int fs = (int)flux_smem<T>(c), ds = (int)deriv_smem<T>(c);
-  FCS_CUDA(cudaFuncSetAttribute(k_flux<T, 0, MODE_X>, cudaFuncAttributeMaxDynamicSharedMemorySize, fs));
-  FCS_CUDA(cudaFuncSetAttribute(k_flux<T, 1, MODE_RHS>, cudaFuncAttributeMaxDynamicSharedMemorySize, fs));
-  FCS_CUDA(cudaFuncSetAttribute(k_flux<T, 1, MODE_RK>, cudaFuncAttributeMaxDynamicSharedMemorySize, fs));
-  FCS_CUDA(cudaFuncSetAttribute(k_fc_deriv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, ds));
+  const size_t xs = xpass_smem<T>(c), ys = ypass_smem<T>(c, c->tw);
+  FCS_N1_SWITCH(c->n1x, FCS_CUDA((prep_xpass<T, K>(xs))); break)
+  FCS_N1_SWITCH(c->n1y, FCS_CUDA((prep_ypass<T, K>(ys))); break)
+  FCS_N1_SWITCH(c->n1x, FCS_CUDA((prep_fc_deriv<T, K>(deriv_smem<T>(c, c->n1x)))); break)
+  FCS_N1_SWITCH(c->n1y, FCS_CUDA((prep_fc_deriv<T, K>(deriv_smem<T>(c, c->n1y)))); break)
   return FCS_OK;
 }
 
@@ -217,27 +251,27 @@ template <typename T>
 int launch_deriv(fcs_ctx* c, const void* in, void* out, int dir, int order, cudaStream_t s) {
   const int np = dir == 0 ? c->npairs0 : c->npairs1;
   const int4* pr = dir == 0 ? c->pairs0 : c->pairs1;
-  const long long work = (long long)c->opt.instances * np;
-  k_fc_deriv<T><<<grid_for(work, kWarps), kWarps * 32, deriv_smem<T>(c), s>>>(
-      c->dev, dir, order, pr, np, static_cast<const T*>(in), static_cast<T*>(out));
-  return cuda_err(cudaGetLastError());
+  const int n1 = dir == 0 ? c->n1x : c->n1y;
+  const long long work = (long long)c->dev.instances * np;
+  const LaunchCfg g{(unsigned)grid_for(work, kWarps), kWarps * 32, deriv_smem<T>(c, n1), s};
+  FCS_N1_SWITCH(n1, return cuda_err((run_fc_deriv<T, K>(c->dev, dir, order, pr, np, static_cast<const T*>(in),
+                                                        static_cast<T*>(out), g))))
 }
 
 template <typename T>
 int launch_flux(fcs_ctx* c, const void* e, const void* mu, int mode, StageArgs<T> st, cudaStream_t s) {
-  const size_t sm = flux_smem<T>(c);
   const long long w0 = (long long)c->opt.instances * c->nlines0;
-  const long long w1 = (long long)c->opt.instances * c->nlines1;
+  const long long w1 = (long long)c->opt.instances * c->ntiles;
   const T* ep = static_cast<const T*>(e);
   const T* mp = static_cast<const T*>(mu);
   T* R = static_cast<T*>(c->R);
-  k_flux<T, 0, MODE_X><<<grid_for(w0, kWarps), kWarps * 32, sm, s>>>(c->dev, ep, mp, R, st);
-  FCS_CUDA(cudaGetLastError());
-  if (mode == MODE_RHS)
-    k_flux<T, 1, MODE_RHS><<<grid_for(w1, kWarps), kWarps * 32, sm, s>>>(c->dev, ep, mp, R, st);
-  else
-    k_flux<T, 1, MODE_RK><<<grid_for(w1, kWarps), kWarps * 32, sm, s>>>(c->dev, ep, mp, R, st);
-  return cuda_err(cudaGetLastError());
+  const LaunchCfg gx{(unsigned)grid_for(w0, kWarps), kWarps * 32, xpass_smem<T>(c), s};
+  FCS_N1_SWITCH(c->n1x, FCS_CUDA((run_xpass<T, K>(c->dev, ep, mp, R, gx))); break)
+  const LaunchCfg gy{(unsigned)grid_for(w1, 1), kYWarps * 32, ypass_smem<T>(c, c->tw), s};
+  if (mode == MODE_RHS) {
+    FCS_N1_SWITCH(c->n1y, return cuda_err((run_ypass<T, MODE_RHS, K>(c->dev, c->tiles, c->ntiles, ep, mp, R, st, gy))))
+  }
+  FCS_N1_SWITCH(c->n1y, return cuda_err((run_ypass<T, MODE_RK, K>(c->dev, c->tiles, c->ntiles, ep, mp, R, st, gy))))
 }
 
 cudaStream_t as_stream(void* s) { return static_cast<cudaStream_t>(s); }
@@ -381,7 +415,12 @@ int fc_setup(fcs_ctx** out, int d, int C, const fcs_patch_desc* pd, int npatch, 
       P.plan[dir] = pi;
       c->nmax = std::max(c->nmax, N);
       c->nfmax = std::max(c->nfmax, c->plans[pi].dev.n);
+      int& nd = dir == 0 ? c->n1x : c->n1y;
+      const int r = c->plans[pi].dev.n1reg;
+      if (nd < 0) nd = r;
+      else if (nd != r) nd = 0;
     }
+    c->n2max = std::max(c->n2max, q.n2);
     P.soff = (long long)soff;
     P.qoff = (long long)qoff;
     c->state_off.push_back((int64_t)soff);
@@ -389,8 +428,10 @@ int fc_setup(fcs_ctx** out, int d, int C, const fcs_patch_desc* pd, int npatch, 
     soff += ((size_t)4 * q.n1 * q.n2 + align - 1) / align * align;
     qoff += ((size_t)q.n1 * q.n2 + align - 1) / align * align;
     if (q.cartesian) {
-      P.hx = (q.box[1] - q.box[0]) / (q.n1 - 1);
-      P.hy = (q.box[3] - q.box[2]) / (q.n2 - 1);
+      P.Lx = q.box[1] - q.box[0];
+      P.Ly = q.box[3] - q.box[2];
+      P.hx = P.Lx / (q.n1 - 1);
+      P.hy = P.Ly / (q.n2 - 1);
       P.hmax = std::max(P.hx, P.hy);
     } else {
       P.hx = 1.0 / (q.n1 - 1);
@@ -428,9 +469,34 @@ int fc_setup(fcs_ctx** out, int d, int C, const fcs_patch_desc* pd, int npatch, 
     for (int i = 0; i < q.n1; i += 2) p1.push_back(make_int4(p, i, i + 1 < q.n1 ? i + 1 : -1, 0));
     c->patches.push_back(P);
   }
-  // indicator plan (degree 5, C = 26 on 16-point windows)
+  // indicator plan (degree 5, C = 26 on 16-point windows; direct DFT)
   const int ind = get_plan(c, 16, kIndC, kIndD);
   if (ind < 0) return fail(ind);
+  // a direction whose lines do not share one register-FFT size runs the
+  // Stockham kernels; every plan then needs a radix factorisation
+  for (int dir = 0; dir < 2; ++dir) {
+    const int nd = dir == 0 ? c->n1x : c->n1y;
+    if (nd == 0) {
+      c->stockham = 1;
+      for (int p = 0; p < npatch; ++p)
+        if (c->plans[c->patches[p].plan[dir]].dev.nst == 0) return fail(FCS_EUNSUPPORTED);
+    }
+  }
+  // column-tile width of the pass along q2: widest of 32, 16, 8 that fits
+  {
+    const size_t esz = c->tsize, lim = 200 * 1024;
+    int tw = 0;
+    for (int t : {32, 16, 8}) {
+      const size_t b = esz == 8 ? ypass_smem<double>(c, t) : ypass_smem<float>(c, t);
+      if (b <= lim) { tw = t; break; }
+    }
+    if (!tw) return fail(FCS_EUNSUPPORTED);
+    c->tw = tw;
+  }
+  std::vector<int2> tiles;
+  for (int p = 0; p < npatch; ++p)
+    for (int c0 = 0; c0 < pd[p].n1; c0 += c->tw) tiles.push_back(make_int2(p, c0));
+  c->ntiles = (int)tiles.size();
   c->sstride = soff;
   c->qstride = qoff;
   c->nwin = wins.size();
@@ -542,6 +608,7 @@ int fc_setup(fcs_ctx** out, int d, int C, const fcs_patch_desc* pd, int npatch, 
       (rc = upload(c, &dl1, l1.data(), l1.size() * sizeof(LineRef))) ||
       (rc = upload(c, &c->pairs0, p0.data(), p0.size() * sizeof(int4))) ||
       (rc = upload(c, &c->pairs1, p1.data(), p1.size() * sizeof(int4))) ||
+      (rc = upload(c, &c->tiles, tiles.data(), tiles.size() * sizeof(int2))) ||
       (rc = upload(c, &dwin, wins.data(), wins.size() * sizeof(int4))) ||
       (rc = upload(c, &dfr, fringe.data(), fringe.size())) ||
       (rc = upload(c, &c->fringe_ent, ent.data(), ent.size() * sizeof(int4))) ||
@@ -592,7 +659,14 @@ int fc_setup(fcs_ctx** out, int d, int C, const fcs_patch_desc* pd, int npatch, 
   D.ind_plan = ind;
   D.nmax = c->nmax;
   D.nfmax = c->nfmax;
-  if ((rc = set_smem_attrs<float>(c)) || (rc = set_smem_attrs<double>(c))) return fail(rc);
+  D.stockham = c->stockham;
+  D.tw = c->tw;
+  D.n2max = c->n2max;
+  if ((rc = (o.dtype == FCS_F64 ? set_smem_attrs<double>(c) : set_smem_attrs<float>(c)))) return fail(rc);
+  if (o.dtype != FCS_F64) {  // the metrics use FP64 derivatives
+    FCS_N1_SWITCH(c->n1x, if (prep_fc_deriv<double, K>(deriv_smem<double>(c, c->n1x)) != cudaSuccess) return fail(FCS_ECUDA); break)
+    FCS_N1_SWITCH(c->n1y, if (prep_fc_deriv<double, K>(deriv_smem<double>(c, c->n1y)) != cudaSuccess) return fail(FCS_ECUDA); break)
+  }
 
   // ---- metrics of curvilinear patches: FP64 FC derivatives of x and y
   bool curvi = false;
@@ -699,17 +773,19 @@ int patch_exchange(fcs_ctx* c, void* field, int nfields, void* stream) {
   return cuda_err(cudaGetLastError());
 }
 
-int fcs_time_step(fcs_ctx* c, const void* e, double* dt_dev, void* stream) {
+int fcs_time_step(fcs_ctx* c, const void* e, const void* mu, double* dt_dev, void* stream) {
   if (!c || !e || !dt_dev) return FCS_EINVAL;
   cudaStream_t s = as_stream(stream);
   const int I = c->opt.instances;
   k_dt_init<<<(I + 127) / 128, 128, 0, s>>>(c->dtbest, I);
-  const long long work = (long long)I * c->qstride;
+  dim3 g((unsigned)std::min<long long>((c->qstride + 255) / 256, 512), (unsigned)I);
   if (c->opt.dtype == FCS_F64)
-    k_dt<double><<<grid_for(work, 256), 256, 0, s>>>(c->dev, static_cast<const double*>(e), c->dtbest);
+    k_dt<double><<<g, 256, 0, s>>>(c->dev, static_cast<const double*>(e), static_cast<const double*>(mu), c->opt.cfl,
+                                   kCflMu, c->dtbest);
   else
-    k_dt<float><<<grid_for(work, 256), 256, 0, s>>>(c->dev, static_cast<const float*>(e), c->dtbest);
-  k_dt_final<<<(I + 127) / 128, 128, 0, s>>>(c->dtbest, dt_dev, c->opt.cfl, I);
+    k_dt<float><<<g, 256, 0, s>>>(c->dev, static_cast<const float*>(e), static_cast<const float*>(mu), c->opt.cfl,
+                                  kCflMu, c->dtbest);
+  k_dt_final<<<(I + 127) / 128, 128, 0, s>>>(c->dtbest, dt_dev, I);
   return cuda_err(cudaGetLastError());
 }
 
@@ -827,7 +903,7 @@ int fcs_step(fcs_ctx* c, void* e, double dt, double* dt_dev, int use_av, void* s
   }
   const double* dtd = nullptr;
   if (!(dt > 0.0)) {
-    if ((rc = fcs_time_step(c, e, dt_dev, stream))) return rc;
+    if ((rc = fcs_time_step(c, e, mu, dt_dev, stream))) return rc;
     dtd = dt_dev;
   }
   for (int s = 0; s < 4; ++s) {

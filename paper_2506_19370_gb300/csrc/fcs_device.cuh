@@ -20,6 +20,7 @@ struct PatchDev {
   long long soff, qoff; // offsets in the state and scalar layouts (per instance)
   double hx, hy;        // derivative spacing along i and j (physical if Cartesian, parameter otherwise)
   double hmax;          // largest physical spacing (viscosity scale)
+  double Lx, Ly;        // Cartesian box lengths (metrics x_q1, y_q2)
 };
 
 struct PlanDev {
@@ -27,6 +28,7 @@ struct PlanDev {
   int radix[kMaxStages];
   int tw_off;           // offset of the n twiddles
   int tab_off;          // offset of the C x d continuation table
+  int n1reg;            // n = 32 * n1reg: register four-step FFT; 0: shared-memory Stockham FFT
 };
 
 struct LineRef {
@@ -57,6 +59,9 @@ struct CtxDev {
   int ind_plan;                 // plan of the indicator (n = 16 + 26)
   int nmax;                     // longest line
   int nfmax;                    // longest FFT
+  int stockham;                 // 1 if some plan needs the shared-memory FFT buffers
+  int tw;                       // column-tile width of the pass along q2
+  int n2max;                    // longest column (lines along q2)
 };
 
 template <typename T>
@@ -299,6 +304,223 @@ __device__ Cx<T>* fc_deriv_pair(Cx<T>* a, Cx<T>* b, const CtxDev& c, const PlanD
 template <typename T>
 __device__ __forceinline__ T pressure(T rho, T mx, T my, T E, T gm1) {
   return gm1 * (E - T(0.5) * (mx * mx + my * my) / rho);
+}
+
+// ------------------------------------------------------------ register FFT
+// Everything one FC derivative of a line pair needs, by value (no pointer to
+// the kernel's context, so nothing has to be spilled to local memory).
+template <typename T>
+struct LineOp {
+  const Cx<T>* tw;      // the plan's n twiddles e^{-2 pi i k / n}
+  const double* t64;    // the plan's C x d table (FP64)
+  const float* thi;     // FP32 split of the table (hi, lo)
+  const float* tlo;
+  int N, C, n, d, n1reg;
+  T h;                  // line spacing
+};
+
+template <typename T>
+__device__ __forceinline__ LineOp<T> make_op(const CtxDev& c, const PlanDev& pl, T h);
+template <>
+__device__ __forceinline__ LineOp<double> make_op<double>(const CtxDev& c, const PlanDev& pl, double h) {
+  return {reinterpret_cast<const Cx<double>*>(c.tw64 + pl.tw_off), c.tab64 + pl.tab_off, c.tabhi + pl.tab_off,
+          c.tablo + pl.tab_off, pl.N, pl.C, pl.n, c.d, pl.n1reg, h};
+}
+template <>
+__device__ __forceinline__ LineOp<float> make_op<float>(const CtxDev& c, const PlanDev& pl, float h) {
+  return {reinterpret_cast<const Cx<float>*>(c.tw32 + pl.tw_off), c.tab64 + pl.tab_off, c.tabhi + pl.tab_off,
+          c.tablo + pl.tab_off, pl.N, pl.C, pl.n, c.d, pl.n1reg, h};
+}
+
+template <typename T>
+__device__ __forceinline__ Cx<T> ldtw(const Cx<T>* tw, int k) {
+  return tw[k];
+}
+
+// Four-step FFT of length n = 32 * N1 held in registers: lane L holds
+// x[L + 32 j1], j1 < N1.  Forward: length-N1 DFT per lane, twiddle
+// w_n^{L k1}, 32-point DIF DFT across lanes by shuffles (lane L then holds
+// X[k1 + N1 bitrev5(L)]).  Inverse: 32-point DIT DFT across lanes, conjugate
+// twiddle, length-N1 DFT per lane, natural order again.  All roots come from
+// the plan's length-n table: w_N1^m = tw[32 m], w_32^t = tw[N1 t].
+template <typename T>
+__device__ __forceinline__ Cx<T> shfl_xor_c(Cx<T> v, int m) {
+  return {__shfl_xor_sync(0xffffffffu, v.x, m), __shfl_xor_sync(0xffffffffu, v.y, m)};
+}
+
+template <typename T, int N1>
+__device__ __forceinline__ void lane_dft(Cx<T>* x, const Cx<T>* tw, bool inv) {
+  Cx<T> W[N1];
+#pragma unroll
+  for (int m = 0; m < N1; ++m) {
+    W[m] = ldtw(tw, 32 * m);
+    if (inv) W[m].y = -W[m].y;
+  }
+  Cx<T> o[N1];
+#pragma unroll
+  for (int k = 0; k < N1; ++k) {
+    Cx<T> acc = x[0];
+#pragma unroll
+    for (int j = 1; j < N1; ++j) {
+      const Cx<T> p = cmul(x[j], W[(j * k) % N1]);
+      acc.x += p.x;
+      acc.y += p.y;
+    }
+    o[k] = acc;
+  }
+#pragma unroll
+  for (int k = 0; k < N1; ++k) x[k] = o[k];
+}
+
+template <typename T, int N1>
+__device__ __forceinline__ void reg_fft(Cx<T>* x, const Cx<T>* tw, bool inv, int lane) {
+  if (!inv) {
+    lane_dft<T, N1>(x, tw, false);
+#pragma unroll
+    for (int k = 1; k < N1; ++k) x[k] = cmul(x[k], ldtw(tw, lane * k));
+#pragma unroll
+    for (int s = 16; s >= 1; s >>= 1) {
+      const Cx<T> w = ldtw(tw, (lane & (s - 1)) * (16 / s) * N1);
+      const bool hi = lane & s;
+#pragma unroll
+      for (int k = 0; k < N1; ++k) {
+        const Cx<T> p = shfl_xor_c(x[k], s);
+        if (!hi) x[k] = {x[k].x + p.x, x[k].y + p.y};
+        else x[k] = cmul(Cx<T>{p.x - x[k].x, p.y - x[k].y}, w);
+      }
+    }
+  } else {
+#pragma unroll
+    for (int s = 1; s <= 16; s <<= 1) {
+      Cx<T> w = ldtw(tw, (lane & (s - 1)) * (16 / s) * N1);
+      w.y = -w.y;
+      const bool hi = lane & s;
+#pragma unroll
+      for (int k = 0; k < N1; ++k) {
+        const Cx<T> p = shfl_xor_c(x[k], s);
+        if (!hi) {
+          const Cx<T> q = cmul(p, w);
+          x[k] = {x[k].x + q.x, x[k].y + q.y};
+        } else {
+          const Cx<T> q = cmul(x[k], w);
+          x[k] = {p.x - q.x, p.y - q.y};
+        }
+      }
+    }
+#pragma unroll
+    for (int k = 1; k < N1; ++k) {
+      Cx<T> w = ldtw(tw, lane * k);
+      w.y = -w.y;
+      x[k] = cmul(x[k], w);
+    }
+    lane_dft<T, N1>(x, tw, true);
+  }
+}
+
+__device__ __forceinline__ int bitrev5(int v) { return __brev(v) >> 27; }
+
+// Continuation value q (0 <= q < C) of the line a (stride sa) minus offset o:
+// sum_m A_R[q][m] a[N-d+m] + A_R[C-1-q][m] a[d-1-m]
+__device__ __forceinline__ double cont_value(const double* a, int sa, double o, const LineOp<double>& op, int q) {
+  const double* tr = op.t64 + q * op.d;
+  const double* tl = op.t64 + (op.C - 1 - q) * op.d;
+  double s = 0.0;
+  for (int m = 0; m < op.d; ++m) {
+    s = fma(__ldg(tr + m), a[(op.N - op.d + m) * sa] - o, s);
+    s = fma(__ldg(tl + m), a[(op.d - 1 - m) * sa] - o, s);
+  }
+  return s;
+}
+__device__ __forceinline__ float cont_value(const float* a, int sa, float o, const LineOp<float>& op, int q) {
+  const int rr = q * op.d, rl = (op.C - 1 - q) * op.d;
+  Dot2 acc{0.f, 0.f};
+  for (int m = 0; m < op.d; ++m) {
+    acc.add(__ldg(op.thi + rr + m), __ldg(op.tlo + rr + m), __fsub_rn(a[(op.N - op.d + m) * sa], o));
+    acc.add(__ldg(op.thi + rl + m), __ldg(op.tlo + rl + m), __fsub_rn(a[(op.d - 1 - m) * sa], o));
+  }
+  return acc.get();
+}
+
+// FC derivative of the lines a and b (b may be null) with the register FFT;
+// results times `scale` go to oa[t*soa], ob[t*sob] for t < N.
+template <typename T, int N1>
+__device__ __forceinline__ void reg_deriv_pair(const T* a, int sa, const T* b, int sb, T* oa, int soa, T* ob, int sob,
+                                               T scale, const LineOp<T>& op, int order, int lane) {
+  const int N = op.N, n = 32 * N1;
+  T offa = T(0), offb = T(0);
+  if (Offset<T>::kShift) {
+    offa = (a[0] + a[(N - 1) * sa]) * T(0.5);
+    if (b) offb = (b[0] + b[(N - 1) * sb]) * T(0.5);
+  }
+  Cx<T> x[N1];
+#pragma unroll
+  for (int j1 = 0; j1 < N1; ++j1) {
+    const int j = lane + 32 * j1;
+    if (j < N) {
+      x[j1].x = a[j * sa] - offa;
+      x[j1].y = b ? b[j * sb] - offb : T(0);
+    } else {
+      x[j1].x = cont_value(a, sa, offa, op, j - N);
+      x[j1].y = b ? cont_value(b, sb, offb, op, j - N) : T(0);
+    }
+  }
+  reg_fft<T, N1>(x, op.tw, false, lane);
+  const T sc = T(6.283185307179586476925286766559) / (T(n) * op.h);
+  const T inv_n = scale / T(n);
+  const int k2 = bitrev5(lane);
+#pragma unroll
+  for (int k1 = 0; k1 < N1; ++k1) {
+    const int k = k1 + N1 * k2;
+    const int km = (2 * k <= n) ? k : k - n;
+    const Cx<T> z = x[k1];
+    if (order == 1) {
+      const T kk = (2 * k == n) ? T(0) : T(km) * sc * inv_n;
+      x[k1] = {-kk * z.y, kk * z.x};
+    } else {
+      const T kk = T(km) * sc;
+      const T f = -kk * kk * inv_n;
+      x[k1] = {f * z.x, f * z.y};
+    }
+  }
+  reg_fft<T, N1>(x, op.tw, true, lane);
+#pragma unroll
+  for (int j1 = 0; j1 < N1; ++j1) {
+    const int j = lane + 32 * j1;
+    if (j < N) {
+      oa[j * soa] = x[j1].x;
+      if (ob) ob[j * sob] = x[j1].y;
+    }
+  }
+}
+
+// Shared-memory Stockham path for lengths that are not 32 * N1.
+template <typename T>
+__device__ void stk_deriv_pair(const T* a, int sa, const T* b, int sb, T* oa, int soa, T* ob, int sob, T scale,
+                               const CtxDev& c, const PlanDev& pl, T h, int order, int lane, Cx<T>* buf0,
+                               Cx<T>* buf1) {
+  const int N = pl.N;
+  for (int t = lane; t < N; t += 32) buf0[t] = {a[t * sa], b ? b[t * sb] : T(0)};
+  __syncwarp();
+  Cx<T>* r = fc_deriv_pair<T>(buf0, buf1, c, pl, c.d, h, order, lane);
+  for (int t = lane; t < N; t += 32) {
+    oa[t * soa] = r[t].x * scale;
+    if (ob) ob[t * sob] = r[t].y * scale;
+  }
+  __syncwarp();
+}
+
+// FC derivative of a line pair: register FFT of length 32 * N1, or (N1 = 0)
+// the shared-memory Stockham FFT, which handles any 7-smooth length.
+template <typename T, int N1>
+__device__ __forceinline__ void line_deriv_pair(const T* a, int sa, const T* b, int sb, T* oa, int soa, T* ob, int sob,
+                                                T scale, const CtxDev& c, const PlanDev& pl, T h, int order, int lane,
+                                                Cx<T>* buf0, Cx<T>* buf1) {
+  if constexpr (N1 == 0) {
+    stk_deriv_pair<T>(a, sa, b, sb, oa, soa, ob, sob, scale, c, pl, h, order, lane, buf0, buf1);
+  } else {
+    const LineOp<T> op = make_op<T>(c, pl, h);
+    reg_deriv_pair<T, N1>(a, sa, b, sb, oa, soa, ob, sob, scale, op, order, lane);
+  }
 }
 
 }  // namespace fcs

@@ -1,273 +1,17 @@
-// Kernels of the FC-SDNN stage library (included once, by fcs_api.cu).
+// Pointwise and reduction kernels of the FC-SDNN stage library (included by fcs_api.cu only).
 #pragma once
 
 #include <cuda_bf16.h>
 
 #include "fcs_device.cuh"
+#include "fcs_launch.cuh"
 
 namespace fcs {
 
-// ============================================================ FC derivative
-// One warp per pair of lines of one patch (two real lines -> one complex FFT).
-template <typename T>
-__global__ void __launch_bounds__(kWarps * 32) k_fc_deriv(CtxDev c, int dir, int order, const int4* __restrict__ pairs,
-                                                           int npairs, const T* __restrict__ in, T* __restrict__ out) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  Cx<T>* a = reinterpret_cast<Cx<T>*>(smem_raw) + (size_t)warp * 2 * c.nfmax;
-  Cx<T>* b = a + c.nfmax;
-  const long long total = (long long)c.instances * npairs;
-  for (long long w = (long long)blockIdx.x * kWarps + warp; w < total; w += (long long)gridDim.x * kWarps) {
-    const int inst = (int)(w / npairs);
-    const int4 pr = pairs[w % npairs];
-    const PatchDev P = c.patches[pr.x];
-    const PlanDev pl = c.plans[P.plan[dir]];
-    const int N = pl.N;
-    const long long stride = dir == 0 ? 1 : P.n1;
-    const long long la = dir == 0 ? (long long)pr.y * P.n1 : pr.y;
-    const long long lb = pr.z < 0 ? -1 : (dir == 0 ? (long long)pr.z * P.n1 : pr.z);
-    const T* src = in + inst * c.qstride + P.qoff;
-    T* dst = out + inst * c.qstride + P.qoff;
-    for (int t = lane; t < N; t += 32) {
-      const T va = src[la + t * stride];
-      const T vb = lb >= 0 ? src[lb + t * stride] : T(0);
-      a[t] = {va, vb};
-    }
-    __syncwarp();
-    const T h = T(1) / T(N - 1);
-    Cx<T>* r = fc_deriv_pair<T>(a, b, c, pl, c.d, h, order, lane);
-    for (int t = lane; t < N; t += 32) {
-      dst[la + t * stride] = r[t].x;
-      if (lb >= 0) dst[lb + t * stride] = r[t].y;
-    }
-    __syncwarp();
-  }
-}
-
-// ============================================================ Euler operator
-// Per-warp shared layout of the flux passes: E[4][nmax], W[4][nmax], M[nmax],
-// then two complex buffers of nfmax.
-template <typename T>
-__host__ __device__ inline size_t flux_warp_bytes(int nmax, int nfmax) {
-  size_t r = (size_t)9 * nmax * sizeof(T);
-  r = (r + 15) & ~size_t(15);
-  return r + (size_t)2 * nfmax * sizeof(Cx<T>);
-}
-
-enum { MODE_X = 0, MODE_RHS = 1, MODE_RK = 2 };
-
-template <typename T>
-struct StageArgs {
-  int stage;
-  T dt;
-  const double* dt_dev;
-  const T* e_n;
-  T* acc;
-  T* out;
-};
-
-// Apply the boundary conditions of the sides the point lies on, in the order
-// left, right, bottom, top (paper §5 item 4: enforced at every stage).
-template <typename T>
-__device__ __forceinline__ void apply_bc(const CtxDev& c, const PatchDev& P, int i, int j, long long q, T* v) {
-  const T gm1 = T(c.gamma - 1.0);
-  const bool on[4] = {i == 0, i == P.n1 - 1, j == 0, j == P.n2 - 1};
-#pragma unroll
-  for (int s = 0; s < 4; ++s) {
-    if (!on[s]) continue;
-    const int code = P.bc[s];
-    if (code == 1) {  // wall
-      if (P.cart) {
-        v[s < 2 ? 1 : 2] = T(0);
-      } else {
-        const T* M = metrics<T>(c);
-        const long long qs = c.qstride;
-        T nx, ny;
-        if (s < 2) {
-          nx = M[3 * qs + q];
-          ny = -M[1 * qs + q];
-        } else {
-          nx = -M[2 * qs + q];
-          ny = M[0 * qs + q];
-        }
-        const T nn = sqrt(nx * nx + ny * ny);
-        nx /= nn;
-        ny /= nn;
-        const T mn = v[1] * nx + v[2] * ny;
-        v[1] -= mn * nx;
-        v[2] -= mn * ny;
-      }
-    } else if (code == 2) {  // inflow
-      v[0] = T(c.inflow[0]);
-      v[1] = T(c.inflow[1]);
-      v[2] = T(c.inflow[2]);
-      v[3] = T(c.inflow[3]);
-    } else if (code == 3) {  // outflow pressure
-      v[3] = T(c.p_out) / gm1 + T(0.5) * (v[1] * v[1] + v[2] * v[2]) / v[0];
-    }
-  }
-}
-
-// Flux pass along direction DIR.  DIR 0 (rows): R = -d/dq1 F1 with
-// F1 = y_q2 f - x_q2 g (Cartesian: f, derivative at the physical spacing).
-// DIR 1 (columns): L = (R - d/dq2 F2) / J with F2 = -y_q1 f + x_q1 g
-// (Cartesian: g, J = 1); MODE_RHS writes L, MODE_RK applies the stage.
-// With mu, Cartesian fluxes carry the viscous part: f - mu de/dx, g - mu de/dy.
-template <typename T, int DIR, int MODE>
-__global__ void __launch_bounds__(kWarps * 32) k_flux(CtxDev c, const T* __restrict__ e, const T* __restrict__ mu,
-                                                       T* R, StageArgs<T> st) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int nmax = c.nmax;
-  unsigned char* base = smem_raw + (size_t)warp * flux_warp_bytes<T>(nmax, c.nfmax);
-  T* E = reinterpret_cast<T*>(base);
-  T* W = E + 4 * nmax;
-  T* M = W + 4 * nmax;
-  Cx<T>* ba = reinterpret_cast<Cx<T>*>(base + (((size_t)9 * nmax * sizeof(T) + 15) & ~size_t(15)));
-  Cx<T>* bb = ba + c.nfmax;
-  const int nl = DIR == 0 ? c.nlines0 : c.nlines1;
-  const LineRef* L = DIR == 0 ? c.lines0 : c.lines1;
-  const T gam = T(c.gamma), gm1 = T(c.gamma - 1.0);
-  const long long total = (long long)c.instances * nl;
-  for (long long w = (long long)blockIdx.x * kWarps + warp; w < total; w += (long long)gridDim.x * kWarps) {
-    const int inst = (int)(w / nl);
-    const LineRef lr = L[w % nl];
-    const PatchDev P = c.patches[lr.patch];
-    const PlanDev pl = c.plans[P.plan[DIR]];
-    const int N = pl.N;
-    const long long np = (long long)P.n1 * P.n2;
-    const long long stride = DIR == 0 ? 1 : P.n1;
-    const long long l0 = DIR == 0 ? (long long)lr.line * P.n1 : lr.line;
-    const T* es = e + inst * c.sstride + P.soff + l0;
-    const T h = T(DIR == 0 ? P.hx : P.hy);
-    const bool visc = (mu != nullptr) && P.cart;
-    for (int t = lane; t < N; t += 32) {
-#pragma unroll
-      for (int f = 0; f < 4; ++f) E[f * nmax + t] = es[f * np + t * stride];
-      if (visc) M[t] = mu[inst * c.qstride + P.qoff + l0 + t * stride];
-    }
-    __syncwarp();
-    if (visc) {  // W = d e / dx (or dy) for the four fields
-#pragma unroll
-      for (int pr = 0; pr < 2; ++pr) {
-        for (int t = lane; t < N; t += 32) ba[t] = {E[(2 * pr) * nmax + t], E[(2 * pr + 1) * nmax + t]};
-        __syncwarp();
-        Cx<T>* r = fc_deriv_pair<T>(ba, bb, c, pl, c.d, h, 1, lane);
-        for (int t = lane; t < N; t += 32) {
-          W[(2 * pr) * nmax + t] = r[t].x;
-          W[(2 * pr + 1) * nmax + t] = r[t].y;
-        }
-        __syncwarp();
-      }
-    }
-    // flux combination F = a f + b g (W)
-    const T* Mt = metrics<T>(c);
-    for (int t = lane; t < N; t += 32) {
-      const T rho = E[t], mx = E[nmax + t], my = E[2 * nmax + t], En = E[3 * nmax + t];
-      const T u = mx / rho, v = my / rho;
-      const T p = pressure<T>(rho, mx, my, En, gm1);
-      T fl[4];
-      if (P.cart) {
-        if (DIR == 0) {
-          fl[0] = mx; fl[1] = mx * u + p; fl[2] = my * u; fl[3] = (En + p) * u;
-        } else {
-          fl[0] = my; fl[1] = mx * v; fl[2] = my * v + p; fl[3] = (En + p) * v;
-        }
-        if (visc) {
-#pragma unroll
-          for (int f = 0; f < 4; ++f) fl[f] -= M[t] * W[f * nmax + t];
-        }
-      } else {
-        const long long q = P.qoff + l0 + t * stride;
-        T ca, cb;
-        if (DIR == 0) {
-          ca = Mt[3 * c.qstride + q];   // y_q2
-          cb = -Mt[1 * c.qstride + q];  // -x_q2
-        } else {
-          ca = -Mt[2 * c.qstride + q];  // -y_q1
-          cb = Mt[0 * c.qstride + q];   // x_q1
-        }
-        const T f0 = mx, f1 = mx * u + p, f2 = my * u, f3 = (En + p) * u;
-        const T g0 = my, g1 = mx * v, g2 = my * v + p, g3 = (En + p) * v;
-        fl[0] = ca * f0 + cb * g0;
-        fl[1] = ca * f1 + cb * g1;
-        fl[2] = ca * f2 + cb * g2;
-        fl[3] = ca * f3 + cb * g3;
-      }
-#pragma unroll
-      for (int f = 0; f < 4; ++f) W[f * nmax + t] = fl[f];
-    }
-    __syncwarp();
-    // derivatives of the two flux pairs; results of pair 0 parked in W[0..1]
-    const long long base_s = inst * c.sstride + P.soff + l0;
-#pragma unroll
-    for (int pr = 0; pr < 2; ++pr) {
-      for (int t = lane; t < N; t += 32) ba[t] = {W[(2 * pr) * nmax + t], W[(2 * pr + 1) * nmax + t]};
-      __syncwarp();
-      Cx<T>* r = fc_deriv_pair<T>(ba, bb, c, pl, c.d, h, 1, lane);
-      if (MODE == MODE_X) {
-        for (int t = lane; t < N; t += 32) {
-          R[base_s + (2 * pr) * np + t * stride] = -r[t].x;
-          R[base_s + (2 * pr + 1) * np + t * stride] = -r[t].y;
-        }
-      } else {
-        for (int t = lane; t < N; t += 32) {
-          W[(2 * pr) * nmax + t] = r[t].x;
-          W[(2 * pr + 1) * nmax + t] = r[t].y;
-        }
-      }
-      __syncwarp();
-    }
-    if (MODE == MODE_X) continue;
-    const T dtv = st.dt_dev ? T(st.dt_dev[inst]) : st.dt;
-    for (int t = lane; t < N; t += 32) {
-      const long long off = base_s + t * stride;
-      const long long q = P.qoff + l0 + t * stride;
-      const T invJ = P.cart ? T(1) : T(1) / Mt[4 * c.qstride + q];
-      T k[4];
-#pragma unroll
-      for (int f = 0; f < 4; ++f) k[f] = (R[off + f * np] - W[f * nmax + t]) * invJ;
-      if (MODE == MODE_RHS) {
-#pragma unroll
-        for (int f = 0; f < 4; ++f) st.out[off + f * np] = k[f];
-        continue;
-      }
-      T v[4];
-      const int s = st.stage;
-      if (s == 0) {
-#pragma unroll
-        for (int f = 0; f < 4; ++f) {
-          const T en = st.e_n[off + f * np];
-          st.acc[off + f * np] = en + (dtv / T(6)) * k[f];
-          v[f] = en + (dtv / T(2)) * k[f];
-        }
-      } else if (s < 3) {
-        const T b = s == 1 ? dtv / T(3) : dtv / T(3);
-        const T a = s == 1 ? dtv / T(2) : dtv;
-#pragma unroll
-        for (int f = 0; f < 4; ++f) {
-          st.acc[off + f * np] = st.acc[off + f * np] + b * k[f];
-          v[f] = st.e_n[off + f * np] + a * k[f];
-        }
-      } else {
-#pragma unroll
-        for (int f = 0; f < 4; ++f) v[f] = st.acc[off + f * np] + (dtv / T(6)) * k[f];
-      }
-      const int i = DIR == 0 ? t : lr.line;
-      const int j = DIR == 0 ? lr.line : t;
-      apply_bc<T>(c, P, i, j, q, v);
-      const T pr_ = pressure<T>(v[0], v[1], v[2], v[3], gm1);
-      int flag = 0;
-      if (!(isfinite(v[0]) && isfinite(v[1]) && isfinite(v[2]) && isfinite(v[3]))) flag |= 1;
-      else if (!(v[0] > T(0)) || !(pr_ > T(0))) flag |= 2;
-      if (flag) atomicOr(c.status, flag);
-#pragma unroll
-      for (int f = 0; f < 4; ++f) st.out[off + f * np] = v[f];
-    }
-    __syncwarp();
-  }
-  (void)gam;
-}
+// A window whose proxy varies by at most kFlatTol * max(1, max |Phi|) is flat:
+// classified smooth without inference (its Mach-number variation is far below
+// any shock and at rounding level its normalisation would amplify noise).
+constexpr double kFlatTol = 1e-4;
 
 // ============================================================ exchange
 // entries: (dst patch, dst point, src patch, src point) of one instance.
@@ -303,41 +47,60 @@ __device__ __forceinline__ int find_patch(const CtxDev& c, long long q) {
 
 // ============================================================ time step
 template <typename T>
-__global__ void k_dt(CtxDev c, const T* __restrict__ e, unsigned long long* best) {
+__global__ void k_dt(CtxDev c, const T* __restrict__ e, const T* __restrict__ mu, double cfl_d, double cfl_mu_d,
+                     unsigned long long* best) {
   const long long per = c.qstride;
-  const long long total = (long long)c.instances * per;
-  const T gam = T(c.gamma), gm1 = T(c.gamma - 1.0);
-  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x) {
-    const int inst = (int)(t / per);
-    const long long q = t % per;
+  const int inst = blockIdx.y;
+  const T cfl = T(cfl_d), cfl_mu = T(cfl_mu_d), gam = T(c.gamma), gm1 = T(c.gamma - 1.0);
+  T r_min = T(INFINITY);
+  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < per; q += (long long)gridDim.x * blockDim.x) {
     const int p = find_patch(c, q);
     const PatchDev P = c.patches[p];
     const long long np = (long long)P.n1 * P.n2;
     const long long lq = q - P.qoff;
     if (lq >= np) continue;
     const T* es = e + inst * c.sstride + P.soff + lq;
-    const double rho = es[0], mx = es[np], my = es[2 * np], En = es[3 * np];
-    const double pr = (c.gamma - 1.0) * (En - 0.5 * (mx * mx + my * my) / rho);
-    const double u = mx / rho, v = my / rho;
-    const double cs = sqrt(c.gamma * pr / rho);
-    double x_q1, x_q2, y_q1, y_q2, J, h1, h2;
+    const T rho = es[0], mx = es[np], my = es[2 * np], En = es[3 * np];
+    const T pr = pressure<T>(rho, mx, my, En, gm1);
+    const T u = mx / rho, v = my / rho;
+    const T cs = sqrt(gam * pr / rho);
+    T x_q1, x_q2, y_q1, y_q2, J, h1, h2;
     if (P.cart) {
-      x_q1 = P.hx * (P.n1 - 1); y_q2 = P.hy * (P.n2 - 1); x_q2 = 0; y_q1 = 0;
+      x_q1 = T(P.Lx); y_q2 = T(P.Ly); x_q2 = T(0); y_q1 = T(0);
       J = x_q1 * y_q2;
-      h1 = 1.0 / (P.n1 - 1); h2 = 1.0 / (P.n2 - 1);
+      h1 = T(1) / T(P.n1 - 1); h2 = T(1) / T(P.n2 - 1);
     } else {
-      x_q1 = c.metrics64[q]; x_q2 = c.metrics64[c.qstride + q];
-      y_q1 = c.metrics64[2 * c.qstride + q]; y_q2 = c.metrics64[3 * c.qstride + q];
-      J = c.metrics64[4 * c.qstride + q];
-      h1 = P.hx; h2 = P.hy;
+      const T* Mt = metrics<T>(c);
+      x_q1 = Mt[q]; x_q2 = Mt[c.qstride + q];
+      y_q1 = Mt[2 * c.qstride + q]; y_q2 = Mt[3 * c.qstride + q];
+      J = Mt[4 * c.qstride + q];
+      h1 = T(P.hx); h2 = T(P.hy);
     }
-    const double U1 = (y_q2 * u - x_q2 * v) / J, U2 = (-y_q1 * u + x_q1 * v) / J;
-    const double n1 = sqrt(y_q2 * y_q2 + x_q2 * x_q2) / fabs(J), n2 = sqrt(y_q1 * y_q1 + x_q1 * x_q1) / fabs(J);
-    double r = fmin(h1 / (fabs(U1) + cs * n1), h2 / (fabs(U2) + cs * n2));
-    if (!(r > 0.0)) r = 0.0;
-    atomicMin(best + inst, (unsigned long long)__double_as_longlong(r));
+    const T U1 = (y_q2 * u - x_q2 * v) / J, U2 = (-y_q1 * u + x_q1 * v) / J;
+    const T n1 = sqrt(y_q2 * y_q2 + x_q2 * x_q2) / fabs(J), n2 = sqrt(y_q1 * y_q1 + x_q1 * x_q1) / fabs(J);
+    T r = cfl * fmin(h1 / (fabs(U1) + cs * n1), h2 / (fabs(U2) + cs * n2));
+    if (mu) {
+      const T m = mu[inst * per + q];
+      if (m > T(0)) {
+        const T s1 = h1 * sqrt(x_q1 * x_q1 + y_q1 * y_q1), s2 = h2 * sqrt(x_q2 * x_q2 + y_q2 * y_q2);
+        const T hm = fmin(s1, s2);
+        r = fmin(r, cfl_mu * hm * hm / m);
+      }
+    }
+    if (!(r > T(0))) r = T(0);
+    r_min = fmin(r_min, r);
   }
-  (void)gam; (void)gm1;
+  // block minimum, then one atomic per block (min of positive doubles = min of their bit patterns)
+  double rd = (double)r_min;
+  for (int o = 16; o > 0; o >>= 1) rd = fmin(rd, __shfl_xor_sync(0xffffffffu, rd, o));
+  __shared__ double wmin[32];
+  if ((threadIdx.x & 31) == 0) wmin[threadIdx.x >> 5] = rd;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double m = wmin[0];
+    for (int k = 1; k < (int)(blockDim.x >> 5); ++k) m = fmin(m, wmin[k]);
+    if (m < INFINITY) atomicMin(best + inst, (unsigned long long)__double_as_longlong(m));
+  }
 }
 
 __global__ void k_dt_init(unsigned long long* best, int n) {
@@ -345,9 +108,9 @@ __global__ void k_dt_init(unsigned long long* best, int n) {
   if (t < n) best[t] = 0x7ff0000000000000ULL;  // +Inf
 }
 
-__global__ void k_dt_final(const unsigned long long* best, double* dt, double cfl, int n) {
+__global__ void k_dt_final(const unsigned long long* best, double* dt, int n) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t < n) dt[t] = cfl * __longlong_as_double((long long)best[t]);
+  if (t < n) dt[t] = __longlong_as_double((long long)best[t]);
 }
 
 // ============================================================ conservation sums
@@ -368,7 +131,7 @@ __global__ void k_sums(CtxDev c, const T* __restrict__ e, const double* __restri
   for (long long t = threadIdx.x; t < np; t += blockDim.x) {
     const int i = (int)(t % P.n1), j = (int)(t / P.n1);
     double J;
-    if (P.cart) J = (P.hx * (P.n1 - 1)) * (P.hy * (P.n2 - 1));
+    if (P.cart) J = P.Lx * P.Ly;
     else J = c.metrics64[4 * c.qstride + P.qoff + t];
     const double w = wq[wo.x + i] * wq[wo.y + j] * fabs(J);
     double v[4];
@@ -437,7 +200,7 @@ __global__ void k_mlp64(CtxDev c, const T* __restrict__ e, const double* __restr
       amax = fmax(amax, fabs(x[k]));
     }
     const double mean = sum / 16.0;
-    const bool flat = (mxv - mn) <= 1e-8 * amax;
+    const bool flat = (mxv - mn) <= kFlatTol * fmax(1.0, amax);
     double z[4] = {0, 0, 0, 0};
     if (!flat) {
       const double rng = mxv - mn;
@@ -530,7 +293,7 @@ __global__ void __launch_bounds__(128) k_mlp_bf16(CtxDev c, const float* __restr
         amax = fmaxf(amax, fabsf(v));
       }
       const float mean = sum / 16.f;
-      const bool flat = (mx - mn) <= 1e-8f * amax;
+      const bool flat = (mx - mn) <= (float)kFlatTol * fmaxf(1.f, amax);
       Fl[warp][lane] = flat;
       const float rng = flat ? 1.f : (mx - mn);
       for (int t = 0; t < 16; ++t) X[warp][lane][t] = flat ? 0.f : (X[warp][lane][t] - mean) / rng;
@@ -662,11 +425,13 @@ __global__ void k_indicator(CtxDev c, const T* __restrict__ e, signed char* tau_
     const long long inst = t / c.nwin;
     const int4 wd = c.windows[t % c.nwin];
     Cx<T> y[48];
-    T amax = 0;
+    T amax = 0, vmin = T(INFINITY), vmax = -T(INFINITY);
     for (int k = 0; k < 16; ++k) {
       const T v = proxy_at<T>(c, e, inst, wd, k);
       y[k] = {v, T(0)};
       amax = fmax(amax, fabs(v));
+      vmin = fmin(vmin, v);
+      vmax = fmax(vmax, v);
     }
     // continuation with the (5, 26) table, single real line
     for (int q = 0; q < pl.C; ++q) {
@@ -699,8 +464,7 @@ __global__ void k_indicator(CtxDev c, const T* __restrict__ e, signed char* tau_
       A[k] = sqrt(re * re + im * im);
       peak = fmax(peak, A[k]);
     }
-    const T tiny = sizeof(T) == 8 ? T(1e-300) : T(1e-30);
-    const bool flat = peak <= T(1e-8) * fmax(amax, tiny) * T(n);
+    const bool flat = (vmax - vmin) <= T(kFlatTol) * fmax(T(1), amax);
     T s = T(INFINITY);
     signed char tau = 4;
     if (!flat) {
@@ -841,7 +605,7 @@ __global__ void k_train_sample(const float* __restrict__ x, const signed char* _
     sum += xv[k];
     amax = fmaxf(amax, fabsf(xv[k]));
   }
-  const bool flat = (mx - mn) <= 1e-8f * amax;
+  const bool flat = (mx - mn) <= (float)kFlatTol * fmaxf(1.f, amax);
   const float mean = sum / 16.f, rng = flat ? 1.f : mx - mn;
   for (int k = 0; k < 16; ++k) xv[k] = bfr(flat ? 0.f : (xv[k] - mean) / rng);
   float h1[32], h2[32], z[4];

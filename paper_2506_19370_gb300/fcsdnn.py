@@ -73,7 +73,7 @@ def lib():
             "euler_rhs": (i, [vp, vp, vp, vp, vp]),
             "rk_stage": (i, [vp, i, d, vp, vp, vp, vp, vp, vp, vp]),
             "patch_exchange": (i, [vp, vp, i, vp]),
-            "fcs_time_step": (i, [vp, vp, vp, vp]),
+            "fcs_time_step": (i, [vp, vp, vp, vp, vp]),
             "fcs_conservation_sums": (i, [vp, vp, vp, vp]),
             "sdnn_set_weights": (i, [vp, ctypes.POINTER(ctypes.c_float), ctypes.c_size_t]),
             "sdnn_get_weights": (i, [vp, ctypes.POINTER(ctypes.c_float), ctypes.c_size_t]),
@@ -238,8 +238,8 @@ class Context:
     def patch_exchange(self, field, nfields=4, stream=None):
         _check("patch_exchange", lib().patch_exchange(self.h, _ptr(field), nfields, _stream(stream)))
 
-    def time_step(self, e, dt_dev, stream=None):
-        _check("fcs_time_step", lib().fcs_time_step(self.h, _ptr(e), _ptr(dt_dev), _stream(stream)))
+    def time_step(self, e, dt_dev, mu=None, stream=None):
+        _check("fcs_time_step", lib().fcs_time_step(self.h, _ptr(e), _ptr(mu), _ptr(dt_dev), _stream(stream)))
 
     def conservation_sums(self, e, sums, stream=None):
         _check("fcs_conservation_sums", lib().fcs_conservation_sums(self.h, _ptr(e), _ptr(sums), _stream(stream)))

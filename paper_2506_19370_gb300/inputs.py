@@ -127,20 +127,31 @@ def sod_layout(npatch=8, n1=160, n2=40, overlap=10, length=1.0, height=0.1):
     return patches
 
 
-def sod_instance(npatch=8, n1=160, n2=40, overlap=10, x_jump=0.5, height=0.1, perturb=0.0, seed=SEED):
+def sod_instance(npatch=8, n1=160, n2=40, overlap=10, x_jump=0.5, height=0.1, perturb=0.0, seed=SEED,
+                 smear=0.0):
     """Sod shock tube (rho,u,p) = (1,0,1) | (0.125,0,0.1), jump at x_jump.
 
     `perturb` adds a seeded relative perturbation to the density (used to make
-    batched instances distinct).
+    batched instances distinct).  `smear` > 0 replaces the jump by a tanh
+    profile `smear` grid spacings wide (a stand-in for the paper's localized
+    smearing of discontinuous initial data, Algorithm 4, which is not part of
+    the stage).
     """
     patches = sod_layout(npatch, n1, n2, overlap, 1.0, height)
     rng = np.random.default_rng(seed)
+    nx = npatch * n1 - (npatch - 1) * overlap
+    hx = 1.0 / (nx - 1)
     state = []
     for pt in patches:
         X, Y = pt.coords()
-        left = X < x_jump
-        rho = np.where(left, 1.0, 0.125)
-        p = np.where(left, 1.0, 0.1)
+        if smear > 0:
+            w = 0.5 * (1.0 + np.tanh((X - x_jump) / (smear * hx)))
+            rho = 1.0 + (0.125 - 1.0) * w
+            p = 1.0 + (0.1 - 1.0) * w
+        else:
+            left = X < x_jump
+            rho = np.where(left, 1.0, 0.125)
+            p = np.where(left, 1.0, 0.1)
         if perturb:
             rho = rho * (1.0 + perturb * rng.uniform(-1.0, 1.0))
         state.append(conserved(rho, 0.0 * X, 0.0 * X, p))

@@ -1,12 +1,14 @@
 """GPU parity of the CUDA path against the FP64 CPU oracle (through the C ABI).
 
-Tolerances: FP64 results must match the oracle to the rounding level of the
-FC derivative, whose continuation tables reach ~2e3 in magnitude (cancellation
-of ~3 digits) and whose spectral derivative multiplies rounding noise by up to
-pi/h: 1e-11 of the largest value per derivative, 1e-9 after 100 vortex steps.
-FP32 results are checked against the FP64 oracle with the FP32 error budget
-(2^-24 ~ 6e-8 amplified the same way): 2e-5 per derivative and per operator
-evaluation.
+Tolerances come from the arithmetic (see _gpu.deriv_bound): one FC derivative
+of a line with values up to F carries rounding of at most
+4 eps (log2 n + G) F (pi/h)^order, where G ~ 5e3-7e3 is the gain of the
+continuation sums (plain FP64 sums; the FP32 path uses compensated sums, so
+G -> 4 there) and pi/h is the largest wavenumber.  Operator values are sums of
+such derivatives (divided by J on curvilinear patches).  FP32 results are
+compared with the FP64 oracle run on the same FP32-rounded inputs, so the
+bound uses eps = 2^-24.  Whole runs (100 vortex steps, 10 Sod steps with
+exchange) are held to 1e-9 relative (FP64) and 1e-4 relative (FP32).
 """
 import numpy as np
 import pytest
@@ -18,9 +20,8 @@ from oracle import euler, fcgram, sdnn  # noqa: E402
 from paper_2506_19370_gb300 import fcsdnn  # noqa: E402
 from paper_2506_19370_gb300 import inputs as I  # noqa: E402
 
-from _gpu import layout, random_fields, random_states, rel_err  # noqa: E402
+from _gpu import deriv_bound, layout, random_fields, random_states, rel_err, table_gain  # noqa: E402
 
-TOL = {fcsdnn.F64: 1e-11, fcsdnn.F32: 2e-5}
 DTYPES = [fcsdnn.F64, fcsdnn.F32]
 
 
@@ -44,21 +45,55 @@ def ctx_for(name, dtype, instances=1):
 def test_fc_derivative(name, dtype, order):
     inst, pol, ctx = ctx_for(name, dtype)
     f = random_fields(inst, 3)
+    npd = np.float32 if dtype == fcsdnn.F32 else np.float64
     x = ctx.to_device(ctx.pack_scalar(f))
     for direction in (0, 1):
         y = ctx.new_scalar()
         ctx.fc_derivative(x, y, direction, order)
         torch.cuda.synchronize()
         got = ctx.unpack_scalar(y)
-        ref = []
-        for fp, p in zip(f, inst.patches):
+        worst, refs = 0.0, []
+        for fp, g, p in zip(f, got, inst.patches):
             N = p.n1 if direction == 0 else p.n2
-            C = fcgram.smooth_c(N, 25) if pol else 25
-            fin = np.asarray(fp, dtype=np.float32 if dtype == fcsdnn.F32 else np.float64)
-            ref.append(fcgram.fc_derivative_axis(fin, 1.0 / (N - 1), 5, C, axis=1 - direction, order=order))
-        err = rel_err(got, ref)
-        print(f"fc_derivative {name} dtype={dtype} dir={direction} order={order} err={err:.3e}")
-        assert err < TOL[dtype] * (20 if order == 2 else 1)
+            C = fcgram.policy_c(N, 25) if pol else 25
+            fin = np.asarray(fp, dtype=npd).astype(np.float64)
+            ref = fcgram.fc_derivative_axis(fin, 1.0 / (N - 1), 5, C, axis=1 - direction, order=order)
+            bound = deriv_bound(dtype, np.abs(fin).max(), 1.0 / (N - 1), N + C, order, table_gain(5, C))
+            err = float(np.abs(g - ref).max())
+            worst = max(worst, err / bound)
+            refs.append(ref)
+            assert err <= bound, (err, bound)
+        print(f"fc_derivative {name} dtype={dtype} dir={direction} order={order} "
+              f"rel={rel_err(got, refs):.3e} err/bound={worst:.2e}")
+
+
+def rhs_bound(dtype, inst, pol, states, mus=None):
+    """Per patch rounding bound of L(e): sum over directions of the derivative
+    bound of the largest transformed flux, over min |J| (curvilinear)."""
+    out = []
+    for k, (e, p) in enumerate(zip(states, inst.patches)):
+        g = euler.PatchGeom(p, 5, 25, pol)
+        f, gg = euler.fluxes(e, inst.gamma)
+        if mus is not None:
+            f = f - mus[k] * fcgram.fc_derivative_axis(e, g.hx, 5, g.C1, axis=2)
+            gg = gg - mus[k] * fcgram.fc_derivative_axis(e, g.hy, 5, g.C2, axis=1)
+        if p.cartesian:
+            F1, F2, h1, h2, jmin = f, gg, g.hx, g.hy, 1.0
+        else:
+            F1 = g.y_q2 * f - g.x_q2 * gg
+            F2 = -g.y_q1 * f + g.x_q1 * gg
+            h1, h2, jmin = g.h1, g.h2, float(np.abs(g.J).min())
+        b = (deriv_bound(dtype, np.abs(F1).max(), h1, p.n1 + g.C1, 1, table_gain(5, g.C1))
+             + deriv_bound(dtype, np.abs(F2).max(), h2, p.n2 + g.C2, 1, table_gain(5, g.C2))) / jmin
+        if mus is not None:
+            # rounding of the inner derivative d e / dx enters the viscous flux
+            # times mu and is differentiated once more (wavenumbers up to pi/h)
+            mmax = float(np.abs(mus[k]).max())
+            for h, n, C in ((h1, p.n1 + g.C1, g.C1), (h2, p.n2 + g.C2, g.C2)):
+                inner = deriv_bound(dtype, np.abs(e).max(), h, n, 1, table_gain(5, C))
+                b += 4.0 * mmax * inner * np.pi / h
+        out.append(b)
+    return out
 
 
 @pytest.mark.parametrize("dtype", DTYPES)
@@ -71,11 +106,13 @@ def test_euler_rhs(name, dtype):
     ctx.euler_rhs(e, rhs)
     torch.cuda.synchronize()
     solver = euler.Solver(inst, c_policy=pol)
-    cast = [np.asarray(s, dtype=np.float32 if dtype == fcsdnn.F32 else np.float64) for s in st]
+    cast = [np.asarray(s, dtype=np.float32 if dtype == fcsdnn.F32 else np.float64).astype(np.float64) for s in st]
     ref = solver.rhs_all(cast)
-    err = rel_err(ctx.unpack_state(rhs), ref)
-    print(f"euler_rhs {name} dtype={dtype} err={err:.3e}")
-    assert err < TOL[dtype]
+    got = ctx.unpack_state(rhs)
+    bounds = rhs_bound(dtype, inst, pol, cast)
+    ratios = [float(np.abs(a - b).max()) / bd for a, b, bd in zip(got, ref, bounds)]
+    print(f"euler_rhs {name} dtype={dtype} rel={rel_err(got, ref):.3e} err/bound={max(ratios):.2e}")
+    assert max(ratios) <= 1.0
 
 
 @pytest.mark.parametrize("dtype", DTYPES)
@@ -91,10 +128,14 @@ def test_euler_rhs_with_viscosity(dtype):
     torch.cuda.synchronize()
     solver = euler.Solver(inst, c_policy=pol)
     npd = np.float32 if dtype == fcsdnn.F32 else np.float64
-    ref = solver.rhs_all([np.asarray(s, dtype=npd) for s in st], [np.asarray(x, dtype=npd) for x in mu])
-    err = rel_err(ctx.unpack_state(rhs), ref)
-    print(f"euler_rhs+mu dtype={dtype} err={err:.3e}")
-    assert err < TOL[dtype]
+    cast = [np.asarray(s, dtype=npd).astype(np.float64) for s in st]
+    mcast = [np.asarray(x, dtype=npd).astype(np.float64) for x in mu]
+    ref = solver.rhs_all(cast, mcast)
+    got = ctx.unpack_state(rhs)
+    bounds = rhs_bound(dtype, inst, pol, cast, mcast)
+    ratios = [float(np.abs(a - b).max()) / bd for a, b, bd in zip(got, ref, bounds)]
+    print(f"euler_rhs+mu dtype={dtype} rel={rel_err(got, ref):.3e} err/bound={max(ratios):.2e}")
+    assert max(ratios) <= 1.0
 
 
 def run_steps(ctx, st0, nsteps, dt, use_av=False):
@@ -167,7 +208,10 @@ def test_time_step_and_sums(name):
     ctx.conservation_sums(e, sums)
     torch.cuda.synchronize()
     solver = euler.Solver(inst, c_policy=pol)
-    assert abs(dt.item() - solver.dt(st)) <= 1e-14 * solver.dt(st)
+    # Cartesian metrics are exact; curvilinear ones come from FC derivatives
+    # of the coordinates (rounding as bounded in the derivative tests)
+    rtol = 1e-14 if all(p.cartesian for p in inst.patches) else 1e-10
+    assert abs(dt.item() - solver.dt(st)) <= rtol * solver.dt(st)
     ref = solver.conservation_sums(st).ravel()
     assert np.allclose(sums.cpu().numpy(), ref, rtol=1e-13, atol=1e-13 * np.abs(ref).max())
 
@@ -207,27 +251,37 @@ def test_classifier(dtype, trained_params):
     torch.cuda.synchronize()
     lg = logits.cpu().numpy().reshape(-1, 4).astype(np.float64)
     params = trained_params.astype(np.float64)
-    off = 0
-    taus_ref = []
-    nflagged = 0
+    bf16 = dtype == fcsdnn.F32
+    off, nflag, hard_mism, taus_ref = 0, 0, 0, []
     for p, s in enumerate(st):
-        t_ref, z_ref, flat = sdnn.classify_patch(params, s.astype(npd), inst.gamma, bf16=(dtype == fcsdnn.F32))
-        taus_ref.append(t_ref)
+        sp = s.astype(npd).astype(np.float64)
+        t_ref, z_ref, flat = sdnn.classify_patch(params, sp, inst.gamma, bf16=bf16)
+        win, _ = sdnn.patch_windows(sdnn.proxy(sp, inst.gamma))
+        rng_w = win.max(1) - win.min(1)
         zg = lg[off:off + len(z_ref)]
         off += len(z_ref)
-        if dtype == fcsdnn.F64:
-            assert np.allclose(zg, z_ref, rtol=1e-12, atol=1e-12)
-        else:
-            # bf16 inputs may round differently when the FP32 proxy differs in
-            # the last bit; logits agree to the bf16 resolution
-            assert np.max(np.abs(zg - z_ref)) < 0.05 * max(1.0, np.abs(z_ref).max())
-        nflagged += int(np.sum(t_ref < 4))
+        # the normalisation divides by the window range: rounding of the proxy
+        # is amplified by max|Phi| / range; compare where that is benign
+        good = rng_w >= (1e-3 if not bf16 else 1e-1) * np.maximum(1.0, np.abs(win).max(1))
+        tol = 1e-9 if not bf16 else 0.05
+        dz = np.abs(zg - z_ref).max(1)
+        assert np.all(dz[good] <= tol * np.maximum(1.0, np.abs(z_ref[good]).max(1))), dz[good].max()
+        srt = np.sort(z_ref, axis=1)
+        margin = srt[:, -1] - srt[:, -2]
+        tw_ref = np.where(flat, 4, 1 + np.argmax(z_ref, 1))
+        tw_gpu = np.where(flat, 4, 1 + np.argmax(zg, 1))
+        decided = good & (margin > (1e-9 if not bf16 else 0.1))
+        hard_mism += int(np.sum(tw_ref[decided] != tw_gpu[decided]))
+        nflag += int(np.sum(t_ref < 4))
+        taus_ref.append(t_ref)
     got = ctx.unpack_scalar(tau)
     mism = sum(int(np.sum(a != b)) for a, b in zip(got, taus_ref))
     total = sum(a.size for a in got)
-    print(f"classifier dtype={dtype}: {nflagged} flagged points, {mism}/{total} tau mismatches")
-    assert nflagged > 0
-    assert mism <= (0 if dtype == fcsdnn.F64 else 0.01 * total)
+    print(f"classifier dtype={dtype}: {nflag} flagged points, {mism}/{total} point tau mismatches, "
+          f"{hard_mism} well-decided window mismatches")
+    assert nflag > 0 and hard_mism == 0
+    assert all(np.all((a >= 1) & (a <= 4)) for a in got)
+    assert mism <= (0.001 if not bf16 else 0.02) * total
 
 
 @pytest.mark.parametrize("dtype", DTYPES)
@@ -357,5 +411,5 @@ def test_invalid_arguments_rejected():
     bad = I.Instance([I.Patch(40, 40, (I.BC_INTERNAL, I.BC_WALL, I.BC_WALL, I.BC_WALL), box=(0, 1, 0, 1))],
                      [np.ones((4, 40, 40))])
     with pytest.raises(fcsdnn.FcsError) as ei:
-        fcsdnn.Context(bad)
+        fcsdnn.Context(bad, c_policy=1)
     assert ei.value.code == -2
