@@ -51,7 +51,8 @@ typedef enum {
   FCS_ECUDA = -4,         /* a CUDA runtime call failed */
   FCS_ENOMEM = -5,        /* device allocation failed in fc_setup */
   FCS_ENONFINITE = -6,    /* (status word) NaN or Inf met in the state */
-  FCS_ENEGATIVE = -7      /* (status word) non-positive density or pressure */
+  FCS_ENEGATIVE = -7,     /* (status word) non-positive density or pressure */
+  FCS_ESCRATCH = -8       /* request larger than the fixed scratch of sdnn_gradient_noalloc */
 } fcs_err;
 
 typedef enum { FCS_F32 = 0, FCS_F64 = 1 } fcs_dtype;
@@ -222,6 +223,26 @@ int sdnn_train_step(fcs_ctx* ctx, const float* x_dev, const int8_t* labels_dev, 
  * grad_dev[1732]; for checking against the CPU oracle. */
 int sdnn_gradient(fcs_ctx* ctx, const float* x_dev, const int8_t* labels_dev, int batch, float* loss_dev,
                   float* grad_dev, void* stream);
+
+/* Classifier gradient without any device allocation (no counterpart in the
+ * paper: it exists for callers that cannot call cudaMalloc, such as hosts
+ * that hand the library only buffers they allocated themselves from their own
+ * memory arenas, or code that must not trigger the allocator's implicit
+ * synchronisation).  Same result as sdnn_gradient, but the weights come in
+ * as an argument (w_dev: 1732 floats, layout of sdnn_set_weights) and no
+ * context is needed.  The per-sample activations live in one file-scope
+ * device array sized for FCS_NOALLOC_BATCH_MAX samples (about 2.4 MB), which
+ * every GPU that loads the library keeps until the process exits.
+ *  - batch > FCS_NOALLOC_BATCH_MAX returns FCS_ESCRATCH; nothing is launched.
+ *  - The first call on a device looks up the array's device address (with
+ *    that device current); make that first call before any stream capture.
+ *  - All calls share the array: calls that may overlap on the GPU (other
+ *    streams, other host threads) race; serialise them.  Every value the
+ *    kernels read from it is written earlier in the same call.
+ *  - loss_dev may be NULL; grad_dev receives 1732 floats. */
+#define FCS_NOALLOC_BATCH_MAX 4096
+int sdnn_gradient_noalloc(const float* w_dev, const float* x_dev, const int8_t* labels_dev, int batch,
+                          float* loss_dev, float* grad_dev, void* stream);
 
 /* One full time step (Algorithm 1 loop body): if use_av, classify and
  * assemble the viscosity; the time step (dt_dev receives it) unless dt > 0

@@ -5,6 +5,7 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <vector>
 
 #include "../../include/fcsdnn.h"
@@ -339,6 +340,7 @@ const char* fcs_strerror(int code) {
     case FCS_ENOMEM: return "device allocation failed";
     case FCS_ENONFINITE: return "non-finite value in the state";
     case FCS_ENEGATIVE: return "non-positive density or pressure";
+    case FCS_ESCRATCH: return "batch larger than the fixed scratch of the no-allocation entry point";
     default: return "unknown error";
   }
 }
@@ -878,6 +880,42 @@ int sdnn_gradient(fcs_ctx* c, const float* x, const int8_t* lab, int B, float* l
   int rc = train_forward_backward(c, x, lab, B, loss, s);
   if (rc) return rc;
   return cuda_err(cudaMemcpyAsync(grad, c->grad, kNParams * 4, cudaMemcpyDeviceToDevice, s));
+}
+
+// ---- no-allocation variant of the classifier gradient.  Its scratch (per
+// sample activations and losses) is a file-scope device array; host code only
+// ever passes the array's device address, looked up once per device.
+constexpr size_t kNoAllocActs = (size_t)FCS_NOALLOC_BATCH_MAX * kActs;
+static __device__ __align__(256) float g_noalloc_scratch[kNoAllocActs + FCS_NOALLOC_BATCH_MAX];
+namespace {
+constexpr int kMaxDevices = 64;
+float* g_noalloc_addr[kMaxDevices] = {};
+std::mutex g_noalloc_mutex;
+}  // namespace
+
+int sdnn_gradient_noalloc(const float* w, const float* x, const int8_t* lab, int B, float* loss, float* grad,
+                          void* stream) {
+  if (!w || !x || !lab || !grad || B < 1) return FCS_EINVAL;
+  if (B > FCS_NOALLOC_BATCH_MAX) return FCS_ESCRATCH;
+  int dev = -1;
+  FCS_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) return FCS_EUNSUPPORTED;
+  float* acts;
+  {
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_addr[dev]) {
+      void* p = nullptr;
+      FCS_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+      g_noalloc_addr[dev] = static_cast<float*>(p);
+    }
+    acts = g_noalloc_addr[dev];
+  }
+  cudaStream_t s = as_stream(stream);
+  k_train_sample<<<(B + 127) / 128, 128, 0, s>>>(x, reinterpret_cast<const signed char*>(lab), B, w, acts,
+                                                 acts + kNoAllocActs);
+  k_train_grad<<<(kNParams + 127) / 128, 128, 0, s>>>(acts, B, grad);
+  k_train_loss<<<1, 256, 0, s>>>(acts + kNoAllocActs, B, loss);
+  return cuda_err(cudaGetLastError());
 }
 
 int sdnn_train_step(fcs_ctx* c, const float* x, const int8_t* lab, int B, float lr, float* loss, void* stream) {

@@ -16,13 +16,15 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libfcsdnn.so")
 F32, F64 = 0, 1
 N_PARAMS = 1732
 ERRORS = {0: "ok", -1: "EINVAL", -2: "EOVERLAP", -3: "EUNSUPPORTED", -4: "ECUDA", -5: "ENOMEM",
-          -6: "ENONFINITE", -7: "ENEGATIVE"}
+          -6: "ENONFINITE", -7: "ENEGATIVE", -8: "ESCRATCH"}
+NOALLOC_BATCH_MAX = 4096
 
 # every entry point of include/fcsdnn.h
 EXPORTS = ("fcs_default_options", "fc_setup", "fc_destroy", "fcs_get_layout", "fcs_build_table", "fcs_line_c",
            "fc_derivative", "euler_rhs", "rk_stage", "patch_exchange", "fcs_time_step", "fcs_conservation_sums",
            "sdnn_set_weights", "sdnn_get_weights", "sdnn_classify", "sdnn_indicator", "av_assemble",
-           "sdnn_train_step", "sdnn_gradient", "fcs_step", "fcs_step_graph", "fcs_status", "fcs_strerror")
+           "sdnn_train_step", "sdnn_gradient", "sdnn_gradient_noalloc", "fcs_step", "fcs_step_graph", "fcs_status",
+           "fcs_strerror")
 
 
 class FcsError(RuntimeError):
@@ -82,6 +84,7 @@ def lib():
             "av_assemble": (i, [vp, vp, vp, vp, vp]),
             "sdnn_train_step": (i, [vp, vp, vp, i, ctypes.c_float, vp, vp]),
             "sdnn_gradient": (i, [vp, vp, vp, i, vp, vp, vp]),
+            "sdnn_gradient_noalloc": (i, [vp, vp, vp, i, vp, vp, vp]),
             "fcs_step": (i, [vp, vp, d, vp, i, vp]),
             "fcs_step_graph": (i, [vp, vp, d, vp, i, vp]),
             "fcs_status": (i, [vp, ctypes.POINTER(ctypes.c_int)]),
@@ -105,6 +108,15 @@ def build_table(d, C):
     out = np.zeros((C, d), dtype=np.float64)
     _check("fcs_build_table", lib().fcs_build_table(d, C, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
     return out
+
+
+def gradient_noalloc(w, x, labels, grad, loss=None, stream=None):
+    """Classifier gradient through sdnn_gradient_noalloc: no context and no
+    device allocation inside the library (for callers that cannot allocate).
+    w: device float weights (1732); x: device float windows (batch x 16);
+    labels: device int8 (batch); grad: device float (1732)."""
+    _check("sdnn_gradient_noalloc", lib().sdnn_gradient_noalloc(_ptr(w), _ptr(x), _ptr(labels), int(x.shape[0]),
+                                                                _ptr(loss), _ptr(grad), _stream(stream)))
 
 
 def _ptr(t):
