@@ -100,7 +100,8 @@ typedef struct {
 void fcs_default_options(fcs_options* opt);
 
 /* Build a context (paper Algorithm 2, initialization): FC-Gram continuation
- * tables for degree d and C continuation points (paper §2; construction is a
+ * tables for degree d (2 <= d <= 8) and C continuation points (2 <= C <= 64;
+ * paper §2; construction is a
  * Tikhonov-regularised oversampled Fourier-extension fit of the Gram
  * polynomials, solved in double-double arithmetic), FFT plans, metrics of
  * curvilinear patches, fringe/donor maps (§3.3; coincident grids only), window

@@ -52,6 +52,7 @@ struct fcs_ctx {
   int4* pairs0 = nullptr;
   int4* pairs1 = nullptr;
   int2* tiles = nullptr;
+  int2* pblk = nullptr;  // point blocks of the pointwise kernels
   int4* fringe_ent = nullptr;
   double* wq = nullptr;
   int2* woff = nullptr;
@@ -210,11 +211,11 @@ int get_plan(fcs_ctx* c, int N, int C, int d) {
 }
 
 template <typename T>
-size_t xpass_smem(const fcs_ctx* c) { return kWarps * warp_line_bytes<T>(9, c->nmax, c->nfmax, c->n1x == 0); }
+size_t xpass_smem(const fcs_ctx* c) { return kWarps * xpass_warp_bytes<T>(c->nmax, c->nfmax, c->n1x); }
 template <typename T>
-size_t deriv_smem(const fcs_ctx* c, int n1) { return kWarps * warp_line_bytes<T>(2, c->nmax, c->nfmax, n1 == 0); }
+size_t deriv_smem(const fcs_ctx* c, int n1) { return kWarps * deriv_warp_bytes<T>(c->nmax, c->nfmax, n1); }
 template <typename T>
-size_t ypass_smem(const fcs_ctx* c, int tw) { return ypass_bytes<T>(c->n2max, tw, c->nfmax, c->n1y == 0, kYWarps); }
+size_t ypass_smem(const fcs_ctx* c, int tw) { return ypass_bytes<T>(c->n2max, tw, c->nfmax, c->n1y, kYWarps); }
 
 int grid_for(long long work, int per_block) {
   long long g = (work + per_block - 1) / per_block;
@@ -253,7 +254,7 @@ int launch_deriv(fcs_ctx* c, const void* in, void* out, int dir, int order, cuda
   const int np = dir == 0 ? c->npairs0 : c->npairs1;
   const int4* pr = dir == 0 ? c->pairs0 : c->pairs1;
   const int n1 = dir == 0 ? c->n1x : c->n1y;
-  const long long work = (long long)c->dev.instances * np;
+  const long long work = ((long long)c->dev.instances * np + jobs_per_round(n1) - 1) / jobs_per_round(n1);
   const LaunchCfg g{(unsigned)grid_for(work, kWarps), kWarps * 32, deriv_smem<T>(c, n1), s};
   FCS_N1_SWITCH(n1, return cuda_err((run_fc_deriv<T, K>(c->dev, dir, order, pr, np, static_cast<const T*>(in),
                                                         static_cast<T*>(out), g))))
@@ -261,7 +262,7 @@ int launch_deriv(fcs_ctx* c, const void* in, void* out, int dir, int order, cuda
 
 template <typename T>
 int launch_flux(fcs_ctx* c, const void* e, const void* mu, int mode, StageArgs<T> st, cudaStream_t s) {
-  const long long w0 = (long long)c->opt.instances * c->nlines0;
+  const long long w0 = (long long)c->opt.instances * ((c->nlines0 + kRowsPerWarp - 1) / kRowsPerWarp);
   const long long w1 = (long long)c->opt.instances * c->ntiles;
   const T* ep = static_cast<const T*>(e);
   const T* mp = static_cast<const T*>(mu);
@@ -282,12 +283,12 @@ cudaStream_t as_stream(void* s) { return static_cast<cudaStream_t>(s); }
 namespace {
 template <typename T>
 int av_impl(fcs_ctx* c, const void* e, const int8_t* tau, void* mu, cudaStream_t s) {
-  const long long np = (long long)c->opt.instances * c->qstride;
-  const int g = grid_for(np, 256), r = c->opt.av_radius;
+  const dim3 g(c->dev.npblk, c->opt.instances);
+  const int r = c->opt.av_radius;
   T* a0 = static_cast<T*>(c->av0);
   T* a1 = static_cast<T*>(c->av1);
   T* m = static_cast<T*>(mu);
-  k_av_speed<T><<<g, 256, 0, s>>>(c->dev, static_cast<const T*>(e), a0);
+  k_av_speed<T><<<g, 256, 0, s>>>(c->dev, static_cast<const T*>(e), a0, 0);
   k_av_prelim<T><<<g, 256, 0, s>>>(c->dev, a0, reinterpret_cast<const signed char*>(tau), T(c->opt.c_mu), a1);
   k_av_boxmax<T><<<g, 256, 0, s>>>(c->dev, a1, a0, r, 0);
   k_av_boxmax<T><<<g, 256, 0, s>>>(c->dev, a0, a1, r, 1);
@@ -366,7 +367,7 @@ void fc_destroy(fcs_ctx* c) {
 int fc_setup(fcs_ctx** out, int d, int C, const fcs_patch_desc* pd, int npatch, const fcs_options* opt) {
   if (!out) return FCS_EINVAL;
   *out = nullptr;
-  if (!pd || npatch <= 0 || d < 2 || d > 12 || C < 2 || C > 64) return FCS_EINVAL;
+  if (!pd || npatch <= 0 || d < 2 || d > 8 || C < 2 || C > 64) return FCS_EINVAL;
   fcs_options o;
   if (opt) o = *opt;
   else fcs_default_options(&o);
@@ -418,7 +419,8 @@ int fc_setup(fcs_ctx** out, int d, int C, const fcs_patch_desc* pd, int npatch, 
       c->nmax = std::max(c->nmax, N);
       c->nfmax = std::max(c->nfmax, c->plans[pi].dev.n);
       int& nd = dir == 0 ? c->n1x : c->n1y;
-      const int r = c->plans[pi].dev.n1reg;
+      int r = c->plans[pi].dev.n1reg;
+      if (r % 2 == 0 && d > 5) r = 0;  // the two-level register FFT handles d <= 5
       if (nd < 0) nd = r;
       else if (nd != r) nd = 0;
     }
@@ -499,6 +501,9 @@ int fc_setup(fcs_ctx** out, int d, int C, const fcs_patch_desc* pd, int npatch, 
   for (int p = 0; p < npatch; ++p)
     for (int c0 = 0; c0 < pd[p].n1; c0 += c->tw) tiles.push_back(make_int2(p, c0));
   c->ntiles = (int)tiles.size();
+  std::vector<int2> pblk;
+  for (int p = 0; p < npatch; ++p)
+    for (int s0 = 0; s0 < pd[p].n1 * pd[p].n2; s0 += 256) pblk.push_back(make_int2(p, s0));
   c->sstride = soff;
   c->qstride = qoff;
   c->nwin = wins.size();
@@ -545,6 +550,24 @@ int fc_setup(fcs_ctx** out, int d, int C, const fcs_patch_desc* pd, int npatch, 
   }
   c->nent = (int)ent.size();
 
+  // ---- Gram basis on the d matching points (QR of the Vandermonde matrix,
+  // modified Gram-Schmidt) and per plan the blend values of the Gram
+  // polynomials T = A_R Q, both FP32 for the FP32 continuation
+  std::vector<double> Qd((size_t)d * d);
+  for (int i = 0; i < d; ++i)
+    for (int j = 0; j < d; ++j) Qd[(size_t)i * d + j] = std::pow((double)i / (d - 1), j);
+  for (int j = 0; j < d; ++j) {
+    for (int k = 0; k < j; ++k) {
+      double dot = 0;
+      for (int i = 0; i < d; ++i) dot += Qd[(size_t)i * d + k] * Qd[(size_t)i * d + j];
+      for (int i = 0; i < d; ++i) Qd[(size_t)i * d + j] -= dot * Qd[(size_t)i * d + k];
+    }
+    double nrm = 0;
+    for (int i = 0; i < d; ++i) nrm += Qd[(size_t)i * d + j] * Qd[(size_t)i * d + j];
+    nrm = std::sqrt(nrm);
+    for (int i = 0; i < d; ++i) Qd[(size_t)i * d + j] /= nrm;
+  }
+  std::vector<float> gramQ(Qd.begin(), Qd.end()), gramT;
   // ---- device tables
   std::vector<double> tab64;
   std::vector<float> thi, tlo;
@@ -552,6 +575,13 @@ int fc_setup(fcs_ctx** out, int d, int C, const fcs_patch_desc* pd, int npatch, 
   std::vector<float2> tw32;
   std::vector<PlanDev> plans;
   for (HostPlan& hp : c->plans) {
+    hp.dev.tg_off = (int)gramT.size();
+    for (int q = 0; q < hp.dev.C; ++q)
+      for (int k = 0; k < d; ++k) {
+        double v = 0;
+        for (int m = 0; m < d; ++m) v += hp.tab[(size_t)q * d + m] * Qd[(size_t)m * d + k];
+        gramT.push_back((float)v);
+      }
     hp.dev.tab_off = (int)tab64.size();
     for (double v : hp.tab) {
       float a, b;
@@ -600,6 +630,9 @@ int fc_setup(fcs_ctx** out, int d, int C, const fcs_patch_desc* pd, int npatch, 
   int4* dwin;
   unsigned char* dfr;
   int* dstatus;
+  float *dgq, *dgt;
+  if ((rc = upload(c, &dgq, gramQ.data(), gramQ.size() * 4)) || (rc = upload(c, &dgt, gramT.data(), gramT.size() * 4)))
+    return fail(rc);
   if ((rc = upload(c, &dpatch, c->patches.data(), c->patches.size() * sizeof(PatchDev))) ||
       (rc = upload(c, &dplan, plans.data(), plans.size() * sizeof(PlanDev))) ||
       (rc = upload(c, &dtab64, tab64.data(), tab64.size() * 8)) ||
@@ -611,6 +644,7 @@ int fc_setup(fcs_ctx** out, int d, int C, const fcs_patch_desc* pd, int npatch, 
       (rc = upload(c, &c->pairs0, p0.data(), p0.size() * sizeof(int4))) ||
       (rc = upload(c, &c->pairs1, p1.data(), p1.size() * sizeof(int4))) ||
       (rc = upload(c, &c->tiles, tiles.data(), tiles.size() * sizeof(int2))) ||
+      (rc = upload(c, &c->pblk, pblk.data(), pblk.size() * sizeof(int2))) ||
       (rc = upload(c, &dwin, wins.data(), wins.size() * sizeof(int4))) ||
       (rc = upload(c, &dfr, fringe.data(), fringe.size())) ||
       (rc = upload(c, &c->fringe_ent, ent.data(), ent.size() * sizeof(int4))) ||
@@ -662,6 +696,10 @@ int fc_setup(fcs_ctx** out, int d, int C, const fcs_patch_desc* pd, int npatch, 
   D.nmax = c->nmax;
   D.nfmax = c->nfmax;
   D.stockham = c->stockham;
+  D.gramQ = dgq;
+  D.gramT = dgt;
+  D.pblk = c->pblk;
+  D.npblk = (int)pblk.size();
   D.tw = c->tw;
   D.n2max = c->n2max;
   if ((rc = (o.dtype == FCS_F64 ? set_smem_attrs<double>(c) : set_smem_attrs<float>(c)))) return fail(rc);
@@ -780,7 +818,7 @@ int fcs_time_step(fcs_ctx* c, const void* e, const void* mu, double* dt_dev, voi
   cudaStream_t s = as_stream(stream);
   const int I = c->opt.instances;
   k_dt_init<<<(I + 127) / 128, 128, 0, s>>>(c->dtbest, I);
-  dim3 g((unsigned)std::min<long long>((c->qstride + 255) / 256, 512), (unsigned)I);
+  const dim3 g(c->dev.npblk, I);
   if (c->opt.dtype == FCS_F64)
     k_dt<double><<<g, 256, 0, s>>>(c->dev, static_cast<const double*>(e), static_cast<const double*>(mu), c->opt.cfl,
                                    kCflMu, c->dtbest);
@@ -836,17 +874,19 @@ int sdnn_classify(fcs_ctx* c, const void* e, int8_t* tau, void* logits, void* st
   if (!c || !e || !tau) return FCS_EINVAL;
   cudaStream_t s = as_stream(stream);
   const long long nw = (long long)c->opt.instances * c->nwin;
+  const dim3 gp(c->dev.npblk, c->opt.instances);
   if (c->opt.dtype == FCS_F64) {
-    k_mlp64<double><<<grid_for(nw, 128), 128, 0, s>>>(c->dev, static_cast<const double*>(e), c->W64, c->tau_w,
+    k_av_speed<double><<<gp, 256, 0, s>>>(c->dev, static_cast<const double*>(e), static_cast<double*>(c->av0), 1);
+    k_mlp64<double><<<grid_for(nw, 128), 128, 0, s>>>(c->dev, static_cast<const double*>(c->av0), c->W64, c->tau_w,
                                                       static_cast<double*>(logits));
   } else {
+    k_av_speed<float><<<gp, 256, 0, s>>>(c->dev, static_cast<const float*>(e), static_cast<float*>(c->av0), 1);
     const long long groups = (nw + 15) / 16;
-    k_mlp_bf16<<<grid_for(groups, 4), 128, 0, s>>>(c->dev, static_cast<const float*>(e), c->Wb, c->bias, c->tau_w,
-                                                    static_cast<float*>(logits));
+    k_mlp_bf16<<<grid_for(groups, 4), 128, 0, s>>>(c->dev, static_cast<const float*>(c->av0), c->Wb, c->bias,
+                                                    c->tau_w, static_cast<float*>(logits));
   }
   FCS_CUDA(cudaGetLastError());
-  const long long np = (long long)c->opt.instances * c->qstride;
-  k_tau_gather<<<grid_for(np, 256), 256, 0, s>>>(c->dev, c->tau_w, reinterpret_cast<signed char*>(tau));
+  k_tau_gather<<<gp, 256, 0, s>>>(c->dev, c->tau_w, reinterpret_cast<signed char*>(tau));
   return cuda_err(cudaGetLastError());
 }
 
@@ -854,15 +894,18 @@ int sdnn_indicator(fcs_ctx* c, const void* e, int8_t* tau, void* s_out, void* st
   if (!c || !e || !tau) return FCS_EINVAL;
   cudaStream_t s = as_stream(stream);
   const long long nw = (long long)c->opt.instances * c->nwin;
-  if (c->opt.dtype == FCS_F64)
-    k_indicator<double><<<grid_for(nw, 128), 128, 0, s>>>(c->dev, static_cast<const double*>(e), c->tau_w,
+  const dim3 gp(c->dev.npblk, c->opt.instances);
+  if (c->opt.dtype == FCS_F64) {
+    k_av_speed<double><<<gp, 256, 0, s>>>(c->dev, static_cast<const double*>(e), static_cast<double*>(c->av0), 1);
+    k_indicator<double><<<grid_for(nw, 128), 128, 0, s>>>(c->dev, static_cast<const double*>(c->av0), c->tau_w,
                                                           static_cast<double*>(s_out));
-  else
-    k_indicator<float><<<grid_for(nw, 128), 128, 0, s>>>(c->dev, static_cast<const float*>(e), c->tau_w,
+  } else {
+    k_av_speed<float><<<gp, 256, 0, s>>>(c->dev, static_cast<const float*>(e), static_cast<float*>(c->av0), 1);
+    k_indicator<float><<<grid_for(nw, 128), 128, 0, s>>>(c->dev, static_cast<const float*>(c->av0), c->tau_w,
                                                          static_cast<float*>(s_out));
+  }
   FCS_CUDA(cudaGetLastError());
-  const long long np = (long long)c->opt.instances * c->qstride;
-  k_tau_gather<<<grid_for(np, 256), 256, 0, s>>>(c->dev, c->tau_w, reinterpret_cast<signed char*>(tau));
+  k_tau_gather<<<gp, 256, 0, s>>>(c->dev, c->tau_w, reinterpret_cast<signed char*>(tau));
   return cuda_err(cudaGetLastError());
 }
 

@@ -27,8 +27,9 @@ struct PlanDev {
   int N, C, n, nst;
   int radix[kMaxStages];
   int tw_off;           // offset of the n twiddles
-  int tab_off;          // offset of the C x d continuation table
-  int n1reg;            // n = 32 * n1reg: register four-step FFT; 0: shared-memory Stockham FFT
+  int tab_off;          // offset of the C x d continuation table (FP64, and its FP32 split)
+  int n1reg;            // n = 32 * n1reg: register FFT (two-level for even n1reg); 0: Stockham FFT
+  int tg_off;           // offset of the C x d Gram blend table (FP32)
 };
 
 struct LineRef {
@@ -62,7 +63,31 @@ struct CtxDev {
   int stockham;                 // 1 if some plan needs the shared-memory FFT buffers
   int tw;                       // column-tile width of the pass along q2
   int n2max;                    // longest column (lines along q2)
+  const float* gramQ;           // d x d Gram basis at the matching points (FP32)
+  const float* gramT;           // Gram blend tables of all plans (FP32)
+  const int2* pblk;             // point blocks of 256 points: (patch, first point), one instance
+  int npblk;
 };
+
+// Point handled by this thread in a pointwise kernel launched on
+// (npblk, instances) blocks of 256 threads; 32-bit indexing within a patch.
+struct PtIdx {
+  int inst, patch, lq, i, j;
+  bool ok;
+};
+__device__ __forceinline__ PtIdx pt_index(const CtxDev& c, const PatchDev** Pp) {
+  const int2 pb = c.pblk[blockIdx.x];
+  const PatchDev& P = c.patches[pb.x];
+  *Pp = &P;
+  PtIdx r;
+  r.inst = blockIdx.y;
+  r.patch = pb.x;
+  r.lq = pb.y + (int)threadIdx.x;
+  r.ok = r.lq < P.n1 * P.n2;
+  r.i = r.lq % P.n1;
+  r.j = r.lq / P.n1;
+  return r;
+}
 
 template <typename T>
 struct Cx {
@@ -509,17 +534,331 @@ __device__ void stk_deriv_pair(const T* a, int sa, const T* b, int sb, T* oa, in
   __syncwarp();
 }
 
-// FC derivative of a line pair: register FFT of length 32 * N1, or (N1 = 0)
-// the shared-memory Stockham FFT, which handles any 7-smooth length.
+}  // namespace fcs
+
+#include <type_traits>
+
+#include "fcs_roots.cuh"
+
+namespace fcs {
+
+// ------------------------------------------------------------ small register DFTs
+// In-place DFT of N complex values held in registers, N a product of small
+// primes.  rdft_fwd leaves X[k] at register position p with k = rsigma(N, p)
+// (Cooley-Tukey N = R M, R the smallest prime factor: R-point DFTs on the
+// stride-M subsets, twiddles w_N^{jm kr}, M-point DFTs on the contiguous
+// blocks).  rdft_inv applies the adjoint steps in reverse order, so
+// rdft_inv(rdft_fwd(x)) = N x and it takes the permuted layout back to the
+// natural one.  Roots come from the constant tables of fcs_roots.cuh (uniform
+// compile-time indices: constant-bank operands).
+__host__ __device__ constexpr int spf(int n) {
+  for (int p = 2; p * p <= n; ++p)
+    if (n % p == 0) return p;
+  return n;
+}
+// Iterative (not recursive) so that it inlines and folds to a constant under
+// unrolling: peel one smallest prime factor R of the size per level.
+__host__ __device__ constexpr int rsigma(int N, int p) {
+  int res = 0, mult = 1;
+  while (spf(N) != N) {
+    const int R = spf(N), M = N / R;
+    res += mult * (p / M);
+    p %= M;
+    mult *= R;
+    N = M;
+  }
+  return res + mult * p;
+}
+
+// Compile-time loop: f(std::integral_constant<int, I>) for I = B .. E-1, so the
+// permutation and root indices below are template constants (always folded).
+template <int I, int E, typename F>
+__device__ __forceinline__ void static_for(F&& f) {
+  if constexpr (I < E) {
+    f(std::integral_constant<int, I>{});
+    static_for<I + 1, E>(f);
+  }
+}
+template <int N, int P>
+struct Sigma {
+  static constexpr int value = rsigma(N, P);
+};
+
+template <typename T, int N>
+__device__ __forceinline__ Cx<T> root(int m) {
+  constexpr int off = kRootOff(N);
+  static_assert(off >= 0, "no root table for this size");
+  if constexpr (sizeof(T) == 8) {
+    const double2 v = kRoots64[off + m % N];
+    return {v.x, v.y};
+  } else {
+    const float2 v = kRoots32[off + m % N];
+    return {v.x, v.y};
+  }
+}
+
+template <typename T, int R, bool INV>
+__device__ __forceinline__ void prime_dft(Cx<T>* v) {
+  if constexpr (R == 2) {
+    const Cx<T> a = v[0], b = v[1];
+    v[0] = {a.x + b.x, a.y + b.y};
+    v[1] = {a.x - b.x, a.y - b.y};
+  } else if constexpr (R == 3) {
+    const T s = T(0.86602540378443864676372317075294);
+    const Cx<T> a = v[0], b = v[1], c = v[2];
+    const Cx<T> t1 = {b.x + c.x, b.y + c.y};
+    const Cx<T> t2 = {a.x - T(0.5) * t1.x, a.y - T(0.5) * t1.y};
+    // -i s (b - c) for the forward transform, +i s (b - c) for the inverse
+    Cx<T> r = {s * (b.y - c.y), -s * (b.x - c.x)};
+    if (INV) r = {-r.x, -r.y};
+    v[0] = {a.x + t1.x, a.y + t1.y};
+    v[1] = {t2.x + r.x, t2.y + r.y};
+    v[2] = {t2.x - r.x, t2.y - r.y};
+  } else {
+    Cx<T> o[R];
+#pragma unroll
+    for (int q = 0; q < R; ++q) {
+      Cx<T> acc = v[0];
+#pragma unroll
+      for (int r = 1; r < R; ++r) {
+        Cx<T> w = root<T, R>((r * q) % R);
+        if (INV) w.y = -w.y;
+        const Cx<T> p = cmul(v[r], w);
+        acc.x += p.x;
+        acc.y += p.y;
+      }
+      o[q] = acc;
+    }
+#pragma unroll
+    for (int q = 0; q < R; ++q) v[q] = o[q];
+  }
+}
+
+template <typename T, int N>
+__device__ __forceinline__ void rdft_fwd(Cx<T>* x) {
+  if constexpr (spf(N) == N) {
+    prime_dft<T, N, false>(x);
+  } else {
+    constexpr int R = spf(N), M = N / R;
+#pragma unroll
+    for (int jm = 0; jm < M; ++jm) {
+      Cx<T> v[R];
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[r] = x[jm + M * r];
+      prime_dft<T, R, false>(v);
+#pragma unroll
+      for (int r = 0; r < R; ++r) x[jm + M * r] = v[r];
+    }
+#pragma unroll
+    for (int jm = 1; jm < M; ++jm)
+#pragma unroll
+      for (int kr = 1; kr < R; ++kr) x[jm + M * kr] = cmul(x[jm + M * kr], root<T, N>(jm * kr));
+#pragma unroll
+    for (int kr = 0; kr < R; ++kr) rdft_fwd<T, M>(x + kr * M);
+  }
+}
+
+template <typename T, int N>
+__device__ __forceinline__ void rdft_inv(Cx<T>* x) {
+  if constexpr (spf(N) == N) {
+    prime_dft<T, N, true>(x);
+  } else {
+    constexpr int R = spf(N), M = N / R;
+#pragma unroll
+    for (int kr = 0; kr < R; ++kr) rdft_inv<T, M>(x + kr * M);
+#pragma unroll
+    for (int jm = 1; jm < M; ++jm)
+#pragma unroll
+      for (int kr = 1; kr < R; ++kr) {
+        Cx<T> w = root<T, N>(jm * kr);
+        w.y = -w.y;
+        x[jm + M * kr] = cmul(x[jm + M * kr], w);
+      }
+#pragma unroll
+    for (int jm = 0; jm < M; ++jm) {
+      Cx<T> v[R];
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[r] = x[jm + M * r];
+      prime_dft<T, R, true>(v);
+#pragma unroll
+      for (int r = 0; r < R; ++r) x[jm + M * r] = v[r];
+    }
+  }
+}
+
+// ------------------------------------------------------------ two-level line FFT
+// Line pair of FFT length n = 8 B handled by a group of 8 lanes (4 groups per
+// warp).  z[j], j = b + B a (a < 8, b < B).  Lane t of the group:
+//   forward: for its b in {t, t+8, ...}: 8-point DFT over a, twiddle
+//   w_n^{b ka}, store Y[ka][b] to the group's shared tile (row pitch B+1);
+//   after the warp barrier, the B-point DFT over b of row ka = t, so the lane
+//   holds X[t + 8 k_b] with k_b = rsigma(B, p) at register p.
+//   inverse: adjoint steps in reverse (B-point inverse DFT, conjugate twiddle,
+//   transpose back, 8-point inverse DFTs), natural order again.
+// FP32 continuation: Gram coefficients of the d end values (Q^T f), then the
+// blend table T = A_R Q (no cancellation for smooth data, so plain FP32
+// sums suffice); FP64: the A_R table directly.
+template <typename T>
+struct GramOp {
+  const float* Q;   // d x d Gram basis (values at the d matching points), FP32
+  const float* Tg;  // C x d blend values of the Gram polynomials, FP32
+};
+
+template <typename T, int B>
+__device__ __forceinline__ void tl_deriv_pair(const T* a, int sa, const T* b, int sb, T* oa, int soa, T* ob, int sob,
+                                              T scale, const LineOp<T>& op, const GramOp<T>& gop, int order, int t,
+                                              Cx<T>* tile, bool active) {
+  constexpr int NB = B / 8;
+  constexpr int MAXD = 5;  // degree bound of this path (contexts with d > 5 use the Stockham kernels)
+  const int N = op.N, n = 8 * B, d = op.d;
+  // ---- end values and continuation coefficients
+  T offa = T(0), offb = T(0);
+  if (active && Offset<T>::kShift) {
+    offa = (a[0] + a[(N - 1) * sa]) * T(0.5);
+    if (b) offb = (b[0] + b[(N - 1) * sb]) * T(0.5);
+  }
+  // FP32: lane t (< d) of the group computes Gram coefficient k = t of both
+  // lines and both ends; the group then shares them by shuffles
+  float gaR[MAXD], gaL[MAXD], gbR[MAXD], gbL[MAXD];
+  if constexpr (sizeof(T) == 4) {
+    float cR = 0.f, cL = 0.f, dR = 0.f, dL = 0.f;
+    if (active && t < d) {
+      for (int m = 0; m < d; ++m) {
+        const float q = __ldg(gop.Q + m * d + t);
+        cR = fmaf(q, a[(N - d + m) * sa] - offa, cR);
+        cL = fmaf(q, a[(d - 1 - m) * sa] - offa, cL);
+        if (b) {
+          dR = fmaf(q, b[(N - d + m) * sb] - offb, dR);
+          dL = fmaf(q, b[(d - 1 - m) * sb] - offb, dL);
+        }
+      }
+    }
+    const int base = (threadIdx.x & 31) & ~7;  // first lane of the group
+#pragma unroll
+    for (int k = 0; k < MAXD; ++k) {
+      gaR[k] = __shfl_sync(0xffffffffu, cR, base + k);
+      gaL[k] = __shfl_sync(0xffffffffu, cL, base + k);
+      gbR[k] = __shfl_sync(0xffffffffu, dR, base + k);
+      gbL[k] = __shfl_sync(0xffffffffu, dL, base + k);
+    }
+  }
+  auto input = [&](int j) -> Cx<T> {
+    Cx<T> z = {T(0), T(0)};
+    if (!active) return z;
+    if (j < N) {
+      z.x = a[j * sa] - offa;
+      z.y = b ? b[j * sb] - offb : T(0);
+    } else {
+      const int q = j - N;
+      if constexpr (sizeof(T) == 4) {
+        float sa_ = 0.f, sb_ = 0.f;
+#pragma unroll
+        for (int k = 0; k < MAXD; ++k) {
+          if (k >= d) continue;
+          const float tr = __ldg(gop.Tg + q * d + k), tl = __ldg(gop.Tg + (op.C - 1 - q) * d + k);
+          sa_ = fmaf(tr, gaR[k], fmaf(tl, gaL[k], sa_));
+          sb_ = fmaf(tr, gbR[k], fmaf(tl, gbL[k], sb_));
+        }
+        z = {T(sa_), b ? T(sb_) : T(0)};
+      } else {
+        z.x = cont_value(a, sa, offa, op, q);
+        z.y = b ? cont_value(b, sb, offb, op, q) : T(0);
+      }
+    }
+    return z;
+  };
+  // ---- stage 1: 8-point DFTs over a for each owned b
+  Cx<T> x[B];
+#pragma unroll
+  for (int i = 0; i < NB; ++i) {
+    const int bb = t + 8 * i;
+    Cx<T>* v = x + 8 * i;
+#pragma unroll
+    for (int aa = 0; aa < 8; ++aa) v[aa] = input(bb + B * aa);
+    rdft_fwd<T, 8>(v);
+    static_for<0, 8>([&](auto P) {
+      constexpr int p = decltype(P)::value;
+      constexpr int ka = Sigma<8, p>::value;
+      if constexpr (ka != 0) v[p] = cmul(v[p], ldtw(op.tw, bb * ka));
+      tile[ka * (B + 1) + bb] = v[p];
+    });
+  }
+  __syncwarp();
+  // ---- stage 2: B-point DFT of row ka = t
+#pragma unroll
+  for (int bb = 0; bb < B; ++bb) x[bb] = tile[t * (B + 1) + bb];
+  rdft_fwd<T, B>(x);
+  // ---- (i k)^order
+  const T sc = T(6.283185307179586476925286766559) / (T(n) * op.h);
+  const T inv_n = scale / T(n);
+  static_for<0, B>([&](auto P) {
+    constexpr int p = decltype(P)::value;
+    const int k = t + 8 * Sigma<B, p>::value;
+    const int km = (2 * k <= n) ? k : k - n;
+    const Cx<T> z = x[p];
+    if (order == 1) {
+      const T kk = (2 * k == n) ? T(0) : T(km) * sc * inv_n;
+      x[p] = {-kk * z.y, kk * z.x};
+    } else {
+      const T kk = T(km) * sc;
+      const T f = -kk * kk * inv_n;
+      x[p] = {f * z.x, f * z.y};
+    }
+  });
+  // ---- inverse: B-point inverse DFT, conjugate twiddle, transpose back
+  rdft_inv<T, B>(x);
+  __syncwarp();
+#pragma unroll
+  for (int bb = 0; bb < B; ++bb) {
+    Cx<T> w = ldtw(op.tw, bb * t);
+    w.y = -w.y;
+    tile[t * (B + 1) + bb] = cmul(x[bb], w);
+  }
+  __syncwarp();
+#pragma unroll
+  for (int i = 0; i < NB; ++i) {
+    const int bb = t + 8 * i;
+    Cx<T>* v = x + 8 * i;
+    static_for<0, 8>([&](auto P) {
+      constexpr int p = decltype(P)::value;
+      v[p] = tile[Sigma<8, p>::value * (B + 1) + bb];
+    });
+    rdft_inv<T, 8>(v);
+    if (active) {
+#pragma unroll
+      for (int aa = 0; aa < 8; ++aa) {
+        const int j = bb + B * aa;
+        if (j < N) {
+          oa[j * soa] = v[aa].x;
+          if (ob) ob[j * sob] = v[aa].y;
+        }
+      }
+    }
+  }
+  __syncwarp();
+}
+
+// Jobs (line pairs) a warp runs at once: 4 on the two-level FFT (even N1),
+// 1 on the 32-lane shuffle FFT (odd N1) and on the Stockham FFT (N1 = 0).
+__host__ __device__ constexpr int jobs_per_round(int N1) { return (N1 > 0 && N1 % 2 == 0) ? 4 : 1; }
+
+// FC derivative of a line pair by the FFT variant N1 selects.  Every lane of
+// the warp calls it together; `active` is false for lanes whose group has no
+// job this round.  tile: the group's transpose tile (two-level path);
+// buf0/buf1: the warp's Stockham buffers (N1 = 0).
 template <typename T, int N1>
 __device__ __forceinline__ void line_deriv_pair(const T* a, int sa, const T* b, int sb, T* oa, int soa, T* ob, int sob,
                                                 T scale, const CtxDev& c, const PlanDev& pl, T h, int order, int lane,
-                                                Cx<T>* buf0, Cx<T>* buf1) {
+                                                Cx<T>* buf0, Cx<T>* buf1, Cx<T>* tile, bool active) {
   if constexpr (N1 == 0) {
-    stk_deriv_pair<T>(a, sa, b, sb, oa, soa, ob, sob, scale, c, pl, h, order, lane, buf0, buf1);
+    if (active) stk_deriv_pair<T>(a, sa, b, sb, oa, soa, ob, sob, scale, c, pl, h, order, lane, buf0, buf1);
+  } else if constexpr (N1 % 2 == 1) {
+    const LineOp<T> op = make_op<T>(c, pl, h);
+    if (active) reg_deriv_pair<T, N1>(a, sa, b, sb, oa, soa, ob, sob, scale, op, order, lane);
   } else {
     const LineOp<T> op = make_op<T>(c, pl, h);
-    reg_deriv_pair<T, N1>(a, sa, b, sb, oa, soa, ob, sob, scale, op, order, lane);
+    const GramOp<T> gop{c.gramQ, c.gramT + pl.tg_off};
+    tl_deriv_pair<T, 4 * N1>(a, sa, b, sb, oa, soa, ob, sob, scale, op, gop, order, lane & 7, tile, active);
   }
 }
 

@@ -49,17 +49,16 @@ __device__ __forceinline__ int find_patch(const CtxDev& c, long long q) {
 template <typename T>
 __global__ void k_dt(CtxDev c, const T* __restrict__ e, const T* __restrict__ mu, double cfl_d, double cfl_mu_d,
                      unsigned long long* best) {
-  const long long per = c.qstride;
-  const int inst = blockIdx.y;
   const T cfl = T(cfl_d), cfl_mu = T(cfl_mu_d), gam = T(c.gamma), gm1 = T(c.gamma - 1.0);
+  const PatchDev* Pp;
+  const PtIdx x = pt_index(c, &Pp);
+  const PatchDev& P = *Pp;
+  const int inst = x.inst;
   T r_min = T(INFINITY);
-  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < per; q += (long long)gridDim.x * blockDim.x) {
-    const int p = find_patch(c, q);
-    const PatchDev P = c.patches[p];
+  if (x.ok) {
     const long long np = (long long)P.n1 * P.n2;
-    const long long lq = q - P.qoff;
-    if (lq >= np) continue;
-    const T* es = e + inst * c.sstride + P.soff + lq;
+    const long long q = P.qoff + x.lq;
+    const T* es = e + inst * c.sstride + P.soff + x.lq;
     const T rho = es[0], mx = es[np], my = es[2 * np], En = es[3 * np];
     const T pr = pressure<T>(rho, mx, my, En, gm1);
     const T u = mx / rho, v = my / rho;
@@ -80,7 +79,7 @@ __global__ void k_dt(CtxDev c, const T* __restrict__ e, const T* __restrict__ mu
     const T n1 = sqrt(y_q2 * y_q2 + x_q2 * x_q2) / fabs(J), n2 = sqrt(y_q1 * y_q1 + x_q1 * x_q1) / fabs(J);
     T r = cfl * fmin(h1 / (fabs(U1) + cs * n1), h2 / (fabs(U2) + cs * n2));
     if (mu) {
-      const T m = mu[inst * per + q];
+      const T m = mu[inst * c.qstride + q];
       if (m > T(0)) {
         const T s1 = h1 * sqrt(x_q1 * x_q1 + y_q1 * y_q1), s2 = h2 * sqrt(x_q2 * x_q2 + y_q2 * y_q2);
         const T hm = fmin(s1, s2);
@@ -88,7 +87,7 @@ __global__ void k_dt(CtxDev c, const T* __restrict__ e, const T* __restrict__ mu
       }
     }
     if (!(r > T(0))) r = T(0);
-    r_min = fmin(r_min, r);
+    r_min = r;
   }
   // block minimum, then one atomic per block (min of positive doubles = min of their bit patterns)
   double rd = (double)r_min;
@@ -168,14 +167,13 @@ __device__ __forceinline__ void window_point(const CtxDev& c, int4 wd, int t, lo
   *np_ = (long long)P.n1 * P.n2;
 }
 
+// Proxy value t of window wd, read from the precomputed proxy field phi
+// (scalar layout, k_av_speed mode 1).
 template <typename T>
-__device__ __forceinline__ T proxy_at(const CtxDev& c, const T* e, long long inst, int4 wd, int t) {
-  long long so, np;
-  window_point<T>(c, wd, t, &so, &np);
-  const T* es = e + inst * c.sstride + so;
-  const T rho = es[0], mx = es[np], my = es[2 * np], En = es[3 * np];
-  const T p = pressure<T>(rho, mx, my, En, T(c.gamma - 1.0));
-  return sqrt(mx * mx + my * my) / rho * sqrt(rho / (T(c.gamma) * p));
+__device__ __forceinline__ T proxy_at(const CtxDev& c, const T* phi, long long inst, int4 wd, int t) {
+  const PatchDev& P = c.patches[wd.x];
+  const int ji = wd.y == 0 ? wd.z * P.n1 + wd.w + t : (wd.w + t) * P.n1 + wd.z;
+  return phi[inst * c.qstride + P.qoff + ji];
 }
 
 struct MlpW64 {
@@ -384,15 +382,13 @@ __global__ void __launch_bounds__(128) k_mlp_bf16(CtxDev c, const float* __restr
 // Point tau = minimum over the windows (both directions) that cover it.
 __global__ void k_tau_gather(CtxDev c, const signed char* __restrict__ tau_w, signed char* tau) {
   const long long per = c.qstride;
-  const long long total = (long long)c.instances * per;
-  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x) {
-    const long long inst = t / per;
-    const long long q = t % per;
-    const int p = find_patch(c, q);
-    const PatchDev P = c.patches[p];
-    const long long lq = q - P.qoff;
-    if (lq >= (long long)P.n1 * P.n2) continue;
-    const int i = (int)(lq % P.n1), j = (int)(lq / P.n1);
+  const PatchDev* Pp;
+  const PtIdx x = pt_index(c, &Pp);
+  const PatchDev& P = *Pp;
+  {
+    if (!x.ok) return;
+    const long long inst = x.inst, t = inst * per + P.qoff + x.lq;
+    const int i = x.i, j = x.j;
     const signed char* tw = tau_w + inst * c.nwin;
     int best = 4;
     // x-windows of row j: regular windows k with 16k <= i < 16k+16, plus the right-aligned one
@@ -484,32 +480,34 @@ __global__ void k_indicator(CtxDev c, const T* __restrict__ e, signed char* tau_
 
 // ============================================================ viscosity
 // (a) wave speed |u| + c per point
+// mode 0: S = |u| + c;  mode 1: S = Phi = |u| sqrt(rho/(gamma p)) (classifier proxy)
 template <typename T>
-__global__ void k_av_speed(CtxDev c, const T* __restrict__ e, T* S) {
-  const long long per = c.qstride, total = (long long)c.instances * per;
+__global__ void k_av_speed(CtxDev c, const T* __restrict__ e, T* S, int mode) {
   const T gm1 = T(c.gamma - 1.0), gam = T(c.gamma);
-  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x) {
-    const long long inst = t / per, q = t % per;
-    const PatchDev P = c.patches[find_patch(c, q)];
-    const long long np = (long long)P.n1 * P.n2, lq = q - P.qoff;
-    if (lq >= np) continue;
-    const T* es = e + inst * c.sstride + P.soff + lq;
-    const T rho = es[0], mx = es[np], my = es[2 * np], En = es[3 * np];
-    const T p = pressure<T>(rho, mx, my, En, gm1);
-    S[t] = sqrt(mx * mx + my * my) / rho + sqrt(gam * p / rho);
-  }
+  const PatchDev* Pp;
+  const PtIdx x = pt_index(c, &Pp);
+  const PatchDev& P = *Pp;
+  if (!x.ok) return;
+  const long long np = (long long)P.n1 * P.n2;
+  const T* es = e + x.inst * c.sstride + P.soff + x.lq;
+  const T rho = es[0], mx = es[np], my = es[2 * np], En = es[3 * np];
+  const T p = pressure<T>(rho, mx, my, En, gm1);
+  const long long t = x.inst * c.qstride + P.qoff + x.lq;
+  if (mode == 0) S[t] = sqrt(mx * mx + my * my) / rho + sqrt(gam * p / rho);
+  else S[t] = sqrt(mx * mx + my * my) / rho * sqrt(rho / (gam * p));
 }
 
 // (b) preliminary viscosity: c_mu h_max max_{3x3}(S) w(tau), zero on fringes
 template <typename T>
 __global__ void k_av_prelim(CtxDev c, const T* __restrict__ S, const signed char* __restrict__ tau, T cmu, T* M) {
-  const long long per = c.qstride, total = (long long)c.instances * per;
-  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x) {
-    const long long inst = t / per, q = t % per;
-    const PatchDev P = c.patches[find_patch(c, q)];
-    const long long np = (long long)P.n1 * P.n2, lq = q - P.qoff;
-    if (lq >= np) continue;
-    const int i = (int)(lq % P.n1), j = (int)(lq / P.n1);
+  const long long per = c.qstride;
+  const PatchDev* Pp;
+  const PtIdx x = pt_index(c, &Pp);
+  const PatchDev& P = *Pp;
+  {
+    if (!x.ok) return;
+    const long long inst = x.inst, q = P.qoff + x.lq, t = inst * per + q;
+    const int i = x.i, j = x.j;
     const int tv = tau[t];
     T w = tv == 1 ? T(1) : (tv == 2 ? T(0.5) : T(0));
     if (c.fringe[q]) w = T(0);
@@ -533,13 +531,14 @@ __global__ void k_av_prelim(CtxDev c, const T* __restrict__ S, const signed char
 // (c) box maximum of radius r along i (dir 0) or j (dir 1)
 template <typename T>
 __global__ void k_av_boxmax(CtxDev c, const T* __restrict__ in, T* out, int r, int dir) {
-  const long long per = c.qstride, total = (long long)c.instances * per;
-  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x) {
-    const long long inst = t / per, q = t % per;
-    const PatchDev P = c.patches[find_patch(c, q)];
-    const long long np = (long long)P.n1 * P.n2, lq = q - P.qoff;
-    if (lq >= np) continue;
-    const int i = (int)(lq % P.n1), j = (int)(lq / P.n1);
+  const long long per = c.qstride;
+  const PatchDev* Pp;
+  const PtIdx x = pt_index(c, &Pp);
+  const PatchDev& P = *Pp;
+  {
+    if (!x.ok) return;
+    const long long inst = x.inst, t = inst * per + P.qoff + x.lq;
+    const int lq = x.lq, i = x.i, j = x.j;
     const T* ip = in + inst * per + P.qoff;
     T m = ip[lq];
     for (int k = -r; k <= r; ++k) {
@@ -554,13 +553,14 @@ __global__ void k_av_boxmax(CtxDev c, const T* __restrict__ in, T* out, int r, i
 // (d) normalised bump average of radius r, b(x) = exp(1 - 1/(1 - x^2)), x = k/(r+1)
 template <typename T>
 __global__ void k_av_bump(CtxDev c, const T* __restrict__ in, T* out, const double* __restrict__ bw, int r, int dir) {
-  const long long per = c.qstride, total = (long long)c.instances * per;
-  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x) {
-    const long long inst = t / per, q = t % per;
-    const PatchDev P = c.patches[find_patch(c, q)];
-    const long long np = (long long)P.n1 * P.n2, lq = q - P.qoff;
-    if (lq >= np) continue;
-    const int i = (int)(lq % P.n1), j = (int)(lq / P.n1);
+  const long long per = c.qstride;
+  const PatchDev* Pp;
+  const PtIdx x = pt_index(c, &Pp);
+  const PatchDev& P = *Pp;
+  {
+    if (!x.ok) return;
+    const long long inst = x.inst, t = inst * per + P.qoff + x.lq;
+    const int i = x.i, j = x.j;
     const T* ip = in + inst * per + P.qoff;
     T num = 0, den = 0;
     for (int k = -r; k <= r; ++k) {

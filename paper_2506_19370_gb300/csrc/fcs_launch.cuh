@@ -22,22 +22,25 @@ struct StageArgs {
   T* out;
 };
 
-// Per-warp shared bytes of the line kernels: `lines` real lines of nmax values
-// plus, when some plan uses it, the two complex buffers of the Stockham FFT.
-template <typename T>
-__host__ __device__ inline size_t warp_line_bytes(int lines, int nmax, int nfmax, int stockham) {
-  size_t r = (size_t)lines * nmax * sizeof(T);
-  r = (r + 15) & ~size_t(15);
-  return r + (stockham ? (size_t)2 * nfmax * sizeof(Cx<T>) : 0);
+// Shared-memory layout helpers of the line kernels (host and device agree).
+// aux: per warp, the Stockham buffers (N1 = 0), nothing (32-lane FFT, odd N1)
+// or four transpose tiles 8 x (B+1), B = 4 N1 (two-level FFT, even N1).
+__host__ __device__ inline size_t aux_cx(int N1, int nfmax) {
+  return N1 == 0 ? (size_t)2 * nfmax : (N1 % 2 ? 0 : (size_t)32 * (4 * N1 + 1));
 }
-
-// Shared bytes of the column pass: E and D tiles [4][n2max][tw+1], mu tile
-// [n2max][tw+1], Stockham buffers of every warp.
+__host__ __device__ inline size_t align16(size_t r) { return (r + 15) & ~size_t(15); }
+constexpr int kRowsPerWarp = 2;  // rows a warp of the pass along q1 handles together
 template <typename T>
-__host__ __device__ inline size_t ypass_bytes(int n2max, int tw, int nfmax, int stockham, int warps) {
-  size_t r = (size_t)9 * n2max * (tw + 1) * sizeof(T);
-  r = (r + 15) & ~size_t(15);
-  return r + (stockham ? (size_t)warps * 2 * nfmax * sizeof(Cx<T>) : 0);
+__host__ __device__ inline size_t xpass_warp_bytes(int nmax, int nfmax, int N1) {
+  return align16((size_t)kRowsPerWarp * 9 * nmax * sizeof(T)) + aux_cx(N1, nfmax) * 2 * sizeof(T);
+}
+template <typename T>
+__host__ __device__ inline size_t deriv_warp_bytes(int nmax, int nfmax, int N1) {
+  return align16((size_t)8 * nmax * sizeof(T)) + aux_cx(N1, nfmax) * 2 * sizeof(T);
+}
+template <typename T>
+__host__ __device__ inline size_t ypass_bytes(int n2max, int tw, int nfmax, int N1, int warps) {
+  return align16((size_t)9 * n2max * (tw + 1) * sizeof(T)) + (size_t)warps * aux_cx(N1, nfmax) * 2 * sizeof(T);
 }
 constexpr int kYWarps = 8;
 

@@ -9,42 +9,58 @@
 namespace fcs {
 
 // ============================================================ FC derivative
-// One warp per pair of lines of one patch (two real lines -> one complex FFT).
+// FC derivative of a scalar field: each warp takes jobs_per_round(N1) line
+// pairs at a time (two real lines -> one complex FFT).
 template <typename T, int N1>
 __global__ void __launch_bounds__(kWarps * 32) k_fc_deriv(CtxDev c, int dir, int order, const int4* __restrict__ pairs,
                                                            int npairs, const T* __restrict__ in, T* __restrict__ out) {
+  constexpr int JPR = jobs_per_round(N1);
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  unsigned char* base = smem_raw + (size_t)warp * warp_line_bytes<T>(2, c.nmax, c.nfmax, N1 == 0);
-  T* A = reinterpret_cast<T*>(base);
-  T* B = A + c.nmax;
-  Cx<T>* b0 = reinterpret_cast<Cx<T>*>(base + (((size_t)2 * c.nmax * sizeof(T) + 15) & ~size_t(15)));
-  Cx<T>* b1 = b0 + c.nfmax;
+  const int nmax = c.nmax;
+  unsigned char* base = smem_raw + (size_t)warp * deriv_warp_bytes<T>(nmax, c.nfmax, N1);
+  T* L = reinterpret_cast<T*>(base);  // [JPR][2][nmax]
+  Cx<T>* aux = reinterpret_cast<Cx<T>*>(base + align16((size_t)8 * nmax * sizeof(T)));
+  const int g = JPR == 4 ? (lane >> 3) : 0;
+  Cx<T>* tile = aux + (size_t)g * 8 * (4 * N1 + 1);
   const long long total = (long long)c.instances * npairs;
-  for (long long w = (long long)blockIdx.x * kWarps + warp; w < total; w += (long long)gridDim.x * kWarps) {
-    const int inst = (int)(w / npairs);
-    const int4 pr = pairs[w % npairs];
-    const PatchDev P = c.patches[pr.x];
-    const PlanDev pl = c.plans[P.plan[dir]];
-    const int N = pl.N;
+  const long long rounds = (total + JPR - 1) / JPR;
+  for (long long r = (long long)blockIdx.x * kWarps + warp; r < rounds; r += (long long)gridDim.x * kWarps) {
+    // stage the JPR line pairs of this round
+    for (int k = 0; k < JPR; ++k) {
+      const long long w = r * JPR + k;
+      if (w >= total) break;
+      const int inst = (int)(w / npairs);
+      const int4 pr = pairs[w % npairs];
+      const PatchDev& P = c.patches[pr.x];
+      const int N = c.plans[P.plan[dir]].N;
+      const long long stride = dir == 0 ? 1 : P.n1;
+      const long long la = dir == 0 ? (long long)pr.y * P.n1 : pr.y;
+      const long long lb = pr.z < 0 ? -1 : (dir == 0 ? (long long)pr.z * P.n1 : pr.z);
+      const T* src = in + inst * c.qstride + P.qoff;
+      for (int t = lane; t < N; t += 32) {
+        L[(2 * k) * nmax + t] = src[la + t * stride];
+        L[(2 * k + 1) * nmax + t] = lb >= 0 ? src[lb + t * stride] : T(0);
+      }
+    }
+    __syncwarp();
+    const long long w = r * JPR + g;
+    const bool active = w < total;
+    const long long wc = active ? w : r * JPR;
+    const int inst = (int)(wc / npairs);
+    const int4 pr = pairs[wc % npairs];
+    const PatchDev& P = c.patches[pr.x];
+    const PlanDev& pl = c.plans[P.plan[dir]];
     const long long stride = dir == 0 ? 1 : P.n1;
     const long long la = dir == 0 ? (long long)pr.y * P.n1 : pr.y;
     const long long lb = pr.z < 0 ? -1 : (dir == 0 ? (long long)pr.z * P.n1 : pr.z);
-    const T* src = in + inst * c.qstride + P.qoff;
     T* dst = out + inst * c.qstride + P.qoff;
-    for (int t = lane; t < N; t += 32) {
-      A[t] = src[la + t * stride];
-      B[t] = lb >= 0 ? src[lb + t * stride] : T(0);
-    }
-    __syncwarp();
-    const T h = T(1) / T(N - 1);
-    line_deriv_pair<T, N1>(A, 1, lb >= 0 ? B : nullptr, 1, dst + la, (int)stride, lb >= 0 ? dst + lb : nullptr, (int)stride,
-                       T(1), c, pl, h, order, lane, b0, b1);
+    line_deriv_pair<T, N1>(L + (2 * g) * nmax, 1, lb >= 0 ? L + (2 * g + 1) * nmax : nullptr, 1, dst + la, (int)stride,
+                           lb >= 0 ? dst + lb : nullptr, (int)stride, T(1), c, pl, T(1) / T(pl.N - 1), order, lane, aux,
+                           aux + c.nfmax, tile, active);
     __syncwarp();
   }
 }
-
-// ============================================================ Euler operator
 
 // Apply the boundary conditions of the sides the point lies on, in the order
 // left, right, bottom, top (paper §5 item 4: enforced at every stage).
@@ -127,60 +143,98 @@ __device__ __forceinline__ void point_flux(const CtxDev& c, const PatchDev& P, l
   }
 }
 
-// Pass along q1 (rows): R = -d/dq1 F1, one warp per row (rows are contiguous).
+// Pass along q1 (rows): R = -d/dq1 F1; a warp takes kRowsPerWarp rows of one
+// patch (rows are contiguous).  Jobs of a phase: (row, field pair); phase 0
+// (viscous only) W = d e/dx, phase 1 R = -d F/dx with F formed in W.
 template <typename T, int N1>
 __global__ void __launch_bounds__(kWarps * 32) k_xpass(CtxDev c, const T* __restrict__ e, const T* __restrict__ mu,
                                                         T* __restrict__ R) {
+  constexpr int JPR = jobs_per_round(N1);
+  constexpr int RW = kRowsPerWarp;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nmax = c.nmax;
-  unsigned char* base = smem_raw + (size_t)warp * warp_line_bytes<T>(9, nmax, c.nfmax, N1 == 0);
-  T* E = reinterpret_cast<T*>(base);
-  T* W = E + 4 * nmax;
-  T* M = W + 4 * nmax;
-  Cx<T>* b0 = reinterpret_cast<Cx<T>*>(base + (((size_t)9 * nmax * sizeof(T) + 15) & ~size_t(15)));
-  Cx<T>* b1 = b0 + c.nfmax;
-  const long long total = (long long)c.instances * c.nlines0;
+  unsigned char* base = smem_raw + (size_t)warp * xpass_warp_bytes<T>(nmax, c.nfmax, N1);
+  T* E = reinterpret_cast<T*>(base);   // [RW][4][nmax]
+  T* W = E + RW * 4 * nmax;            // [RW][4][nmax]
+  T* M = W + RW * 4 * nmax;            // [RW][nmax]
+  Cx<T>* aux = reinterpret_cast<Cx<T>*>(base + align16((size_t)RW * 9 * nmax * sizeof(T)));
+  const int g = JPR == 4 ? (lane >> 3) : 0;
+  Cx<T>* tile = aux + (size_t)g * 8 * (4 * N1 + 1);
+  const long long groups = ((long long)c.nlines0 + RW - 1) / RW;   // row groups per instance (rows of one
+  const long long total = (long long)c.instances * groups;          // patch are contiguous in lines0)
   for (long long w = (long long)blockIdx.x * kWarps + warp; w < total; w += (long long)gridDim.x * kWarps) {
-    const int inst = (int)(w / c.nlines0);
-    const LineRef lr = c.lines0[w % c.nlines0];
-    const PatchDev P = c.patches[lr.patch];
-    const PlanDev pl = c.plans[P.plan[0]];
-    const int N = pl.N;
-    const long long np = (long long)P.n1 * P.n2;
-    const long long l0 = (long long)lr.line * P.n1;
-    const T* es = e + inst * c.sstride + P.soff + l0;
-    const T h = T(P.hx);
-    const bool visc = (mu != nullptr) && P.cart;
-    for (int t = lane; t < N; t += 32) {
+    const int inst = (int)(w / groups);
+    const int l0 = (int)(w % groups) * RW;
+    int pid[RW], row[RW];
+    bool has[RW];
 #pragma unroll
-      for (int f = 0; f < 4; ++f) E[f * nmax + t] = es[f * np + t];
-      if (visc) M[t] = mu[inst * c.qstride + P.qoff + l0 + t];
+    for (int k = 0; k < RW; ++k) {
+      has[k] = l0 + k < c.nlines0;
+      const LineRef lr = c.lines0[has[k] ? l0 + k : l0];
+      pid[k] = lr.patch;
+      row[k] = lr.line;
+      const PatchDev& P = c.patches[lr.patch];
+      const long long np = (long long)P.n1 * P.n2;
+      const T* es = e + inst * c.sstride + P.soff + (long long)lr.line * P.n1;
+      const bool visc = (mu != nullptr) && P.cart;
+      if (has[k])
+        for (int t = lane; t < P.n1; t += 32) {
+#pragma unroll
+          for (int f = 0; f < 4; ++f) E[(k * 4 + f) * nmax + t] = es[f * np + t];
+          if (visc) M[k * nmax + t] = mu[inst * c.qstride + P.qoff + (long long)lr.line * P.n1 + t];
+        }
     }
     __syncwarp();
-    T* Rs = R + inst * c.sstride + P.soff + l0;
-    // jobs 0,1: W = d e/dx (viscous part, field pairs); jobs 2,3: R = -d F/dx
-    for (int job = visc ? 0 : 2; job < 4; ++job) {
-      if (job == 2) {
-        for (int t = lane; t < N; t += 32) {
-          T v[4], dv[4], F[4];
+    const bool visc_any = mu != nullptr;
+    for (int phase = visc_any ? 0 : 1; phase < 2; ++phase) {
+      if (phase == 1) {
 #pragma unroll
-          for (int f = 0; f < 4; ++f) {
-            v[f] = E[f * nmax + t];
-            dv[f] = visc ? W[f * nmax + t] : T(0);
+        for (int k = 0; k < RW; ++k) {
+          if (!has[k]) continue;
+          const PatchDev& P = c.patches[pid[k]];
+          const bool visc = (mu != nullptr) && P.cart;
+          const long long q0 = P.qoff + (long long)row[k] * P.n1;
+          for (int t = lane; t < P.n1; t += 32) {
+            T v[4], dv[4], F[4];
+#pragma unroll
+            for (int f = 0; f < 4; ++f) {
+              v[f] = E[(k * 4 + f) * nmax + t];
+              dv[f] = visc ? W[(k * 4 + f) * nmax + t] : T(0);
+            }
+            point_flux<T, 0>(c, P, q0 + t, v, dv, visc ? M[k * nmax + t] : T(0), visc, F);
+#pragma unroll
+            for (int f = 0; f < 4; ++f) W[(k * 4 + f) * nmax + t] = F[f];
           }
-          point_flux<T, 0>(c, P, P.qoff + l0 + t, v, dv, visc ? M[t] : T(0), visc, F);
-#pragma unroll
-          for (int f = 0; f < 4; ++f) W[f * nmax + t] = F[f];
         }
         __syncwarp();
       }
-      const int pr = job & 1;
-      const T* src = job < 2 ? E : W;
-      T* oa = job < 2 ? W + 2 * pr * nmax : Rs + 2 * pr * np;
-      T* ob = job < 2 ? W + (2 * pr + 1) * nmax : Rs + (2 * pr + 1) * np;
-      line_deriv_pair<T, N1>(src + 2 * pr * nmax, 1, src + (2 * pr + 1) * nmax, 1, oa, 1, ob, 1, job < 2 ? T(1) : T(-1), c,
-                         pl, h, 1, lane, b0, b1);
+      // jobs: (row k, field pair pr), 2 RW of them (row data chosen by
+      // selects, not by indexing, so the small per-row arrays stay in registers)
+      static_assert(RW == 2, "row selection below assumes two rows per warp");
+      for (int r0 = 0; r0 < 2 * RW; r0 += JPR) {
+        const int job = r0 + g;
+        const int k = job >> 1, pr = job & 1;
+        const int kk = k == 1 ? 1 : 0;
+        const int pidk = kk ? pid[1] : pid[0], rowk = kk ? row[1] : row[0];
+        bool active = job < 2 * RW && (kk ? has[1] : has[0]);
+        const PatchDev& P = c.patches[pidk];
+        const PlanDev& pl = c.plans[P.plan[0]];
+        if (phase == 0 && !((mu != nullptr) && P.cart)) active = false;
+        const long long np = (long long)P.n1 * P.n2;
+        const T* src = (phase == 0 ? E : W) + (kk * 4 + 2 * pr) * nmax;
+        T* oa;
+        T* ob;
+        if (phase == 0) {
+          oa = W + (kk * 4 + 2 * pr) * nmax;
+          ob = oa + nmax;
+        } else {
+          oa = R + inst * c.sstride + P.soff + (long long)rowk * P.n1 + (2 * pr) * np;
+          ob = oa + np;
+        }
+        line_deriv_pair<T, N1>(src, 1, src + nmax, 1, oa, 1, ob, 1, phase == 0 ? T(1) : T(-1), c, pl, T(P.hx), 1, lane,
+                               aux, aux + c.nfmax, tile, active);
+      }
       __syncwarp();
     }
   }
@@ -193,15 +247,17 @@ template <typename T, int MODE, int N1>
 __global__ void __launch_bounds__(kYWarps * 32) k_ypass(CtxDev c, const int2* __restrict__ tiles, int ntiles,
                                                          const T* __restrict__ e, const T* __restrict__ mu,
                                                          const T* __restrict__ R, StageArgs<T> st) {
+  constexpr int JPR = jobs_per_round(N1);
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int tw = c.tw, ld = c.tw + 1, n2m = c.n2max;
   T* E = reinterpret_cast<T*>(smem_raw);           // [4][n2m][ld]
   T* D = E + 4 * n2m * ld;                         // [4][n2m][ld]
   T* M = D + 4 * n2m * ld;                         // [n2m][ld]
-  Cx<T>* b0 = reinterpret_cast<Cx<T>*>(smem_raw + (((size_t)9 * n2m * ld * sizeof(T) + 15) & ~size_t(15))) +
-              (size_t)warp * 2 * c.nfmax;
-  Cx<T>* b1 = b0 + c.nfmax;
+  Cx<T>* aux = reinterpret_cast<Cx<T>*>(smem_raw + align16((size_t)9 * n2m * ld * sizeof(T))) +
+               (size_t)warp * aux_cx(N1, c.nfmax);
+  const int g = JPR == 4 ? (lane >> 3) : 0;
+  Cx<T>* tile = aux + (size_t)g * 8 * (4 * N1 + 1);
   const T gm1 = T(c.gamma - 1.0);
   const long long total = (long long)c.instances * ntiles;
   for (long long wk = blockIdx.x; wk < total; wk += gridDim.x) {
@@ -215,23 +271,21 @@ __global__ void __launch_bounds__(kYWarps * 32) k_ypass(CtxDev c, const int2* __
     const long long sbase = inst * c.sstride + P.soff + c0;
     const long long qbase = P.qoff + c0;
     const bool visc = (mu != nullptr) && P.cart;
-    for (int k = threadIdx.x; k < 4 * N * tw; k += blockDim.x) {
-      const int cc = k % tw, j = (k / tw) % N, f = k / (tw * N);
-      if (cc < width) E[(f * n2m + j) * ld + cc] = e[sbase + f * np + (long long)j * P.n1 + cc];
-    }
-    if (visc)
-      for (int k = threadIdx.x; k < N * tw; k += blockDim.x) {
-        const int cc = k % tw, j = k / tw;
-        if (cc < width) M[j * ld + cc] = mu[inst * c.qstride + qbase + (long long)j * P.n1 + cc];
+    // each thread keeps one column cc of the tile and strides over rows
+    const int cc = threadIdx.x % tw, jr = threadIdx.x / tw, js = blockDim.x / tw;
+    const bool colok = cc < width && jr < js;
+    if (colok)
+      for (int j = jr; j < N; j += js) {
+#pragma unroll
+        for (int f = 0; f < 4; ++f) E[(f * n2m + j) * ld + cc] = e[sbase + f * np + (long long)j * P.n1 + cc];
+        if (visc) M[j * ld + cc] = mu[inst * c.qstride + qbase + (long long)j * P.n1 + cc];
       }
     __syncthreads();
     const T h = T(P.hy);
     // phase 0 (viscous): D = d e/dy; phase 1: E = d F2/dq2 with F2 formed in D
     for (int phase = visc ? 0 : 1; phase < 2; ++phase) {
       if (phase == 1) {
-        for (int k = threadIdx.x; k < N * tw; k += blockDim.x) {
-          const int cc = k % tw, j = k / tw;
-          if (cc >= width) continue;
+        for (int j = jr; colok && j < N; j += js) {
           T v[4], dv[4], F[4];
 #pragma unroll
           for (int f = 0; f < 4; ++f) {
@@ -246,18 +300,19 @@ __global__ void __launch_bounds__(kYWarps * 32) k_ypass(CtxDev c, const int2* __
       }
       const T* src = phase == 0 ? E : D;
       T* dst = phase == 0 ? D : E;
-      for (int u = warp; u < 2 * width; u += kYWarps) {
-        const int cc = u >> 1, pr = u & 1;
+      // jobs (column, field pair): 2 width of them, JPR per warp and round
+      for (int u0 = warp * JPR; u0 < 2 * width; u0 += kYWarps * JPR) {
+        const int u = u0 + g;
+        const bool active = u < 2 * width;
+        const int cc = active ? (u >> 1) : 0, pr = u & 1;
         line_deriv_pair<T, N1>(src + (2 * pr) * n2m * ld + cc, ld, src + (2 * pr + 1) * n2m * ld + cc, ld,
-                           dst + (2 * pr) * n2m * ld + cc, ld, dst + (2 * pr + 1) * n2m * ld + cc, ld, T(1), c, pl, h,
-                           1, lane, b0, b1);
+                               dst + (2 * pr) * n2m * ld + cc, ld, dst + (2 * pr + 1) * n2m * ld + cc, ld, T(1), c, pl,
+                               h, 1, lane, aux, aux + c.nfmax, tile, active);
       }
       __syncthreads();
     }
     const T dtv = st.dt_dev ? T(st.dt_dev[inst]) : st.dt;
-    for (int k = threadIdx.x; k < N * tw; k += blockDim.x) {
-      const int cc = k % tw, j = k / tw;
-      if (cc >= width) continue;
+    for (int j = jr; colok && j < N; j += js) {
       const long long off = sbase + (long long)j * P.n1 + cc;
       const long long q = qbase + (long long)j * P.n1 + cc;
       const T invJ = P.cart ? T(1) : T(1) / metrics<T>(c)[4 * c.qstride + q];
