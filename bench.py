@@ -52,7 +52,8 @@ def config(args, points):
                         f"instance, x {args.instances} independent instances; SDNN classifier + artificial "
                         f"viscosity + CFL dt + 4 RK stages + exchange per step",
             "instances": args.instances, "points_per_instance": points // args.instances, "points": points,
-            "d": 5, "C": "25, raised per line to a 7-smooth FFT length (185->189, 65->70)",
+            "d": 5, "C": "25 requested; FFT-length policy gives 32 on 160-point rows (n = 192) and 24 on 40-point "
+                         "columns (n = 64)",
             "classifier": "16-32-32-4 MLP, seeded weights", "l2": "flushed (256 MiB write) between timed steps",
             "parallelism": f"replicas x{args.gpus}" if args.gpus > 1 else "1 GPU"}
 
@@ -173,14 +174,15 @@ def measured_peak():
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("fcs_device.cuh", "fcs_kernels.cuh"):
+    for f in ("fcs_device.cuh", "fcs_line_kernels.cuh", "fcs_launch.cuh", "fcs_roots.cuh"):
         h.update(open(os.path.join(ROOT, "paper_2506_19370_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
 
 def recorded_traffic(per_launch_points):
-    """DRAM bytes per launch of the stage operator from the committed ncu summary,
-    scaled to this launch's points; None if the kernels changed since."""
+    """DRAM bytes per launch of the stage operator (both flux passes) from the
+    committed ncu capture, scaled to this launch's points; None if the kernel
+    sources changed since the capture."""
     p = os.path.join(ROOT, "profiles", "rk_stage_traffic.json")
     try:
         d = json.load(open(p))
@@ -238,7 +240,7 @@ def run_ours(args):
         ctx.classify(e, tau, None, stream)
         ctx.av_assemble(e, tau, mu, stream)
         ctx.time_step(e, dtd, mu, stream)
-        launches["n"] += 2 + 7 + 3
+        launches["n"] += 3 + 7 + 3   # proxy, MLP, tau gather; 6 viscosity kernels + exchange; dt init/min/final
         for s in range(4):
             es = e if s == 0 else S
             out = e if s == 3 else S
@@ -303,16 +305,28 @@ def run_ours(args):
     e2e_val = world * points * 4 * n_e2e / (e2e_ms / 1000.0)
     nbytes = e.numel() * e.element_size()
 
-    # roofline of the stage operator (flux passes + stage update): algorithmic
-    # bytes per point-stage averaged over the 4 stages (state reads/writes,
-    # accumulator, viscosity), see the design notes
-    ts = 8 if dtype == fcsdnn.F64 else 4
-    # elements per point: stage 0 reads e_n, writes acc and out (12); stages 1-2
-    # read e_s, e_n, acc, write acc, out (20); stage 3 reads e_s, acc, writes
-    # out (12); every stage reads mu (1): mean 17 elements per point-stage
-    alg_bytes_pt = ts * 17
+    # roofline of the stage operator rk_stage (flux pass along q1 + flux pass
+    # along q2 with the stage update: two launches sharing the partial
+    # operator through L2).  Bound: ALU issue (counters: DRAM 1-3 %, SM 25 %).
+    # Algorithmic FLOPs per point-stage: 16 line derivatives (8 viscous, 8 of
+    # the fluxes) of [10 n log2 n (FFT pair) + 2 n (i k) + 8 d C (both
+    # continuations)] / (2 N) each, plus ~70 pointwise (fluxes, viscous flux,
+    # stage update); peak = 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz.
+    import math
+    def per_point(N, n, C, d=5):
+        return (10 * n * math.log2(n) + 2 * n + 8 * d * C) / (2 * N)
+    flops_pt = 8 * per_point(160, 192, 32) + 8 * per_point(40, 64, 24) + 70
     stage_avg_ms = sum(stage_ms) / len(stage_ms)
-    achieved = alg_bytes_pt * points / (stage_avg_ms / 1000.0) / 1e9
+    achieved_tf = flops_pt * points / (stage_avg_ms / 1000.0) / 1e12
+    alu_peak = 152 * 128 * 2 * 2.07e9 / 1e12
+    if dtype == fcsdnn.F64:
+        alu_peak /= 64.0   # GB300 FP64 vector rate (1/64 of FP32), see the design notes
+    ts = 8 if dtype == fcsdnn.F64 else 4
+    # minimum state traffic per point-stage (elements): stage 0 reads e_n, writes
+    # acc and out (12); stages 1-2 read e_s, e_n, acc, write acc, out (20); stage 3
+    # reads e_s, acc, writes out (12); every stage reads mu (1): mean 17
+    alg_bytes_pt = ts * 17
+    hbm_gbs = alg_bytes_pt * points / (stage_avg_ms / 1000.0) / 1e9
     peak, peak_kind = measured_peak()
     traffic = recorded_traffic(points)
     if rank == 0:
@@ -323,10 +337,14 @@ def run_ours(args):
                 "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
                         "note": "pinned host state -> device, one graph-captured step, state -> host"},
                 "gpu_launches": launches["n"],
-                "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                             "frac": achieved / peak, "traffic": traffic, "peak_source": peak_kind,
+                "roofline": {"bound": "alu", "achieved": achieved_tf, "peak": alu_peak, "unit": "TFLOP/s",
+                             "frac": achieved_tf / alu_peak, "traffic": traffic,
+                             "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz"
+                                            + (" / 64 (FP64)" if dtype == fcsdnn.F64 else ""),
                              "kernel": "rk_stage (flux pass along q1 + flux pass along q2 with stage update)",
-                             "alg_bytes_per_point_stage": alg_bytes_pt, "stage_ms": stage_avg_ms},
+                             "alg_flops_per_point_stage": flops_pt, "stage_ms": stage_avg_ms,
+                             "hbm_context": {"alg_bytes_per_point_stage": alg_bytes_pt, "achieved_gbs": hbm_gbs,
+                                             "peak_gbs": peak, "frac": hbm_gbs / peak, "peak_source": peak_kind}},
                 "clocks": clocks, "status": rc}
         if not args.no_cpu_baseline and world == 1:
             line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)

@@ -147,7 +147,7 @@ __device__ __forceinline__ void point_flux(const CtxDev& c, const PatchDev& P, l
 // patch (rows are contiguous).  Jobs of a phase: (row, field pair); phase 0
 // (viscous only) W = d e/dx, phase 1 R = -d F/dx with F formed in W.
 template <typename T, int N1>
-__global__ void __launch_bounds__(kWarps * 32) k_xpass(CtxDev c, const T* __restrict__ e, const T* __restrict__ mu,
+__global__ void __launch_bounds__(kWarps * 32, 4) k_xpass(CtxDev c, const T* __restrict__ e, const T* __restrict__ mu,
                                                         T* __restrict__ R) {
   constexpr int JPR = jobs_per_round(N1);
   constexpr int RW = kRowsPerWarp;
@@ -244,7 +244,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_xpass(CtxDev c, const T* __rest
 // segments staged in shared memory): L = (R - d/dq2 F2)/J, then either L
 // (MODE_RHS) or the Runge-Kutta stage with boundary conditions (MODE_RK).
 template <typename T, int MODE, int N1>
-__global__ void __launch_bounds__(kYWarps * 32) k_ypass(CtxDev c, const int2* __restrict__ tiles, int ntiles,
+__global__ void __launch_bounds__(kYWarps * 32, 3) k_ypass(CtxDev c, const int2* __restrict__ tiles, int ntiles,
                                                          const T* __restrict__ e, const T* __restrict__ mu,
                                                          const T* __restrict__ R, StageArgs<T> st) {
   constexpr int JPR = jobs_per_round(N1);
