@@ -193,6 +193,20 @@ def recorded_traffic(per_launch_points):
     return d["dram_bytes_per_point_stage"] * per_launch_points
 
 
+# ---------------------------------------------------------------- ranks
+def job_throughput(total_ms, points_per_rank, stages, steps, world, dist=None):
+    """Whole-job pt-stage/s: all ranks' points over the slowest rank's time
+    (max over ranks; replicas, no data-path collective)."""
+    import torch
+    t = torch.tensor([float(total_ms)], dtype=torch.float64)
+    if world > 1 and dist is not None:
+        if dist.get_backend() == "nccl":
+            t = t.cuda()
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    slowest = float(t.item())
+    return world * points_per_rank * stages * steps / (slowest / 1000.0), slowest
+
+
 # ---------------------------------------------------------------- GPU arm
 def run_ours(args):
     import numpy as np
@@ -206,6 +220,7 @@ def run_ours(args):
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if world > 1:
         dist.init_process_group("nccl")
+        dist.barrier()
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     dtype = fcsdnn.F64 if args.dtype == "f64" else fcsdnn.F32
@@ -278,12 +293,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     clocks = clk.stop()
     rc, flags = ctx.status()
-    total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = t.item()
-    value = world * points * 4 * args.steps / (total_ms / 1000.0)
+    value, total_ms = job_throughput(sum(step_ms), points, 4, args.steps, world, dist if world > 1 else None)
 
     # end to end through the C ABI: pinned host state in, step (graph), state out
     pinned = torch.from_numpy(host).pin_memory()
@@ -302,7 +312,7 @@ def run_ours(args):
             stream.synchronize()
             e2e_ms += 1000.0 * (time.perf_counter() - t0)
     n_e2e = max(3, args.steps // 2)
-    e2e_val = world * points * 4 * n_e2e / (e2e_ms / 1000.0)
+    e2e_val, _ = job_throughput(e2e_ms, points, 4, n_e2e, world, dist if world > 1 else None)
     nbytes = e.numel() * e.element_size()
 
     # roofline of the stage operator rk_stage (flux pass along q1 + flux pass

@@ -171,10 +171,10 @@ int patch_exchange(fcs_ctx* ctx, void* field_dev, int nfields, void* stream);
 
 /* Per-instance time step (Algorithm 1, the step-size evaluation; formula of
  * Part I (31) read as the CFL condition): dt = min over points of
- * min(cfl * min_k h_k / (|U_k| + c |grad q_k|), 0.25 h_min^2 / mu), U_k the
- * contravariant velocity, h_k the parameter spacing, h_min the smaller
- * physical spacing; mu_dev (scalar layout) may be NULL (no viscous limit).
- * Writes dt_dev (instances doubles). */
+ * 1 / (1/dt_a + 1/dt_v), dt_a = cfl * min_k h_k / (|U_k| + c |grad q_k|),
+ * dt_v = 0.2 / (mu (1/s_1^2 + 1/s_2^2)); U_k the contravariant velocity, h_k
+ * the parameter spacing, s_k the physical spacing along q_k; mu_dev (scalar
+ * layout) may be NULL (no viscous limit).  Writes dt_dev (instances doubles). */
 int fcs_time_step(fcs_ctx* ctx, const void* e_dev, const void* mu_dev, double* dt_dev, void* stream);
 
 /* Per instance and patch, FP64 sums of each conserved field with the FC

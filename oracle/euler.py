@@ -15,17 +15,21 @@ Follows:
     L(e) = -(df/dx + dg/dy) with FC derivatives at the physical spacings;
   * artificial viscosity term (reading; the paper's form is in Part I):
     d_t e + div f = div(mu grad e), folded into the fluxes as
-    f - mu de/dx, g - mu de/dy (Cartesian patches);
+    f - mu de/dx, g - mu de/dy (Cartesian patches); the normal viscous flux is
+    zero on wall, outflow and free sides (impermeable, adiabatic for the
+    diffusion term: the parabolic term needs a condition on every variable);
   * §5 item 4 / Algorithm 1: explicit four-stage Runge-Kutta (classical RK4
     coefficients, reading of "SSPRK-4"), boundary conditions enforced after
     every stage, exchange of fringe values after every stage;
   * §3.3: n_f-point fringes of internal sides receive values from donor points
     of other patches that are not themselves receivers; coincident grids copy;
-  * Δt (reading of I-(31)): min over points of
-        min( CFL h_k / (|U_k| + c |grad q_k|),  CFL_MU h_min^2 / mu )
-    with U_k the contravariant velocity along parameter direction k, h_k the
-    parameter spacing, h_min the smaller physical spacing and CFL_MU = 0.25
-    (the viscous limit keeps mu dt (pi/h)^2 inside the RK4 stability region).
+  * Δt (reading of I-(31)): min over points of 1 / (1/dt_a + 1/dt_v) with
+        dt_a = CFL min_k h_k / (|U_k| + c |grad q_k|),
+        dt_v = CFL_MU / (mu (1/s_1^2 + 1/s_2^2))   (only where mu > 0),
+    U_k the contravariant velocity along parameter direction k, h_k the
+    parameter spacing, s_k the physical spacing along q_k and CFL_MU = 0.2: the
+    FC diffusion operator has eigenvalues down to about -9.5/s^2 per direction,
+    and RK4 is stable on the negative real axis down to -2.78.
 """
 import numpy as np
 
@@ -87,8 +91,20 @@ def rhs(e, geom, d, C, gamma, mu=None):
     C1, C2 = geom.C1, geom.C2
     if geom.patch.cartesian:
         if mu is not None:
-            f = f - mu * fcgram.fc_derivative_axis(e, geom.hx, d, C1, axis=2)
-            g = g - mu * fcgram.fc_derivative_axis(e, geom.hy, d, C2, axis=1)
+            vf = mu * fcgram.fc_derivative_axis(e, geom.hx, d, C1, axis=2)
+            vg = mu * fcgram.fc_derivative_axis(e, geom.hy, d, C2, axis=1)
+            noflux = (I.BC_WALL, I.BC_OUTFLOW, I.BC_FREE)
+            bc = geom.patch.bc
+            if bc[0] in noflux:
+                vf[:, :, 0] = 0.0
+            if bc[1] in noflux:
+                vf[:, :, -1] = 0.0
+            if bc[2] in noflux:
+                vg[:, 0, :] = 0.0
+            if bc[3] in noflux:
+                vg[:, -1, :] = 0.0
+            f = f - vf
+            g = g - vg
         return -(fcgram.fc_derivative_axis(f, geom.hx, d, C1, axis=2)
                  + fcgram.fc_derivative_axis(g, geom.hy, d, C2, axis=1))
     if mu is not None:
@@ -206,11 +222,11 @@ def exchange(state, fmap):
     return state
 
 
-CFL_MU = 0.25
+CFL_MU = 0.2
 
 
 def time_step(state, geoms, gamma, cfl, mu=None):
-    """Δt = min over all points of min(CFL min_k h_k/(|U_k| + c|grad q_k|), CFL_MU h_min^2/mu)."""
+    """Δt = min over points of 1/(1/dt_a + 1/dt_v) (advective and viscous limits)."""
     best = np.inf
     for k, (e, g) in enumerate(zip(state, geoms)):
         rho, mx, my, E = e
@@ -225,10 +241,8 @@ def time_step(state, geoms, gamma, cfl, mu=None):
         if mu is not None:
             s1 = g.h1 * np.sqrt(g.x_q1 ** 2 + g.y_q1 ** 2)
             s2 = g.h2 * np.sqrt(g.x_q2 ** 2 + g.y_q2 ** 2)
-            hmin = np.minimum(s1, s2)
-            with np.errstate(divide="ignore"):
-                visc = np.where(mu[k] > 0, CFL_MU * hmin * hmin / np.where(mu[k] > 0, mu[k], 1.0), np.inf)
-            adv = np.minimum(adv, visc)
+            # 1/dt = 1/dt_a + mu (1/s1^2 + 1/s2^2) / CFL_MU
+            adv = 1.0 / (1.0 / adv + mu[k] * (1.0 / (s1 * s1) + 1.0 / (s2 * s2)) / CFL_MU)
         best = min(best, float(np.min(adv)))
     return best
 

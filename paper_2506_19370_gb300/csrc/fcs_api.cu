@@ -20,7 +20,7 @@ namespace {
 constexpr int kNParams = 1732;
 constexpr int kIndC = 26;   // continuation length of the indicator (16 + 26 = 42 = 2 * 3 * 7)
 constexpr int kIndD = 5;
-constexpr double kCflMu = 0.25;  // viscous limit of the time step: dt <= 0.25 h_min^2 / mu
+constexpr double kCflMu = 0.2;  // viscous limit: 1/dt = 1/dt_a + mu (1/s1^2 + 1/s2^2) / 0.2
 
 struct DevBuf {
   void* p = nullptr;

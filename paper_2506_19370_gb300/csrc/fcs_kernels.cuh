@@ -78,13 +78,10 @@ __global__ void k_dt(CtxDev c, const T* __restrict__ e, const T* __restrict__ mu
     const T U1 = (y_q2 * u - x_q2 * v) / J, U2 = (-y_q1 * u + x_q1 * v) / J;
     const T n1 = sqrt(y_q2 * y_q2 + x_q2 * x_q2) / fabs(J), n2 = sqrt(y_q1 * y_q1 + x_q1 * x_q1) / fabs(J);
     T r = cfl * fmin(h1 / (fabs(U1) + cs * n1), h2 / (fabs(U2) + cs * n2));
-    if (mu) {
+    if (mu) {  // 1/dt = 1/dt_a + mu (1/s1^2 + 1/s2^2) / cfl_mu
       const T m = mu[inst * c.qstride + q];
-      if (m > T(0)) {
-        const T s1 = h1 * sqrt(x_q1 * x_q1 + y_q1 * y_q1), s2 = h2 * sqrt(x_q2 * x_q2 + y_q2 * y_q2);
-        const T hm = fmin(s1, s2);
-        r = fmin(r, cfl_mu * hm * hm / m);
-      }
+      const T s1 = h1 * sqrt(x_q1 * x_q1 + y_q1 * y_q1), s2 = h2 * sqrt(x_q2 * x_q2 + y_q2 * y_q2);
+      r = T(1) / (T(1) / r + m * (T(1) / (s1 * s1) + T(1) / (s2 * s2)) / cfl_mu);
     }
     if (!(r > T(0))) r = T(0);
     r_min = r;

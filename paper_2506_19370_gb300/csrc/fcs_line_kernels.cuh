@@ -107,9 +107,20 @@ __device__ __forceinline__ void apply_bc(const CtxDev& c, const PatchDev& P, int
 // Flux of Eq. (1) along direction DIR at one point, transformed for the
 // parameter direction: DIR 0: y_q2 f - x_q2 g, DIR 1: -y_q1 f + x_q1 g;
 // Cartesian: f resp. g, minus mu times the derivative dv (viscous flux).
+// t is the point's index along the line: the normal viscous flux is zero on
+// wall, outflow and free sides (the diffusion term needs a condition on every
+// variable there; this one is impermeable and adiabatic).
 template <typename T, int DIR>
 __device__ __forceinline__ void point_flux(const CtxDev& c, const PatchDev& P, long long q, const T* v, const T* dv,
-                                           T mu, bool visc, T* F) {
+                                           T mu, bool visc, T* F, int t) {
+  if (visc) {
+    const int N = DIR == 0 ? P.n1 : P.n2;
+    const int side = t == 0 ? 2 * DIR : (t == N - 1 ? 2 * DIR + 1 : -1);
+    if (side >= 0) {
+      const int code = P.bc[side];
+      if (code == 1 || code == 3 || code == 4) visc = false;
+    }
+  }
   const T gm1 = T(c.gamma - 1.0);
   const T rho = v[0], mx = v[1], my = v[2], En = v[3];
   const T u = mx / rho, w = my / rho;
@@ -202,7 +213,7 @@ __global__ void __launch_bounds__(kWarps * 32, 4) k_xpass(CtxDev c, const T* __r
               v[f] = E[(k * 4 + f) * nmax + t];
               dv[f] = visc ? W[(k * 4 + f) * nmax + t] : T(0);
             }
-            point_flux<T, 0>(c, P, q0 + t, v, dv, visc ? M[k * nmax + t] : T(0), visc, F);
+            point_flux<T, 0>(c, P, q0 + t, v, dv, visc ? M[k * nmax + t] : T(0), visc, F, t);
 #pragma unroll
             for (int f = 0; f < 4; ++f) W[(k * 4 + f) * nmax + t] = F[f];
           }
@@ -292,7 +303,7 @@ __global__ void __launch_bounds__(kYWarps * 32, 3) k_ypass(CtxDev c, const int2*
             v[f] = E[(f * n2m + j) * ld + cc];
             dv[f] = visc ? D[(f * n2m + j) * ld + cc] : T(0);
           }
-          point_flux<T, 1>(c, P, qbase + (long long)j * P.n1 + cc, v, dv, visc ? M[j * ld + cc] : T(0), visc, F);
+          point_flux<T, 1>(c, P, qbase + (long long)j * P.n1 + cc, v, dv, visc ? M[j * ld + cc] : T(0), visc, F, j);
 #pragma unroll
           for (int f = 0; f < 4; ++f) D[(f * n2m + j) * ld + cc] = F[f];
         }
