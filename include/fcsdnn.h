@@ -94,6 +94,8 @@ typedef struct {
   int c_policy;      /* 0: use C as given; 1: per line length, smallest C' >= C
                         making N + C' a product of 2, 3, 5, 7 (at most C + 16) */
   int train_batch_max; /* largest batch sdnn_train_step accepts (4096) */
+  int autotune;      /* 1: fc_setup times the column-tile widths (lines per CTA of the
+                        pass along q2) that fit and keeps the fastest; 0: widest (0) */
 } fcs_options;
 
 /* Defaults listed in the comments above. */
@@ -122,6 +124,7 @@ typedef struct {
   const int64_t* state_off;   /* per patch offset in the state layout (host, ctx-owned) */
   const int64_t* scalar_off;  /* per patch offset in the scalar layout */
   const int64_t* window_off;  /* per patch offset of its first window */
+  int tile_width;             /* columns per CTA of the pass along q2 (autotuned or widest) */
 } fcs_layout;
 
 int fcs_get_layout(const fcs_ctx* ctx, fcs_layout* out);
@@ -232,7 +235,7 @@ int sdnn_gradient(fcs_ctx* ctx, const float* x_dev, const int8_t* labels_dev, in
  * synchronisation).  Same result as sdnn_gradient, but the weights come in
  * as an argument (w_dev: 1732 floats, layout of sdnn_set_weights) and no
  * context is needed.  The per-sample activations live in one file-scope
- * device array sized for FCS_NOALLOC_BATCH_MAX samples (about 2.4 MB), which
+ * device array sized for FCS_NOALLOC_BATCH_MAX samples (about 2.9 MB), which
  * every GPU that loads the library keeps until the process exits.
  *  - batch > FCS_NOALLOC_BATCH_MAX returns FCS_ESCRATCH; nothing is launched.
  *  - The first call on a device looks up the array's device address (with

@@ -46,6 +46,7 @@ struct fcs_ctx {
   int nlines0 = 0, nlines1 = 0, npairs0 = 0, npairs1 = 0, nent = 0, ntiles = 0;
   int nmax = 0, nfmax = 0, n2max = 0, stockham = 0, tw = 32;
   int n1x = -1, n1y = -1;  // register-FFT size shared by all lines along q1 / q2 (0: Stockham kernels)
+  std::vector<int> tw_options;  // column-tile widths that fit in shared memory (widest first)
   CtxDev dev{};
   std::vector<void*> allocs;
   // device arrays
@@ -76,6 +77,7 @@ struct fcs_ctx {
   double* W64 = nullptr;
   float* acts = nullptr;
   float* loss_s = nullptr;
+  double* gpart = nullptr;  // per batch-chunk partial gradients
   int adam_t = 0;
   // graph of fcs_step
   cudaGraphExec_t gexec = nullptr;
@@ -303,11 +305,83 @@ namespace {
 int train_forward_backward(fcs_ctx* c, const float* x, const int8_t* lab, int B, float* loss, cudaStream_t s) {
   k_train_sample<<<(B + 127) / 128, 128, 0, s>>>(x, reinterpret_cast<const signed char*>(lab), B, c->Wm, c->acts,
                                                  c->loss_s);
-  k_train_grad<<<(kNParams + 127) / 128, 128, 0, s>>>(c->acts, B, c->grad);
+  const int nchunk = (B + kGradChunk - 1) / kGradChunk;
+  k_train_grad<<<dim3((kNParams + 127) / 128, nchunk), 128, 0, s>>>(c->acts, B, c->gpart);
+  k_train_grad_final<<<(kNParams + 127) / 128, 128, 0, s>>>(c->gpart, nchunk, c->grad);
   k_train_loss<<<1, 256, 0, s>>>(c->loss_s, B, loss);
   return cuda_err(cudaGetLastError());
 }
 }  // namespace
+
+// Column tiles of the pass along q2 for tile width tw (one instance).
+int set_tiles(fcs_ctx* c, const fcs_patch_desc* pd, int tw) {
+  std::vector<int2> tiles;
+  for (int p = 0; p < c->npatch; ++p)
+    for (int c0 = 0; c0 < pd[p].n1; c0 += tw) tiles.push_back(make_int2(p, c0));
+  int2* t = nullptr;
+  int rc = upload(c, &t, tiles.data(), tiles.size() * sizeof(int2));
+  if (rc) return rc;
+  c->tiles = t;
+  c->ntiles = (int)tiles.size();
+  c->tw = tw;
+  c->dev.tw = tw;
+  return FCS_OK;
+}
+
+template <typename T>
+int time_rhs(fcs_ctx* c, float* ms) {
+  cudaEvent_t a, b;
+  FCS_CUDA(cudaEventCreate(&a));
+  FCS_CUDA(cudaEventCreate(&b));
+  StageArgs<T> st{0, T(0), nullptr, nullptr, nullptr, static_cast<T*>(c->A)};
+  int rc = FCS_OK;
+  for (int k = 0; k < 2 && !rc; ++k) rc = launch_flux<T>(c, c->S, nullptr, MODE_RHS, st, 0);
+  cudaEventRecord(a, 0);
+  for (int k = 0; k < 5 && !rc; ++k) rc = launch_flux<T>(c, c->S, nullptr, MODE_RHS, st, 0);
+  cudaEventRecord(b, 0);
+  cudaEventSynchronize(b);
+  cudaEventElapsedTime(ms, a, b);
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  return rc;
+}
+
+// Autotuner of the lines per CTA of the pass along q2: time L(e) on a
+// uniform state for every column-tile width that fits, keep the fastest.
+// Results do not depend on the width (each column is transformed by the same
+// lanes and instructions), only the work partition does.
+int autotune_tile_width(fcs_ctx* c, const fcs_patch_desc* pd) {
+  // uniform valid state (rho = 1, u = v = 0, p = 1) in the stage buffer
+  std::vector<double> one(c->sstride * c->opt.instances, 0.0);
+  for (size_t k = 0; k < (size_t)c->opt.instances; ++k)
+    for (int p = 0; p < c->npatch; ++p) {
+      const size_t np = (size_t)pd[p].n1 * pd[p].n2, base = k * c->sstride + c->state_off[p];
+      for (size_t q = 0; q < np; ++q) {
+        one[base + q] = 1.0;
+        one[base + 3 * np + q] = 1.0 / (c->opt.gamma - 1.0);
+      }
+    }
+  if (c->tsize == 8) {
+    FCS_CUDA(cudaMemcpy(c->S, one.data(), one.size() * 8, cudaMemcpyHostToDevice));
+  } else {
+    std::vector<float> f(one.begin(), one.end());
+    FCS_CUDA(cudaMemcpy(c->S, f.data(), f.size() * 4, cudaMemcpyHostToDevice));
+  }
+  float best = 1e30f;
+  int best_tw = c->tw;
+  for (int tw : c->tw_options) {
+    int rc = set_tiles(c, pd, tw);
+    if (rc) return rc;
+    float ms = 0.f;
+    rc = c->tsize == 8 ? time_rhs<double>(c, &ms) : time_rhs<float>(c, &ms);
+    if (rc) return rc;
+    if (ms < best) {
+      best = ms;
+      best_tw = tw;
+    }
+  }
+  return set_tiles(c, pd, best_tw);
+}
 
 // =====================================================================
 extern "C" {
@@ -329,6 +403,7 @@ void fcs_default_options(fcs_options* o) {
   o->av_radius = 4;
   o->c_policy = 0;
   o->train_batch_max = 4096;
+  o->autotune = 0;
 }
 
 const char* fcs_strerror(int code) {
@@ -492,7 +567,10 @@ int fc_setup(fcs_ctx** out, int d, int C, const fcs_patch_desc* pd, int npatch, 
     int tw = 0;
     for (int t : {32, 16, 8}) {
       const size_t b = esz == 8 ? ypass_smem<double>(c, t) : ypass_smem<float>(c, t);
-      if (b <= lim) { tw = t; break; }
+      if (b <= lim) {
+        if (!tw) tw = t;
+        c->tw_options.push_back(t);
+      }
     }
     if (!tw) return fail(FCS_EUNSUPPORTED);
     c->tw = tw;
@@ -663,7 +741,8 @@ int fc_setup(fcs_ctx** out, int d, int C, const fcs_patch_desc* pd, int npatch, 
       (rc = dalloc(c, &c->Av, kNParams * 4)) || (rc = dalloc(c, &c->grad, kNParams * 4)) ||
       (rc = dalloc(c, &c->Wb, 1664 * 2)) || (rc = dalloc(c, &c->bias, 68 * 4)) ||
       (rc = dalloc(c, &dW64, kNParams * 8)) || (rc = dalloc(c, &c->acts, (size_t)o.train_batch_max * kActs * 4)) ||
-      (rc = dalloc(c, &c->loss_s, (size_t)o.train_batch_max * 4)) || (rc = dalloc(c, &m64, 5 * c->qstride * 8)) ||
+      (rc = dalloc(c, &c->loss_s, (size_t)o.train_batch_max * 4)) ||
+      (rc = dalloc(c, &c->gpart, (size_t)((o.train_batch_max + kGradChunk - 1) / kGradChunk) * kNParams * 8)) || (rc = dalloc(c, &m64, 5 * c->qstride * 8)) ||
       (rc = dalloc(c, &m32, 5 * c->qstride * 4)))
     return fail(rc);
   c->W64 = dW64;
@@ -748,6 +827,9 @@ int fc_setup(fcs_ctx** out, int d, int C, const fcs_patch_desc* pd, int npatch, 
         cudaMemcpy(m32, Mf.data(), 5 * Q * 4, cudaMemcpyHostToDevice) != cudaSuccess)
       return fail(FCS_ECUDA);
   }
+  if (o.autotune && c->tw_options.size() > 1) {
+    if ((rc = autotune_tile_width(c, pd))) return fail(rc);
+  }
   if (cudaDeviceSynchronize() != cudaSuccess) return fail(FCS_ECUDA);
   *out = c;
   return FCS_OK;
@@ -765,6 +847,7 @@ int fcs_get_layout(const fcs_ctx* c, fcs_layout* o) {
   o->state_off = c->state_off.data();
   o->scalar_off = c->scalar_off.data();
   o->window_off = c->window_off.data();
+  o->tile_width = c->tw;
   return FCS_OK;
 }
 
@@ -929,7 +1012,10 @@ int sdnn_gradient(fcs_ctx* c, const float* x, const int8_t* lab, int B, float* l
 // sample activations and losses) is a file-scope device array; host code only
 // ever passes the array's device address, looked up once per device.
 constexpr size_t kNoAllocActs = (size_t)FCS_NOALLOC_BATCH_MAX * kActs;
-static __device__ __align__(256) float g_noalloc_scratch[kNoAllocActs + FCS_NOALLOC_BATCH_MAX];
+constexpr size_t kNoAllocChunks = (FCS_NOALLOC_BATCH_MAX + kGradChunk - 1) / kGradChunk;
+// activations, per-sample losses, then (8-byte aligned) the FP64 partial gradients
+static __device__ __align__(256) float g_noalloc_scratch[kNoAllocActs + FCS_NOALLOC_BATCH_MAX +
+                                                          2 * kNoAllocChunks * kNParams];
 namespace {
 constexpr int kMaxDevices = 64;
 float* g_noalloc_addr[kMaxDevices] = {};
@@ -956,7 +1042,10 @@ int sdnn_gradient_noalloc(const float* w, const float* x, const int8_t* lab, int
   cudaStream_t s = as_stream(stream);
   k_train_sample<<<(B + 127) / 128, 128, 0, s>>>(x, reinterpret_cast<const signed char*>(lab), B, w, acts,
                                                  acts + kNoAllocActs);
-  k_train_grad<<<(kNParams + 127) / 128, 128, 0, s>>>(acts, B, grad);
+  double* part = reinterpret_cast<double*>(acts + kNoAllocActs + FCS_NOALLOC_BATCH_MAX);
+  const int nchunk = (B + kGradChunk - 1) / kGradChunk;
+  k_train_grad<<<dim3((kNParams + 127) / 128, nchunk), 128, 0, s>>>(acts, B, part);
+  k_train_grad_final<<<(kNParams + 127) / 128, 128, 0, s>>>(part, nchunk, grad);
   k_train_loss<<<1, 256, 0, s>>>(acts + kNoAllocActs, B, loss);
   return cuda_err(cudaGetLastError());
 }

@@ -653,22 +653,38 @@ __global__ void k_train_sample(const float* __restrict__ x, const signed char* _
   for (int o = 0; o < 4; ++o) A[144 + o] = dz3[o];
 }
 
-// gradient of every parameter: fixed-order FP64 sum over the batch
-__global__ void k_train_grad(const float* __restrict__ acts, int B, float* grad) {
+// gradient of every parameter: the batch is cut into chunks of kGradChunk
+// samples; block (param-chunk, batch-chunk) writes FP64 partial sums, and
+// k_train_grad_final adds the partials of each parameter in chunk order
+// (deterministic, no atomics).
+constexpr int kGradChunk = 128;
+__device__ __forceinline__ void grad_cols(int t, int* dz, int* in) {
+  if (t < 512) { *dz = 80 + t / 16; *in = t % 16; }
+  else if (t < 544) { *dz = 80 + (t - 512); *in = -1; }
+  else if (t < 1568) { *dz = 112 + (t - 544) / 32; *in = 16 + (t - 544) % 32; }
+  else if (t < 1600) { *dz = 112 + (t - 1568); *in = -1; }
+  else if (t < 1728) { *dz = 144 + (t - 1600) / 32; *in = 48 + (t - 1600) % 32; }
+  else { *dz = 144 + (t - 1728); *in = -1; }
+}
+__global__ void k_train_grad(const float* __restrict__ acts, int B, double* partial) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int chunk = blockIdx.y;
+  if (t >= 1732) return;
+  int dz, in;
+  grad_cols(t, &dz, &in);
+  const int s0 = chunk * kGradChunk, s1 = min(B, s0 + kGradChunk);
+  double a = 0.0;
+  for (int s = s0; s < s1; ++s) {
+    const float* A = acts + (long long)s * kActs;
+    a += (double)(A[dz] * (in >= 0 ? A[in] : 1.0f));
+  }
+  partial[(long long)chunk * 1732 + t] = a;
+}
+__global__ void k_train_grad_final(const double* __restrict__ partial, int nchunk, float* grad) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= 1732) return;
-  int dz, in;  // column of dz and of the input in the activation record (in < 0: bias)
-  if (t < 512) { dz = 80 + t / 16; in = t % 16; }
-  else if (t < 544) { dz = 80 + (t - 512); in = -1; }
-  else if (t < 1568) { dz = 112 + (t - 544) / 32; in = 16 + (t - 544) % 32; }
-  else if (t < 1600) { dz = 112 + (t - 1568); in = -1; }
-  else if (t < 1728) { dz = 144 + (t - 1600) / 32; in = 48 + (t - 1600) % 32; }
-  else { dz = 144 + (t - 1728); in = -1; }
   double a = 0.0;
-  for (int s = 0; s < B; ++s) {
-    const float* A = acts + (long long)s * kActs;
-    a += (double)A[dz] * (in >= 0 ? (double)A[in] : 1.0);
-  }
+  for (int k = 0; k < nchunk; ++k) a += partial[(long long)k * 1732 + t];
   grad[t] = (float)a;
 }
 

@@ -178,7 +178,7 @@ __global__ void __launch_bounds__(kWarps * 32, 4) k_xpass(CtxDev c, const T* __r
     const int inst = (int)(w / groups);
     const int l0 = (int)(w % groups) * RW;
     int pid[RW], row[RW];
-    bool has[RW];
+    bool has[RW], vrow[RW];
 #pragma unroll
     for (int k = 0; k < RW; ++k) {
       has[k] = l0 + k < c.nlines0;
@@ -189,22 +189,30 @@ __global__ void __launch_bounds__(kWarps * 32, 4) k_xpass(CtxDev c, const T* __r
       const long long np = (long long)P.n1 * P.n2;
       const T* es = e + inst * c.sstride + P.soff + (long long)lr.line * P.n1;
       const bool visc = (mu != nullptr) && P.cart;
+      bool any_mu = false;
       if (has[k])
         for (int t = lane; t < P.n1; t += 32) {
 #pragma unroll
           for (int f = 0; f < 4; ++f) E[(k * 4 + f) * nmax + t] = es[f * np + t];
-          if (visc) M[k * nmax + t] = mu[inst * c.qstride + P.qoff + (long long)lr.line * P.n1 + t];
+          if (visc) {
+            const T m = mu[inst * c.qstride + P.qoff + (long long)lr.line * P.n1 + t];
+            M[k * nmax + t] = m;
+            any_mu |= m != T(0);
+          }
         }
+      // the viscous flux of a row with mu == 0 everywhere vanishes: skip its
+      // derivatives (localized viscosity)
+      vrow[k] = __any_sync(0xffffffffu, any_mu);
     }
     __syncwarp();
-    const bool visc_any = mu != nullptr;
+    const bool visc_any = vrow[0] || vrow[1];
     for (int phase = visc_any ? 0 : 1; phase < 2; ++phase) {
       if (phase == 1) {
 #pragma unroll
         for (int k = 0; k < RW; ++k) {
           if (!has[k]) continue;
           const PatchDev& P = c.patches[pid[k]];
-          const bool visc = (mu != nullptr) && P.cart;
+          const bool visc = vrow[k];
           const long long q0 = P.qoff + (long long)row[k] * P.n1;
           for (int t = lane; t < P.n1; t += 32) {
             T v[4], dv[4], F[4];
@@ -231,7 +239,7 @@ __global__ void __launch_bounds__(kWarps * 32, 4) k_xpass(CtxDev c, const T* __r
         bool active = job < 2 * RW && (kk ? has[1] : has[0]);
         const PatchDev& P = c.patches[pidk];
         const PlanDev& pl = c.plans[P.plan[0]];
-        if (phase == 0 && !((mu != nullptr) && P.cart)) active = false;
+        if (phase == 0 && !(kk ? vrow[1] : vrow[0])) active = false;
         const long long np = (long long)P.n1 * P.n2;
         const T* src = (phase == 0 ? E : W) + (kk * 4 + 2 * pr) * nmax;
         T* oa;
@@ -285,25 +293,45 @@ __global__ void __launch_bounds__(kYWarps * 32, 3) k_ypass(CtxDev c, const int2*
     // each thread keeps one column cc of the tile and strides over rows
     const int cc = threadIdx.x % tw, jr = threadIdx.x / tw, js = blockDim.x / tw;
     const bool colok = cc < width && jr < js;
-    if (colok)
+    __shared__ int colv[32];   // column has mu != 0 somewhere (tw <= 32)
+    __shared__ int act[32];    // compacted list of such columns
+    __shared__ int nact;
+    if (threadIdx.x < 32) colv[threadIdx.x] = 0;
+    __syncthreads();
+    if (colok) {
+      bool any_mu = false;
       for (int j = jr; j < N; j += js) {
 #pragma unroll
         for (int f = 0; f < 4; ++f) E[(f * n2m + j) * ld + cc] = e[sbase + f * np + (long long)j * P.n1 + cc];
-        if (visc) M[j * ld + cc] = mu[inst * c.qstride + qbase + (long long)j * P.n1 + cc];
+        if (visc) {
+          const T m = mu[inst * c.qstride + qbase + (long long)j * P.n1 + cc];
+          M[j * ld + cc] = m;
+          any_mu |= m != T(0);
+        }
       }
+      if (any_mu) atomicOr(&colv[cc], 1);
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {   // warp 0 compacts the viscous columns
+      const bool v = threadIdx.x < width && colv[threadIdx.x];
+      const unsigned bal = __ballot_sync(0xffffffffu, v);
+      if (v) act[__popc(bal & ((1u << threadIdx.x) - 1u))] = threadIdx.x;
+      if (threadIdx.x == 0) nact = __popc(bal);
+    }
     __syncthreads();
     const T h = T(P.hy);
-    // phase 0 (viscous): D = d e/dy; phase 1: E = d F2/dq2 with F2 formed in D
-    for (int phase = visc ? 0 : 1; phase < 2; ++phase) {
+    // phase 0 (viscous columns only): D = d e/dy; phase 1: E = d F2/dq2 with F2 formed in D
+    for (int phase = (visc && nact > 0) ? 0 : 1; phase < 2; ++phase) {
       if (phase == 1) {
         for (int j = jr; colok && j < N; j += js) {
           T v[4], dv[4], F[4];
 #pragma unroll
           for (int f = 0; f < 4; ++f) {
             v[f] = E[(f * n2m + j) * ld + cc];
-            dv[f] = visc ? D[(f * n2m + j) * ld + cc] : T(0);
+            dv[f] = (visc && colv[cc]) ? D[(f * n2m + j) * ld + cc] : T(0);
           }
-          point_flux<T, 1>(c, P, qbase + (long long)j * P.n1 + cc, v, dv, visc ? M[j * ld + cc] : T(0), visc, F, j);
+          const bool vc = visc && colv[cc];
+          point_flux<T, 1>(c, P, qbase + (long long)j * P.n1 + cc, v, dv, vc ? M[j * ld + cc] : T(0), vc, F, j);
 #pragma unroll
           for (int f = 0; f < 4; ++f) D[(f * n2m + j) * ld + cc] = F[f];
         }
@@ -311,11 +339,12 @@ __global__ void __launch_bounds__(kYWarps * 32, 3) k_ypass(CtxDev c, const int2*
       }
       const T* src = phase == 0 ? E : D;
       T* dst = phase == 0 ? D : E;
-      // jobs (column, field pair): 2 width of them, JPR per warp and round
-      for (int u0 = warp * JPR; u0 < 2 * width; u0 += kYWarps * JPR) {
+      // jobs (column, field pair): phase 0 over the viscous columns only
+      const int ncol = phase == 0 ? nact : width;
+      for (int u0 = warp * JPR; u0 < 2 * ncol; u0 += kYWarps * JPR) {
         const int u = u0 + g;
-        const bool active = u < 2 * width;
-        const int cc = active ? (u >> 1) : 0, pr = u & 1;
+        const bool active = u < 2 * ncol;
+        const int cc = active ? (phase == 0 ? act[u >> 1] : (u >> 1)) : 0, pr = u & 1;
         line_deriv_pair<T, N1>(src + (2 * pr) * n2m * ld + cc, ld, src + (2 * pr + 1) * n2m * ld + cc, ld,
                                dst + (2 * pr) * n2m * ld + cc, ld, dst + (2 * pr + 1) * n2m * ld + cc, ld, T(1), c, pl,
                                h, 1, lane, aux, aux + c.nfmax, tile, active);

@@ -43,14 +43,14 @@ class Options(ctypes.Structure):
     _fields_ = [("gamma", ctypes.c_double), ("cfl", ctypes.c_double), ("n_f", ctypes.c_int), ("dtype", ctypes.c_int),
                 ("instances", ctypes.c_int), ("inflow", ctypes.c_double * 4), ("p_out", ctypes.c_double),
                 ("c_mu", ctypes.c_double), ("av_radius", ctypes.c_int), ("c_policy", ctypes.c_int),
-                ("train_batch_max", ctypes.c_int)]
+                ("train_batch_max", ctypes.c_int), ("autotune", ctypes.c_int)]
 
 
 class Layout(ctypes.Structure):
     _fields_ = [("instances", ctypes.c_int), ("npatch", ctypes.c_int), ("dtype", ctypes.c_int), ("d", ctypes.c_int),
                 ("state_elems", ctypes.c_size_t), ("scalar_elems", ctypes.c_size_t), ("windows", ctypes.c_size_t),
                 ("state_off", ctypes.POINTER(ctypes.c_int64)), ("scalar_off", ctypes.POINTER(ctypes.c_int64)),
-                ("window_off", ctypes.POINTER(ctypes.c_int64))]
+                ("window_off", ctypes.POINTER(ctypes.c_int64)), ("tile_width", ctypes.c_int)]
 
 
 _lib = None
@@ -133,7 +133,7 @@ class Context:
     """An fcs_ctx for one patch layout (an ``inputs.Instance``) and its options."""
 
     def __init__(self, inst, d=5, C=25, dtype=F32, instances=1, cfl=0.5, n_f=5, c_mu=1.0, av_radius=4,
-                 c_policy=0, train_batch_max=4096):
+                 c_policy=0, train_batch_max=4096, autotune=0):
         import torch  # device memory and streams
         self.torch = torch
         L = lib()
@@ -148,6 +148,7 @@ class Context:
             opt.inflow[k] = inst.inflow[k]
         opt.p_out, opt.c_mu, opt.av_radius, opt.c_policy = inst.p_out, c_mu, av_radius, c_policy
         opt.train_batch_max = train_batch_max
+        opt.autotune = autotune
         descs = (PatchDesc * len(inst.patches))()
         self._keep = []
         for k, p in enumerate(inst.patches):
@@ -178,6 +179,7 @@ class Context:
         self.state_off = [lay.state_off[k] for k in range(self.npatch)]
         self.scalar_off = [lay.scalar_off[k] for k in range(self.npatch)]
         self.window_off = [lay.window_off[k] for k in range(self.npatch)]
+        self.tile_width = lay.tile_width
         self.dev = torch.device("cuda", torch.cuda.current_device()) if torch.cuda.is_available() else None
 
     def close(self):

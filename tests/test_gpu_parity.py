@@ -413,3 +413,22 @@ def test_invalid_arguments_rejected():
     with pytest.raises(fcsdnn.FcsError) as ei:
         fcsdnn.Context(bad, c_policy=1)
     assert ei.value.code == -2
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+def test_autotuned_tile_width_gives_identical_results(dtype):
+    # the autotuner only changes how columns are partitioned among CTAs; every
+    # column is transformed by the same lanes and instructions
+    inst, pol = layout("sod")
+    a = fcsdnn.Context(inst, dtype=dtype, c_policy=pol, instances=4, autotune=1)
+    b = fcsdnn.Context(inst, dtype=dtype, c_policy=pol, instances=4, autotune=0)
+    assert a.tile_width in (8, 16, 32) and b.tile_width in (8, 16, 32)
+    st = [random_states(inst, 40 + k) for k in range(4)]
+    e = a.to_device(a.pack_state(st))
+    ra, rb = a.new_state(), b.new_state()
+    mu = a.to_device(a.pack_scalar([[0.002 * np.ones((p.n2, p.n1)) for p in inst.patches]] * 4))
+    a.euler_rhs(e, ra, mu=mu)
+    b.euler_rhs(e, rb, mu=mu)
+    torch.cuda.synchronize()
+    print(f"autotuned tile width {a.tile_width} (default {b.tile_width})")
+    assert torch.equal(ra, rb)
