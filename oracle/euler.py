@@ -22,7 +22,9 @@ Follows:
     coefficients, reading of "SSPRK-4"), boundary conditions enforced after
     every stage, exchange of fringe values after every stage;
   * §3.3: n_f-point fringes of internal sides receive values from donor points
-    of other patches that are not themselves receivers; coincident grids copy;
+    of other patches that are not themselves receivers; coincident grids copy,
+    other grids interpolate (tensor Lagrange, 6 x 6 donor nodes, reading of
+    I-3.4), the donor parameter found by Newton's method on the donor map;
   * Δt (reading of I-(31)): min over points of 1 / (1/dt_a + 1/dt_v) with
         dt_a = CFL min_k h_k / (|U_k| + c |grad q_k|),
         dt_v = CFL_MU / (mu (1/s_1^2 + 1/s_2^2))   (only where mu > 0),
@@ -177,48 +179,155 @@ def receiver_mask(patch, n_f):
     return m
 
 
-def fringe_map(patches, n_f=5):
-    """Donor for every fringe point: rows (dst patch, j, i, src patch, j', i').
+# ---------------------------------------------------------------------------
+# donors and interpolation (§3.3; reading of I-3.4: tensor-product Lagrange
+# interpolation on a STENCIL x STENCIL block of donor grid points, in the
+# donor's parameter (index) space)
+# ---------------------------------------------------------------------------
+STENCIL = 6
+COPY_TOL = 1e-9     # a receiver this close (in index units) to a donor node copies it
+INSIDE_TOL = 1e-6   # slack of the inside-the-donor test (index units): the interpolated
+                    # map of a curved donor misses its true boundary by rounding-level amounts
 
-    Coincident Cartesian grids only: the donor is the lowest-numbered other
-    patch holding a grid point at the same location outside its own fringe.
+
+def lagrange_weights(t, m=STENCIL):
+    """Values at t of the m Lagrange basis polynomials on the nodes 0..m-1."""
+    w = np.ones(m)
+    for a in range(m):
+        for b in range(m):
+            if b != a:
+                w[a] *= (t - b) / (a - b)
+    return w
+
+
+def lagrange_dweights(t, m=STENCIL):
+    """Derivatives at t of the m Lagrange basis polynomials on 0..m-1."""
+    dw = np.zeros(m)
+    for a in range(m):
+        for c in range(m):
+            if c == a:
+                continue
+            term = 1.0 / (a - c)
+            for b in range(m):
+                if b != a and b != c:
+                    term *= (t - b) / (a - b)
+            dw[a] += term
+    return dw
+
+
+def stencil_start(f, n, m=STENCIL):
+    """First node of the m-point stencil around fractional index f (clamped to the line)."""
+    return min(max(int(np.floor(f)) - (m // 2 - 1), 0), n - m)
+
+
+def donor_index(patch, x, y, max_iter=40):
+    """Fractional grid index (fi, fj) of the physical point (x, y) in `patch`.
+
+    Cartesian patches invert their affine map.  Curvilinear patches invert the
+    tensor Lagrange interpolant of their grid coordinates by Newton's method,
+    starting from the nearest grid point; the stencil follows the iterate.
+    Returns None when the iteration leaves the patch or does not converge.
+    """
+    if patch.cartesian:
+        x0, x1, y0, y1 = patch.box
+        return (x - x0) / ((x1 - x0) / (patch.n1 - 1)), (y - y0) / ((y1 - y0) / (patch.n2 - 1))
+    X, Y = patch.coords()
+    k = int(np.argmin((X - x) ** 2 + (Y - y) ** 2))
+    fj, fi = float(k // patch.n1), float(k % patch.n1)
+    for _ in range(max_iter):
+        i0, j0 = stencil_start(fi, patch.n1), stencil_start(fj, patch.n2)
+        wi, wj = lagrange_weights(fi - i0), lagrange_weights(fj - j0)
+        di, dj = lagrange_dweights(fi - i0), lagrange_dweights(fj - j0)
+        bx = X[j0:j0 + STENCIL, i0:i0 + STENCIL]
+        by = Y[j0:j0 + STENCIL, i0:i0 + STENCIL]
+        xm, ym = wj @ bx @ wi, wj @ by @ wi
+        a11, a12 = wj @ bx @ di, dj @ bx @ wi
+        a21, a22 = wj @ by @ di, dj @ by @ wi
+        det = a11 * a22 - a12 * a21
+        rx, ry = x - xm, y - ym
+        di_ = (a22 * rx - a12 * ry) / det
+        dj_ = (-a21 * rx + a11 * ry) / det
+        fi += di_
+        fj += dj_
+        if not (-2.0 <= fi <= patch.n1 + 1.0 and -2.0 <= fj <= patch.n2 + 1.0):
+            return None
+        if abs(di_) + abs(dj_) < 1e-12:
+            return fi, fj
+    return None
+
+
+class FringeMap:
+    """Donor data of every fringe point of one layout.
+
+    copies: int array of rows (dst patch, j, i, src patch, j', i');
+    interp: list of (dst patch, j, i, src patch, j0, i0, W) with W the
+            STENCIL x STENCIL tensor Lagrange weights on the donor block
+            starting at (j0, i0).
+    """
+
+    def __init__(self, copies, interp):
+        self.copies = np.array(copies, dtype=np.int64).reshape(-1, 6)
+        self.interp = interp
+
+    def __len__(self):
+        return len(self.copies) + len(self.interp)
+
+
+def fringe_map(patches, n_f=5):
+    """Donor of every fringe point (§3.3: donors are never receivers).
+
+    For each receiver, the donor is the lowest-numbered other patch that
+    contains the point and either has a grid node there (copy) or whose
+    interpolation stencil holds no receiver of its own (interpolation).
     """
     masks = [receiver_mask(p, n_f) for p in patches]
-    rows = []
+    copies, interp = [], []
     for p, pt in enumerate(patches):
-        if not pt.cartesian and masks[p].any():
-            raise NotImplementedError("exchange on curvilinear patches")
         X, Y = pt.coords()
         for j, i in zip(*np.nonzero(masks[p])):
             x, y = X[j, i], Y[j, i]
-            found = None
+            found = False
             for q, qt in enumerate(patches):
                 if q == p:
                     continue
-                x0, x1, y0, y1 = qt.box
-                hx = (x1 - x0) / (qt.n1 - 1)
-                hy = (y1 - y0) / (qt.n2 - 1)
-                fi = (x - x0) / hx
-                fj = (y - y0) / hy
-                ii, jj = int(round(fi)), int(round(fj))
-                if abs(fi - ii) > 1e-6 or abs(fj - jj) > 1e-6:
+                loc = donor_index(qt, x, y)
+                if loc is None:
                     continue
-                if not (0 <= ii < qt.n1 and 0 <= jj < qt.n2):
+                fi, fj = loc
+                if not (-INSIDE_TOL <= fi <= qt.n1 - 1 + INSIDE_TOL and -INSIDE_TOL <= fj <= qt.n2 - 1 + INSIDE_TOL):
                     continue
-                if masks[q][jj, ii]:
+                ri, rj = int(round(fi)), int(round(fj))
+                if abs(fi - ri) <= COPY_TOL and abs(fj - rj) <= COPY_TOL:
+                    if masks[q][rj, ri]:
+                        continue
+                    copies.append((p, j, i, q, rj, ri))
+                    found = True
+                    break
+                i0, j0 = stencil_start(fi, qt.n1), stencil_start(fj, qt.n2)
+                if masks[q][j0:j0 + STENCIL, i0:i0 + STENCIL].any():
                     continue
-                found = (q, jj, ii)
+                W = np.outer(lagrange_weights(fj - j0), lagrange_weights(fi - i0))
+                interp.append((p, j, i, q, j0, i0, W))
+                found = True
                 break
-            if found is None:
+            if not found:
                 raise ValueError(f"no donor for patch {p} point ({j},{i})")
-            rows.append((p, j, i) + found)
-    return np.array(rows, dtype=np.int64).reshape(-1, 6)
+    return FringeMap(copies, interp)
 
 
-def exchange(state, fmap):
-    """Copy donor values into every fringe point (all four fields)."""
-    for p, j, i, q, jj, ii in fmap:
-        state[p][:, j, i] = state[q][:, jj, ii]
+def exchange(state, fmap, clamp=False):
+    """Donor values into every fringe point (all leading components).
+
+    Copies first, then interpolations; donors are never receivers, so the
+    order does not matter.  clamp=True floors interpolated values at zero
+    (used for the viscosity, which must stay non-negative).
+    """
+    for p, j, i, q, jj, ii in fmap.copies:
+        state[p][..., j, i] = state[q][..., jj, ii]
+    for p, j, i, q, j0, i0, W in fmap.interp:
+        blk = state[q][..., j0:j0 + STENCIL, i0:i0 + STENCIL]
+        v = np.sum(blk * W, axis=(-2, -1))
+        state[p][..., j, i] = np.maximum(v, 0.0) if clamp else v
     return state
 
 

@@ -302,6 +302,4 @@ def av_assemble(solver, state, taus, c_mu=1.0, radius=4):
     """Viscosity on every patch, fringe values from donors (Algorithm 3 + blend)."""
     mus = [av_patch(e, t, g, solver.inst.gamma, solver.n_f, c_mu, radius)
            for e, t, g in zip(state, taus, solver.geoms)]
-    for p, j, i, q, jj, ii in solver.fmap:
-        mus[p][j, i] = mus[q][jj, ii]
-    return mus
+    return euler.exchange(mus, solver.fmap, clamp=True)

@@ -127,20 +127,46 @@ def sod_layout(npatch=8, n1=160, n2=40, overlap=10, length=1.0, height=0.1):
     return patches
 
 
+def strip_layout(n1s, n2=40, length=1.0, height=0.1, overlap=0.08):
+    """Overlapping Cartesian patches along x with different point counts.
+
+    Patch k spans [a_k, a_k + w] (equal widths w, consecutive patches overlap
+    by `overlap`), with n1s[k] points along x: the grids do not coincide, so
+    fringes are filled by interpolation.  Outer ends and y sides are walls.
+    """
+    P = len(n1s)
+    w = (length + (P - 1) * overlap) / P
+    patches = []
+    for k, n1 in enumerate(n1s):
+        a = k * (w - overlap)
+        bc = [BC_INTERNAL, BC_INTERNAL, BC_WALL, BC_WALL]
+        if k == 0:
+            bc[0] = BC_WALL
+        if k == P - 1:
+            bc[1] = BC_WALL
+        patches.append(Patch(n1, n2, tuple(bc), box=(a, min(a + w, length) if k == P - 1 else a + w, 0.0, height)))
+    return patches
+
+
 def sod_instance(npatch=8, n1=160, n2=40, overlap=10, x_jump=0.5, height=0.1, perturb=0.0, seed=SEED,
-                 smear=0.0):
+                 smear=0.0, patches=None):
     """Sod shock tube (rho,u,p) = (1,0,1) | (0.125,0,0.1), jump at x_jump.
 
     `perturb` adds a seeded relative perturbation to the density (used to make
     batched instances distinct).  `smear` > 0 replaces the jump by a tanh
     profile `smear` grid spacings wide (a stand-in for the paper's localized
     smearing of discontinuous initial data, Algorithm 4, which is not part of
-    the stage).
+    the stage).  `patches` replaces the default layout (any Cartesian
+    patches covering [0,1] x [0,height]); the smearing width then uses the
+    finest x spacing.
     """
-    patches = sod_layout(npatch, n1, n2, overlap, 1.0, height)
+    if patches is None:
+        patches = sod_layout(npatch, n1, n2, overlap, 1.0, height)
+        nx = npatch * n1 - (npatch - 1) * overlap
+        hx = 1.0 / (nx - 1)
+    else:
+        hx = min((p.box[1] - p.box[0]) / (p.n1 - 1) for p in patches)
     rng = np.random.default_rng(seed)
-    nx = npatch * n1 - (npatch - 1) * overlap
-    hx = 1.0 / (nx - 1)
     state = []
     for pt in patches:
         X, Y = pt.coords()
@@ -167,6 +193,23 @@ def annulus_patch(n1=48, n2=32, r0=0.5, r1=1.0, th0=0.3, th1=1.4, bc=(BC_FREE,) 
     th = th0 + (th1 - th0) * Q1
     r = r0 + (r1 - r0) * Q2
     return Patch(n1, n2, tuple(bc), x=r * np.cos(th), y=r * np.sin(th))
+
+
+def annulus_ring(sizes=((64, 24), (56, 20), (72, 28)), r0=0.5, r1=1.0, overlap=0.9, rot=0.0):
+    """Annulus r0 <= r <= r1 covered by overlapping curvilinear sectors.
+
+    Sector k has sizes[k] = (n1, n2) points (angle, radius) and spans the
+    angles [k 2pi/P - overlap/2, (k+1) 2pi/P + overlap/2] + rot; the sectors'
+    grids differ, so their fringes are filled by interpolation.  Angle sides
+    are internal, r = r0 a wall (the cylinder), r = r1 free.
+    """
+    P = len(sizes)
+    patches = []
+    for k, (n1, n2) in enumerate(sizes):
+        th0 = rot + k * 2 * np.pi / P - overlap / 2
+        th1 = rot + (k + 1) * 2 * np.pi / P + overlap / 2
+        patches.append(annulus_patch(n1, n2, r0, r1, th0, th1, bc=(BC_INTERNAL, BC_INTERNAL, BC_WALL, BC_FREE)))
+    return patches
 
 
 def mach_flow_state(M, gamma=GAMMA):

@@ -95,9 +95,9 @@ def test_sod_fringe_map():
     inst = I.sod_instance()
     fmap = euler.fringe_map(inst.patches, 5)
     # two fringes of 5 columns per internal interface, 40 rows each
-    assert len(fmap) == 7 * 2 * 5 * 40
+    assert len(fmap) == 7 * 2 * 5 * 40 and not fmap.interp   # coincident grids: copies only
     masks = [euler.receiver_mask(p, 5) for p in inst.patches]
-    for p, j, i, q, jj, ii in fmap:
+    for p, j, i, q, jj, ii in fmap.copies:
         assert masks[p][j, i] and not masks[q][jj, ii]       # donors are never receivers
         Xp, Yp = inst.patches[p].coords()
         Xq, Yq = inst.patches[q].coords()
@@ -146,3 +146,86 @@ def test_sod_mean_energy():
     import json, os
     g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_values.json")))
     assert abs(sums[0, 3] / 0.1 - g["sod_mean_energy"]["E_mean"]) < 2e-2
+
+
+# ---------------------------------------------------------------- interpolation
+def test_lagrange_weights_reproduce_degree_five():
+    # the 6-node Lagrange basis reproduces every polynomial of degree <= 5 and
+    # its derivative, and no polynomial of degree 6
+    a = np.arange(euler.STENCIL, dtype=np.float64)
+    for t in (0.0, 0.37, 2.5, 4.91):
+        w, dw = euler.lagrange_weights(t), euler.lagrange_dweights(t)
+        for k in range(6):
+            assert abs(w @ a ** k - t ** k) < 1e-11 * max(1.0, t ** k)
+            assert abs(dw @ a ** k - (k * t ** (k - 1) if k else 0.0)) < 1e-10 * max(1.0, t ** k)
+    assert abs(euler.lagrange_weights(2.5) @ a ** 6 - 2.5 ** 6) > 1.0
+
+
+def test_strip_interpolation_exact_for_tensor_quintics():
+    patches = I.strip_layout((96, 128, 80))
+    fm = euler.fringe_map(patches, 5)
+    assert len(fm.copies) == 0 and len(fm.interp) == 2 * 2 * 5 * 40
+    masks = [euler.receiver_mask(p, 5) for p in patches]
+    for p, j, i, q, j0, i0, W in fm.interp:   # donors are never receivers
+        assert masks[p][j, i] and not masks[q][j0:j0 + 6, i0:i0 + 6].any()
+        assert abs(W.sum() - 1.0) < 1e-13
+
+    def f(x, y):
+        return (1.0 + 3 * x - 2 * x ** 3 + 5 * x ** 5) * (2.0 - 40 * y ** 2 + 9e4 * y ** 5)
+
+    st, ex = [], []
+    for pt in patches:
+        X, Y = pt.coords()
+        ex.append(f(X, Y))
+        s = f(X, Y)
+        s[euler.receiver_mask(pt, 5)] = -99.0
+        st.append(s)
+    euler.exchange(st, fm)
+    for a, b in zip(st, ex):
+        assert np.max(np.abs(a - b)) < 1e-12 * np.max(np.abs(b))
+
+
+def test_annulus_donor_index_matches_polar_inverse():
+    ring = I.annulus_ring()
+    pt = ring[1]
+    th0, th1 = 2 * np.pi / 3 - 0.45, 4 * np.pi / 3 + 0.45
+    rng = np.random.default_rng(3)
+    for _ in range(40):
+        th, r = rng.uniform(th0, th1), rng.uniform(0.5, 1.0)
+        fi, fj = euler.donor_index(pt, r * np.cos(th), r * np.sin(th))
+        assert abs(fi - (th - th0) / (th1 - th0) * (pt.n1 - 1)) < 1e-6
+        assert abs(fj - (r - 0.5) / 0.5 * (pt.n2 - 1)) < 1e-6
+
+
+def test_annulus_interpolation_converges_at_sixth_order():
+    def f(x, y):
+        return np.sin(2 * x + 0.3) * np.cos(3 * y) + x * y
+
+    errs = []
+    for s in (1, 2, 4):
+        ring = I.annulus_ring(sizes=((64 * s, 24 * s), (56 * s, 20 * s), (72 * s, 28 * s)))
+        fm = euler.fringe_map(ring, 5)
+        assert len(fm.interp) > 0
+        st, ex = [], []
+        for pt in ring:
+            X, Y = pt.coords()
+            ex.append(f(X, Y))
+            v = f(X, Y)
+            v[euler.receiver_mask(pt, 5)] = 0.0
+            st.append(v)
+        euler.exchange(st, fm)
+        errs.append(max(np.max(np.abs(a - b)) for a, b in zip(st, ex)))
+    assert errs[0] / errs[1] > 2 ** 5 and errs[1] / errs[2] > 2 ** 5
+
+
+def test_interpolated_viscosity_stays_non_negative():
+    patches = I.strip_layout((96, 128, 80))
+    fm = euler.fringe_map(patches, 5)
+    mu = []
+    for pt in patches:
+        X, _ = pt.coords()
+        mu.append(np.where(np.abs(X - 0.372) < 0.003, 1.0, 0.0))   # a sharp bump in the overlap
+    raw = euler.exchange([m.copy() for m in mu], fm)
+    clamped = euler.exchange([m.copy() for m in mu], fm, clamp=True)
+    assert min(r.min() for r in raw) < 0.0                         # Lagrange overshoot
+    assert min(c.min() for c in clamped) == 0.0
