@@ -1,5 +1,6 @@
 // C ABI of the FC-SDNN stage library: context setup and the entry points
 // declared in include/fcsdnn.h.  Device code lives in fcs_kernels.cuh.
+#include <algorithm>
 #include <cmath>
 #include <complex>
 #include <cstdio>
@@ -32,6 +33,12 @@ struct HostPlan {
   std::vector<double> tab;  // C x d
 };
 
+// A contiguous range of a work list (rows, line pairs, column tiles) whose
+// lines share one compile-time FFT size n1 (0: Stockham); one launch each.
+struct Group {
+  int n1, begin, count;
+};
+
 }  // namespace
 
 struct fcs_ctx {
@@ -45,7 +52,9 @@ struct fcs_ctx {
   size_t sstride = 0, qstride = 0, nwin = 0;
   int nlines0 = 0, nlines1 = 0, npairs0 = 0, npairs1 = 0, nent = 0, ntiles = 0;
   int nmax = 0, nfmax = 0, n2max = 0, stockham = 0, tw = 32;
-  int n1x = -1, n1y = -1;  // register-FFT size shared by all lines along q1 / q2 (0: Stockham kernels)
+  std::vector<int> patch_n1[2];  // per patch: FFT size of its lines along q1 / q2
+  std::vector<int> n1_dir[2];    // distinct FFT sizes per direction
+  std::vector<Group> g_rows, g_pairs[2], g_tiles;
   std::vector<int> tw_options;  // column-tile widths that fit in shared memory (widest first)
   CtxDev dev{};
   std::vector<void*> allocs;
@@ -54,7 +63,11 @@ struct fcs_ctx {
   int4* pairs1 = nullptr;
   int2* tiles = nullptr;
   int2* pblk = nullptr;  // point blocks of the pointwise kernels
-  int4* fringe_ent = nullptr;
+  int4* fringe_ent = nullptr;     // copies: (dst patch, dst point, src patch, src point)
+  int4* interp_ent = nullptr;     // interpolations: (dst patch, dst point, src patch, first block node)
+  double* interp_w64 = nullptr;   // 36 weights per interpolation
+  float* interp_w32 = nullptr;
+  int ninterp = 0;
   double* wq = nullptr;
   int2* woff = nullptr;
   double* bump = nullptr;
@@ -213,11 +226,11 @@ int get_plan(fcs_ctx* c, int N, int C, int d) {
 }
 
 template <typename T>
-size_t xpass_smem(const fcs_ctx* c) { return kWarps * xpass_warp_bytes<T>(c->nmax, c->nfmax, c->n1x); }
+size_t xpass_smem(const fcs_ctx* c, int n1) { return kWarps * xpass_warp_bytes<T>(c->nmax, c->nfmax, n1); }
 template <typename T>
 size_t deriv_smem(const fcs_ctx* c, int n1) { return kWarps * deriv_warp_bytes<T>(c->nmax, c->nfmax, n1); }
 template <typename T>
-size_t ypass_smem(const fcs_ctx* c, int tw) { return ypass_bytes<T>(c->n2max, tw, c->nfmax, c->n1y, kYWarps); }
+size_t ypass_smem(const fcs_ctx* c, int tw, int n1) { return ypass_bytes<T>(c->n2max, tw, c->nfmax, n1, kYWarps); }
 
 int grid_for(long long work, int per_block) {
   long long g = (work + per_block - 1) / per_block;
@@ -243,39 +256,70 @@ int grid_for(long long work, int per_block) {
 
 template <typename T>
 int set_smem_attrs(const fcs_ctx* c) {
-  const size_t xs = xpass_smem<T>(c), ys = ypass_smem<T>(c, c->tw);
-  FCS_N1_SWITCH(c->n1x, FCS_CUDA((prep_xpass<T, K>(xs))); break)
-  FCS_N1_SWITCH(c->n1y, FCS_CUDA((prep_ypass<T, K>(ys))); break)
-  FCS_N1_SWITCH(c->n1x, FCS_CUDA((prep_fc_deriv<T, K>(deriv_smem<T>(c, c->n1x)))); break)
-  FCS_N1_SWITCH(c->n1y, FCS_CUDA((prep_fc_deriv<T, K>(deriv_smem<T>(c, c->n1y)))); break)
+  for (int n1 : c->n1_dir[0]) {
+    FCS_N1_SWITCH(n1, FCS_CUDA((prep_xpass<T, K>(xpass_smem<T>(c, n1)))); break)
+  }
+  for (int n1 : c->n1_dir[1]) {
+    FCS_N1_SWITCH(n1, FCS_CUDA((prep_ypass<T, K>(ypass_smem<T>(c, c->tw, n1)))); break)
+  }
+  for (int dir = 0; dir < 2; ++dir)
+    for (int n1 : c->n1_dir[dir]) {
+      FCS_N1_SWITCH(n1, FCS_CUDA((prep_fc_deriv<T, K>(deriv_smem<T>(c, n1)))); break)
+    }
   return FCS_OK;
 }
 
+// FC derivative of a scalar field: one launch per FFT-size group of line pairs.
 template <typename T>
 int launch_deriv(fcs_ctx* c, const void* in, void* out, int dir, int order, cudaStream_t s) {
-  const int np = dir == 0 ? c->npairs0 : c->npairs1;
   const int4* pr = dir == 0 ? c->pairs0 : c->pairs1;
-  const int n1 = dir == 0 ? c->n1x : c->n1y;
-  const long long work = ((long long)c->dev.instances * np + jobs_per_round(n1) - 1) / jobs_per_round(n1);
-  const LaunchCfg g{(unsigned)grid_for(work, kWarps), kWarps * 32, deriv_smem<T>(c, n1), s};
-  FCS_N1_SWITCH(n1, return cuda_err((run_fc_deriv<T, K>(c->dev, dir, order, pr, np, static_cast<const T*>(in),
-                                                        static_cast<T*>(out), g))))
+  for (const Group& gr : c->g_pairs[dir]) {
+    const long long work = ((long long)c->dev.instances * gr.count + jobs_per_round(gr.n1) - 1) / jobs_per_round(gr.n1);
+    const LaunchCfg g{(unsigned)grid_for(work, kWarps), kWarps * 32, deriv_smem<T>(c, gr.n1), s};
+    FCS_N1_SWITCH(gr.n1, FCS_CUDA((run_fc_deriv<T, K>(c->dev, dir, order, pr + gr.begin, gr.count,
+                                                      static_cast<const T*>(in), static_cast<T*>(out), g))); break)
+  }
+  return FCS_OK;
 }
 
+// The operator (and stage): row passes, then column-tile passes, one launch
+// per FFT-size group; every row pass precedes every column pass in the stream.
 template <typename T>
 int launch_flux(fcs_ctx* c, const void* e, const void* mu, int mode, StageArgs<T> st, cudaStream_t s) {
-  const long long w0 = (long long)c->opt.instances * ((c->nlines0 + kRowsPerWarp - 1) / kRowsPerWarp);
-  const long long w1 = (long long)c->opt.instances * c->ntiles;
   const T* ep = static_cast<const T*>(e);
   const T* mp = static_cast<const T*>(mu);
   T* R = static_cast<T*>(c->R);
-  const LaunchCfg gx{(unsigned)grid_for(w0, kWarps), kWarps * 32, xpass_smem<T>(c), s};
-  FCS_N1_SWITCH(c->n1x, FCS_CUDA((run_xpass<T, K>(c->dev, ep, mp, R, gx))); break)
-  const LaunchCfg gy{(unsigned)grid_for(w1, 1), kYWarps * 32, ypass_smem<T>(c, c->tw), s};
-  if (mode == MODE_RHS) {
-    FCS_N1_SWITCH(c->n1y, return cuda_err((run_ypass<T, MODE_RHS, K>(c->dev, c->tiles, c->ntiles, ep, mp, R, st, gy))))
+  for (const Group& gr : c->g_rows) {
+    const long long w0 = (long long)c->opt.instances * ((gr.count + kRowsPerWarp - 1) / kRowsPerWarp);
+    const LaunchCfg gx{(unsigned)grid_for(w0, kWarps), kWarps * 32, xpass_smem<T>(c, gr.n1), s};
+    FCS_N1_SWITCH(gr.n1, FCS_CUDA((run_xpass<T, K>(c->dev, gr.begin, gr.count, ep, mp, R, gx))); break)
   }
-  FCS_N1_SWITCH(c->n1y, return cuda_err((run_ypass<T, MODE_RK, K>(c->dev, c->tiles, c->ntiles, ep, mp, R, st, gy))))
+  for (const Group& gr : c->g_tiles) {
+    const long long w1 = (long long)c->opt.instances * gr.count;
+    const LaunchCfg gy{(unsigned)grid_for(w1, 1), kYWarps * 32, ypass_smem<T>(c, c->tw, gr.n1), s};
+    const int2* tl = c->tiles + gr.begin;
+    if (mode == MODE_RHS) {
+      FCS_N1_SWITCH(gr.n1, FCS_CUDA((run_ypass<T, MODE_RHS, K>(c->dev, tl, gr.count, ep, mp, R, st, gy))); break)
+    } else {
+      FCS_N1_SWITCH(gr.n1, FCS_CUDA((run_ypass<T, MODE_RK, K>(c->dev, tl, gr.count, ep, mp, R, st, gy))); break)
+    }
+  }
+  return FCS_OK;
+}
+
+// Group a per-patch work list by the FFT size of its patches' lines: items of
+// all patches with size n1[0], then n1[1], ... (patch order kept inside).
+template <typename Item, typename Gen>
+void grouped(const fcs_ctx* c, int dir, std::vector<Item>* out, std::vector<Group>* groups, Gen gen) {
+  out->clear();
+  groups->clear();
+  for (int n1 : c->n1_dir[dir]) {
+    Group g{n1, (int)out->size(), 0};
+    for (int p = 0; p < c->npatch; ++p)
+      if (c->patch_n1[dir][p] == n1) gen(p, out);
+    g.count = (int)out->size() - g.begin;
+    if (g.count) groups->push_back(g);
+  }
 }
 
 cudaStream_t as_stream(void* s) { return static_cast<cudaStream_t>(s); }
@@ -283,6 +327,29 @@ cudaStream_t as_stream(void* s) { return static_cast<cudaStream_t>(s); }
 }  // namespace
 
 namespace {
+// Fringe exchange: copies, then interpolations (donors are never receivers, so
+// the two launches write and read disjoint points).  clamp floors the
+// interpolated values at zero (viscosity).
+int exchange_impl(fcs_ctx* c, void* field, int nfields, int clamp, cudaStream_t s) {
+  const long long I = c->opt.instances;
+  const bool f64 = c->opt.dtype == FCS_F64;
+  if (c->nent) {
+    const int g = grid_for(I * c->nent * nfields, 256);
+    if (f64) k_exchange<double><<<g, 256, 0, s>>>(c->dev, c->fringe_ent, c->nent, static_cast<double*>(field), nfields);
+    else k_exchange<float><<<g, 256, 0, s>>>(c->dev, c->fringe_ent, c->nent, static_cast<float*>(field), nfields);
+  }
+  if (c->ninterp) {
+    const int g = grid_for(I * c->ninterp * nfields, 256);
+    if (f64)
+      k_interp<double><<<g, 256, 0, s>>>(c->dev, c->interp_ent, c->interp_w64, c->ninterp,
+                                         static_cast<double*>(field), nfields, clamp);
+    else
+      k_interp<float><<<g, 256, 0, s>>>(c->dev, c->interp_ent, c->interp_w32, c->ninterp,
+                                        static_cast<float*>(field), nfields, clamp);
+  }
+  return cuda_err(cudaGetLastError());
+}
+
 template <typename T>
 int av_impl(fcs_ctx* c, const void* e, const int8_t* tau, void* mu, cudaStream_t s) {
   const dim3 g(c->dev.npblk, c->opt.instances);
@@ -297,7 +364,7 @@ int av_impl(fcs_ctx* c, const void* e, const int8_t* tau, void* mu, cudaStream_t
   k_av_bump<T><<<g, 256, 0, s>>>(c->dev, a1, a0, c->bump, r, 0);
   k_av_bump<T><<<g, 256, 0, s>>>(c->dev, a0, m, c->bump, r, 1);
   FCS_CUDA(cudaGetLastError());
-  return patch_exchange(c, mu, 1, s);
+  return exchange_impl(c, mu, 1, 1, s);
 }
 }  // namespace
 
@@ -313,11 +380,13 @@ int train_forward_backward(fcs_ctx* c, const float* x, const int8_t* lab, int B,
 }
 }  // namespace
 
-// Column tiles of the pass along q2 for tile width tw (one instance).
+// Column tiles of the pass along q2 for tile width tw (one instance),
+// grouped by FFT size.
 int set_tiles(fcs_ctx* c, const fcs_patch_desc* pd, int tw) {
   std::vector<int2> tiles;
-  for (int p = 0; p < c->npatch; ++p)
-    for (int c0 = 0; c0 < pd[p].n1; c0 += tw) tiles.push_back(make_int2(p, c0));
+  grouped(c, 1, &tiles, &c->g_tiles, [&](int p, std::vector<int2>* o) {
+    for (int c0 = 0; c0 < pd[p].n1; c0 += tw) o->push_back(make_int2(p, c0));
+  });
   int2* t = nullptr;
   int rc = upload(c, &t, tiles.data(), tiles.size() * sizeof(int2));
   if (rc) return rc;
@@ -458,8 +527,6 @@ int fc_setup(fcs_ctx** out, int d, int C, const fcs_patch_desc* pd, int npatch, 
       if (!(q.box[1] > q.box[0]) || !(q.box[3] > q.box[2])) return FCS_EINVAL;
     } else {
       if (!q.x || !q.y) return FCS_EINVAL;
-      for (int s = 0; s < 4; ++s)
-        if (q.bc[s] == FCS_BC_INTERNAL) return FCS_EUNSUPPORTED;
     }
     if (2 * o.n_f >= q.n1 || 2 * o.n_f >= q.n2) return FCS_EINVAL;
   }
@@ -493,11 +560,11 @@ int fc_setup(fcs_ctx** out, int d, int C, const fcs_patch_desc* pd, int npatch, 
       P.plan[dir] = pi;
       c->nmax = std::max(c->nmax, N);
       c->nfmax = std::max(c->nfmax, c->plans[pi].dev.n);
-      int& nd = dir == 0 ? c->n1x : c->n1y;
       int r = c->plans[pi].dev.n1reg;
       if (r % 2 == 0 && d > 5) r = 0;  // the two-level register FFT handles d <= 5
-      if (nd < 0) nd = r;
-      else if (nd != r) nd = 0;
+      c->patch_n1[dir].push_back(r);
+      if (std::find(c->n1_dir[dir].begin(), c->n1_dir[dir].end(), r) == c->n1_dir[dir].end())
+        c->n1_dir[dir].push_back(r);
     }
     c->n2max = std::max(c->n2max, q.n2);
     P.soff = (long long)soff;
@@ -542,31 +609,38 @@ int fc_setup(fcs_ctx** out, int d, int C, const fcs_patch_desc* pd, int npatch, 
     for (int i = 0; i < q.n1; ++i)
       for (int s : sy) wins.push_back(make_int4(p, 1, i, s));
     woff_ = wins.size();
-    for (int j = 0; j < q.n2; ++j) l0.push_back({p, j});
     for (int i = 0; i < q.n1; ++i) l1.push_back({p, i});
-    for (int j = 0; j < q.n2; j += 2) p0.push_back(make_int4(p, j, j + 1 < q.n2 ? j + 1 : -1, 0));
-    for (int i = 0; i < q.n1; i += 2) p1.push_back(make_int4(p, i, i + 1 < q.n1 ? i + 1 : -1, 0));
     c->patches.push_back(P);
   }
+  // rows and line pairs grouped by FFT size (one launch per group)
+  for (int dir = 0; dir < 2; ++dir) std::sort(c->n1_dir[dir].begin(), c->n1_dir[dir].end());
+  grouped(c, 0, &l0, &c->g_rows, [&](int p, std::vector<LineRef>* o) {
+    for (int j = 0; j < pd[p].n2; ++j) o->push_back({p, j});
+  });
+  grouped(c, 0, &p0, &c->g_pairs[0], [&](int p, std::vector<int4>* o) {
+    for (int j = 0; j < pd[p].n2; j += 2) o->push_back(make_int4(p, j, j + 1 < pd[p].n2 ? j + 1 : -1, 0));
+  });
+  grouped(c, 1, &p1, &c->g_pairs[1], [&](int p, std::vector<int4>* o) {
+    for (int i = 0; i < pd[p].n1; i += 2) o->push_back(make_int4(p, i, i + 1 < pd[p].n1 ? i + 1 : -1, 0));
+  });
   // indicator plan (degree 5, C = 26 on 16-point windows; direct DFT)
   const int ind = get_plan(c, 16, kIndC, kIndD);
   if (ind < 0) return fail(ind);
-  // a direction whose lines do not share one register-FFT size runs the
-  // Stockham kernels; every plan then needs a radix factorisation
-  for (int dir = 0; dir < 2; ++dir) {
-    const int nd = dir == 0 ? c->n1x : c->n1y;
-    if (nd == 0) {
-      c->stockham = 1;
-      for (int p = 0; p < npatch; ++p)
+  // lines in the Stockham group need a radix factorisation of their length
+  for (int dir = 0; dir < 2; ++dir)
+    for (int p = 0; p < npatch; ++p)
+      if (c->patch_n1[dir][p] == 0) {
+        c->stockham = 1;
         if (c->plans[c->patches[p].plan[dir]].dev.nst == 0) return fail(FCS_EUNSUPPORTED);
-    }
-  }
+      }
   // column-tile width of the pass along q2: widest of 32, 16, 8 that fits
   {
     const size_t esz = c->tsize, lim = 200 * 1024;
     int tw = 0;
     for (int t : {32, 16, 8}) {
-      const size_t b = esz == 8 ? ypass_smem<double>(c, t) : ypass_smem<float>(c, t);
+      size_t b = 0;
+      for (int n1 : c->n1_dir[1])
+        b = std::max(b, esz == 8 ? ypass_smem<double>(c, t, n1) : ypass_smem<float>(c, t, n1));
       if (b <= lim) {
         if (!tw) tw = t;
         c->tw_options.push_back(t);
@@ -576,8 +650,9 @@ int fc_setup(fcs_ctx** out, int d, int C, const fcs_patch_desc* pd, int npatch, 
     c->tw = tw;
   }
   std::vector<int2> tiles;
-  for (int p = 0; p < npatch; ++p)
-    for (int c0 = 0; c0 < pd[p].n1; c0 += c->tw) tiles.push_back(make_int2(p, c0));
+  grouped(c, 1, &tiles, &c->g_tiles, [&](int p, std::vector<int2>* o) {
+    for (int c0 = 0; c0 < pd[p].n1; c0 += c->tw) o->push_back(make_int2(p, c0));
+  });
   c->ntiles = (int)tiles.size();
   std::vector<int2> pblk;
   for (int p = 0; p < npatch; ++p)
@@ -591,42 +666,25 @@ int fc_setup(fcs_ctx** out, int d, int C, const fcs_patch_desc* pd, int npatch, 
   c->npairs1 = (int)p1.size();
 
   // ---- fringe map (§3.3): receivers within n_f points of an internal side;
-  // donor = lowest-numbered other Cartesian patch holding the same grid point
-  // outside its own fringe
+  // donors by fcs_donors.cpp (copies on coincident nodes, else interpolation)
   std::vector<unsigned char> fringe(qoff, 0);
-  auto is_recv = [&](int p, int i, int j) {
-    const fcs_patch_desc& q = pd[p];
-    return (q.bc[0] == FCS_BC_INTERNAL && i < o.n_f) || (q.bc[1] == FCS_BC_INTERNAL && i >= q.n1 - o.n_f) ||
-           (q.bc[2] == FCS_BC_INTERNAL && j < o.n_f) || (q.bc[3] == FCS_BC_INTERNAL && j >= q.n2 - o.n_f);
-  };
-  std::vector<int4> ent;
-  for (int p = 0; p < npatch; ++p) {
-    const fcs_patch_desc& q = pd[p];
-    for (int j = 0; j < q.n2; ++j)
-      for (int i = 0; i < q.n1; ++i) {
-        if (!is_recv(p, i, j)) continue;
-        fringe[c->scalar_off[p] + (long long)j * q.n1 + i] = 1;
-        const double x = q.box[0] + (q.box[1] - q.box[0]) * i / (q.n1 - 1);
-        const double y = q.box[2] + (q.box[3] - q.box[2]) * j / (q.n2 - 1);
-        int found = -1, fi = 0, fj = 0;
-        for (int r = 0; r < npatch && found < 0; ++r) {
-          if (r == p || !pd[r].cartesian) continue;
-          const fcs_patch_desc& s = pd[r];
-          const double hx = (s.box[1] - s.box[0]) / (s.n1 - 1), hy = (s.box[3] - s.box[2]) / (s.n2 - 1);
-          const double ui = (x - s.box[0]) / hx, uj = (y - s.box[2]) / hy;
-          const long long ii = std::llround(ui), jj = std::llround(uj);
-          if (std::fabs(ui - ii) > 1e-6 || std::fabs(uj - jj) > 1e-6) continue;
-          if (ii < 0 || ii >= s.n1 || jj < 0 || jj >= s.n2) continue;
-          if (is_recv(r, (int)ii, (int)jj)) continue;
-          found = r;
-          fi = (int)ii;
-          fj = (int)jj;
-        }
-        if (found < 0) return fail(FCS_EOVERLAP);
-        ent.push_back(make_int4(p, j * q.n1 + i, found, fj * pd[found].n1 + fi));
-      }
+  for (int p = 0; p < npatch; ++p)
+    for (int j = 0; j < pd[p].n2; ++j)
+      for (int i = 0; i < pd[p].n1; ++i)
+        if (is_receiver(pd[p], o.n_f, i, j)) fringe[c->scalar_off[p] + (long long)j * pd[p].n1 + i] = 1;
+  std::vector<FringeCopy> fcopy;
+  std::vector<FringeInterp> finterp;
+  if (build_fringe(pd, npatch, o.n_f, &fcopy, &finterp) != 0) return fail(FCS_EOVERLAP);
+  std::vector<int4> ent, ient;
+  std::vector<double> iw64;
+  for (const FringeCopy& f : fcopy) ent.push_back(make_int4(f.dst_patch, f.dst_point, f.src_patch, f.src_point));
+  for (const FringeInterp& f : finterp) {
+    ient.push_back(make_int4(f.dst_patch, f.dst_point, f.src_patch, f.src_point));
+    iw64.insert(iw64.end(), f.w, f.w + kStencil * kStencil);
   }
+  std::vector<float> iw32(iw64.begin(), iw64.end());
   c->nent = (int)ent.size();
+  c->ninterp = (int)ient.size();
 
   // ---- Gram basis on the d matching points (QR of the Vandermonde matrix,
   // modified Gram-Schmidt) and per plan the blend values of the Gram
@@ -726,6 +784,9 @@ int fc_setup(fcs_ctx** out, int d, int C, const fcs_patch_desc* pd, int npatch, 
       (rc = upload(c, &dwin, wins.data(), wins.size() * sizeof(int4))) ||
       (rc = upload(c, &dfr, fringe.data(), fringe.size())) ||
       (rc = upload(c, &c->fringe_ent, ent.data(), ent.size() * sizeof(int4))) ||
+      (rc = upload(c, &c->interp_ent, ient.data(), ient.size() * sizeof(int4))) ||
+      (rc = upload(c, &c->interp_w64, iw64.data(), iw64.size() * 8)) ||
+      (rc = upload(c, &c->interp_w32, iw32.data(), iw32.size() * 4)) ||
       (rc = upload(c, &c->wq, wq.data(), wq.size() * 8)) || (rc = upload(c, &c->woff, wo.data(), wo.size() * sizeof(int2))) ||
       (rc = upload(c, &c->bump, bump.data(), bump.size() * 8)) || (rc = dalloc(c, &dstatus, 16)))
     return fail(rc);
@@ -783,8 +844,10 @@ int fc_setup(fcs_ctx** out, int d, int C, const fcs_patch_desc* pd, int npatch, 
   D.n2max = c->n2max;
   if ((rc = (o.dtype == FCS_F64 ? set_smem_attrs<double>(c) : set_smem_attrs<float>(c)))) return fail(rc);
   if (o.dtype != FCS_F64) {  // the metrics use FP64 derivatives
-    FCS_N1_SWITCH(c->n1x, if (prep_fc_deriv<double, K>(deriv_smem<double>(c, c->n1x)) != cudaSuccess) return fail(FCS_ECUDA); break)
-    FCS_N1_SWITCH(c->n1y, if (prep_fc_deriv<double, K>(deriv_smem<double>(c, c->n1y)) != cudaSuccess) return fail(FCS_ECUDA); break)
+    for (int dir = 0; dir < 2; ++dir)
+      for (int n1 : c->n1_dir[dir]) {
+        FCS_N1_SWITCH(n1, if (prep_fc_deriv<double, K>(deriv_smem<double>(c, n1)) != cudaSuccess) return fail(FCS_ECUDA); break)
+      }
   }
 
   // ---- metrics of curvilinear patches: FP64 FC derivatives of x and y
@@ -885,15 +948,7 @@ int rk_stage(fcs_ctx* c, int stage, double dt, const double* dt_dev, const void*
 
 int patch_exchange(fcs_ctx* c, void* field, int nfields, void* stream) {
   if (!c || !field || (nfields != 1 && nfields != 4)) return FCS_EINVAL;
-  if (c->nent == 0) return FCS_OK;
-  const long long work = (long long)c->opt.instances * c->nent * nfields;
-  if (c->opt.dtype == FCS_F64)
-    k_exchange<double><<<grid_for(work, 256), 256, 0, as_stream(stream)>>>(c->dev, c->fringe_ent, c->nent,
-                                                                           static_cast<double*>(field), nfields);
-  else
-    k_exchange<float><<<grid_for(work, 256), 256, 0, as_stream(stream)>>>(c->dev, c->fringe_ent, c->nent,
-                                                                         static_cast<float*>(field), nfields);
-  return cuda_err(cudaGetLastError());
+  return exchange_impl(c, field, nfields, 0, as_stream(stream));
 }
 
 int fcs_time_step(fcs_ctx* c, const void* e, const void* mu, double* dt_dev, void* stream) {

@@ -1,8 +1,32 @@
-// Internal declarations shared by the host table builder (fcs_tables.cpp) and
-// the CUDA translation unit (fcs_api.cu).
+// Internal declarations shared by the host parts (fcs_tables.cpp: FC-Gram
+// tables, fcs_donors.cpp: donor search) and the CUDA translation unit
+// (fcs_api.cu).
 #pragma once
 
+#include <vector>
+
+#include "../../include/fcsdnn.h"
+
 namespace fcs {
+
+// Nodes per direction of the interpolation stencil of the fringe exchange.
+constexpr int kStencil = 6;
+
+struct FringeCopy {
+  int dst_patch, dst_point, src_patch, src_point;  // points as j * n1 + i of their patch
+};
+struct FringeInterp {
+  int dst_patch, dst_point, src_patch, src_point;  // src_point: first node of the stencil block
+  double w[kStencil * kStencil];                   // weights [b][a], b along j
+};
+
+// 1 if (i, j) of patch q lies in an n_f-point fringe of an internal side.
+bool is_receiver(const fcs_patch_desc& q, int n_f, int i, int j);
+
+// Donor of every receiver (copies for coincident nodes, tensor Lagrange
+// interpolation otherwise); -1 if some receiver has no donor.
+int build_fringe(const fcs_patch_desc* pd, int npatch, int n_f, std::vector<FringeCopy>* copies,
+                 std::vector<FringeInterp>* interp);
 
 // Period P and highest mode K of the blend-to-zero fit for (d, C).
 void fit_params(int d, int C, int* P, int* K);

@@ -34,6 +34,45 @@ __global__ void k_exchange(CtxDev c, const int4* __restrict__ ent, int nent, T* 
   }
 }
 
+// Interpolated fringe points: entries (dst patch, dst point, src patch, first
+// node of the donor block); w holds the kStencil x kStencil tensor Lagrange
+// weights of each entry ([b][a], b along j).  clamp floors the result at zero
+// (viscosity).
+template <typename T>
+__global__ void k_interp(CtxDev c, const int4* __restrict__ ent, const T* __restrict__ w, int nent, T* field,
+                         int nfields, int clamp) {
+  constexpr int S = 6;
+  const long long total = (long long)c.instances * nent * nfields;
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x) {
+    const int f = (int)(t % nfields);
+    const long long r = t / nfields;
+    const int inst = (int)(r / nent);
+    const int k = (int)(r % nent);
+    const int4 x = ent[k];
+    const PatchDev& Pd = c.patches[x.x];
+    const PatchDev& Ps = c.patches[x.z];
+    const T* src;
+    T* dst;
+    if (nfields == 4) {
+      src = field + inst * c.sstride + Ps.soff + (long long)f * Ps.n1 * Ps.n2 + x.w;
+      dst = field + inst * c.sstride + Pd.soff + (long long)f * Pd.n1 * Pd.n2 + x.y;
+    } else {
+      src = field + inst * c.qstride + Ps.qoff + x.w;
+      dst = field + inst * c.qstride + Pd.qoff + x.y;
+    }
+    const T* wk = w + (size_t)k * S * S;
+    T acc = T(0);
+#pragma unroll
+    for (int b = 0; b < S; ++b) {
+      T row = T(0);
+#pragma unroll
+      for (int a = 0; a < S; ++a) row += wk[b * S + a] * src[(long long)b * Ps.n1 + a];
+      acc += row;
+    }
+    *dst = clamp && acc < T(0) ? T(0) : acc;
+  }
+}
+
 // ============================================================ point helpers
 __device__ __forceinline__ int find_patch(const CtxDev& c, long long q) {
   int lo = 0, hi = c.npatch - 1;

@@ -29,8 +29,8 @@ cudaError_t run_fc_deriv(const CtxDev& c, int dir, int order, const int4* pairs,
   return cudaGetLastError();
 }
 template <typename T, int N1>
-cudaError_t run_xpass(const CtxDev& c, const T* e, const T* mu, T* R, LaunchCfg g) {
-  k_xpass<T, N1><<<g.grid, g.block, g.smem, g.stream>>>(c, e, mu, R);
+cudaError_t run_xpass(const CtxDev& c, int lbeg, int lcnt, const T* e, const T* mu, T* R, LaunchCfg g) {
+  k_xpass<T, N1><<<g.grid, g.block, g.smem, g.stream>>>(c, lbeg, lcnt, e, mu, R);
   return cudaGetLastError();
 }
 template <typename T, int MODE, int N1>
@@ -48,7 +48,7 @@ cudaError_t run_ypass(const CtxDev& c, const int2* tiles, int ntiles, const T* e
   template cudaError_t fcs::prep_fc_deriv<T, N1>(size_t);                                                     \
   template cudaError_t fcs::run_fc_deriv<T, N1>(const CtxDev&, int, int, const int4*, int, const T*, T*,     \
                                                 LaunchCfg);                                                   \
-  template cudaError_t fcs::run_xpass<T, N1>(const CtxDev&, const T*, const T*, T*, LaunchCfg);               \
+  template cudaError_t fcs::run_xpass<T, N1>(const CtxDev&, int, int, const T*, const T*, T*, LaunchCfg);     \
   template cudaError_t fcs::run_ypass<T, fcs::MODE_RHS, N1>(const CtxDev&, const int2*, int, const T*,       \
                                                             const T*, const T*, StageArgs<T>, LaunchCfg);     \
   template cudaError_t fcs::run_ypass<T, fcs::MODE_RK, N1>(const CtxDev&, const int2*, int, const T*,        \

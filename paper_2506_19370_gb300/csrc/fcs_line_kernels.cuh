@@ -154,12 +154,13 @@ __device__ __forceinline__ void point_flux(const CtxDev& c, const PatchDev& P, l
   }
 }
 
-// Pass along q1 (rows): R = -d/dq1 F1; a warp takes kRowsPerWarp rows of one
-// patch (rows are contiguous).  Jobs of a phase: (row, field pair); phase 0
-// (viscous only) W = d e/dx, phase 1 R = -d F/dx with F formed in W.
+// Pass along q1 (rows lbeg .. lbeg + lcnt - 1 of the row list, one FFT-size
+// group): R = -d/dq1 F1; a warp takes kRowsPerWarp rows.  Jobs of a phase:
+// (row, field pair); phase 0 (viscous only) W = d e/dx, phase 1 R = -d F/dx
+// with F formed in W.
 template <typename T, int N1>
-__global__ void __launch_bounds__(kWarps * 32, 4) k_xpass(CtxDev c, const T* __restrict__ e, const T* __restrict__ mu,
-                                                        T* __restrict__ R) {
+__global__ void __launch_bounds__(kWarps * 32, 4) k_xpass(CtxDev c, int lbeg, int lcnt, const T* __restrict__ e,
+                                                        const T* __restrict__ mu, T* __restrict__ R) {
   constexpr int JPR = jobs_per_round(N1);
   constexpr int RW = kRowsPerWarp;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -172,16 +173,16 @@ __global__ void __launch_bounds__(kWarps * 32, 4) k_xpass(CtxDev c, const T* __r
   Cx<T>* aux = reinterpret_cast<Cx<T>*>(base + align16((size_t)RW * 9 * nmax * sizeof(T)));
   const int g = JPR == 4 ? (lane >> 3) : 0;
   Cx<T>* tile = aux + (size_t)g * 8 * (4 * N1 + 1);
-  const long long groups = ((long long)c.nlines0 + RW - 1) / RW;   // row groups per instance (rows of one
-  const long long total = (long long)c.instances * groups;          // patch are contiguous in lines0)
+  const long long groups = ((long long)lcnt + RW - 1) / RW;   // row groups per instance
+  const long long total = (long long)c.instances * groups;
   for (long long w = (long long)blockIdx.x * kWarps + warp; w < total; w += (long long)gridDim.x * kWarps) {
     const int inst = (int)(w / groups);
-    const int l0 = (int)(w % groups) * RW;
+    const int l0 = lbeg + (int)(w % groups) * RW;
     int pid[RW], row[RW];
     bool has[RW], vrow[RW];
 #pragma unroll
     for (int k = 0; k < RW; ++k) {
-      has[k] = l0 + k < c.nlines0;
+      has[k] = l0 + k < lbeg + lcnt;
       const LineRef lr = c.lines0[has[k] ? l0 + k : l0];
       pid[k] = lr.patch;
       row[k] = lr.line;

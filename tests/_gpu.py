@@ -30,6 +30,22 @@ def layout(name):
                I.Patch(32, 36, (I.BC_INTERNAL, I.BC_WALL, I.BC_INTERNAL, I.BC_WALL), box=(29 / 60, 1, 25 / 60, 1))]
         rng = np.random.default_rng(7)
         return I.Instance(pts, [I.random_state(p, rng) for p in pts], name="split"), 1
+    if name == "strip":
+        # Sod on three patches of 96, 128 and 80 points along x: non-coincident
+        # grids (interpolated fringes) and two FFT sizes along x
+        return I.sod_instance(smear=3.0, patches=I.strip_layout((96, 128, 80))), 1
+    if name == "ring":
+        # annulus covered by three curvilinear sectors of different resolutions
+        # (interpolated fringes between curvilinear grids, two FFT sizes)
+        pts = I.annulus_ring(sizes=((64, 24), (100, 30), (72, 28)))
+        rng = np.random.default_rng(9)
+        st = []
+        for p in pts:
+            X, Y = p.coords()
+            a, b = rng.uniform(1, 3, 2)
+            st.append(I.conserved(1.4 * (1 + 0.05 * np.sin(a * X + b * Y)), 0.4 + 0.05 * np.cos(b * X), 0.2,
+                                  1.0 + 0.05 * np.cos(a * Y)))
+        return I.Instance(pts, st, name="ring"), 1
     raise KeyError(name)
 
 

@@ -20,7 +20,7 @@ from oracle import euler, fcgram, sdnn  # noqa: E402
 from paper_2506_19370_gb300 import fcsdnn  # noqa: E402
 from paper_2506_19370_gb300 import inputs as I  # noqa: E402
 
-from _gpu import deriv_bound, layout, random_fields, random_states, rel_err, table_gain  # noqa: E402
+from _gpu import EPS, deriv_bound, layout, random_fields, random_states, rel_err, table_gain  # noqa: E402
 
 DTYPES = [fcsdnn.F64, fcsdnn.F32]
 
@@ -97,7 +97,7 @@ def rhs_bound(dtype, inst, pol, states, mus=None):
 
 
 @pytest.mark.parametrize("dtype", DTYPES)
-@pytest.mark.parametrize("name", ["vortex", "sod", "annulus", "split"])
+@pytest.mark.parametrize("name", ["vortex", "sod", "annulus", "split", "strip", "ring"])
 def test_euler_rhs(name, dtype):
     inst, pol, ctx = ctx_for(name, dtype)
     st = random_states(inst, 11)
@@ -195,6 +195,48 @@ def test_exchange_is_bitwise():
     ref = euler.exchange([s[None].copy() for s in mu], euler.fringe_map(inst.patches, 5))
     for a, b in zip(ctx.unpack_scalar(m), ref):
         assert np.array_equal(a, b[0])
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("name", ["strip", "ring"])
+def test_interpolated_exchange(name, dtype):
+    # non-coincident grids: fringe values are 6 x 6 tensor Lagrange sums of
+    # donor values; every other point is untouched
+    inst, pol, ctx = ctx_for(name, dtype)
+    fm = euler.fringe_map(inst.patches, 5)
+    assert len(fm.interp) > 0
+    st = random_states(inst, 23)
+    npd = np.float32 if dtype == fcsdnn.F32 else np.float64
+    cast = [np.asarray(s, dtype=npd).astype(np.float64) for s in st]
+    e = ctx.to_device(ctx.pack_state(st))
+    ctx.patch_exchange(e, 4)
+    torch.cuda.synchronize()
+    ref = euler.exchange([s.copy() for s in cast], fm)
+    got = ctx.unpack_state(e)
+    # a sum of 36 products with weights of Lebesgue constant < 10 (tolerance:
+    # 36 roundings of the largest term, both sides)
+    tol = 2 * 36 * 10 * EPS[dtype] * max(np.abs(s).max() for s in cast)
+    err = max(float(np.abs(a - b).max()) for a, b in zip(got, ref))
+    print(f"interpolated exchange {name} dtype={dtype} max err {err:.3e} tol {tol:.3e} entries {len(fm.interp)}")
+    assert err <= tol
+    for a, b, p in zip(got, cast, inst.patches):
+        keep = ~euler.receiver_mask(p, 5)
+        assert np.array_equal(a[:, keep], b[:, keep])
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("name", ["strip", "ring"])
+def test_steps_with_interpolation(name, dtype):
+    inst, pol, ctx = ctx_for(name, dtype)
+    solver = euler.Solver(inst, c_policy=pol)
+    dt = 0.3 * solver.dt(inst.state)
+    got = run_steps(ctx, inst.state, 8, dt)
+    ref = [e.copy() for e in inst.state]
+    for _ in range(8):
+        ref = solver.step(ref, dt)
+    err = rel_err(got, ref)
+    print(f"{name} 8 steps with interpolation dtype={dtype} err={err:.3e}")
+    assert err < (1e-9 if dtype == fcsdnn.F64 else 1e-4)
 
 
 @pytest.mark.parametrize("name", ["vortex", "sod", "annulus"])
