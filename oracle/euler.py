@@ -15,8 +15,9 @@ Follows:
     L(e) = -(df/dx + dg/dy) with FC derivatives at the physical spacings;
   * artificial viscosity term (reading; the paper's form is in Part I):
     d_t e + div f = div(mu grad e), folded into the fluxes as
-    f - mu de/dx, g - mu de/dy (Cartesian patches); the normal viscous flux is
-    zero on wall, outflow and free sides (impermeable, adiabatic for the
+    f - mu de/dx, g - mu de/dy (on curvilinear patches the physical gradient
+    comes from the chain rule with the same metrics); the normal viscous flux
+    is zero on wall, outflow and free sides (impermeable, adiabatic for the
     diffusion term: the parabolic term needs a condition on every variable);
   * §5 item 4 / Algorithm 1: explicit four-stage Runge-Kutta (classical RK4
     coefficients, reading of "SSPRK-4"), boundary conditions enforced after
@@ -109,10 +110,30 @@ def rhs(e, geom, d, C, gamma, mu=None):
             g = g - vg
         return -(fcgram.fc_derivative_axis(f, geom.hx, d, C1, axis=2)
                  + fcgram.fc_derivative_axis(g, geom.hy, d, C2, axis=1))
-    if mu is not None:
-        raise NotImplementedError("artificial viscosity on curvilinear patches")
     F1 = geom.y_q2 * f - geom.x_q2 * g
     F2 = -geom.y_q1 * f + geom.x_q1 * g
+    if mu is not None:
+        # physical gradient by the chain rule, e_x = (y_q2 e_q1 - y_q1 e_q2)/J,
+        # e_y = (-x_q2 e_q1 + x_q1 e_q2)/J; viscous fluxes mu e_x, mu e_y in
+        # the same contravariant combination as f, g
+        e1 = fcgram.fc_derivative_axis(e, geom.h1, d, C1, axis=2)
+        e2 = fcgram.fc_derivative_axis(e, geom.h2, d, C2, axis=1)
+        ex = (geom.y_q2 * e1 - geom.y_q1 * e2) / geom.J
+        ey = (-geom.x_q2 * e1 + geom.x_q1 * e2) / geom.J
+        V1 = mu * (geom.y_q2 * ex - geom.x_q2 * ey)
+        V2 = mu * (-geom.y_q1 * ex + geom.x_q1 * ey)
+        noflux = (I.BC_WALL, I.BC_OUTFLOW, I.BC_FREE)
+        bc = geom.patch.bc
+        if bc[0] in noflux:
+            V1[:, :, 0] = 0.0
+        if bc[1] in noflux:
+            V1[:, :, -1] = 0.0
+        if bc[2] in noflux:
+            V2[:, 0, :] = 0.0
+        if bc[3] in noflux:
+            V2[:, -1, :] = 0.0
+        F1 = F1 - V1
+        F2 = F2 - V2
     div = (fcgram.fc_derivative_axis(F1, geom.h1, d, C1, axis=2)
            + fcgram.fc_derivative_axis(F2, geom.h2, d, C2, axis=1))
     return -div / geom.J
