@@ -54,13 +54,16 @@ struct fcs_ctx {
   int nmax = 0, nfmax = 0, n2max = 0, stockham = 0, tw = 32;
   std::vector<int> patch_n1[2];  // per patch: FFT size of its lines along q1 / q2
   std::vector<int> n1_dir[2];    // distinct FFT sizes per direction
-  std::vector<Group> g_rows, g_pairs[2], g_tiles;
+  std::vector<Group> g_rows, g_pairs[2], g_tiles, g_vpairs;
   std::vector<int> tw_options;  // column-tile widths that fit in shared memory (widest first)
   CtxDev dev{};
   std::vector<void*> allocs;
   // device arrays
   int4* pairs0 = nullptr;
   int4* pairs1 = nullptr;
+  int4* vpairs = nullptr;  // column pairs x fields of curvilinear patches (viscous gradient e_q2)
+  void* G1 = nullptr;      // e_q1, e_q2 of curvilinear patches (state-sized; viscous passes)
+  void* G2 = nullptr;
   int2* tiles = nullptr;
   int2* pblk = nullptr;  // point blocks of the pointwise kernels
   int4* fringe_ent = nullptr;     // copies: (dst patch, dst point, src patch, src point)
@@ -289,19 +292,28 @@ int launch_flux(fcs_ctx* c, const void* e, const void* mu, int mode, StageArgs<T
   const T* ep = static_cast<const T*>(e);
   const T* mp = static_cast<const T*>(mu);
   T* R = static_cast<T*>(c->R);
+  T* G1 = static_cast<T*>(c->G1);
+  T* G2 = static_cast<T*>(c->G2);
+  if (mu) {  // viscous fluxes of curvilinear patches need e_q2 before the row pass
+    for (const Group& gr : c->g_vpairs) {
+      const long long work = ((long long)c->dev.instances * gr.count + jobs_per_round(gr.n1) - 1) / jobs_per_round(gr.n1);
+      const LaunchCfg g{(unsigned)grid_for(work, kWarps), kWarps * 32, deriv_smem<T>(c, gr.n1), s};
+      FCS_N1_SWITCH(gr.n1, FCS_CUDA((run_fc_deriv<T, K>(c->dev, 1, 1, c->vpairs + gr.begin, gr.count, ep, G2, g))); break)
+    }
+  }
   for (const Group& gr : c->g_rows) {
     const long long w0 = (long long)c->opt.instances * ((gr.count + kRowsPerWarp - 1) / kRowsPerWarp);
     const LaunchCfg gx{(unsigned)grid_for(w0, kWarps), kWarps * 32, xpass_smem<T>(c, gr.n1), s};
-    FCS_N1_SWITCH(gr.n1, FCS_CUDA((run_xpass<T, K>(c->dev, gr.begin, gr.count, ep, mp, R, gx))); break)
+    FCS_N1_SWITCH(gr.n1, FCS_CUDA((run_xpass<T, K>(c->dev, gr.begin, gr.count, ep, mp, R, G1, G2, gx))); break)
   }
   for (const Group& gr : c->g_tiles) {
     const long long w1 = (long long)c->opt.instances * gr.count;
     const LaunchCfg gy{(unsigned)grid_for(w1, 1), kYWarps * 32, ypass_smem<T>(c, c->tw, gr.n1), s};
     const int2* tl = c->tiles + gr.begin;
     if (mode == MODE_RHS) {
-      FCS_N1_SWITCH(gr.n1, FCS_CUDA((run_ypass<T, MODE_RHS, K>(c->dev, tl, gr.count, ep, mp, R, st, gy))); break)
+      FCS_N1_SWITCH(gr.n1, FCS_CUDA((run_ypass<T, MODE_RHS, K>(c->dev, tl, gr.count, ep, mp, R, G1, st, gy))); break)
     } else {
-      FCS_N1_SWITCH(gr.n1, FCS_CUDA((run_ypass<T, MODE_RK, K>(c->dev, tl, gr.count, ep, mp, R, st, gy))); break)
+      FCS_N1_SWITCH(gr.n1, FCS_CUDA((run_ypass<T, MODE_RK, K>(c->dev, tl, gr.count, ep, mp, R, G1, st, gy))); break)
     }
   }
   return FCS_OK;
@@ -618,10 +630,16 @@ int fc_setup(fcs_ctx** out, int d, int C, const fcs_patch_desc* pd, int npatch, 
     for (int j = 0; j < pd[p].n2; ++j) o->push_back({p, j});
   });
   grouped(c, 0, &p0, &c->g_pairs[0], [&](int p, std::vector<int4>* o) {
-    for (int j = 0; j < pd[p].n2; j += 2) o->push_back(make_int4(p, j, j + 1 < pd[p].n2 ? j + 1 : -1, 0));
+    for (int j = 0; j < pd[p].n2; j += 2) o->push_back(make_int4(p, j, j + 1 < pd[p].n2 ? j + 1 : -1, -1));
   });
   grouped(c, 1, &p1, &c->g_pairs[1], [&](int p, std::vector<int4>* o) {
-    for (int i = 0; i < pd[p].n1; i += 2) o->push_back(make_int4(p, i, i + 1 < pd[p].n1 ? i + 1 : -1, 0));
+    for (int i = 0; i < pd[p].n1; i += 2) o->push_back(make_int4(p, i, i + 1 < pd[p].n1 ? i + 1 : -1, -1));
+  });
+  std::vector<int4> vp;  // state-layout column pairs of curvilinear patches, 4 fields
+  grouped(c, 1, &vp, &c->g_vpairs, [&](int p, std::vector<int4>* o) {
+    if (pd[p].cartesian) return;
+    for (int f = 0; f < 4; ++f)
+      for (int i = 0; i < pd[p].n1; i += 2) o->push_back(make_int4(p, i, i + 1 < pd[p].n1 ? i + 1 : -1, f));
   });
   // indicator plan (degree 5, C = 26 on 16-point windows; direct DFT)
   const int ind = get_plan(c, 16, kIndC, kIndD);
@@ -779,6 +797,7 @@ int fc_setup(fcs_ctx** out, int d, int C, const fcs_patch_desc* pd, int npatch, 
       (rc = upload(c, &dl1, l1.data(), l1.size() * sizeof(LineRef))) ||
       (rc = upload(c, &c->pairs0, p0.data(), p0.size() * sizeof(int4))) ||
       (rc = upload(c, &c->pairs1, p1.data(), p1.size() * sizeof(int4))) ||
+      (rc = upload(c, &c->vpairs, vp.data(), vp.size() * sizeof(int4))) ||
       (rc = upload(c, &c->tiles, tiles.data(), tiles.size() * sizeof(int2))) ||
       (rc = upload(c, &c->pblk, pblk.data(), pblk.size() * sizeof(int2))) ||
       (rc = upload(c, &dwin, wins.data(), wins.size() * sizeof(int4))) ||
@@ -805,6 +824,8 @@ int fc_setup(fcs_ctx** out, int d, int C, const fcs_patch_desc* pd, int npatch, 
       (rc = dalloc(c, &c->loss_s, (size_t)o.train_batch_max * 4)) ||
       (rc = dalloc(c, &c->gpart, (size_t)((o.train_batch_max + kGradChunk - 1) / kGradChunk) * kNParams * 8)) || (rc = dalloc(c, &m64, 5 * c->qstride * 8)) ||
       (rc = dalloc(c, &m32, 5 * c->qstride * 4)))
+    return fail(rc);
+  if (!vp.empty() && ((rc = dalloc(c, &c->G1, I * c->sstride * ts)) || (rc = dalloc(c, &c->G2, I * c->sstride * ts))))
     return fail(rc);
   c->W64 = dW64;
   D.patches = dpatch;

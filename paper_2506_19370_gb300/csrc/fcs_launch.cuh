@@ -63,9 +63,10 @@ template <typename T, int N1>
 cudaError_t run_fc_deriv(const CtxDev& c, int dir, int order, const int4* pairs, int npairs, const T* in, T* out,
                          LaunchCfg g);
 template <typename T, int N1>
-cudaError_t run_xpass(const CtxDev& c, int lbeg, int lcnt, const T* e, const T* mu, T* R, LaunchCfg g);
+cudaError_t run_xpass(const CtxDev& c, int lbeg, int lcnt, const T* e, const T* mu, T* R, T* G1, const T* G2,
+                      LaunchCfg g);
 template <typename T, int MODE, int N1>
 cudaError_t run_ypass(const CtxDev& c, const int2* tiles, int ntiles, const T* e, const T* mu, const T* R,
-                      StageArgs<T> st, LaunchCfg g);
+                      const T* G1, StageArgs<T> st, LaunchCfg g);
 
 }  // namespace fcs

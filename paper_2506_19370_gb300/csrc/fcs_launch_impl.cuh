@@ -29,14 +29,15 @@ cudaError_t run_fc_deriv(const CtxDev& c, int dir, int order, const int4* pairs,
   return cudaGetLastError();
 }
 template <typename T, int N1>
-cudaError_t run_xpass(const CtxDev& c, int lbeg, int lcnt, const T* e, const T* mu, T* R, LaunchCfg g) {
-  k_xpass<T, N1><<<g.grid, g.block, g.smem, g.stream>>>(c, lbeg, lcnt, e, mu, R);
+cudaError_t run_xpass(const CtxDev& c, int lbeg, int lcnt, const T* e, const T* mu, T* R, T* G1, const T* G2,
+                      LaunchCfg g) {
+  k_xpass<T, N1><<<g.grid, g.block, g.smem, g.stream>>>(c, lbeg, lcnt, e, mu, R, G1, G2);
   return cudaGetLastError();
 }
 template <typename T, int MODE, int N1>
 cudaError_t run_ypass(const CtxDev& c, const int2* tiles, int ntiles, const T* e, const T* mu, const T* R,
-                      StageArgs<T> st, LaunchCfg g) {
-  k_ypass<T, MODE, N1><<<g.grid, g.block, g.smem, g.stream>>>(c, tiles, ntiles, e, mu, R, st);
+                      const T* G1, StageArgs<T> st, LaunchCfg g) {
+  k_ypass<T, MODE, N1><<<g.grid, g.block, g.smem, g.stream>>>(c, tiles, ntiles, e, mu, R, G1, st);
   return cudaGetLastError();
 }
 
@@ -48,8 +49,11 @@ cudaError_t run_ypass(const CtxDev& c, const int2* tiles, int ntiles, const T* e
   template cudaError_t fcs::prep_fc_deriv<T, N1>(size_t);                                                     \
   template cudaError_t fcs::run_fc_deriv<T, N1>(const CtxDev&, int, int, const int4*, int, const T*, T*,     \
                                                 LaunchCfg);                                                   \
-  template cudaError_t fcs::run_xpass<T, N1>(const CtxDev&, int, int, const T*, const T*, T*, LaunchCfg);     \
+  template cudaError_t fcs::run_xpass<T, N1>(const CtxDev&, int, int, const T*, const T*, T*, T*, const T*,    \
+                                             LaunchCfg);                                                      \
   template cudaError_t fcs::run_ypass<T, fcs::MODE_RHS, N1>(const CtxDev&, const int2*, int, const T*,       \
-                                                            const T*, const T*, StageArgs<T>, LaunchCfg);     \
+                                                            const T*, const T*, const T*, StageArgs<T>,       \
+                                                            LaunchCfg);                                       \
   template cudaError_t fcs::run_ypass<T, fcs::MODE_RK, N1>(const CtxDev&, const int2*, int, const T*,        \
-                                                           const T*, const T*, StageArgs<T>, LaunchCfg);
+                                                           const T*, const T*, const T*, StageArgs<T>,        \
+                                                           LaunchCfg);

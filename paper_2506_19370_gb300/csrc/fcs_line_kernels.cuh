@@ -10,7 +10,8 @@ namespace fcs {
 
 // ============================================================ FC derivative
 // FC derivative of a scalar field: each warp takes jobs_per_round(N1) line
-// pairs at a time (two real lines -> one complex FFT).
+// pairs at a time (two real lines -> one complex FFT).  A pair (patch, line a,
+// line b, w) reads the scalar layout if w < 0, else field w of the state layout.
 template <typename T, int N1>
 __global__ void __launch_bounds__(kWarps * 32) k_fc_deriv(CtxDev c, int dir, int order, const int4* __restrict__ pairs,
                                                            int npairs, const T* __restrict__ in, T* __restrict__ out) {
@@ -37,7 +38,8 @@ __global__ void __launch_bounds__(kWarps * 32) k_fc_deriv(CtxDev c, int dir, int
       const long long stride = dir == 0 ? 1 : P.n1;
       const long long la = dir == 0 ? (long long)pr.y * P.n1 : pr.y;
       const long long lb = pr.z < 0 ? -1 : (dir == 0 ? (long long)pr.z * P.n1 : pr.z);
-      const T* src = in + inst * c.qstride + P.qoff;
+      const T* src = in + (pr.w < 0 ? inst * c.qstride + P.qoff
+                                    : inst * c.sstride + P.soff + (long long)pr.w * P.n1 * P.n2);
       for (int t = lane; t < N; t += 32) {
         L[(2 * k) * nmax + t] = src[la + t * stride];
         L[(2 * k + 1) * nmax + t] = lb >= 0 ? src[lb + t * stride] : T(0);
@@ -54,7 +56,8 @@ __global__ void __launch_bounds__(kWarps * 32) k_fc_deriv(CtxDev c, int dir, int
     const long long stride = dir == 0 ? 1 : P.n1;
     const long long la = dir == 0 ? (long long)pr.y * P.n1 : pr.y;
     const long long lb = pr.z < 0 ? -1 : (dir == 0 ? (long long)pr.z * P.n1 : pr.z);
-    T* dst = out + inst * c.qstride + P.qoff;
+    T* dst = out + (pr.w < 0 ? inst * c.qstride + P.qoff
+                             : inst * c.sstride + P.soff + (long long)pr.w * P.n1 * P.n2);
     line_deriv_pair<T, N1>(L + (2 * g) * nmax, 1, lb >= 0 ? L + (2 * g + 1) * nmax : nullptr, 1, dst + la, (int)stride,
                            lb >= 0 ? dst + lb : nullptr, (int)stride, T(1), c, pl, T(1) / T(pl.N - 1), order, lane, aux,
                            aux + c.nfmax, tile, active);
@@ -106,13 +109,15 @@ __device__ __forceinline__ void apply_bc(const CtxDev& c, const PatchDev& P, int
 
 // Flux of Eq. (1) along direction DIR at one point, transformed for the
 // parameter direction: DIR 0: y_q2 f - x_q2 g, DIR 1: -y_q1 f + x_q1 g;
-// Cartesian: f resp. g, minus mu times the derivative dv (viscous flux).
-// t is the point's index along the line: the normal viscous flux is zero on
-// wall, outflow and free sides (the diffusion term needs a condition on every
-// variable there; this one is impermeable and adiabatic).
+// Cartesian: f resp. g.  With viscosity the physical fluxes become f - mu e_x,
+// g - mu e_y: dv is the derivative of e along this direction's parameter and
+// dvo (curvilinear only) along the other one; e_x, e_y follow by the chain
+// rule.  t is the point's index along the line: the normal viscous flux is
+// zero on wall, outflow and free sides (the diffusion term needs a condition
+// on every variable there; this one is impermeable and adiabatic).
 template <typename T, int DIR>
 __device__ __forceinline__ void point_flux(const CtxDev& c, const PatchDev& P, long long q, const T* v, const T* dv,
-                                           T mu, bool visc, T* F, int t) {
+                                           const T* dvo, T mu, bool visc, T* F, int t) {
   if (visc) {
     const int N = DIR == 0 ? P.n1 : P.n2;
     const int side = t == 0 ? 2 * DIR : (t == N - 1 ? 2 * DIR + 1 : -1);
@@ -137,30 +142,37 @@ __device__ __forceinline__ void point_flux(const CtxDev& c, const PatchDev& P, l
     }
   } else {
     const T* Mt = metrics<T>(c);
-    T ca, cb;
-    if (DIR == 0) {
-      ca = Mt[3 * c.qstride + q];
-      cb = -Mt[1 * c.qstride + q];
-    } else {
-      ca = -Mt[2 * c.qstride + q];
-      cb = Mt[0 * c.qstride + q];
-    }
+    const long long qs = c.qstride;
+    const T x_q1 = Mt[q], x_q2 = Mt[qs + q], y_q1 = Mt[2 * qs + q], y_q2 = Mt[3 * qs + q];
+    const T ca = DIR == 0 ? y_q2 : -y_q1;
+    const T cb = DIR == 0 ? -x_q2 : x_q1;
     const T f0 = mx, f1 = mx * u + p, f2 = my * u, f3 = (En + p) * u;
     const T g0 = my, g1 = mx * w, g2 = my * w + p, g3 = (En + p) * w;
     F[0] = ca * f0 + cb * g0;
     F[1] = ca * f1 + cb * g1;
     F[2] = ca * f2 + cb * g2;
     F[3] = ca * f3 + cb * g3;
+    if (visc) {
+      const T invJ = T(1) / Mt[4 * qs + q];
+#pragma unroll
+      for (int f = 0; f < 4; ++f) {
+        const T d1 = DIR == 0 ? dv[f] : dvo[f], d2 = DIR == 0 ? dvo[f] : dv[f];
+        const T ex = (y_q2 * d1 - y_q1 * d2) * invJ, ey = (-x_q2 * d1 + x_q1 * d2) * invJ;
+        F[f] -= mu * (ca * ex + cb * ey);
+      }
+    }
   }
 }
 
 // Pass along q1 (rows lbeg .. lbeg + lcnt - 1 of the row list, one FFT-size
 // group): R = -d/dq1 F1; a warp takes kRowsPerWarp rows.  Jobs of a phase:
-// (row, field pair); phase 0 (viscous only) W = d e/dx, phase 1 R = -d F/dx
-// with F formed in W.
+// (row, field pair); phase 0 (viscous only) W = d e/dq1, phase 1 R = -d F/dq1
+// with F formed in W.  Curvilinear viscous rows read e_q2 from G2 (computed
+// before this pass) and leave e_q1 in G1 for the pass along q2.
 template <typename T, int N1>
 __global__ void __launch_bounds__(kWarps * 32, 4) k_xpass(CtxDev c, int lbeg, int lcnt, const T* __restrict__ e,
-                                                        const T* __restrict__ mu, T* __restrict__ R) {
+                                                        const T* __restrict__ mu, T* __restrict__ R,
+                                                        T* __restrict__ G1, const T* __restrict__ G2) {
   constexpr int JPR = jobs_per_round(N1);
   constexpr int RW = kRowsPerWarp;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -189,7 +201,7 @@ __global__ void __launch_bounds__(kWarps * 32, 4) k_xpass(CtxDev c, int lbeg, in
       const PatchDev& P = c.patches[lr.patch];
       const long long np = (long long)P.n1 * P.n2;
       const T* es = e + inst * c.sstride + P.soff + (long long)lr.line * P.n1;
-      const bool visc = (mu != nullptr) && P.cart;
+      const bool visc = mu != nullptr;
       bool any_mu = false;
       if (has[k])
         for (int t = lane; t < P.n1; t += 32) {
@@ -214,15 +226,20 @@ __global__ void __launch_bounds__(kWarps * 32, 4) k_xpass(CtxDev c, int lbeg, in
           if (!has[k]) continue;
           const PatchDev& P = c.patches[pid[k]];
           const bool visc = vrow[k];
+          const bool curv = visc && !P.cart;
           const long long q0 = P.qoff + (long long)row[k] * P.n1;
+          const long long np = (long long)P.n1 * P.n2;
+          const long long s0 = inst * c.sstride + P.soff + (long long)row[k] * P.n1;
           for (int t = lane; t < P.n1; t += 32) {
-            T v[4], dv[4], F[4];
+            T v[4], dv[4], dvo[4], F[4];
 #pragma unroll
             for (int f = 0; f < 4; ++f) {
               v[f] = E[(k * 4 + f) * nmax + t];
               dv[f] = visc ? W[(k * 4 + f) * nmax + t] : T(0);
+              dvo[f] = curv ? G2[s0 + f * np + t] : T(0);
+              if (curv) G1[s0 + f * np + t] = dv[f];
             }
-            point_flux<T, 0>(c, P, q0 + t, v, dv, visc ? M[k * nmax + t] : T(0), visc, F, t);
+            point_flux<T, 0>(c, P, q0 + t, v, dv, dvo, visc ? M[k * nmax + t] : T(0), visc, F, t);
 #pragma unroll
             for (int f = 0; f < 4; ++f) W[(k * 4 + f) * nmax + t] = F[f];
           }
@@ -263,10 +280,13 @@ __global__ void __launch_bounds__(kWarps * 32, 4) k_xpass(CtxDev c, int lbeg, in
 // Pass along q2 on a tile of tw adjacent columns of one patch (coalesced row
 // segments staged in shared memory): L = (R - d/dq2 F2)/J, then either L
 // (MODE_RHS) or the Runge-Kutta stage with boundary conditions (MODE_RK).
+// Curvilinear viscous columns read e_q1 from G1 (left by the row pass; rows
+// without viscosity leave stale values there, which only meet mu = 0).
 template <typename T, int MODE, int N1>
 __global__ void __launch_bounds__(kYWarps * 32, 3) k_ypass(CtxDev c, const int2* __restrict__ tiles, int ntiles,
                                                          const T* __restrict__ e, const T* __restrict__ mu,
-                                                         const T* __restrict__ R, StageArgs<T> st) {
+                                                         const T* __restrict__ R, const T* __restrict__ G1,
+                                                         StageArgs<T> st) {
   constexpr int JPR = jobs_per_round(N1);
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -290,7 +310,7 @@ __global__ void __launch_bounds__(kYWarps * 32, 3) k_ypass(CtxDev c, const int2*
     const long long np = (long long)P.n1 * P.n2;
     const long long sbase = inst * c.sstride + P.soff + c0;
     const long long qbase = P.qoff + c0;
-    const bool visc = (mu != nullptr) && P.cart;
+    const bool visc = mu != nullptr;
     // each thread keeps one column cc of the tile and strides over rows
     const int cc = threadIdx.x % tw, jr = threadIdx.x / tw, js = blockDim.x / tw;
     const bool colok = cc < width && jr < js;
@@ -325,14 +345,16 @@ __global__ void __launch_bounds__(kYWarps * 32, 3) k_ypass(CtxDev c, const int2*
     for (int phase = (visc && nact > 0) ? 0 : 1; phase < 2; ++phase) {
       if (phase == 1) {
         for (int j = jr; colok && j < N; j += js) {
-          T v[4], dv[4], F[4];
+          T v[4], dv[4], dvo[4], F[4];
+          const bool vc = visc && colv[cc];
+          const bool curv = vc && !P.cart;
 #pragma unroll
           for (int f = 0; f < 4; ++f) {
             v[f] = E[(f * n2m + j) * ld + cc];
-            dv[f] = (visc && colv[cc]) ? D[(f * n2m + j) * ld + cc] : T(0);
+            dv[f] = vc ? D[(f * n2m + j) * ld + cc] : T(0);
+            dvo[f] = curv ? G1[sbase + f * np + (long long)j * P.n1 + cc] : T(0);
           }
-          const bool vc = visc && colv[cc];
-          point_flux<T, 1>(c, P, qbase + (long long)j * P.n1 + cc, v, dv, vc ? M[j * ld + cc] : T(0), vc, F, j);
+          point_flux<T, 1>(c, P, qbase + (long long)j * P.n1 + cc, v, dv, dvo, vc ? M[j * ld + cc] : T(0), vc, F, j);
 #pragma unroll
           for (int f = 0; f < 4; ++f) D[(f * n2m + j) * ld + cc] = F[f];
         }

@@ -74,24 +74,37 @@ def rhs_bound(dtype, inst, pol, states, mus=None):
     for k, (e, p) in enumerate(zip(states, inst.patches)):
         g = euler.PatchGeom(p, 5, 25, pol)
         f, gg = euler.fluxes(e, inst.gamma)
-        if mus is not None:
-            f = f - mus[k] * fcgram.fc_derivative_axis(e, g.hx, 5, g.C1, axis=2)
-            gg = gg - mus[k] * fcgram.fc_derivative_axis(e, g.hy, 5, g.C2, axis=1)
         if p.cartesian:
-            F1, F2, h1, h2, jmin = f, gg, g.hx, g.hy, 1.0
+            h1, h2, jmin, mfac = g.hx, g.hy, 1.0, 1.0
+        else:
+            h1, h2, jmin = g.h1, g.h2, float(np.abs(g.J).min())
+            # metric factor of the chain rule and the contravariant combination
+            mfac = sum(float(np.abs(m).max()) for m in (g.x_q1, g.x_q2, g.y_q1, g.y_q2)) ** 2 / jmin
+        if mus is not None:
+            e1 = fcgram.fc_derivative_axis(e, h1, 5, g.C1, axis=2)
+            e2 = fcgram.fc_derivative_axis(e, h2, 5, g.C2, axis=1)
+            if p.cartesian:
+                ex, ey = e1, e2
+            else:
+                ex = (g.y_q2 * e1 - g.y_q1 * e2) / g.J
+                ey = (-g.x_q2 * e1 + g.x_q1 * e2) / g.J
+            f = f - mus[k] * ex
+            gg = gg - mus[k] * ey
+        if p.cartesian:
+            F1, F2 = f, gg
         else:
             F1 = g.y_q2 * f - g.x_q2 * gg
             F2 = -g.y_q1 * f + g.x_q1 * gg
-            h1, h2, jmin = g.h1, g.h2, float(np.abs(g.J).min())
         b = (deriv_bound(dtype, np.abs(F1).max(), h1, p.n1 + g.C1, 1, table_gain(5, g.C1))
              + deriv_bound(dtype, np.abs(F2).max(), h2, p.n2 + g.C2, 1, table_gain(5, g.C2))) / jmin
         if mus is not None:
-            # rounding of the inner derivative d e / dx enters the viscous flux
-            # times mu and is differentiated once more (wavenumbers up to pi/h)
+            # rounding of the inner derivatives enters the viscous flux times mu
+            # (and the metric factors) and is differentiated once more
+            # (wavenumbers up to pi/h)
             mmax = float(np.abs(mus[k]).max())
             for h, n, C in ((h1, p.n1 + g.C1, g.C1), (h2, p.n2 + g.C2, g.C2)):
                 inner = deriv_bound(dtype, np.abs(e).max(), h, n, 1, table_gain(5, C))
-                b += 4.0 * mmax * inner * np.pi / h
+                b += 4.0 * mmax * inner * mfac * np.pi / min(h1, h2) / jmin
         out.append(b)
     return out
 
@@ -116,8 +129,9 @@ def test_euler_rhs(name, dtype):
 
 
 @pytest.mark.parametrize("dtype", DTYPES)
-def test_euler_rhs_with_viscosity(dtype):
-    inst, pol, ctx = ctx_for("sod", dtype)
+@pytest.mark.parametrize("name", ["sod", "annulus", "ring"])
+def test_euler_rhs_with_viscosity(name, dtype):
+    inst, pol, ctx = ctx_for(name, dtype)
     st = random_states(inst, 12)
     rng = np.random.default_rng(4)
     mu = [0.01 * rng.uniform(0, 1) * (1 + np.sin(p.coords()[0] * 7)) for p in inst.patches]
@@ -134,7 +148,7 @@ def test_euler_rhs_with_viscosity(dtype):
     got = ctx.unpack_state(rhs)
     bounds = rhs_bound(dtype, inst, pol, cast, mcast)
     ratios = [float(np.abs(a - b).max()) / bd for a, b, bd in zip(got, ref, bounds)]
-    print(f"euler_rhs+mu dtype={dtype} rel={rel_err(got, ref):.3e} err/bound={max(ratios):.2e}")
+    print(f"euler_rhs+mu {name} dtype={dtype} rel={rel_err(got, ref):.3e} err/bound={max(ratios):.2e}")
     assert max(ratios) <= 1.0
 
 
