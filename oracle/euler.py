@@ -60,16 +60,24 @@ def fluxes(e, gamma):
 
 
 class PatchGeom:
-    """Per-patch quantities the operator needs: spacings and metrics."""
+    """Per-patch quantities the operator needs: spacings, metrics, line segments.
+
+    Grid lines of an L-shaped patch (§3.2, parameter space L) are the
+    segments of the rows and columns that lie in the patch: rows j < m2 and
+    columns i < m1 are shorter; every segment is differentiated on its own,
+    with its own continuation length.
+    """
 
     def __init__(self, patch, d, C, c_policy=0):
         self.patch = patch
-        # continuation length per direction (lines along q1 have n1 points)
-        self.C1 = fcgram.policy_c(patch.n1, C) if c_policy else C
-        self.C2 = fcgram.policy_c(patch.n2, C) if c_policy else C
+        self.d, self.C, self.c_policy = d, C, c_policy
+        # continuation length per direction (full lines along q1 have n1 points)
+        self.C1 = self.C_of(patch.n1)
+        self.C2 = self.C_of(patch.n2)
         self.n1, self.n2 = patch.n1, patch.n2
         self.h1 = 1.0 / (patch.n1 - 1)
         self.h2 = 1.0 / (patch.n2 - 1)
+        self.active = patch.active()
         if patch.cartesian:
             x0, x1, y0, y1 = patch.box
             self.hx = (x1 - x0) / (patch.n1 - 1)
@@ -80,63 +88,98 @@ class PatchGeom:
             self.y_q1 = np.zeros((self.n2, self.n1))
         else:
             X, Y = patch.coords()
-            self.x_q1 = fcgram.fc_derivative_axis(X, self.h1, d, self.C1, axis=1)
-            self.x_q2 = fcgram.fc_derivative_axis(X, self.h2, d, self.C2, axis=0)
-            self.y_q1 = fcgram.fc_derivative_axis(Y, self.h1, d, self.C1, axis=1)
-            self.y_q2 = fcgram.fc_derivative_axis(Y, self.h2, d, self.C2, axis=0)
+            self.x_q1 = self.D(X, 0, self.h1)
+            self.x_q2 = self.D(X, 1, self.h2)
+            self.y_q1 = self.D(Y, 0, self.h1)
+            self.y_q2 = self.D(Y, 1, self.h2)
+            for m in (self.x_q1, self.x_q2, self.y_q1, self.y_q2):
+                m[~self.active] = 1.0 if m is self.x_q1 or m is self.y_q2 else 0.0
         self.J = self.x_q1 * self.y_q2 - self.x_q2 * self.y_q1
+
+    def C_of(self, N):
+        return fcgram.policy_c(N, self.C) if self.c_policy else self.C
+
+    def segments(self, dirn):
+        """(index block, line length) of the line segments along q1 (dirn 0) or q2 (1)."""
+        n1, n2 = self.patch.n1, self.patch.n2
+        m1, m2 = self.patch.lcut if self.patch.is_l else (0, 0)
+        if dirn == 0:
+            out = [((slice(m2, n2), slice(0, n1)), n1)]
+            if m2:
+                out.append(((slice(0, m2), slice(m1, n1)), n1 - m1))
+        else:
+            out = [((slice(0, n2), slice(m1, n1)), n2)]
+            if m1:
+                out.append(((slice(m2, n2), slice(0, m1)), n2 - m2))
+        return out
+
+    def D(self, a, dirn, h, order=1):
+        """FC derivative of a (..., n2, n1) along q1 (dirn 0) or q2 (dirn 1),
+        segment by segment; zero outside the patch."""
+        a = np.asarray(a, dtype=np.float64)
+        out = np.zeros_like(a)
+        axis = a.ndim - 1 if dirn == 0 else a.ndim - 2
+        for blk, N in self.segments(dirn):
+            idx = (Ellipsis,) + blk
+            out[idx] = fcgram.fc_derivative_axis(a[idx], h, self.d, self.C_of(N), axis=axis, order=order)
+        return out
+
+
+def _zero_normal_viscous(V1, V2, patch):
+    """Zero normal viscous flux on wall, outflow and free sides, and on the
+    inner (wall) edges of an L-shaped patch."""
+    noflux = (I.BC_WALL, I.BC_OUTFLOW, I.BC_FREE)
+    bc = patch.bc
+    if bc[0] in noflux:
+        V1[:, :, 0] = 0.0
+    if bc[1] in noflux:
+        V1[:, :, -1] = 0.0
+    if bc[2] in noflux:
+        V2[:, 0, :] = 0.0
+    if bc[3] in noflux:
+        V2[:, -1, :] = 0.0
+    if patch.is_l:
+        m1, m2 = patch.lcut
+        V1[:, :m2, m1] = 0.0
+        V2[:, m2, :m1] = 0.0
 
 
 def rhs(e, geom, d, C, gamma, mu=None):
-    """L(e) on one patch (Algorithm 5, operator evaluation); e is (4, n2, n1)."""
+    """L(e) on one patch (Algorithm 5, operator evaluation); e is (4, n2, n1).
+
+    Points outside an L-shaped patch get zero.
+    """
     e = np.asarray(e, dtype=np.float64)
+    if geom.patch.is_l:
+        # outside values never enter a line segment; keep them harmless
+        e = np.where(geom.active, e, np.array([1.0, 0.0, 0.0, 2.5])[:, None, None])
     f, g = fluxes(e, gamma)
-    C1, C2 = geom.C1, geom.C2
     if geom.patch.cartesian:
         if mu is not None:
-            vf = mu * fcgram.fc_derivative_axis(e, geom.hx, d, C1, axis=2)
-            vg = mu * fcgram.fc_derivative_axis(e, geom.hy, d, C2, axis=1)
-            noflux = (I.BC_WALL, I.BC_OUTFLOW, I.BC_FREE)
-            bc = geom.patch.bc
-            if bc[0] in noflux:
-                vf[:, :, 0] = 0.0
-            if bc[1] in noflux:
-                vf[:, :, -1] = 0.0
-            if bc[2] in noflux:
-                vg[:, 0, :] = 0.0
-            if bc[3] in noflux:
-                vg[:, -1, :] = 0.0
+            vf = mu * geom.D(e, 0, geom.hx)
+            vg = mu * geom.D(e, 1, geom.hy)
+            _zero_normal_viscous(vf, vg, geom.patch)
             f = f - vf
             g = g - vg
-        return -(fcgram.fc_derivative_axis(f, geom.hx, d, C1, axis=2)
-                 + fcgram.fc_derivative_axis(g, geom.hy, d, C2, axis=1))
+        L = -(geom.D(f, 0, geom.hx) + geom.D(g, 1, geom.hy))
+        return np.where(geom.active, L, 0.0)
     F1 = geom.y_q2 * f - geom.x_q2 * g
     F2 = -geom.y_q1 * f + geom.x_q1 * g
     if mu is not None:
         # physical gradient by the chain rule, e_x = (y_q2 e_q1 - y_q1 e_q2)/J,
         # e_y = (-x_q2 e_q1 + x_q1 e_q2)/J; viscous fluxes mu e_x, mu e_y in
         # the same contravariant combination as f, g
-        e1 = fcgram.fc_derivative_axis(e, geom.h1, d, C1, axis=2)
-        e2 = fcgram.fc_derivative_axis(e, geom.h2, d, C2, axis=1)
+        e1 = geom.D(e, 0, geom.h1)
+        e2 = geom.D(e, 1, geom.h2)
         ex = (geom.y_q2 * e1 - geom.y_q1 * e2) / geom.J
         ey = (-geom.x_q2 * e1 + geom.x_q1 * e2) / geom.J
         V1 = mu * (geom.y_q2 * ex - geom.x_q2 * ey)
         V2 = mu * (-geom.y_q1 * ex + geom.x_q1 * ey)
-        noflux = (I.BC_WALL, I.BC_OUTFLOW, I.BC_FREE)
-        bc = geom.patch.bc
-        if bc[0] in noflux:
-            V1[:, :, 0] = 0.0
-        if bc[1] in noflux:
-            V1[:, :, -1] = 0.0
-        if bc[2] in noflux:
-            V2[:, 0, :] = 0.0
-        if bc[3] in noflux:
-            V2[:, -1, :] = 0.0
+        _zero_normal_viscous(V1, V2, geom.patch)
         F1 = F1 - V1
         F2 = F2 - V2
-    div = (fcgram.fc_derivative_axis(F1, geom.h1, d, C1, axis=2)
-           + fcgram.fc_derivative_axis(F2, geom.h2, d, C2, axis=1))
-    return -div / geom.J
+    div = geom.D(F1, 0, geom.h1) + geom.D(F2, 1, geom.h2)
+    return np.where(geom.active, -div / geom.J, 0.0)
 
 
 def _side_index(side, n1, n2):
@@ -149,17 +192,55 @@ def _side_index(side, n1, n2):
     return (slice(None), n2 - 1, slice(None))
 
 
+def _sides(patch):
+    """(side, code, index) of every boundary side in application order: left,
+    right, bottom, top, then for an L-shaped patch its inner vertical edge
+    (i = m1, j < m2; a q1 = const side like left), inner horizontal edge
+    (j = m2, i < m1; like bottom), both walls, and the corner node (m1, m2)
+    (side -1: wall along the bisector of the two edge normals).  Outer sides
+    of an L-shaped patch hold only its points (left: j >= m2, bottom:
+    i >= m1)."""
+    n1, n2 = patch.n1, patch.n2
+    out = []
+    for side, code in enumerate(patch.bc):
+        idx = _side_index(side, n1, n2)
+        if patch.is_l and side == 0:
+            idx = (slice(None), slice(patch.lcut[1], n2), 0)
+        if patch.is_l and side == 2:
+            idx = (slice(None), 0, slice(patch.lcut[0], n1))
+        out.append((side, code, idx))
+    if patch.is_l:
+        m1, m2 = patch.lcut
+        out.append((0, I.BC_WALL, (slice(None), slice(0, m2), m1)))
+        out.append((2, I.BC_WALL, (slice(None), m2, slice(0, m1))))
+        out.append((-1, I.BC_WALL, (slice(None), m2, m1)))
+    return out
+
+
 def apply_bc(e, geom, inst):
-    """Boundary conditions of one patch, sides in the order left, right, bottom, top.
+    """Boundary conditions of one patch, sides in the order left, right, bottom,
+    top (then the inner wall edges of an L-shaped patch).
 
     Wall: normal momentum removed (Cartesian: the normal component is set to
     zero); inflow: the prescribed conserved state; outflow: energy recomputed
     for the prescribed pressure.  Acts in place on e (4, n2, n1).
     """
-    n1, n2 = geom.n1, geom.n2
     gamma = inst.gamma
-    for side, code in enumerate(geom.patch.bc):
-        idx = _side_index(side, n1, n2)
+    for side, code, idx in _sides(geom.patch):
+        if side == -1:
+            # corner node of an L-shaped patch: both edge normals, as unit
+            # vectors along grad q1 and grad q2 (pointing into the flow), are
+            # summed; the velocity component along that bisector is removed
+            j, i = idx[1], idx[2]
+            sg = np.sign(geom.J[j, i])
+            n1 = sg * np.array([geom.y_q2[j, i], -geom.x_q2[j, i]])
+            n2 = sg * np.array([-geom.y_q1[j, i], geom.x_q1[j, i]])
+            nb = n1 / np.hypot(*n1) + n2 / np.hypot(*n2)
+            nb = nb / np.hypot(*nb)
+            mn = e[1, j, i] * nb[0] + e[2, j, i] * nb[1]
+            e[1, j, i] -= mn * nb[0]
+            e[2, j, i] -= mn * nb[1]
+            continue
         if code == I.BC_WALL:
             if geom.patch.cartesian:
                 comp = 1 if side < 2 else 2
@@ -197,7 +278,7 @@ def receiver_mask(patch, n_f):
         m[:n_f, :] = True
     if b[3] == I.BC_INTERNAL:
         m[patch.n2 - n_f:, :] = True
-    return m
+    return m & patch.active()
 
 
 # ---------------------------------------------------------------------------
@@ -239,6 +320,24 @@ def lagrange_dweights(t, m=STENCIL):
 def stencil_start(f, n, m=STENCIL):
     """First node of the m-point stencil around fractional index f (clamped to the line)."""
     return min(max(int(np.floor(f)) - (m // 2 - 1), 0), n - m)
+
+
+def stencil_block(patch, fi, fj):
+    """First node (i0, j0) of the donor block around fractional index (fi, fj).
+
+    On an L-shaped patch a block that would reach into the missing quadrant
+    is moved out of it along the direction needing the smaller shift (ties:
+    along j), so that every node belongs to the patch.
+    """
+    i0, j0 = stencil_start(fi, patch.n1), stencil_start(fj, patch.n2)
+    if patch.is_l:
+        m1, m2 = patch.lcut
+        if i0 < m1 and j0 < m2:
+            if m2 - j0 <= m1 - i0:
+                j0 = m2
+            else:
+                i0 = m1
+    return i0, j0
 
 
 def donor_index(patch, x, y, max_iter=40):
@@ -302,6 +401,7 @@ def fringe_map(patches, n_f=5):
     interpolation stencil holds no receiver of its own (interpolation).
     """
     masks = [receiver_mask(p, n_f) for p in patches]
+    usable = [p.active() & ~m for p, m in zip(patches, masks)]   # possible donor nodes
     copies, interp = [], []
     for p, pt in enumerate(patches):
         X, Y = pt.coords()
@@ -317,15 +417,17 @@ def fringe_map(patches, n_f=5):
                 fi, fj = loc
                 if not (-INSIDE_TOL <= fi <= qt.n1 - 1 + INSIDE_TOL and -INSIDE_TOL <= fj <= qt.n2 - 1 + INSIDE_TOL):
                     continue
+                if qt.is_l and fi < qt.lcut[0] - INSIDE_TOL and fj < qt.lcut[1] - INSIDE_TOL:
+                    continue                                   # in the missing quadrant
                 ri, rj = int(round(fi)), int(round(fj))
                 if abs(fi - ri) <= COPY_TOL and abs(fj - rj) <= COPY_TOL:
-                    if masks[q][rj, ri]:
+                    if not usable[q][rj, ri]:
                         continue
                     copies.append((p, j, i, q, rj, ri))
                     found = True
                     break
-                i0, j0 = stencil_start(fi, qt.n1), stencil_start(fj, qt.n2)
-                if masks[q][j0:j0 + STENCIL, i0:i0 + STENCIL].any():
+                i0, j0 = stencil_block(qt, fi, fj)
+                if not usable[q][j0:j0 + STENCIL, i0:i0 + STENCIL].all():
                     continue
                 W = np.outer(lagrange_weights(fj - j0), lagrange_weights(fi - i0))
                 interp.append((p, j, i, q, j0, i0, W))
@@ -373,7 +475,7 @@ def time_step(state, geoms, gamma, cfl, mu=None):
             s2 = g.h2 * np.sqrt(g.x_q2 ** 2 + g.y_q2 ** 2)
             # 1/dt = 1/dt_a + mu (1/s1^2 + 1/s2^2) / CFL_MU
             adv = 1.0 / (1.0 / adv + mu[k] * (1.0 / (s1 * s1) + 1.0 / (s2 * s2)) / CFL_MU)
-        best = min(best, float(np.min(adv)))
+        best = min(best, float(np.min(adv[g.active])))
     return best
 
 
@@ -427,6 +529,8 @@ class Solver:
         """Per patch: FC quadrature of each conserved field times |J| (4 sums)."""
         out = []
         for e, g in zip(state, self.geoms):
+            if g.patch.is_l:
+                raise NotImplementedError("quadrature on L-shaped patches")
             W1 = fcgram.fc_quadrature_weights(g.n1, self.d, g.C1)
             W2 = fcgram.fc_quadrature_weights(g.n2, self.d, g.C2)
             w = np.outer(W2, W1) * np.abs(g.J)

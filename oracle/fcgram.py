@@ -35,6 +35,7 @@ Nyquist mode is zeroed for odd orders and kept, times -(pi n/beta)^2, for the
 second derivative (reading of a point the paper leaves open).
 """
 import functools
+import os
 
 import mpmath as mp
 import numpy as np
@@ -141,14 +142,30 @@ def blend_fit(d, C):
     return T, resid
 
 
+_STORE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "fcgram_tables.npz")
+
+
 @functools.lru_cache(maxsize=None)
-def continuation_tables(d, C):
-    """FP64 continuation tables (A_R, A_L), each C x d (FC-Gram, §2)."""
-    T, _ = blend_fit(d, C)
-    Q, _ = gram_basis(d)
-    with mp.workdps(DIGITS):
-        AR = T * Q.T
-    A_R = np.array([[float(AR[c, m]) for m in range(d)] for c in range(C)], dtype=np.float64)
+def _stored():
+    return dict(np.load(_STORE)) if os.path.exists(_STORE) else {}
+
+
+@functools.lru_cache(maxsize=None)
+def continuation_tables(d, C, use_store=True):
+    """FP64 continuation tables (A_R, A_L), each C x d (FC-Gram, §2).
+
+    With use_store the tables written by oracle/make_tables.py (this very
+    function, run once) are read instead of redoing the 40-digit fit.
+    """
+    key = f"d{d}_C{C}"
+    if use_store and key in _stored():
+        A_R = _stored()[key].copy()
+    else:
+        T, _ = blend_fit(d, C)
+        Q, _ = gram_basis(d)
+        with mp.workdps(DIGITS):
+            AR = T * Q.T
+        A_R = np.array([[float(AR[c, m]) for m in range(d)] for c in range(C)], dtype=np.float64)
     A_L = A_R[::-1, ::-1].copy()
     return A_R, A_L
 

@@ -66,21 +66,33 @@ def window_starts(N, W=WINDOW):
     return starts
 
 
-def patch_windows(phi):
-    """All windows of one patch: x-lines (j outer) then y-lines (i outer).
+def line_span(n1, n2, lcut, dirn, line):
+    """(first index, length) of a grid line (row j for dirn 0, column i for
+    dirn 1) of a patch, L-shaped when lcut = (m1, m2) > 0."""
+    m1, m2 = lcut
+    if dirn == 0:
+        return (m1, n1 - m1) if (m1 > 0 and m2 > 0 and line < m2) else (0, n1)
+    return (m2, n2 - m2) if (m1 > 0 and m2 > 0 and line < m1) else (0, n2)
+
+
+def patch_windows(phi, lcut=(0, 0)):
+    """All windows of one patch: x-lines (j outer) then y-lines (i outer);
+    on an L-shaped patch the windows tile each line's segment.
 
     Returns (win (nwin, 16), cover) where cover[w] = (direction, line, start).
     """
     n2, n1 = phi.shape
     wins, cover = [], []
     for j in range(n2):
-        for s in window_starts(n1):
-            wins.append(phi[j, s:s + WINDOW])
-            cover.append((0, j, s))
+        a, N = line_span(n1, n2, lcut, 0, j)
+        for s in window_starts(N):
+            wins.append(phi[j, a + s:a + s + WINDOW])
+            cover.append((0, j, a + s))
     for i in range(n1):
-        for s in window_starts(n2):
-            wins.append(phi[s:s + WINDOW, i])
-            cover.append((1, i, s))
+        a, N = line_span(n1, n2, lcut, 1, i)
+        for s in window_starts(N):
+            wins.append(phi[a + s:a + s + WINDOW, i])
+            cover.append((1, i, a + s))
     return np.array(wins), cover
 
 
@@ -149,10 +161,10 @@ def classify_windows(params, win, bf16=False):
     return tau.astype(np.int8), z, flat
 
 
-def classify_patch(params, e, gamma, bf16=False):
+def classify_patch(params, e, gamma, bf16=False, lcut=(0, 0)):
     """Point-wise tau of one patch (min over covering windows) and window logits."""
     phi = proxy(e, gamma)
-    win, cover = patch_windows(phi)
+    win, cover = patch_windows(phi, lcut)
     tw, z, flat = classify_windows(params, win, bf16)
     tau = np.full(phi.shape, 4, dtype=np.int8)
     for t, (dirn, line, s) in zip(tw, cover):
@@ -240,25 +252,43 @@ def decay_indicator(win):
 
 
 # ---------------------------------------------------------------- viscosity
-def mwsb(e, gamma):
-    """Max wave speed bound: max of |u| + c over the 3x3 neighbourhood."""
+def _active(shape, lcut):
+    m = np.ones(shape, dtype=bool)
+    if lcut[0] > 0 and lcut[1] > 0:
+        m[:lcut[1], :lcut[0]] = False
+    return m
+
+
+def mwsb(e, gamma, lcut=(0, 0)):
+    """Max wave speed bound: max of |u| + c over the 3x3 neighbourhood (points
+    of the patch only)."""
     rho, mx, my, _ = e
-    c = np.sqrt(gamma * euler.pressure(e, gamma) / rho)
-    s = np.sqrt(mx * mx + my * my) / rho + c
-    return _box_max(s, 1)
+    act = _active(rho.shape, lcut)
+    safe = np.where(act, 1.0, 0.0)
+    rho_s = np.where(act, rho, 1.0)
+    p = euler.pressure(np.stack([rho_s, mx * safe, my * safe, np.where(act, e[3], 2.5)]), gamma)
+    s = np.where(act, np.sqrt(mx * mx + my * my) / rho_s + np.sqrt(gamma * p / rho_s), -np.inf)
+    n2, n1 = s.shape
+    pad = np.full((n2 + 2, n1 + 2), -np.inf)
+    pad[1:-1, 1:-1] = s
+    out = np.max([pad[1 + dj:n2 + 1 + dj, 1 + di:n1 + 1 + di] for dj in (-1, 0, 1) for di in (-1, 0, 1)], axis=0)
+    return np.where(act, out, 0.0)
 
 
-def _box_max(a, r):
-    out = a.copy()
+def _box_max(a, r, lcut=(0, 0)):
+    """Maximum over a (2r+1) x (2r+1) box, taken separably (along the rows,
+    then along the columns), each line restricted to its segment in the patch."""
     n2, n1 = a.shape
-    tmp = a.copy()
-    for k in range(1, r + 1):
-        tmp[:, :n1 - k] = np.maximum(tmp[:, :n1 - k], a[:, k:])
-        tmp[:, k:] = np.maximum(tmp[:, k:], a[:, :n1 - k])
-    out = tmp.copy()
-    for k in range(1, r + 1):
-        out[:n2 - k, :] = np.maximum(out[:n2 - k, :], tmp[k:, :])
-        out[k:, :] = np.maximum(out[k:, :], tmp[:n2 - k, :])
+    tmp = np.zeros_like(a)
+    for j in range(n2):
+        s0, N = line_span(n1, n2, lcut, 0, j)
+        row = a[j, s0:s0 + N]
+        tmp[j, s0:s0 + N] = [row[max(0, t - r):t + r + 1].max() for t in range(N)]
+    out = np.zeros_like(a)
+    for i in range(n1):
+        s0, N = line_span(n1, n2, lcut, 1, i)
+        col = tmp[s0:s0 + N, i]
+        out[s0:s0 + N, i] = [col[max(0, t - r):t + r + 1].max() for t in range(N)]
     return out
 
 
@@ -267,35 +297,56 @@ def bump_weights(r):
     return np.exp(1.0 - 1.0 / (1.0 - t * t))
 
 
-def _bump_avg(a, r, axis):
+def _bump_avg_line(v, r):
+    """Normalised bump average along one line segment."""
     b = bump_weights(r)
-    a = np.moveaxis(a, axis, -1)
-    n = a.shape[-1]
-    num = np.zeros_like(a)
+    n = len(v)
+    num = np.zeros(n)
     den = np.zeros(n)
     for k in range(-r, r + 1):
         lo, hi = max(0, -k), min(n, n - k)
-        num[..., lo:hi] += b[k + r] * a[..., lo + k:hi + k]
+        num[lo:hi] += b[k + r] * v[lo + k:hi + k]
         den[lo:hi] += b[k + r]
-    return np.moveaxis(num / den, -1, axis)
+    return num / den
+
+
+def _bump_avg(a, r, axis, lcut=(0, 0)):
+    """Bump average along rows (axis 1) or columns (axis 0), segment by segment."""
+    n2, n1 = a.shape
+    out = np.zeros_like(a)
+    if axis == 1:
+        for j in range(n2):
+            s0, N = line_span(n1, n2, lcut, 0, j)
+            out[j, s0:s0 + N] = _bump_avg_line(a[j, s0:s0 + N], r)
+    else:
+        for i in range(n1):
+            s0, N = line_span(n1, n2, lcut, 1, i)
+            out[s0:s0 + N, i] = _bump_avg_line(a[s0:s0 + N, i], r)
+    return out
 
 
 def h_max(geom):
+    """Largest physical grid spacing of a patch: the box spacings, or the
+    largest distance between neighbouring nodes of the patch (curvilinear)."""
     if geom.patch.cartesian:
         return max(geom.hx, geom.hy)
-    s1 = np.sqrt(geom.x_q1 ** 2 + geom.y_q1 ** 2) * geom.h1
-    s2 = np.sqrt(geom.x_q2 ** 2 + geom.y_q2 ** 2) * geom.h2
-    return float(max(s1.max(), s2.max()))
+    X, Y = geom.patch.coords()
+    act = geom.active
+    d1 = np.hypot(np.diff(X, axis=1), np.diff(Y, axis=1))[act[:, 1:] & act[:, :-1]]
+    d2 = np.hypot(np.diff(X, axis=0), np.diff(Y, axis=0))[act[1:, :] & act[:-1, :]]
+    return float(max(d1.max(), d2.max()))
 
 
 def av_patch(e, tau, geom, gamma, n_f, c_mu=1.0, radius=4):
     """Smooth viscosity of one patch before the fringe exchange."""
-    S = mwsb(e, gamma)
+    lc = tuple(geom.patch.lcut) if geom.patch.is_l else (0, 0)
+    S = mwsb(e, gamma, lc)
     w = np.asarray(VISC_WEIGHT)[np.asarray(tau, dtype=np.int64) - 1]
     mu0 = c_mu * h_max(geom) * S * w
     mu0[euler.receiver_mask(geom.patch, n_f)] = 0.0
-    m = _box_max(mu0, radius)
-    return _bump_avg(_bump_avg(m, radius, 1), radius, 0)
+    mu0[~geom.active] = 0.0
+    m = _box_max(mu0, radius, lc)
+    return _bump_avg(_bump_avg(m, radius, 1, lc), radius, 0, lc)
 
 
 def av_assemble(solver, state, taus, c_mu=1.0, radius=4):

@@ -34,10 +34,13 @@ BC_FREE = 4       # nothing imposed (supersonic outflow)
 
 @dataclass
 class Patch:
-    """One logically rectangular patch with an n1 x n2 grid (i along q1).
+    """One patch with an n1 x n2 parameter grid (i along q1).
 
     Cartesian patches carry their box; curvilinear ones carry the physical
-    coordinates x[j, i], y[j, i] of every grid point.
+    coordinates x[j, i], y[j, i] of every grid point.  lcut = (m1, m2) > 0
+    makes an L-shaped corner patch (type C1 of §3.2, parameter space L of
+    the paper): the points with i < m1 and j < m2 are not part of the patch
+    and the two inner edges (i = m1, j < m2 and j = m2, i < m1) are walls.
     """
     n1: int
     n2: int
@@ -45,10 +48,23 @@ class Patch:
     box: Optional[Sequence[float]] = None          # (x0, x1, y0, y1)
     x: Optional[np.ndarray] = None
     y: Optional[np.ndarray] = None
+    lcut: Sequence[int] = (0, 0)
+    kind: str = ""                                   # S, C1, C2 or I (label only)
 
     @property
     def cartesian(self):
         return self.box is not None
+
+    @property
+    def is_l(self):
+        return self.lcut[0] > 0 and self.lcut[1] > 0
+
+    def active(self):
+        """Mask of the grid points that belong to the patch."""
+        m = np.ones((self.n2, self.n1), dtype=bool)
+        if self.is_l:
+            m[:self.lcut[1], :self.lcut[0]] = False
+        return m
 
     def coords(self):
         if self.cartesian:
@@ -210,6 +226,74 @@ def annulus_ring(sizes=((64, 24), (56, 20), (72, 28)), r0=0.5, r1=1.0, overlap=0
         th1 = rot + (k + 1) * 2 * np.pi / P + overlap / 2
         patches.append(annulus_patch(n1, n2, r0, r1, th0, th1, bc=(BC_INTERNAL, BC_INTERNAL, BC_WALL, BC_FREE)))
     return patches
+
+
+def ffs_instance(h0=0.002, length=3.0, seed=SEED, delta_pts=8, jitter=0.15, mach=3.0):
+    """Mach-`mach` flow over a forward-facing step (§7 problem shape).
+
+    Channel [0, length] x [0, 1] with a step [0.6, length] x [0, 0.2].  The
+    flow region is cut into cells at x = 0.2, 0.4, ... and y = 0.1, 0.2, 0.4,
+    0.6, 0.8; every cell becomes a Cartesian patch extended by delta on its
+    internal sides, with its own seeded spacing h0 (1 +- jitter), so that
+    neighbouring grids do not coincide.  The three cells around the step's
+    top corner (0.6, 0.2) (interior angle 270 degrees) form one L-shaped C1
+    corner patch (§3.2), on a grid rotated by 90 degrees so that the missing
+    quadrant of its parameter space maps onto the step; the cell at the
+    step's foot (0.6, 0) is the C2 corner patch (interior angle 90 degrees).
+    Left: inflow, right: free (supersonic outflow), walls elsewhere.  Initial
+    state: the uniform Mach flow (1.4, mach, 0, 1) of §7.
+    """
+    rng = np.random.default_rng(seed)
+    hmax = h0 * (1 + jitter)
+    k = int(round(0.1 / h0))
+    hs = 0.1 / k                              # C1 spacing: the corner lines are grid lines
+    dn = int(np.ceil(delta_pts * hmax / hs))
+    delta = dn * hs
+    xb = list(np.round(np.arange(0.0, length + 1e-9, 0.2), 12))
+    yb = [0.0, 0.1, 0.2, 0.4, 0.6, 0.8, 1.0]
+    corner_cells = {(0.4, 0.2), (0.6, 0.2), (0.4, 0.1)}   # (x0, y0) of the cells inside the C1 patch
+    patches = []
+    for iy in range(len(yb) - 1):
+        for ix in range(len(xb) - 1):
+            x0, x1, y0, y1 = xb[ix], xb[ix + 1], yb[iy], yb[iy + 1]
+            if x0 >= 0.6 - 1e-12 and y1 <= 0.2 + 1e-12:
+                continue                                  # inside the step
+            if (round(x0, 6), round(y0, 6)) in corner_cells:
+                continue
+            on_step_top = x0 >= 0.6 - 1e-12 and abs(y0 - 0.2) < 1e-12
+            on_face = abs(x1 - 0.6) < 1e-12 and y1 <= 0.2 + 1e-12
+            bc = [BC_INTERNAL] * 4
+            if x0 == 0.0:
+                bc[0] = BC_INFLOW
+            if abs(x1 - length) < 1e-12:
+                bc[1] = BC_FREE
+            if on_face:
+                bc[1] = BC_WALL
+            if y0 == 0.0 or on_step_top:
+                bc[2] = BC_WALL
+            if abs(y1 - 1.0) < 1e-12:
+                bc[3] = BC_WALL
+            box = [x0 - delta * (bc[0] == BC_INTERNAL), x1 + delta * (bc[1] == BC_INTERNAL),
+                   y0 - delta * (bc[2] == BC_INTERNAL), y1 + delta * (bc[3] == BC_INTERNAL)]
+            h = h0 * (1 + jitter * rng.uniform(-1.0, 1.0))
+            n1 = int(round((box[1] - box[0]) / h)) + 1
+            n2 = int(round((box[3] - box[2]) / h)) + 1
+            kind = "C2" if (on_face and y0 == 0.0) else ("S" if BC_WALL in bc or BC_INFLOW in bc or BC_FREE in bc else "I")
+            patches.append(Patch(n1, n2, tuple(bc), box=tuple(box), kind=kind))
+    # C1 corner patch: x = xr - hs j, y = yb0 + hs i on the bounding square,
+    # points i < m1 (y < 0.2) with j < m2 (x > 0.6) missing
+    xr, yb0 = 0.8 + delta, 0.1 - delta
+    m1, m2 = k + dn, 2 * k + dn
+    n1, n2 = 3 * k + 2 * dn + 1, 4 * k + 2 * dn + 1
+    I_, J_ = np.meshgrid(np.arange(n1), np.arange(n2))
+    c1 = Patch(n1, n2, (BC_INTERNAL,) * 4, x=xr - hs * J_, y=yb0 + hs * I_, lcut=(m1, m2), kind="C1")
+    patches.insert(0, c1)
+    state = []
+    for p in patches:
+        X, _ = p.coords()
+        state.append(conserved(np.full(X.shape, 1.4), mach, 0.0, 1.0))
+    return Instance(patches, state, inflow=tuple(float(a) for a in conserved(1.4, mach, 0.0, 1.0)), p_out=1.0,
+                    name="ffs", meta=dict(h0=h0, delta=delta, length=length))
 
 
 def mach_flow_state(M, gamma=GAMMA):

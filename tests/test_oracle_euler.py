@@ -267,3 +267,88 @@ def test_interpolated_viscosity_stays_non_negative():
     clamped = euler.exchange([m.copy() for m in mu], fm, clamp=True)
     assert min(r.min() for r in raw) < 0.0                         # Lagrange overshoot
     assert min(c.min() for c in clamped) == 0.0
+
+
+# ---------------------------------------------------------------- L-shaped patches
+def _l_patch(curvilinear=False, bc=(I.BC_WALL,) * 4):
+    # 60 x 52 bounding grid, points i < 24, j < 20 missing (corner at the
+    # node (24, 20)); as a box, or as the same grid rotated by 90 degrees
+    n1, n2, m1, m2 = 60, 52, 24, 20
+    if not curvilinear:
+        return I.Patch(n1, n2, bc, box=(0.1, 1.3, -0.2, 0.82), lcut=(m1, m2), kind="C1")
+    q1 = np.arange(n1) / (n1 - 1)
+    q2 = np.arange(n2) / (n2 - 1)
+    Q1, Q2 = np.meshgrid(q1, q2)
+    return I.Patch(n1, n2, bc, x=0.9 - 1.02 * Q2, y=-0.3 + 1.2 * Q1, lcut=(m1, m2), kind="C1")
+
+
+def test_l_patch_derivative_exact_on_low_degree_polynomials():
+    for curv in (False, True):
+        p = _l_patch(curv)
+        g = euler.PatchGeom(p, 5, 25, 1)
+        X, Y = p.coords()
+        f = X ** 3 * Y ** 2 - 2 * X * Y ** 3 + 0.5
+        act = p.active()
+        if curv:   # d/dq of x(q), y(q) affine in q
+            fx, fy = 3 * X ** 2 * Y ** 2 - 2 * Y ** 3, 2 * X ** 3 * Y - 6 * X * Y ** 2
+            d1 = fx * g.x_q1 + fy * g.y_q1
+            d2 = fx * g.x_q2 + fy * g.y_q2
+            got1, got2 = g.D(f, 0, g.h1), g.D(f, 1, g.h2)
+        else:
+            d1 = 3 * X ** 2 * Y ** 2 - 2 * Y ** 3
+            d2 = 2 * X ** 3 * Y - 6 * X * Y ** 2
+            got1, got2 = g.D(f, 0, g.hx), g.D(f, 1, g.hy)
+        for got, ref in ((got1, d1), (got2, d2)):
+            assert np.abs(got - ref)[act].max() < 2e-8 * np.abs(ref[act]).max()
+            assert np.all(got[~act] == 0.0)
+
+
+def test_l_patch_full_lines_match_rectangle():
+    # where both lines through a point are full, the L patch and its bounding
+    # rectangle apply the same operators to the same data
+    p = _l_patch()
+    r = I.Patch(p.n1, p.n2, p.bc, box=p.box)
+    e = I.random_state(r, np.random.default_rng(8))
+    mu = 0.01 * (1 + np.cos(3 * r.coords()[0]))
+    a = euler.rhs(e, euler.PatchGeom(p, 5, 25, 1), 5, 25, G, mu)
+    b = euler.rhs(e, euler.PatchGeom(r, 5, 25, 1), 5, 25, G, mu)
+    m1, m2 = p.lcut
+    assert np.array_equal(a[:, m2 + 1:-1, m1 + 1:-1], b[:, m2 + 1:-1, m1 + 1:-1])
+    assert not np.allclose(a[:, :m2, m1 + 1:-1], b[:, :m2, m1 + 1:-1])   # short columns differ
+    assert np.all(a[:, :m2, :m1] == 0.0)
+
+
+def test_l_patch_free_stream_preserved():
+    for curv in (False, True):
+        p = _l_patch(curv, bc=(I.BC_INTERNAL,) * 4)
+        e = I.conserved(np.full((p.n2, p.n1), 1.3), 0.7, -0.4, 1.1)
+        L = euler.rhs(e, euler.PatchGeom(p, 5, 25, 1), 5, 25, G)
+        assert np.abs(L).max() < 1e-6          # fit residual of FC-Gram times 1/h, as on rectangles
+        X, _ = p.coords()
+        e2 = I.conserved(1.3 + 0.1 * np.sin(3 * X), 0.7, -0.4, 1.1)
+        assert np.abs(euler.rhs(e2, euler.PatchGeom(p, 5, 25, 1), 5, 25, G)).max() > 1e-2
+
+
+def test_l_patch_inner_walls():
+    for curv in (False, True):
+        p = _l_patch(curv)
+        inst = I.Instance([p], [I.conserved(np.ones((p.n2, p.n1)), 0.5, 0.3, 1.0)])
+        s = euler.Solver(inst, c_policy=1)
+        e = inst.state[0].copy()
+        euler.apply_bc(e, s.geoms[0], inst)
+        m1, m2 = p.lcut
+        g = s.geoms[0]
+        # inner vertical edge i = m1 (j < m2): velocity along grad q1 removed
+        v = e[1:3, :m2, m1] / e[0, :m2, m1]
+        n = np.stack([g.y_q2[:m2, m1], -g.x_q2[:m2, m1]])
+        assert np.abs((v * n).sum(0)).max() < 1e-12
+        v = e[1:3, m2, :m1] / e[0, m2, :m1]
+        n = np.stack([-g.y_q1[m2, :m1], g.x_q1[m2, :m1]])
+        assert np.abs((v * n).sum(0)).max() < 1e-12
+        # the corner node keeps only the velocity across the bisector of the
+        # two inward normals: for this grid (normals along the axes) u' = -v'
+        n1 = np.array([g.y_q2[m2, m1], -g.x_q2[m2, m1]])
+        n2 = np.array([-g.y_q1[m2, m1], g.x_q1[m2, m1]])
+        nb = n1 / np.linalg.norm(n1) + n2 / np.linalg.norm(n2)
+        assert abs(e[1:3, m2, m1] @ nb) < 1e-12 * np.abs(e[1:3, m2, m1]).max()
+        assert np.abs(e[1:3, m2, m1]).max() > 0.1                  # not a stagnation point

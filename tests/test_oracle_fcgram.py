@@ -118,3 +118,11 @@ def test_tables_reflection():
     c = fcgram.continue_lines(np.full(40, 3.0), 5, 25)
     assert np.abs(c[40:] - c[40:][::-1]).max() < 5e-12
     assert np.abs(fcgram.fc_derivative(np.full(40, 3.0), 1 / 39, 5, 25)).max() < 5e-9
+
+
+def test_stored_tables_match_fresh_fits():
+    # the stored tables (oracle/make_tables.py) are this module's own fits
+    for C in (20, 25, 33):
+        stored, _ = fcgram.continuation_tables(5, C)
+        fresh, _ = fcgram.continuation_tables(5, C, use_store=False)
+        assert np.array_equal(stored, fresh)

@@ -111,3 +111,25 @@ def test_classify_patch_min_over_windows():
     for (dirn, line, s), t in zip(cover, tw):
         seg = tau[line, s:s + 16] if dirn == 0 else tau[s:s + 16, line]
         assert np.all(seg <= t)
+
+
+def test_l_patch_windows_and_viscosity():
+    from oracle import euler
+    n1, n2, m1, m2 = 60, 52, 24, 20
+    p = I.Patch(n1, n2, (I.BC_WALL,) * 4, box=(0.0, 1.18, 0.0, 1.02), lcut=(m1, m2))
+    act = p.active()
+    phi = np.random.default_rng(2).uniform(size=(n2, n1))
+    win, cover = sdnn.patch_windows(phi, (m1, m2))
+    hits = [np.zeros((n2, n1), int), np.zeros((n2, n1), int)]
+    for dirn, line, s in cover:
+        if dirn == 0:
+            hits[0][line, s:s + 16] += 1
+        else:
+            hits[1][s:s + 16, line] += 1
+    for h in hits:
+        assert np.all(h[act] >= 1) and np.all(h[~act] == 0)   # windows tile the segments only
+    # constant wave speed and tau = 1 everywhere: mu = c_mu h S on every point
+    e = I.conserved(np.full((n2, n1), 1.4), 0.0, 0.0, 1.0)            # c = 1
+    g = euler.PatchGeom(p, 5, 25)
+    mu = sdnn.av_patch(e, np.ones((n2, n1), dtype=np.int8), g, G, 5, c_mu=0.7)
+    assert np.allclose(mu[act], 0.7 * 0.02 * 1.0, rtol=1e-13) and np.all(mu[~act] == 0.0)
