@@ -68,10 +68,18 @@ typedef enum {
   FCS_BC_FREE = 4       /* nothing imposed */
 } fcs_bc;
 
-/* One logically rectangular patch (paper §3.1-3.2: patches are images of
- * Cartesian parameter grids).  Cartesian patches give their box; curvilinear
- * patches give host FP64 coordinates x[j*n1+i], y[j*n1+i] (copied in
- * fc_setup, not retained).  16 <= n1, n2 <= 256. */
+/* One patch (paper §3.1-3.2: patches are images of Cartesian parameter
+ * grids).  Cartesian patches give their box; curvilinear patches give host
+ * FP64 coordinates x[j*n1+i], y[j*n1+i] (copied in fc_setup, not retained).
+ * 16 <= n1, n2 <= 256.
+ * lcut = {m1, m2}, both > 0, makes an L-shaped corner patch (type C1 of
+ * §3.2, parameter space L): the points i < m1, j < m2 do not belong to it
+ * (they keep whatever the caller stores there and are never written), and
+ * its inner edges i = m1 (j < m2) and j = m2 (i < m1) are walls; the corner
+ * node (m1, m2) is a wall along the bisector of the two edge normals.  Each
+ * remaining line segment needs at least 16 points.  Coordinates of
+ * curvilinear L patches are given on the whole n1 x n2 grid (the patch map
+ * extends over the missing quadrant).  {0, 0}: rectangular patch. */
 typedef struct {
   int n1, n2;
   int bc[4];
@@ -79,6 +87,7 @@ typedef struct {
   double box[4];     /* x0, x1, y0, y1 */
   const double* x;   /* host, n1*n2, cartesian == 0 only */
   const double* y;
+  int lcut[2];       /* {m1, m2}: L-shaped corner patch; {0, 0}: rectangle */
 } fcs_patch_desc;
 
 typedef struct {
@@ -96,6 +105,11 @@ typedef struct {
   int train_batch_max; /* largest batch sdnn_train_step accepts (4096) */
   int autotune;      /* 1: fc_setup times the column-tile widths (lines per CTA of the
                         pass along q2) that fit and keeps the fastest; 0: widest (0) */
+  double filter_alpha; /* spectral filter sigma(k) = exp(-alpha (|k|/k_max)^(2p))
+                          (§5 item 3; I-(32) read with alpha = 16 ln 10) */
+  int filter_p;        /* filter order p (18) */
+  int filter_step;     /* 1: fcs_step ends with fcs_filter, so every step after
+                          the first starts from filtered data; 0: off (0) */
 } fcs_options;
 
 /* Defaults listed in the comments above. */
@@ -180,10 +194,22 @@ int patch_exchange(fcs_ctx* ctx, void* field_dev, int nfields, void* stream);
  * layout) may be NULL (no viscous limit).  Writes dt_dev (instances doubles). */
 int fcs_time_step(fcs_ctx* ctx, const void* e_dev, const void* mu_dev, double* dt_dev, void* stream);
 
+/* Spectral filter of the state, in place (§5 item 3, Algorithm 4 for t > 0):
+ * on every line segment, along q1 then along q2, the FC-continued values of
+ * rho, rho u, rho v and the temperature theta = p / rho are Fourier
+ * transformed, multiplied by sigma(k) = exp(-filter_alpha (|k| / (n/2))^(2
+ * filter_p)) for the mode numbers |k| <= n/2 of the continued line of n
+ * points, transformed back and restricted; E follows from the filtered
+ * theta, then the boundary conditions and the fringe exchange are applied.
+ * Uses the context's work buffers (not concurrently with other calls). */
+int fcs_filter(fcs_ctx* ctx, void* e_dev, void* stream);
+
 /* Per instance and patch, FP64 sums of each conserved field with the FC
  * quadrature weights (tensor product along q1 and q2) times |J|:
  * sums_dev[(instance * npatch + patch) * 4 + field].  Also checks the state
- * and latches FCS_ENONFINITE / FCS_ENEGATIVE into the status word. */
+ * and latches FCS_ENONFINITE / FCS_ENEGATIVE into the status word.
+ * FCS_EUNSUPPORTED if the layout has an L-shaped patch (the tensor-product
+ * quadrature does not apply there). */
 int fcs_conservation_sums(fcs_ctx* ctx, const void* e_dev, double* sums_dev, void* stream);
 
 /* Classifier weights (the paper's ANN, §4/§5 item 2): FP32 master copy,

@@ -182,6 +182,31 @@ def rhs(e, geom, d, C, gamma, mu=None):
     return np.where(geom.active, -div / geom.J, 0.0)
 
 
+def filter_state(e, geom, gamma, alpha=fcgram.FILTER_ALPHA, p=fcgram.FILTER_P):
+    """Spectral filter of one patch's state (§5 item 3, Algorithm 4, t > 0).
+
+    Filters rho, rho u, rho v and the temperature theta = p / rho (the energy
+    follows from theta: E = rho theta / (gamma - 1) + |rho u|^2 / (2 rho)),
+    along q1 then q2, each line segment with its own continuation.  Points
+    outside an L-shaped patch keep their values.
+    """
+    e = np.asarray(e, dtype=np.float64)
+    act = geom.active
+    safe = np.where(act, e, np.array([1.0, 0.0, 0.0, 2.5])[:, None, None])
+    w = np.stack([safe[0], safe[1], safe[2], pressure(safe, gamma) / safe[0]])
+    for dirn in (0, 1):
+        out = w.copy()
+        axis = 2 if dirn == 0 else 1
+        for blk, N in geom.segments(dirn):
+            idx = (Ellipsis,) + blk
+            sub = np.moveaxis(w[idx], axis, -1)
+            out[idx] = np.moveaxis(fcgram.fc_filter(sub, geom.d, geom.C_of(N), alpha, p), -1, axis)
+        w = out
+    rho, mx, my, th = w
+    f = np.stack([rho, mx, my, rho * th / (gamma - 1.0) + 0.5 * (mx * mx + my * my) / rho])
+    return np.where(act, f, e)
+
+
 def _side_index(side, n1, n2):
     if side == 0:
         return (slice(None), slice(None), 0)
@@ -514,6 +539,13 @@ class Solver:
             acc_new.append(a)
         exchange(out, self.fmap)
         return out, acc_new
+
+    def filter(self, state):
+        """Filter every patch, then boundary conditions and fringe exchange."""
+        out = [filter_state(e, g, self.inst.gamma) for e, g in zip(state, self.geoms)]
+        for e, g in zip(out, self.geoms):
+            apply_bc(e, g, self.inst)
+        return exchange(out, self.fmap)
 
     def step(self, state, dt, mu=None):
         e_n = [e.copy() for e in state]

@@ -208,6 +208,32 @@ def fc_derivative_axis(f, h, d, C, axis, order=1):
     return np.moveaxis(fc_derivative(g, h, d, C, order), -1, axis)
 
 
+# spectral filter (§5 item 3, Algorithm 4; reading of I-(32)):
+# sigma(k) = exp(-alpha (|k| / k_max)^(2p)), k the mode number in
+# (-n/2, n/2], k_max = n/2
+FILTER_ALPHA = 16.0 * np.log(10.0)
+FILTER_P = 18
+
+
+def filter_factors(n, alpha=FILTER_ALPHA, p=FILTER_P):
+    """sigma(k) for the n FFT modes in numpy order."""
+    k = np.abs(np.fft.fftfreq(n, d=1.0 / n))
+    return np.exp(-alpha * (k / (n / 2.0)) ** (2 * p))
+
+
+def filter_periodic(y, alpha=FILTER_ALPHA, p=FILTER_P):
+    """Filter of periodic lines y (..., n): Fourier coefficients times sigma."""
+    y = np.asarray(y, dtype=np.float64)
+    return np.real(np.fft.ifft(np.fft.fft(y, axis=-1) * filter_factors(y.shape[-1], alpha, p), axis=-1))
+
+
+def fc_filter(f, d, C, alpha=FILTER_ALPHA, p=FILTER_P):
+    """Spectral filter of every line of f along the last axis: continue, filter
+    the periodic extension, restrict to the N data points."""
+    f = np.asarray(f, dtype=np.float64)
+    return filter_periodic(continue_lines(f, d, C), alpha, p)[..., :f.shape[-1]]
+
+
 def naive_dft(y, sign=-1):
     """O(n^2) DFT, sum_j y_j exp(sign 2 pi i j k / n); pins the FFT use."""
     y = np.asarray(y)

@@ -52,7 +52,8 @@ struct fcs_ctx {
   size_t sstride = 0, qstride = 0, nwin = 0;
   int nlines0 = 0, nlines1 = 0, npairs0 = 0, npairs1 = 0, nent = 0, ntiles = 0;
   int nmax = 0, nfmax = 0, n2max = 0, stockham = 0, tw = 32;
-  std::vector<int> patch_n1[2];  // per patch: FFT size of its lines along q1 / q2
+  std::vector<int> kind_n1[2][2];  // [dir][kind][patch]: FFT size of the full (kind 0) and short
+                                   // (kind 1, L-shaped patches) lines along q1 / q2; -1: none
   std::vector<int> n1_dir[2];    // distinct FFT sizes per direction
   std::vector<Group> g_rows, g_pairs[2], g_tiles, g_vpairs;
   std::vector<int> tw_options;  // column-tile widths that fit in shared memory (widest first)
@@ -62,6 +63,8 @@ struct fcs_ctx {
   int4* pairs0 = nullptr;
   int4* pairs1 = nullptr;
   int4* vpairs = nullptr;  // column pairs x fields of curvilinear patches (viscous gradient e_q2)
+  int4* fpairs[2] = {nullptr, nullptr};  // row / column pairs x 4 fields of every patch (filter)
+  std::vector<Group> g_fpairs[2];
   void* G1 = nullptr;      // e_q1, e_q2 of curvilinear patches (state-sized; viscous passes)
   void* G2 = nullptr;
   int2* tiles = nullptr;
@@ -319,8 +322,21 @@ int launch_flux(fcs_ctx* c, const void* e, const void* mu, int mode, StageArgs<T
   return FCS_OK;
 }
 
-// Group a per-patch work list by the FFT size of its patches' lines: items of
-// all patches with size n1[0], then n1[1], ... (patch order kept inside).
+// Lines of kind 0 (full) or 1 (short, L-shaped patches only) of patch P along
+// direction dir: rows j (dir 0) or columns i (dir 1) in [*lo, *hi).
+void kind_range(const PatchDev& P, int dir, int kind, int* lo, int* hi) {
+  if (dir == 0) {
+    *lo = kind ? 0 : P.m2;
+    *hi = kind ? P.m2 : P.n2;
+  } else {
+    *lo = kind ? 0 : P.m1;
+    *hi = kind ? P.m1 : P.n1;
+  }
+}
+
+// Group a per-line work list by FFT size: gen(p, lo, hi, out) emits the items
+// of lines [lo, hi) of patch p; lines of size n1[0] come first, then n1[1], ...
+// (patch order kept inside a group).
 template <typename Item, typename Gen>
 void grouped(const fcs_ctx* c, int dir, std::vector<Item>* out, std::vector<Group>* groups, Gen gen) {
   out->clear();
@@ -328,7 +344,12 @@ void grouped(const fcs_ctx* c, int dir, std::vector<Item>* out, std::vector<Grou
   for (int n1 : c->n1_dir[dir]) {
     Group g{n1, (int)out->size(), 0};
     for (int p = 0; p < c->npatch; ++p)
-      if (c->patch_n1[dir][p] == n1) gen(p, out);
+      for (int kind = 0; kind < 2; ++kind)
+        if (c->kind_n1[dir][kind][p] == n1) {
+          int lo, hi;
+          kind_range(c->patches[p], dir, kind, &lo, &hi);
+          gen(p, lo, hi, out);
+        }
     g.count = (int)out->size() - g.begin;
     if (g.count) groups->push_back(g);
   }
@@ -396,8 +417,8 @@ int train_forward_backward(fcs_ctx* c, const float* x, const int8_t* lab, int B,
 // grouped by FFT size.
 int set_tiles(fcs_ctx* c, const fcs_patch_desc* pd, int tw) {
   std::vector<int2> tiles;
-  grouped(c, 1, &tiles, &c->g_tiles, [&](int p, std::vector<int2>* o) {
-    for (int c0 = 0; c0 < pd[p].n1; c0 += tw) o->push_back(make_int2(p, c0));
+  grouped(c, 1, &tiles, &c->g_tiles, [&](int p, int lo, int hi, std::vector<int2>* o) {
+    for (int c0 = lo; c0 < hi; c0 += tw) o->push_back(make_int2(p, c0));
   });
   int2* t = nullptr;
   int rc = upload(c, &t, tiles.data(), tiles.size() * sizeof(int2));
@@ -485,6 +506,9 @@ void fcs_default_options(fcs_options* o) {
   o->c_policy = 0;
   o->train_batch_max = 4096;
   o->autotune = 0;
+  o->filter_alpha = 16.0 * std::log(10.0);
+  o->filter_p = 18;
+  o->filter_step = 0;
 }
 
 const char* fcs_strerror(int code) {
@@ -528,7 +552,8 @@ int fc_setup(fcs_ctx** out, int d, int C, const fcs_patch_desc* pd, int npatch, 
   if (opt) o = *opt;
   else fcs_default_options(&o);
   if (o.instances < 1 || (o.dtype != FCS_F32 && o.dtype != FCS_F64) || o.n_f < 1 || o.gamma <= 1.0 ||
-      o.av_radius < 0 || o.av_radius > 32 || o.train_batch_max < 1)
+      o.av_radius < 0 || o.av_radius > 32 || o.train_batch_max < 1 || !(o.filter_alpha >= 0.0) || o.filter_p < 1 ||
+      o.filter_p > 64)
     return FCS_EINVAL;
   for (int p = 0; p < npatch; ++p) {
     const fcs_patch_desc& q = pd[p];
@@ -541,6 +566,9 @@ int fc_setup(fcs_ctx** out, int d, int C, const fcs_patch_desc* pd, int npatch, 
       if (!q.x || !q.y) return FCS_EINVAL;
     }
     if (2 * o.n_f >= q.n1 || 2 * o.n_f >= q.n2) return FCS_EINVAL;
+    if (q.lcut[0] != 0 || q.lcut[1] != 0) {  // L-shaped: both cuts, segments of >= 16 points
+      if (q.lcut[0] <= 0 || q.lcut[1] <= 0 || q.n1 - q.lcut[0] < 16 || q.n2 - q.lcut[1] < 16) return FCS_EINVAL;
+    }
   }
   fcs_ctx* c = new fcs_ctx();
   c->opt = o;
@@ -565,19 +593,27 @@ int fc_setup(fcs_ctx** out, int d, int C, const fcs_patch_desc* pd, int npatch, 
     P.n2 = q.n2;
     P.cart = q.cartesian ? 1 : 0;
     for (int s = 0; s < 4; ++s) P.bc[s] = q.bc[s];
-    for (int dir = 0; dir < 2; ++dir) {
-      const int N = dir == 0 ? q.n1 : q.n2;
-      const int pi = get_plan(c, N, choose_c(o, C, N), d);
-      if (pi < 0) return fail(pi);
-      P.plan[dir] = pi;
-      c->nmax = std::max(c->nmax, N);
-      c->nfmax = std::max(c->nfmax, c->plans[pi].dev.n);
-      int r = c->plans[pi].dev.n1reg;
-      if (r % 2 == 0 && d > 5) r = 0;  // the two-level register FFT handles d <= 5
-      c->patch_n1[dir].push_back(r);
-      if (std::find(c->n1_dir[dir].begin(), c->n1_dir[dir].end(), r) == c->n1_dir[dir].end())
-        c->n1_dir[dir].push_back(r);
-    }
+    const bool lshape = q.lcut[0] > 0 && q.lcut[1] > 0;
+    P.m1 = lshape ? q.lcut[0] : 0;
+    P.m2 = lshape ? q.lcut[1] : 0;
+    for (int dir = 0; dir < 2; ++dir)
+      for (int kind = 0; kind < 2; ++kind) {
+        if (kind == 1 && !lshape) {
+          c->kind_n1[dir][kind].push_back(-1);
+          continue;
+        }
+        const int N = (dir == 0 ? q.n1 : q.n2) - (kind ? (dir == 0 ? P.m1 : P.m2) : 0);
+        const int pi = get_plan(c, N, choose_c(o, C, N), d);
+        if (pi < 0) return fail(pi);
+        (kind ? P.plan_s : P.plan)[dir] = pi;
+        c->nmax = std::max(c->nmax, N);
+        c->nfmax = std::max(c->nfmax, c->plans[pi].dev.n);
+        int r = c->plans[pi].dev.n1reg;
+        if (r % 2 == 0 && d > 5) r = 0;  // the two-level register FFT handles d <= 5
+        c->kind_n1[dir][kind].push_back(r);
+        if (std::find(c->n1_dir[dir].begin(), c->n1_dir[dir].end(), r) == c->n1_dir[dir].end())
+          c->n1_dir[dir].push_back(r);
+      }
     c->n2max = std::max(c->n2max, q.n2);
     P.soff = (long long)soff;
     P.qoff = (long long)qoff;
@@ -598,6 +634,7 @@ int fc_setup(fcs_ctx** out, int d, int C, const fcs_patch_desc* pd, int npatch, 
       for (int j = 0; j < q.n2; ++j)
         for (int i = 0; i < q.n1; ++i) {
           const long long k = (long long)j * q.n1 + i;
+          if (!pt_active(P, i, j)) continue;
           if (i + 1 < q.n1) hm = std::max(hm, std::hypot(q.x[k + 1] - q.x[k], q.y[k + 1] - q.y[k]));
           if (j + 1 < q.n2) hm = std::max(hm, std::hypot(q.x[k + q.n1] - q.x[k], q.y[k + q.n1] - q.y[k]));
         }
@@ -610,36 +647,53 @@ int fc_setup(fcs_ctx** out, int d, int C, const fcs_patch_desc* pd, int npatch, 
       if (s.back() + 16 < N) s.push_back(N - 16);
       return s;
     };
+    // windows tile each line segment (rows j < m2 and columns i < m1 of an
+    // L-shaped patch are short); the list is x-lines (j outer), then y-lines
     const std::vector<int> sx = starts(q.n1), sy = starts(q.n2);
+    const std::vector<int> sxs = lshape ? starts(q.n1 - P.m1) : std::vector<int>();
+    const std::vector<int> sys = lshape ? starts(q.n2 - P.m2) : std::vector<int>();
     P.wpl_x = (int)sx.size();
     P.wpl_y = (int)sy.size();
+    P.wpl_xs = (int)sxs.size();
+    P.wpl_ys = (int)sys.size();
     P.wx_off = (int)woff_;
     c->window_off.push_back((int64_t)woff_);
-    for (int j = 0; j < q.n2; ++j)
-      for (int s : sx) wins.push_back(make_int4(p, 0, j, s));
-    P.wy_off = (int)(woff_ + (size_t)q.n2 * sx.size());
-    for (int i = 0; i < q.n1; ++i)
-      for (int s : sy) wins.push_back(make_int4(p, 1, i, s));
+    for (int j = 0; j < q.n2; ++j) {
+      const int a = line_start(P, 0, j);
+      for (int s : (a ? sxs : sx)) wins.push_back(make_int4(p, 0, j, a + s));
+    }
+    P.wy_off = (int)wins.size();
+    for (int i = 0; i < q.n1; ++i) {
+      const int a = line_start(P, 1, i);
+      for (int s : (a ? sys : sy)) wins.push_back(make_int4(p, 1, i, a + s));
+    }
     woff_ = wins.size();
     for (int i = 0; i < q.n1; ++i) l1.push_back({p, i});
     c->patches.push_back(P);
   }
   // rows and line pairs grouped by FFT size (one launch per group)
   for (int dir = 0; dir < 2; ++dir) std::sort(c->n1_dir[dir].begin(), c->n1_dir[dir].end());
-  grouped(c, 0, &l0, &c->g_rows, [&](int p, std::vector<LineRef>* o) {
-    for (int j = 0; j < pd[p].n2; ++j) o->push_back({p, j});
+  // the two lines of a pair always have the same segment
+  grouped(c, 0, &l0, &c->g_rows, [&](int p, int lo, int hi, std::vector<LineRef>* o) {
+    for (int j = lo; j < hi; ++j) o->push_back({p, j});
   });
-  grouped(c, 0, &p0, &c->g_pairs[0], [&](int p, std::vector<int4>* o) {
-    for (int j = 0; j < pd[p].n2; j += 2) o->push_back(make_int4(p, j, j + 1 < pd[p].n2 ? j + 1 : -1, -1));
+  grouped(c, 0, &p0, &c->g_pairs[0], [&](int p, int lo, int hi, std::vector<int4>* o) {
+    for (int j = lo; j < hi; j += 2) o->push_back(make_int4(p, j, j + 1 < hi ? j + 1 : -1, -1));
   });
-  grouped(c, 1, &p1, &c->g_pairs[1], [&](int p, std::vector<int4>* o) {
-    for (int i = 0; i < pd[p].n1; i += 2) o->push_back(make_int4(p, i, i + 1 < pd[p].n1 ? i + 1 : -1, -1));
+  grouped(c, 1, &p1, &c->g_pairs[1], [&](int p, int lo, int hi, std::vector<int4>* o) {
+    for (int i = lo; i < hi; i += 2) o->push_back(make_int4(p, i, i + 1 < hi ? i + 1 : -1, -1));
   });
+  std::vector<int4> fp[2];  // state-layout line pairs of every patch, 4 fields (filter)
+  for (int dir = 0; dir < 2; ++dir)
+    grouped(c, dir, &fp[dir], &c->g_fpairs[dir], [&](int p, int lo, int hi, std::vector<int4>* o) {
+      for (int f = 0; f < 4; ++f)
+        for (int l = lo; l < hi; l += 2) o->push_back(make_int4(p, l, l + 1 < hi ? l + 1 : -1, f));
+    });
   std::vector<int4> vp;  // state-layout column pairs of curvilinear patches, 4 fields
-  grouped(c, 1, &vp, &c->g_vpairs, [&](int p, std::vector<int4>* o) {
+  grouped(c, 1, &vp, &c->g_vpairs, [&](int p, int lo, int hi, std::vector<int4>* o) {
     if (pd[p].cartesian) return;
     for (int f = 0; f < 4; ++f)
-      for (int i = 0; i < pd[p].n1; i += 2) o->push_back(make_int4(p, i, i + 1 < pd[p].n1 ? i + 1 : -1, f));
+      for (int i = lo; i < hi; i += 2) o->push_back(make_int4(p, i, i + 1 < hi ? i + 1 : -1, f));
   });
   // indicator plan (degree 5, C = 26 on 16-point windows; direct DFT)
   const int ind = get_plan(c, 16, kIndC, kIndD);
@@ -647,10 +701,12 @@ int fc_setup(fcs_ctx** out, int d, int C, const fcs_patch_desc* pd, int npatch, 
   // lines in the Stockham group need a radix factorisation of their length
   for (int dir = 0; dir < 2; ++dir)
     for (int p = 0; p < npatch; ++p)
-      if (c->patch_n1[dir][p] == 0) {
-        c->stockham = 1;
-        if (c->plans[c->patches[p].plan[dir]].dev.nst == 0) return fail(FCS_EUNSUPPORTED);
-      }
+      for (int kind = 0; kind < 2; ++kind)
+        if (c->kind_n1[dir][kind][p] == 0) {
+          c->stockham = 1;
+          const PatchDev& P = c->patches[p];
+          if (c->plans[(kind ? P.plan_s : P.plan)[dir]].dev.nst == 0) return fail(FCS_EUNSUPPORTED);
+        }
   // column-tile width of the pass along q2: widest of 32, 16, 8 that fits
   {
     const size_t esz = c->tsize, lim = 200 * 1024;
@@ -668,8 +724,8 @@ int fc_setup(fcs_ctx** out, int d, int C, const fcs_patch_desc* pd, int npatch, 
     c->tw = tw;
   }
   std::vector<int2> tiles;
-  grouped(c, 1, &tiles, &c->g_tiles, [&](int p, std::vector<int2>* o) {
-    for (int c0 = 0; c0 < pd[p].n1; c0 += c->tw) o->push_back(make_int2(p, c0));
+  grouped(c, 1, &tiles, &c->g_tiles, [&](int p, int lo, int hi, std::vector<int2>* o) {
+    for (int c0 = lo; c0 < hi; c0 += c->tw) o->push_back(make_int2(p, c0));
   });
   c->ntiles = (int)tiles.size();
   std::vector<int2> pblk;
@@ -727,6 +783,8 @@ int fc_setup(fcs_ctx** out, int d, int C, const fcs_patch_desc* pd, int npatch, 
   std::vector<float> thi, tlo;
   std::vector<double2> tw64;
   std::vector<float2> tw32;
+  std::vector<double> flt64;
+  std::vector<float> flt32;
   std::vector<PlanDev> plans;
   for (HostPlan& hp : c->plans) {
     hp.dev.tg_off = (int)gramT.size();
@@ -750,6 +808,11 @@ int fc_setup(fcs_ctx** out, int d, int C, const fcs_patch_desc* pd, int npatch, 
     for (int k = 0; k < hp.dev.n; ++k) {
       tw64.push_back(make_double2(re[k], im[k]));
       tw32.push_back(make_float2((float)re[k], (float)im[k]));
+      // filter factor of mode number min(k, n - k) (same offsets as the twiddles)
+      const double kk = std::min(k, hp.dev.n - k) / (0.5 * hp.dev.n);
+      const double sg = std::exp(-o.filter_alpha * std::pow(kk, 2.0 * o.filter_p));
+      flt64.push_back(sg);
+      flt32.push_back((float)sg);
     }
     plans.push_back(hp.dev);
   }
@@ -780,6 +843,8 @@ int fc_setup(fcs_ctx** out, int d, int C, const fcs_patch_desc* pd, int npatch, 
   float *dthi, *dtlo;
   double2* dtw64;
   float2* dtw32;
+  double* dflt64;
+  float* dflt32;
   LineRef *dl0, *dl1;
   int4* dwin;
   unsigned char* dfr;
@@ -793,11 +858,14 @@ int fc_setup(fcs_ctx** out, int d, int C, const fcs_patch_desc* pd, int npatch, 
       (rc = upload(c, &dthi, thi.data(), thi.size() * 4)) || (rc = upload(c, &dtlo, tlo.data(), tlo.size() * 4)) ||
       (rc = upload(c, &dtw64, tw64.data(), tw64.size() * sizeof(double2))) ||
       (rc = upload(c, &dtw32, tw32.data(), tw32.size() * sizeof(float2))) ||
+      (rc = upload(c, &dflt64, flt64.data(), flt64.size() * 8)) || (rc = upload(c, &dflt32, flt32.data(), flt32.size() * 4)) ||
       (rc = upload(c, &dl0, l0.data(), l0.size() * sizeof(LineRef))) ||
       (rc = upload(c, &dl1, l1.data(), l1.size() * sizeof(LineRef))) ||
       (rc = upload(c, &c->pairs0, p0.data(), p0.size() * sizeof(int4))) ||
       (rc = upload(c, &c->pairs1, p1.data(), p1.size() * sizeof(int4))) ||
       (rc = upload(c, &c->vpairs, vp.data(), vp.size() * sizeof(int4))) ||
+      (rc = upload(c, &c->fpairs[0], fp[0].data(), fp[0].size() * sizeof(int4))) ||
+      (rc = upload(c, &c->fpairs[1], fp[1].data(), fp[1].size() * sizeof(int4))) ||
       (rc = upload(c, &c->tiles, tiles.data(), tiles.size() * sizeof(int2))) ||
       (rc = upload(c, &c->pblk, pblk.data(), pblk.size() * sizeof(int2))) ||
       (rc = upload(c, &dwin, wins.data(), wins.size() * sizeof(int4))) ||
@@ -835,6 +903,8 @@ int fc_setup(fcs_ctx** out, int d, int C, const fcs_patch_desc* pd, int npatch, 
   D.tablo = dtlo;
   D.tw64 = dtw64;
   D.tw32 = dtw32;
+  D.flt64 = dflt64;
+  D.flt32 = dflt32;
   D.lines0 = dl0;
   D.lines1 = dl1;
   D.windows = dwin;
@@ -990,6 +1060,8 @@ int fcs_time_step(fcs_ctx* c, const void* e, const void* mu, double* dt_dev, voi
 
 int fcs_conservation_sums(fcs_ctx* c, const void* e, double* sums, void* stream) {
   if (!c || !e || !sums) return FCS_EINVAL;
+  for (const PatchDev& P : c->patches)
+    if (P.m1 > 0) return FCS_EUNSUPPORTED;  // no tensor quadrature on an L-shaped patch
   const int blocks = c->opt.instances * c->npatch;
   if (c->opt.dtype == FCS_F64)
     k_sums<double><<<blocks, 256, 0, as_stream(stream)>>>(c->dev, static_cast<const double*>(e), c->wq, c->woff, sums);
@@ -1137,6 +1209,39 @@ int sdnn_train_step(fcs_ctx* c, const float* x, const int8_t* lab, int B, float 
   return cuda_err(cudaGetLastError());
 }
 
+int fcs_filter(fcs_ctx* c, void* e, void* stream) {
+  if (!c || !e) return FCS_EINVAL;
+  cudaStream_t s = as_stream(stream);
+  const dim3 g(c->dev.npblk, c->opt.instances);
+  const bool f64 = c->opt.dtype == FCS_F64;
+  if (f64) k_filter_prep<double><<<g, 256, 0, s>>>(c->dev, static_cast<const double*>(e), static_cast<double*>(c->R));
+  else k_filter_prep<float><<<g, 256, 0, s>>>(c->dev, static_cast<const float*>(e), static_cast<float*>(c->R));
+  FCS_CUDA(cudaGetLastError());
+  // rows R -> S, columns S -> R (order 0 of the line transform: filter)
+  for (int dir = 0; dir < 2; ++dir) {
+    void* src = dir == 0 ? c->R : c->S;
+    void* dst = dir == 0 ? c->S : c->R;
+    for (const Group& gr : c->g_fpairs[dir]) {
+      const long long work = ((long long)c->dev.instances * gr.count + jobs_per_round(gr.n1) - 1) / jobs_per_round(gr.n1);
+      if (f64) {
+        const LaunchCfg lc{(unsigned)grid_for(work, kWarps), kWarps * 32, deriv_smem<double>(c, gr.n1), s};
+        FCS_N1_SWITCH(gr.n1, FCS_CUDA((run_fc_deriv<double, K>(c->dev, dir, 0, c->fpairs[dir] + gr.begin, gr.count,
+                                                               static_cast<const double*>(src),
+                                                               static_cast<double*>(dst), lc))); break)
+      } else {
+        const LaunchCfg lc{(unsigned)grid_for(work, kWarps), kWarps * 32, deriv_smem<float>(c, gr.n1), s};
+        FCS_N1_SWITCH(gr.n1, FCS_CUDA((run_fc_deriv<float, K>(c->dev, dir, 0, c->fpairs[dir] + gr.begin, gr.count,
+                                                              static_cast<const float*>(src),
+                                                              static_cast<float*>(dst), lc))); break)
+      }
+    }
+  }
+  if (f64) k_filter_done<double><<<g, 256, 0, s>>>(c->dev, static_cast<const double*>(c->R), static_cast<double*>(e));
+  else k_filter_done<float><<<g, 256, 0, s>>>(c->dev, static_cast<const float*>(c->R), static_cast<float*>(e));
+  FCS_CUDA(cudaGetLastError());
+  return exchange_impl(c, e, 4, 0, s);
+}
+
 int fcs_step(fcs_ctx* c, void* e, double dt, double* dt_dev, int use_av, void* stream) {
   if (!c || !e) return FCS_EINVAL;
   if (!(dt > 0.0) && !dt_dev) return FCS_EINVAL;
@@ -1158,6 +1263,7 @@ int fcs_step(fcs_ctx* c, void* e, double dt, double* dt_dev, int use_av, void* s
     if ((rc = rk_stage(c, s, dt, dtd, e, es, c->A, out, mu, stream))) return rc;
     if ((rc = patch_exchange(c, out, 4, stream))) return rc;
   }
+  if (c->opt.filter_step) return fcs_filter(c, e, stream);
   return FCS_OK;
 }
 

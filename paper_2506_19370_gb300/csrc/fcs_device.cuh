@@ -14,9 +14,12 @@ constexpr int kWarps = 4;             // warps per block of the line kernels
 struct PatchDev {
   int n1, n2, cart, pad0;
   int bc[4];
-  int plan[2];          // FFT plan of lines along i (length n1) and along j (length n2)
+  int plan[2];          // FFT plan of full lines along i (length n1) and along j (length n2)
+  int m1, m2;           // L-shaped patch: points i < m1, j < m2 missing (0, 0: rectangle)
+  int plan_s[2];        // L-shaped patch: plans of the short rows (n1 - m1) and columns (n2 - m2)
   int wx_off, wy_off;   // first x-window and first y-window of the patch (per instance)
-  int wpl_x, wpl_y;     // windows per x-line, per y-line
+  int wpl_x, wpl_y;     // windows per full x-line, per full y-line
+  int wpl_xs, wpl_ys;   // windows per short x-line, short y-line (L-shaped patches)
   long long soff, qoff; // offsets in the state and scalar layouts (per instance)
   double hx, hy;        // derivative spacing along i and j (physical if Cartesian, parameter otherwise)
   double hmax;          // largest physical spacing (viscosity scale)
@@ -44,6 +47,8 @@ struct CtxDev {
   const float* tablo;
   const double2* tw64;
   const float2* tw32;
+  const double* flt64;    // per plan, n filter factors sigma(k) (same offsets as the twiddles)
+  const float* flt32;
   const LineRef* lines0;  // rows (lines along i)
   const LineRef* lines1;  // columns (lines along j)
   const int4* windows;    // per window of one instance: patch, dir, line, start
@@ -71,6 +76,18 @@ struct CtxDev {
 
 // Point handled by this thread in a pointwise kernel launched on
 // (npblk, instances) blocks of 256 threads; 32-bit indexing within a patch.
+// L-shaped patches: point membership, first index and plan of a line
+// (dir 0: row `line`, dir 1: column `line`).  Rectangles have m1 = m2 = 0.
+__host__ __device__ __forceinline__ bool pt_active(const PatchDev& P, int i, int j) {
+  return !(i < P.m1 && j < P.m2);
+}
+__host__ __device__ __forceinline__ int line_start(const PatchDev& P, int dir, int line) {
+  return dir == 0 ? (line < P.m2 ? P.m1 : 0) : (line < P.m1 ? P.m2 : 0);
+}
+__host__ __device__ __forceinline__ int line_plan(const PatchDev& P, int dir, int line) {
+  return line_start(P, dir, line) ? P.plan_s[dir] : P.plan[dir];
+}
+
 struct PtIdx {
   int inst, patch, lq, i, j;
   bool ok;
@@ -83,9 +100,9 @@ __device__ __forceinline__ PtIdx pt_index(const CtxDev& c, const PatchDev** Pp) 
   r.inst = blockIdx.y;
   r.patch = pb.x;
   r.lq = pb.y + (int)threadIdx.x;
-  r.ok = r.lq < P.n1 * P.n2;
   r.i = r.lq % P.n1;
   r.j = r.lq / P.n1;
+  r.ok = r.lq < P.n1 * P.n2 && pt_active(P, r.i, r.j);
   return r;
 }
 
@@ -286,17 +303,28 @@ struct Offset<float> {
   static constexpr bool kShift = true;
 };
 
+// Filter factor sigma(k) of the plan table at idx.
+template <typename T>
+__device__ __forceinline__ T flt_at(const CtxDev& c, int idx);
+template <>
+__device__ __forceinline__ double flt_at<double>(const CtxDev& c, int idx) { return __ldg(c.flt64 + idx); }
+template <>
+__device__ __forceinline__ float flt_at<float>(const CtxDev& c, int idx) { return __ldg(c.flt32 + idx); }
+
 // FC derivative of two real lines packed in buf[0..N) (buf = a, scratch b):
-// continuation, FFT, multiply by (i k)^order, inverse FFT.  On return res[0..N)
-// holds (d^order a, d^order b) / n... already divided by n and scaled by
-// (2 pi / (n h))^order; returns the result buffer.
+// continuation, FFT, multiply by (i k)^order (order 0: by the filter factors
+// sigma(k)), inverse FFT.  On return res[0..N) holds (d^order a, d^order b),
+// already divided by n and scaled by (2 pi / (n h))^order; returns the result
+// buffer.
 template <typename T>
 __device__ Cx<T>* fc_deriv_pair(Cx<T>* a, Cx<T>* b, const CtxDev& c, const PlanDev& pl, int d, T h, int order,
                                 int lane) {
   const int N = pl.N, n = pl.n;
+  T oa = T(0), ob = T(0);
   if (Offset<T>::kShift) {
     const Cx<T> f0 = a[0], f1 = a[N - 1];
-    const T oa = (f0.x + f1.x) * T(0.5), ob = (f0.y + f1.y) * T(0.5);
+    oa = (f0.x + f1.x) * T(0.5);
+    ob = (f0.y + f1.y) * T(0.5);
     __syncwarp();
     for (int t = lane; t < N; t += 32) a[t] = {a[t].x - oa, a[t].y - ob};
     __syncwarp();
@@ -314,15 +342,24 @@ __device__ Cx<T>* fc_deriv_pair(Cx<T>* a, Cx<T>* b, const CtxDev& c, const PlanD
     if (order == 1) {
       const T k = (2 * m == n) ? T(0) : T(km) * sc * inv_n;
       o = {-k * z.y, k * z.x};  // i k z
-    } else {
+    } else if (order == 2) {
       const T k = T(km) * sc;
       const T f = -k * k * inv_n;
+      o = {f * z.x, f * z.y};
+    } else {
+      const T f = flt_at<T>(c, pl.tw_off + m) * inv_n;
       o = {f * z.x, f * z.y};
     }
     r[m] = o;
   }
   __syncwarp();
-  return warp_fft<T>(r, s, c, pl, true, lane);
+  Cx<T>* res = warp_fft<T>(r, s, c, pl, true, lane);
+  if (order == 0 && Offset<T>::kShift) {  // a filtered line keeps its offset
+    __syncwarp();
+    for (int t = lane; t < N; t += 32) res[t] = {res[t].x + oa, res[t].y + ob};
+    __syncwarp();
+  }
+  return res;
 }
 
 // ------------------------------------------------------------ gas dynamics
@@ -331,12 +368,79 @@ __device__ __forceinline__ T pressure(T rho, T mx, T my, T E, T gm1) {
   return gm1 * (E - T(0.5) * (mx * mx + my * my) / rho);
 }
 
+// Wall: remove the velocity component along the unit normal (nx, ny).
+template <typename T>
+__device__ __forceinline__ void wall_project(T* v, T nx, T ny) {
+  const T nn = sqrt(nx * nx + ny * ny);
+  nx /= nn;
+  ny /= nn;
+  const T mn = v[1] * nx + v[2] * ny;
+  v[1] -= mn * nx;
+  v[2] -= mn * ny;
+}
+
+// Apply the boundary conditions of the sides the point lies on, in the order
+// left, right, bottom, top (paper §5 item 4: enforced at every stage), then
+// for an L-shaped patch its inner wall edges i = m1 (j < m2) and j = m2
+// (i < m1) and the corner node (m1, m2), a wall along the bisector of the
+// two inward edge normals grad q1 / |grad q1| + grad q2 / |grad q2|.
+template <typename T>
+__device__ __forceinline__ void apply_bc(const CtxDev& c, const PatchDev& P, int i, int j, long long q, T* v) {
+  const T gm1 = T(c.gamma - 1.0);
+  const bool on[4] = {i == 0 && j >= P.m2, i == P.n1 - 1, j == 0 && i >= P.m1, j == P.n2 - 1};
+  const T* M = metrics<T>(c);
+  const long long qs = c.qstride;
+#pragma unroll
+  for (int s = 0; s < 4; ++s) {
+    if (!on[s]) continue;
+    const int code = P.bc[s];
+    if (code == 1) {  // wall
+      if (P.cart) {
+        v[s < 2 ? 1 : 2] = T(0);
+      } else if (s < 2) {
+        wall_project(v, M[3 * qs + q], -M[1 * qs + q]);
+      } else {
+        wall_project(v, -M[2 * qs + q], M[0 * qs + q]);
+      }
+    } else if (code == 2) {  // inflow
+      v[0] = T(c.inflow[0]);
+      v[1] = T(c.inflow[1]);
+      v[2] = T(c.inflow[2]);
+      v[3] = T(c.inflow[3]);
+    } else if (code == 3) {  // outflow pressure
+      v[3] = T(c.p_out) / gm1 + T(0.5) * (v[1] * v[1] + v[2] * v[2]) / v[0];
+    }
+  }
+  if (P.m1 > 0) {
+    if (i == P.m1 && j < P.m2) {
+      if (P.cart) v[1] = T(0);
+      else wall_project(v, M[3 * qs + q], -M[1 * qs + q]);
+    } else if (j == P.m2 && i < P.m1) {
+      if (P.cart) v[2] = T(0);
+      else wall_project(v, -M[2 * qs + q], M[0 * qs + q]);
+    } else if (i == P.m1 && j == P.m2) {
+      T ax = T(1), ay = T(0), bx = T(0), by = T(1);
+      if (!P.cart) {
+        const T sg = M[4 * qs + q] < T(0) ? T(-1) : T(1);
+        ax = sg * M[3 * qs + q];
+        ay = -sg * M[1 * qs + q];
+        bx = -sg * M[2 * qs + q];
+        by = sg * M[0 * qs + q];
+      }
+      const T na = sqrt(ax * ax + ay * ay), nb = sqrt(bx * bx + by * by);
+      wall_project(v, ax / na + bx / nb, ay / na + by / nb);
+    }
+  }
+}
+
+
 // ------------------------------------------------------------ register FFT
 // Everything one FC derivative of a line pair needs, by value (no pointer to
 // the kernel's context, so nothing has to be spilled to local memory).
 template <typename T>
 struct LineOp {
   const Cx<T>* tw;      // the plan's n twiddles e^{-2 pi i k / n}
+  const T* flt;         // the plan's n filter factors sigma(k)
   const double* t64;    // the plan's C x d table (FP64)
   const float* thi;     // FP32 split of the table (hi, lo)
   const float* tlo;
@@ -348,13 +452,13 @@ template <typename T>
 __device__ __forceinline__ LineOp<T> make_op(const CtxDev& c, const PlanDev& pl, T h);
 template <>
 __device__ __forceinline__ LineOp<double> make_op<double>(const CtxDev& c, const PlanDev& pl, double h) {
-  return {reinterpret_cast<const Cx<double>*>(c.tw64 + pl.tw_off), c.tab64 + pl.tab_off, c.tabhi + pl.tab_off,
-          c.tablo + pl.tab_off, pl.N, pl.C, pl.n, c.d, pl.n1reg, h};
+  return {reinterpret_cast<const Cx<double>*>(c.tw64 + pl.tw_off), c.flt64 + pl.tw_off, c.tab64 + pl.tab_off,
+          c.tabhi + pl.tab_off, c.tablo + pl.tab_off, pl.N, pl.C, pl.n, c.d, pl.n1reg, h};
 }
 template <>
 __device__ __forceinline__ LineOp<float> make_op<float>(const CtxDev& c, const PlanDev& pl, float h) {
-  return {reinterpret_cast<const Cx<float>*>(c.tw32 + pl.tw_off), c.tab64 + pl.tab_off, c.tabhi + pl.tab_off,
-          c.tablo + pl.tab_off, pl.N, pl.C, pl.n, c.d, pl.n1reg, h};
+  return {reinterpret_cast<const Cx<float>*>(c.tw32 + pl.tw_off), c.flt32 + pl.tw_off, c.tab64 + pl.tab_off,
+          c.tabhi + pl.tab_off, c.tablo + pl.tab_off, pl.N, pl.C, pl.n, c.d, pl.n1reg, h};
 }
 
 template <typename T>
@@ -501,19 +605,24 @@ __device__ __forceinline__ void reg_deriv_pair(const T* a, int sa, const T* b, i
     if (order == 1) {
       const T kk = (2 * k == n) ? T(0) : T(km) * sc * inv_n;
       x[k1] = {-kk * z.y, kk * z.x};
-    } else {
+    } else if (order == 2) {
       const T kk = T(km) * sc;
       const T f = -kk * kk * inv_n;
+      x[k1] = {f * z.x, f * z.y};
+    } else {
+      const T f = __ldg(op.flt + k) * inv_n;
       x[k1] = {f * z.x, f * z.y};
     }
   }
   reg_fft<T, N1>(x, op.tw, true, lane);
+  // a filtered line (order 0) keeps its offset
+  const T ra = order == 0 ? offa * scale : T(0), rb = order == 0 ? offb * scale : T(0);
 #pragma unroll
   for (int j1 = 0; j1 < N1; ++j1) {
     const int j = lane + 32 * j1;
     if (j < N) {
-      oa[j * soa] = x[j1].x;
-      if (ob) ob[j * sob] = x[j1].y;
+      oa[j * soa] = x[j1].x + ra;
+      if (ob) ob[j * sob] = x[j1].y + rb;
     }
   }
 }
@@ -799,9 +908,12 @@ __device__ __forceinline__ void tl_deriv_pair(const T* a, int sa, const T* b, in
     if (order == 1) {
       const T kk = (2 * k == n) ? T(0) : T(km) * sc * inv_n;
       x[p] = {-kk * z.y, kk * z.x};
-    } else {
+    } else if (order == 2) {
       const T kk = T(km) * sc;
       const T f = -kk * kk * inv_n;
+      x[p] = {f * z.x, f * z.y};
+    } else {
+      const T f = __ldg(op.flt + k) * inv_n;
       x[p] = {f * z.x, f * z.y};
     }
   });
@@ -825,12 +937,13 @@ __device__ __forceinline__ void tl_deriv_pair(const T* a, int sa, const T* b, in
     });
     rdft_inv<T, 8>(v);
     if (active) {
+      const T ra = order == 0 ? offa * scale : T(0), rb = order == 0 ? offb * scale : T(0);
 #pragma unroll
       for (int aa = 0; aa < 8; ++aa) {
         const int j = bb + B * aa;
         if (j < N) {
-          oa[j * soa] = v[aa].x;
-          if (ob) ob[j * sob] = v[aa].y;
+          oa[j * soa] = v[aa].x + ra;
+          if (ob) ob[j * sob] = v[aa].y + rb;
         }
       }
     }

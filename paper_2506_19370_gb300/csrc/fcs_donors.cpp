@@ -4,7 +4,8 @@
 // another patch.  The donor is the lowest-numbered other patch that contains
 // the point and either has a grid node there (copy) or whose 6 x 6 tensor
 // Lagrange stencil around the point holds none of its own receivers (donors
-// are never receivers).  The donor parameter of a point is the affine inverse
+// are never receivers; on an L-shaped donor every stencil node belongs to the
+// patch).  The donor parameter of a point is the affine inverse
 // on Cartesian patches and, on curvilinear ones, Newton's method on the
 // tensor Lagrange interpolant of the donor's grid coordinates.  Host FP64.
 #include <algorithm>
@@ -56,6 +57,22 @@ void basis(double t, double* v, double* dv) {
 int block_start(double f, int n) {
   const int s = (int)std::floor(f) - (kS / 2 - 1);
   return std::min(std::max(s, 0), n - kS);
+}
+
+bool lshaped(const fcs_patch_desc& q) { return q.lcut[0] > 0 && q.lcut[1] > 0; }
+
+bool active(const fcs_patch_desc& q, int i, int j) { return !(lshaped(q) && i < q.lcut[0] && j < q.lcut[1]); }
+
+// Donor block around (fi, fj): on an L-shaped patch a block reaching into the
+// missing quadrant moves out of it along the direction needing the smaller
+// shift (ties: along j).
+void donor_block(const fcs_patch_desc& s, double fi, double fj, int* i0, int* j0) {
+  *i0 = block_start(fi, s.n1);
+  *j0 = block_start(fj, s.n2);
+  if (lshaped(s) && *i0 < s.lcut[0] && *j0 < s.lcut[1]) {
+    if (s.lcut[1] - *j0 <= s.lcut[0] - *i0) *j0 = s.lcut[1];
+    else *i0 = s.lcut[0];
+  }
 }
 
 // Fractional index (fi, fj) of (x, y) in patch P; false if not found.
@@ -121,6 +138,7 @@ bool locate(const PatchView& P, double x, double y, double* fi, double* fj) {
 }  // namespace
 
 bool is_receiver(const fcs_patch_desc& q, int n_f, int i, int j) {
+  if (!active(q, i, j)) return false;
   return (q.bc[0] == 0 && i < n_f) || (q.bc[1] == 0 && i >= q.n1 - n_f) || (q.bc[2] == 0 && j < n_f) ||
          (q.bc[3] == 0 && j >= q.n2 - n_f);
 }
@@ -145,7 +163,7 @@ int build_fringe(const fcs_patch_desc* pd, int npatch, int n_f, std::vector<Frin
     const fcs_patch_desc& q = pd[p];
     for (int j = 0; j < q.n2; ++j)
       for (int i = 0; i < q.n1; ++i) {
-        if (!is_receiver(q, n_f, i, j)) continue;
+        if (!is_receiver(q, n_f, i, j)) continue;   // (only points of the patch receive)
         const double x = V[p].X(i, j), y = V[p].Y(i, j);
         bool found = false;
         for (int r = 0; r < npatch && !found; ++r) {
@@ -159,17 +177,20 @@ int build_fringe(const fcs_patch_desc* pd, int npatch, int n_f, std::vector<Frin
           const fcs_patch_desc& s = pd[r];
           if (fi < -kInsideTol || fi > s.n1 - 1 + kInsideTol || fj < -kInsideTol || fj > s.n2 - 1 + kInsideTol)
             continue;
+          if (lshaped(s) && fi < s.lcut[0] - kInsideTol && fj < s.lcut[1] - kInsideTol) continue;
           const long long ri = std::llround(fi), rj = std::llround(fj);
           if (std::fabs(fi - ri) <= kCopyTol && std::fabs(fj - rj) <= kCopyTol) {
-            if (is_receiver(s, n_f, (int)ri, (int)rj)) continue;
+            if (!active(s, (int)ri, (int)rj) || is_receiver(s, n_f, (int)ri, (int)rj)) continue;
             copies->push_back({p, j * q.n1 + i, r, (int)rj * s.n1 + (int)ri});
             found = true;
             break;
           }
-          const int i0 = block_start(fi, s.n1), j0 = block_start(fj, s.n2);
+          int i0, j0;
+          donor_block(s, fi, fj, &i0, &j0);
           bool clean = true;
           for (int b = 0; b < kS && clean; ++b)
-            for (int a = 0; a < kS && clean; ++a) clean = !is_receiver(s, n_f, i0 + a, j0 + b);
+            for (int a = 0; a < kS && clean; ++a)
+              clean = active(s, i0 + a, j0 + b) && !is_receiver(s, n_f, i0 + a, j0 + b);
           if (!clean) continue;
           FringeInterp e{};
           e.dst_patch = p;

@@ -73,6 +73,42 @@ __global__ void k_interp(CtxDev c, const int4* __restrict__ ent, const T* __rest
   }
 }
 
+// ============================================================ filter
+// Spectral filter of the state (§5 item 3, Algorithm 4): the line filters act
+// on W = (rho, rho u, rho v, theta), theta = p / rho; then E is rebuilt from
+// theta and the boundary conditions are imposed again.
+template <typename T>
+__global__ void k_filter_prep(CtxDev c, const T* __restrict__ e, T* W) {
+  const PatchDev* Pp;
+  const PtIdx x = pt_index(c, &Pp);
+  const PatchDev& P = *Pp;
+  if (!x.ok) return;
+  const long long np = (long long)P.n1 * P.n2, o = x.inst * c.sstride + P.soff + x.lq;
+  const T rho = e[o], mx = e[o + np], my = e[o + 2 * np], En = e[o + 3 * np];
+  W[o] = rho;
+  W[o + np] = mx;
+  W[o + 2 * np] = my;
+  W[o + 3 * np] = pressure<T>(rho, mx, my, En, T(c.gamma - 1.0)) / rho;
+}
+
+// End of the filter: E from the filtered temperature, boundary conditions.
+template <typename T>
+__global__ void k_filter_done(CtxDev c, const T* __restrict__ W, T* e) {
+  const PatchDev* Pp;
+  const PtIdx x = pt_index(c, &Pp);
+  const PatchDev& P = *Pp;
+  if (!x.ok) return;
+  const long long np = (long long)P.n1 * P.n2, o = x.inst * c.sstride + P.soff + x.lq;
+  T v[4];
+  v[0] = W[o];
+  v[1] = W[o + np];
+  v[2] = W[o + 2 * np];
+  v[3] = v[0] * W[o + 3 * np] / T(c.gamma - 1.0) + T(0.5) * (v[1] * v[1] + v[2] * v[2]) / v[0];
+  apply_bc<T>(c, P, x.i, x.j, P.qoff + x.lq, v);
+#pragma unroll
+  for (int f = 0; f < 4; ++f) e[o + f * np] = v[f];
+}
+
 // ============================================================ point helpers
 __device__ __forceinline__ int find_patch(const CtxDev& c, long long q) {
   int lo = 0, hi = c.npatch - 1;
@@ -427,18 +463,24 @@ __global__ void k_tau_gather(CtxDev c, const signed char* __restrict__ tau_w, si
     const int i = x.i, j = x.j;
     const signed char* tw = tau_w + inst * c.nwin;
     int best = 4;
-    // x-windows of row j: regular windows k with 16k <= i < 16k+16, plus the right-aligned one
+    // x-windows of row j: regular windows k with 16k <= i' < 16k+16 of its
+    // segment (i' = i - first index, length N), plus the right-aligned one;
+    // rows j < m2 of an L-shaped patch (short segments) come first
     {
-      const int nw = P.wpl_x, base = P.wx_off + j * nw;
-      const int k = i / 16;
-      if (k < nw && 16 * k + 16 <= P.n1) best = min(best, (int)tw[base + k]);
-      if (P.n1 % 16 != 0 && i >= P.n1 - 16) best = min(best, (int)tw[base + nw - 1]);
+      const bool sh = j < P.m2;
+      const int nw = sh ? P.wpl_xs : P.wpl_x, a = sh ? P.m1 : 0, N = P.n1 - a, ii = i - a;
+      const int base = P.wx_off + (sh ? j * P.wpl_xs : P.m2 * P.wpl_xs + (j - P.m2) * P.wpl_x);
+      const int k = ii / 16;
+      if (k < nw && 16 * k + 16 <= N) best = min(best, (int)tw[base + k]);
+      if (N % 16 != 0 && ii >= N - 16) best = min(best, (int)tw[base + nw - 1]);
     }
     {
-      const int nw = P.wpl_y, base = P.wy_off + i * nw;
-      const int k = j / 16;
-      if (k < nw && 16 * k + 16 <= P.n2) best = min(best, (int)tw[base + k]);
-      if (P.n2 % 16 != 0 && j >= P.n2 - 16) best = min(best, (int)tw[base + nw - 1]);
+      const bool sh = i < P.m1;
+      const int nw = sh ? P.wpl_ys : P.wpl_y, a = sh ? P.m2 : 0, N = P.n2 - a, jj = j - a;
+      const int base = P.wy_off + (sh ? i * P.wpl_ys : P.m1 * P.wpl_ys + (i - P.m1) * P.wpl_y);
+      const int k = jj / 16;
+      if (k < nw && 16 * k + 16 <= N) best = min(best, (int)tw[base + k]);
+      if (N % 16 != 0 && jj >= N - 16) best = min(best, (int)tw[base + nw - 1]);
     }
     tau[t] = (signed char)best;
   }
@@ -555,7 +597,7 @@ __global__ void k_av_prelim(CtxDev c, const T* __restrict__ S, const signed char
         if (jj < 0 || jj >= P.n2) continue;
         for (int di = -1; di <= 1; ++di) {
           const int ii = i + di;
-          if (ii < 0 || ii >= P.n1) continue;
+          if (ii < 0 || ii >= P.n1 || !pt_active(P, ii, jj)) continue;
           m = fmax(m, Sp[(long long)jj * P.n1 + ii]);
         }
       }
@@ -579,7 +621,7 @@ __global__ void k_av_boxmax(CtxDev c, const T* __restrict__ in, T* out, int r, i
     T m = ip[lq];
     for (int k = -r; k <= r; ++k) {
       const int ii = dir == 0 ? i + k : i, jj = dir == 0 ? j : j + k;
-      if (ii < 0 || ii >= P.n1 || jj < 0 || jj >= P.n2) continue;
+      if (ii < 0 || ii >= P.n1 || jj < 0 || jj >= P.n2 || !pt_active(P, ii, jj)) continue;
       m = fmax(m, ip[(long long)jj * P.n1 + ii]);
     }
     out[t] = m;
@@ -601,7 +643,7 @@ __global__ void k_av_bump(CtxDev c, const T* __restrict__ in, T* out, const doub
     T num = 0, den = 0;
     for (int k = -r; k <= r; ++k) {
       const int ii = dir == 0 ? i + k : i, jj = dir == 0 ? j : j + k;
-      if (ii < 0 || ii >= P.n1 || jj < 0 || jj >= P.n2) continue;
+      if (ii < 0 || ii >= P.n1 || jj < 0 || jj >= P.n2 || !pt_active(P, ii, jj)) continue;
       const T b = T(bw[k + r]);
       num += b * ip[(long long)jj * P.n1 + ii];
       den += b;

@@ -9,8 +9,10 @@
 namespace fcs {
 
 // ============================================================ FC derivative
-// FC derivative of a scalar field: each warp takes jobs_per_round(N1) line
-// pairs at a time (two real lines -> one complex FFT).  A pair (patch, line a,
+// FC derivative (with respect to the patch parameter, spacing 1/(n1 - 1) or
+// 1/(n2 - 1) also on the short lines of an L-shaped patch) of a scalar field:
+// each warp takes jobs_per_round(N1) line pairs at a time (two real lines ->
+// one complex FFT).  A pair (patch, line a,
 // line b, w) reads the scalar layout if w < 0, else field w of the state layout.
 template <typename T, int N1>
 __global__ void __launch_bounds__(kWarps * 32) k_fc_deriv(CtxDev c, int dir, int order, const int4* __restrict__ pairs,
@@ -34,10 +36,11 @@ __global__ void __launch_bounds__(kWarps * 32) k_fc_deriv(CtxDev c, int dir, int
       const int inst = (int)(w / npairs);
       const int4 pr = pairs[w % npairs];
       const PatchDev& P = c.patches[pr.x];
-      const int N = c.plans[P.plan[dir]].N;
+      const int N = c.plans[line_plan(P, dir, pr.y)].N;
       const long long stride = dir == 0 ? 1 : P.n1;
-      const long long la = dir == 0 ? (long long)pr.y * P.n1 : pr.y;
-      const long long lb = pr.z < 0 ? -1 : (dir == 0 ? (long long)pr.z * P.n1 : pr.z);
+      const long long s0 = (long long)line_start(P, dir, pr.y) * stride;   // both lines of a pair share it
+      const long long la = (dir == 0 ? (long long)pr.y * P.n1 : pr.y) + s0;
+      const long long lb = pr.z < 0 ? -1 : (dir == 0 ? (long long)pr.z * P.n1 : pr.z) + s0;
       const T* src = in + (pr.w < 0 ? inst * c.qstride + P.qoff
                                     : inst * c.sstride + P.soff + (long long)pr.w * P.n1 * P.n2);
       for (int t = lane; t < N; t += 32) {
@@ -52,58 +55,18 @@ __global__ void __launch_bounds__(kWarps * 32) k_fc_deriv(CtxDev c, int dir, int
     const int inst = (int)(wc / npairs);
     const int4 pr = pairs[wc % npairs];
     const PatchDev& P = c.patches[pr.x];
-    const PlanDev& pl = c.plans[P.plan[dir]];
+    const PlanDev& pl = c.plans[line_plan(P, dir, pr.y)];
     const long long stride = dir == 0 ? 1 : P.n1;
-    const long long la = dir == 0 ? (long long)pr.y * P.n1 : pr.y;
-    const long long lb = pr.z < 0 ? -1 : (dir == 0 ? (long long)pr.z * P.n1 : pr.z);
+    const long long s0 = (long long)line_start(P, dir, pr.y) * stride;
+    const long long la = (dir == 0 ? (long long)pr.y * P.n1 : pr.y) + s0;
+    const long long lb = pr.z < 0 ? -1 : (dir == 0 ? (long long)pr.z * P.n1 : pr.z) + s0;
     T* dst = out + (pr.w < 0 ? inst * c.qstride + P.qoff
                              : inst * c.sstride + P.soff + (long long)pr.w * P.n1 * P.n2);
+    const T hq = T(1) / T((dir == 0 ? P.n1 : P.n2) - 1);
     line_deriv_pair<T, N1>(L + (2 * g) * nmax, 1, lb >= 0 ? L + (2 * g + 1) * nmax : nullptr, 1, dst + la, (int)stride,
-                           lb >= 0 ? dst + lb : nullptr, (int)stride, T(1), c, pl, T(1) / T(pl.N - 1), order, lane, aux,
-                           aux + c.nfmax, tile, active);
+                           lb >= 0 ? dst + lb : nullptr, (int)stride, T(1), c, pl, hq, order, lane, aux, aux + c.nfmax,
+                           tile, active);
     __syncwarp();
-  }
-}
-
-// Apply the boundary conditions of the sides the point lies on, in the order
-// left, right, bottom, top (paper §5 item 4: enforced at every stage).
-template <typename T>
-__device__ __forceinline__ void apply_bc(const CtxDev& c, const PatchDev& P, int i, int j, long long q, T* v) {
-  const T gm1 = T(c.gamma - 1.0);
-  const bool on[4] = {i == 0, i == P.n1 - 1, j == 0, j == P.n2 - 1};
-#pragma unroll
-  for (int s = 0; s < 4; ++s) {
-    if (!on[s]) continue;
-    const int code = P.bc[s];
-    if (code == 1) {  // wall
-      if (P.cart) {
-        v[s < 2 ? 1 : 2] = T(0);
-      } else {
-        const T* M = metrics<T>(c);
-        const long long qs = c.qstride;
-        T nx, ny;
-        if (s < 2) {
-          nx = M[3 * qs + q];
-          ny = -M[1 * qs + q];
-        } else {
-          nx = -M[2 * qs + q];
-          ny = M[0 * qs + q];
-        }
-        const T nn = sqrt(nx * nx + ny * ny);
-        nx /= nn;
-        ny /= nn;
-        const T mn = v[1] * nx + v[2] * ny;
-        v[1] -= mn * nx;
-        v[2] -= mn * ny;
-      }
-    } else if (code == 2) {  // inflow
-      v[0] = T(c.inflow[0]);
-      v[1] = T(c.inflow[1]);
-      v[2] = T(c.inflow[2]);
-      v[3] = T(c.inflow[3]);
-    } else if (code == 3) {  // outflow pressure
-      v[3] = T(c.p_out) / gm1 + T(0.5) * (v[1] * v[1] + v[2] * v[2]) / v[0];
-    }
   }
 }
 
@@ -112,19 +75,17 @@ __device__ __forceinline__ void apply_bc(const CtxDev& c, const PatchDev& P, int
 // Cartesian: f resp. g.  With viscosity the physical fluxes become f - mu e_x,
 // g - mu e_y: dv is the derivative of e along this direction's parameter and
 // dvo (curvilinear only) along the other one; e_x, e_y follow by the chain
-// rule.  t is the point's index along the line: the normal viscous flux is
-// zero on wall, outflow and free sides (the diffusion term needs a condition
-// on every variable there; this one is impermeable and adiabatic).
+// rule.  t is the point's index along its line segment of N points, code_lo
+// the boundary code at the segment's start (a wall for the short lines of an
+// L-shaped patch): the normal viscous flux is zero on wall, outflow and free
+// sides (the diffusion term needs a condition on every variable there; this
+// one is impermeable and adiabatic).
 template <typename T, int DIR>
 __device__ __forceinline__ void point_flux(const CtxDev& c, const PatchDev& P, long long q, const T* v, const T* dv,
-                                           const T* dvo, T mu, bool visc, T* F, int t) {
+                                           const T* dvo, T mu, bool visc, T* F, int t, int N, int code_lo) {
   if (visc) {
-    const int N = DIR == 0 ? P.n1 : P.n2;
-    const int side = t == 0 ? 2 * DIR : (t == N - 1 ? 2 * DIR + 1 : -1);
-    if (side >= 0) {
-      const int code = P.bc[side];
-      if (code == 1 || code == 3 || code == 4) visc = false;
-    }
+    const int code = t == 0 ? code_lo : (t == N - 1 ? P.bc[2 * DIR + 1] : 0);
+    if (code == 1 || code == 3 || code == 4) visc = false;
   }
   const T gm1 = T(c.gamma - 1.0);
   const T rho = v[0], mx = v[1], my = v[2], En = v[3];
@@ -200,15 +161,16 @@ __global__ void __launch_bounds__(kWarps * 32, 4) k_xpass(CtxDev c, int lbeg, in
       row[k] = lr.line;
       const PatchDev& P = c.patches[lr.patch];
       const long long np = (long long)P.n1 * P.n2;
-      const T* es = e + inst * c.sstride + P.soff + (long long)lr.line * P.n1;
+      const int s0 = line_start(P, 0, lr.line), N = P.n1 - s0;
+      const T* es = e + inst * c.sstride + P.soff + (long long)lr.line * P.n1 + s0;
       const bool visc = mu != nullptr;
       bool any_mu = false;
       if (has[k])
-        for (int t = lane; t < P.n1; t += 32) {
+        for (int t = lane; t < N; t += 32) {
 #pragma unroll
           for (int f = 0; f < 4; ++f) E[(k * 4 + f) * nmax + t] = es[f * np + t];
           if (visc) {
-            const T m = mu[inst * c.qstride + P.qoff + (long long)lr.line * P.n1 + t];
+            const T m = mu[inst * c.qstride + P.qoff + (long long)lr.line * P.n1 + s0 + t];
             M[k * nmax + t] = m;
             any_mu |= m != T(0);
           }
@@ -227,10 +189,12 @@ __global__ void __launch_bounds__(kWarps * 32, 4) k_xpass(CtxDev c, int lbeg, in
           const PatchDev& P = c.patches[pid[k]];
           const bool visc = vrow[k];
           const bool curv = visc && !P.cart;
-          const long long q0 = P.qoff + (long long)row[k] * P.n1;
+          const int a0 = line_start(P, 0, row[k]), N = P.n1 - a0;
+          const int code_lo = a0 ? 1 : P.bc[0];
+          const long long q0 = P.qoff + (long long)row[k] * P.n1 + a0;
           const long long np = (long long)P.n1 * P.n2;
-          const long long s0 = inst * c.sstride + P.soff + (long long)row[k] * P.n1;
-          for (int t = lane; t < P.n1; t += 32) {
+          const long long s0 = inst * c.sstride + P.soff + (long long)row[k] * P.n1 + a0;
+          for (int t = lane; t < N; t += 32) {
             T v[4], dv[4], dvo[4], F[4];
 #pragma unroll
             for (int f = 0; f < 4; ++f) {
@@ -239,7 +203,7 @@ __global__ void __launch_bounds__(kWarps * 32, 4) k_xpass(CtxDev c, int lbeg, in
               dvo[f] = curv ? G2[s0 + f * np + t] : T(0);
               if (curv) G1[s0 + f * np + t] = dv[f];
             }
-            point_flux<T, 0>(c, P, q0 + t, v, dv, dvo, visc ? M[k * nmax + t] : T(0), visc, F, t);
+            point_flux<T, 0>(c, P, q0 + t, v, dv, dvo, visc ? M[k * nmax + t] : T(0), visc, F, t, N, code_lo);
 #pragma unroll
             for (int f = 0; f < 4; ++f) W[(k * 4 + f) * nmax + t] = F[f];
           }
@@ -256,7 +220,7 @@ __global__ void __launch_bounds__(kWarps * 32, 4) k_xpass(CtxDev c, int lbeg, in
         const int pidk = kk ? pid[1] : pid[0], rowk = kk ? row[1] : row[0];
         bool active = job < 2 * RW && (kk ? has[1] : has[0]);
         const PatchDev& P = c.patches[pidk];
-        const PlanDev& pl = c.plans[P.plan[0]];
+        const PlanDev& pl = c.plans[line_plan(P, 0, rowk)];
         if (phase == 0 && !(kk ? vrow[1] : vrow[0])) active = false;
         const long long np = (long long)P.n1 * P.n2;
         const T* src = (phase == 0 ? E : W) + (kk * 4 + 2 * pr) * nmax;
@@ -266,7 +230,7 @@ __global__ void __launch_bounds__(kWarps * 32, 4) k_xpass(CtxDev c, int lbeg, in
           oa = W + (kk * 4 + 2 * pr) * nmax;
           ob = oa + nmax;
         } else {
-          oa = R + inst * c.sstride + P.soff + (long long)rowk * P.n1 + (2 * pr) * np;
+          oa = R + inst * c.sstride + P.soff + (long long)rowk * P.n1 + line_start(P, 0, rowk) + (2 * pr) * np;
           ob = oa + np;
         }
         line_deriv_pair<T, N1>(src, 1, src + nmax, 1, oa, 1, ob, 1, phase == 0 ? T(1) : T(-1), c, pl, T(P.hx), 1, lane,
@@ -304,12 +268,15 @@ __global__ void __launch_bounds__(kYWarps * 32, 3) k_ypass(CtxDev c, const int2*
     const int inst = (int)(wk / ntiles);
     const int2 tl = tiles[wk % ntiles];
     const PatchDev P = c.patches[tl.x];
-    const PlanDev pl = c.plans[P.plan[1]];
-    const int N = P.n2, c0 = tl.y;
-    const int width = min(tw, P.n1 - c0);
+    const int c0 = tl.y;
+    // all columns of a tile share their segment (tiles never straddle i = m1)
+    const int j0 = line_start(P, 1, c0), N = P.n2 - j0;
+    const PlanDev pl = c.plans[line_plan(P, 1, c0)];
+    const int code_lo = j0 ? 1 : P.bc[2];
+    const int width = min(tw, (c0 < P.m1 ? P.m1 : P.n1) - c0);
     const long long np = (long long)P.n1 * P.n2;
-    const long long sbase = inst * c.sstride + P.soff + c0;
-    const long long qbase = P.qoff + c0;
+    const long long sbase = inst * c.sstride + P.soff + (long long)j0 * P.n1 + c0;   // row j0 of the tile
+    const long long qbase = P.qoff + (long long)j0 * P.n1 + c0;
     const bool visc = mu != nullptr;
     // each thread keeps one column cc of the tile and strides over rows
     const int cc = threadIdx.x % tw, jr = threadIdx.x / tw, js = blockDim.x / tw;
@@ -354,7 +321,8 @@ __global__ void __launch_bounds__(kYWarps * 32, 3) k_ypass(CtxDev c, const int2*
             dv[f] = vc ? D[(f * n2m + j) * ld + cc] : T(0);
             dvo[f] = curv ? G1[sbase + f * np + (long long)j * P.n1 + cc] : T(0);
           }
-          point_flux<T, 1>(c, P, qbase + (long long)j * P.n1 + cc, v, dv, dvo, vc ? M[j * ld + cc] : T(0), vc, F, j);
+          point_flux<T, 1>(c, P, qbase + (long long)j * P.n1 + cc, v, dv, dvo, vc ? M[j * ld + cc] : T(0), vc, F, j, N,
+                           code_lo);
 #pragma unroll
           for (int f = 0; f < 4; ++f) D[(f * n2m + j) * ld + cc] = F[f];
         }
@@ -407,7 +375,7 @@ __global__ void __launch_bounds__(kYWarps * 32, 3) k_ypass(CtxDev c, const int2*
 #pragma unroll
         for (int f = 0; f < 4; ++f) v[f] = st.acc[off + f * np] + (dtv / T(6)) * kv[f];
       }
-      apply_bc<T>(c, P, c0 + cc, j, q, v);
+      apply_bc<T>(c, P, c0 + cc, j0 + j, q, v);
       const T pr_ = pressure<T>(v[0], v[1], v[2], v[3], gm1);
       int flag = 0;
       if (!(isfinite(v[0]) && isfinite(v[1]) && isfinite(v[2]) && isfinite(v[3]))) flag |= 1;

@@ -24,7 +24,7 @@ EXPORTS = ("fcs_default_options", "fc_setup", "fc_destroy", "fcs_get_layout", "f
            "fc_derivative", "euler_rhs", "rk_stage", "patch_exchange", "fcs_time_step", "fcs_conservation_sums",
            "sdnn_set_weights", "sdnn_get_weights", "sdnn_classify", "sdnn_indicator", "av_assemble",
            "sdnn_train_step", "sdnn_gradient", "sdnn_gradient_noalloc", "fcs_step", "fcs_step_graph", "fcs_status",
-           "fcs_strerror")
+           "fcs_strerror", "fcs_filter")
 
 
 class FcsError(RuntimeError):
@@ -36,14 +36,15 @@ class FcsError(RuntimeError):
 class PatchDesc(ctypes.Structure):
     _fields_ = [("n1", ctypes.c_int), ("n2", ctypes.c_int), ("bc", ctypes.c_int * 4), ("cartesian", ctypes.c_int),
                 ("box", ctypes.c_double * 4), ("x", ctypes.POINTER(ctypes.c_double)),
-                ("y", ctypes.POINTER(ctypes.c_double))]
+                ("y", ctypes.POINTER(ctypes.c_double)), ("lcut", ctypes.c_int * 2)]
 
 
 class Options(ctypes.Structure):
     _fields_ = [("gamma", ctypes.c_double), ("cfl", ctypes.c_double), ("n_f", ctypes.c_int), ("dtype", ctypes.c_int),
                 ("instances", ctypes.c_int), ("inflow", ctypes.c_double * 4), ("p_out", ctypes.c_double),
                 ("c_mu", ctypes.c_double), ("av_radius", ctypes.c_int), ("c_policy", ctypes.c_int),
-                ("train_batch_max", ctypes.c_int), ("autotune", ctypes.c_int)]
+                ("train_batch_max", ctypes.c_int), ("autotune", ctypes.c_int), ("filter_alpha", ctypes.c_double),
+                ("filter_p", ctypes.c_int), ("filter_step", ctypes.c_int)]
 
 
 class Layout(ctypes.Structure):
@@ -86,6 +87,7 @@ def lib():
             "sdnn_gradient": (i, [vp, vp, vp, i, vp, vp, vp]),
             "sdnn_gradient_noalloc": (i, [vp, vp, vp, i, vp, vp, vp]),
             "fcs_step": (i, [vp, vp, d, vp, i, vp]),
+            "fcs_filter": (i, [vp, vp, vp]),
             "fcs_step_graph": (i, [vp, vp, d, vp, i, vp]),
             "fcs_status": (i, [vp, ctypes.POINTER(ctypes.c_int)]),
             "fcs_strerror": (ctypes.c_char_p, [i]),
@@ -133,7 +135,7 @@ class Context:
     """An fcs_ctx for one patch layout (an ``inputs.Instance``) and its options."""
 
     def __init__(self, inst, d=5, C=25, dtype=F32, instances=1, cfl=0.5, n_f=5, c_mu=1.0, av_radius=4,
-                 c_policy=0, train_batch_max=4096, autotune=0):
+                 c_policy=0, train_batch_max=4096, autotune=0, filter_step=0, filter_p=None, filter_alpha=None):
         import torch  # device memory and streams
         self.torch = torch
         L = lib()
@@ -149,10 +151,17 @@ class Context:
         opt.p_out, opt.c_mu, opt.av_radius, opt.c_policy = inst.p_out, c_mu, av_radius, c_policy
         opt.train_batch_max = train_batch_max
         opt.autotune = autotune
+        opt.filter_step = filter_step
+        if filter_p is not None:
+            opt.filter_p = filter_p
+        if filter_alpha is not None:
+            opt.filter_alpha = filter_alpha
         descs = (PatchDesc * len(inst.patches))()
         self._keep = []
         for k, p in enumerate(inst.patches):
             descs[k].n1, descs[k].n2 = p.n1, p.n2
+            if getattr(p, "is_l", False):
+                descs[k].lcut[0], descs[k].lcut[1] = int(p.lcut[0]), int(p.lcut[1])
             for s in range(4):
                 descs[k].bc[s] = int(p.bc[s])
             if p.cartesian:
@@ -285,6 +294,9 @@ class Context:
     def gradient(self, x, labels, grad, loss=None, stream=None):
         _check("sdnn_gradient", lib().sdnn_gradient(self.h, _ptr(x), _ptr(labels), int(x.shape[0]), _ptr(loss),
                                                     _ptr(grad), _stream(stream)))
+
+    def filter(self, e, stream=None):
+        _check("fcs_filter", lib().fcs_filter(self.h, _ptr(e), _stream(stream)))
 
     def step(self, e, dt=0.0, dt_dev=None, use_av=False, stream=None):
         _check("fcs_step", lib().fcs_step(self.h, _ptr(e), float(dt), _ptr(dt_dev), int(use_av), _stream(stream)))

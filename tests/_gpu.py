@@ -46,7 +46,33 @@ def layout(name):
             st.append(I.conserved(1.4 * (1 + 0.05 * np.sin(a * X + b * Y)), 0.4 + 0.05 * np.cos(b * X), 0.2,
                                   1.0 + 0.05 * np.cos(a * Y)))
         return I.Instance(pts, st, name="ring"), 1
+    if name in ("lbox", "lcurv"):
+        # one L-shaped corner patch (60 x 52 grid, points i < 24, j < 20
+        # missing), as a box or on a grid rotated by 90 degrees, walls around
+        n1, n2, m1, m2 = 60, 52, 24, 20
+        if name == "lbox":
+            p = I.Patch(n1, n2, (I.BC_WALL,) * 4, box=(0.1, 1.3, -0.2, 0.82), lcut=(m1, m2), kind="C1")
+        else:
+            Q1, Q2 = np.meshgrid(np.arange(n1) / (n1 - 1), np.arange(n2) / (n2 - 1))
+            p = I.Patch(n1, n2, (I.BC_WALL,) * 4, x=0.9 - 1.02 * Q2, y=-0.3 + 1.2 * Q1, lcut=(m1, m2), kind="C1")
+        rng = np.random.default_rng(13)
+        return I.Instance([p], [I.random_state(p, rng)], name=name), 1
+    if name == "ffs":
+        # forward-facing step at Mach 3, 32 patches of uneven resolution with
+        # a C1 (L-shaped) and a C2 corner patch (coarse version of the
+        # 64-patch, ~1M-point layout)
+        return I.ffs_instance(h0=0.005, length=1.4), 1
     raise KeyError(name)
+
+
+def active_only(arrs, inst):
+    """Zero the points outside L-shaped patches (never written by the library)."""
+    out = []
+    for a, p in zip(arrs, inst.patches):
+        a = np.array(a, dtype=np.float64, copy=True)
+        a[..., ~p.active()] = 0.0
+        out.append(a)
+    return out
 
 
 def random_fields(inst, seed):

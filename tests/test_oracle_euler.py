@@ -352,3 +352,17 @@ def test_l_patch_inner_walls():
         nb = n1 / np.linalg.norm(n1) + n2 / np.linalg.norm(n2)
         assert abs(e[1:3, m2, m1] @ nb) < 1e-12 * np.abs(e[1:3, m2, m1]).max()
         assert np.abs(e[1:3, m2, m1]).max() > 0.1                  # not a stagnation point
+
+
+def test_filter_state_keeps_uniform_and_smooth_states():
+    p = I.Patch(48, 40, (I.BC_WALL,) * 4, box=(0.0, 1.0, 0.0, 0.8))
+    g = euler.PatchGeom(p, 5, 25, 1)
+    e = I.conserved(np.full((40, 48), 1.3), 0.4, -0.2, 0.9)
+    assert np.abs(euler.filter_state(e, g, G) - e).max() < 1e-8 * np.abs(e).max()   # FC-Gram fit residual
+    s = I.random_state(p, np.random.default_rng(3))
+    assert np.abs(euler.filter_state(s, g, G) - s).max() < 1e-8
+    lp = _l_patch()
+    gl = euler.PatchGeom(lp, 5, 25, 1)
+    sl = I.random_state(lp, np.random.default_rng(4))
+    fl = euler.filter_state(sl, gl, G)
+    assert np.abs(fl - sl).max() < 1e-8

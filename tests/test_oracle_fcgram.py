@@ -126,3 +126,26 @@ def test_stored_tables_match_fresh_fits():
         stored, _ = fcgram.continuation_tables(5, C)
         fresh, _ = fcgram.continuation_tables(5, C, use_store=False)
         assert np.array_equal(stored, fresh)
+
+
+def test_filter_factors_on_single_modes():
+    # sigma(k) = exp(-16 ln 10 (|k| / (n/2))^36) multiplies mode k and -k alike
+    n = 64
+    j = np.arange(n)
+    for k0 in (0, 3, 16, 28, 31, 32):
+        y = np.cos(2 * np.pi * k0 * j / n + (0.3 if k0 not in (0, 32) else 0.0))
+        sig = np.exp(-16 * np.log(10) * (k0 / 32) ** 36)
+        assert np.allclose(fcgram.filter_periodic(y), sig * y, atol=1e-14)
+    assert fcgram.filter_factors(n)[32] < 1.01e-16          # Nyquist: exp(-alpha) = 1e-16
+    assert abs(fcgram.filter_factors(n)[16] - 1.0) < 1e-9   # half the band is untouched
+
+
+def test_fc_filter_keeps_smooth_data_and_damps_grid_noise():
+    N = 101
+    x = np.linspace(0.0, 1.0, N)
+    f = np.exp(x) * np.sin(3 * x + 0.2)
+    g = fcgram.fc_filter(f, 5, 25)
+    assert np.abs(g - f).max() < 1e-9
+    noise = 1e-2 * (-1.0) ** np.arange(N)
+    r = fcgram.fc_filter(f + noise, 5, 25) - f
+    assert np.abs(r[10:-10]).max() < 0.2 * np.abs(noise).max()
