@@ -264,7 +264,7 @@ def run_ours(args):
         ctx.classify(e, tau, None, stream)
         ctx.av_assemble(e, tau, mu, stream)
         ctx.time_step(e, dtd, mu, stream)
-        launches["n"] += 3 + 7 + 3   # proxy, MLP, tau gather; 6 viscosity kernels + exchange; dt init/min/final
+        launches["n"] += 3 + 6 + 3   # proxy, MLP, tau gather; 5 viscosity kernels + exchange; dt init/min/final
         for s in range(4):
             es = e if s == 0 else S
             out = e if s == 3 else S
@@ -287,6 +287,8 @@ def run_ours(args):
     time.sleep(0.3)
     step_ms, stage_ms = [], []
     launches["n"] = 0
+    # NVTX range of the timed steps (lets a profiler capture exactly these launches)
+    torch.cuda.nvtx.range_push("fcs_timed")
     with torch.cuda.stream(stream):
         for _ in range(args.steps):
             flush.fill_(1.0)
@@ -299,6 +301,7 @@ def run_ours(args):
             stream.synchronize()
             step_ms.append(t0.elapsed_time(t1))
             stage_ms += [a.elapsed_time(b) for a, b in ev]
+    torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     clocks = clk.stop()
     rc, flags = ctx.status()

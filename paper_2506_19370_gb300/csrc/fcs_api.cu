@@ -390,8 +390,8 @@ int av_impl(fcs_ctx* c, const void* e, const int8_t* tau, void* mu, cudaStream_t
   T* a0 = static_cast<T*>(c->av0);
   T* a1 = static_cast<T*>(c->av1);
   T* m = static_cast<T*>(mu);
-  k_av_speed<T><<<g, 256, 0, s>>>(c->dev, static_cast<const T*>(e), a0, 0);
-  k_av_prelim<T><<<g, 256, 0, s>>>(c->dev, a0, reinterpret_cast<const signed char*>(tau), T(c->opt.c_mu), a1);
+  k_av_prelim<T><<<g, 256, 0, s>>>(c->dev, static_cast<const T*>(e), reinterpret_cast<const signed char*>(tau),
+                                   T(c->opt.c_mu), a1);
   k_av_boxmax<T><<<g, 256, 0, s>>>(c->dev, a1, a0, r, 0);
   k_av_boxmax<T><<<g, 256, 0, s>>>(c->dev, a0, a1, r, 1);
   k_av_bump<T><<<g, 256, 0, s>>>(c->dev, a1, a0, c->bump, r, 0);

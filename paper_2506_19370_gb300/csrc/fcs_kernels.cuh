@@ -136,8 +136,9 @@ __global__ void k_dt(CtxDev c, const T* __restrict__ e, const T* __restrict__ mu
     const T* es = e + inst * c.sstride + P.soff + x.lq;
     const T rho = es[0], mx = es[np], my = es[2 * np], En = es[3 * np];
     const T pr = pressure<T>(rho, mx, my, En, gm1);
-    const T u = mx / rho, v = my / rho;
-    const T cs = sqrt(gam * pr / rho);
+    const T ir = T(1) / rho;
+    const T u = mx * ir, v = my * ir;
+    const T cs = sqrt(gam * pr * ir);
     T x_q1, x_q2, y_q1, y_q2, J, h1, h2;
     if (P.cart) {
       x_q1 = T(P.Lx); y_q2 = T(P.Ly); x_q2 = T(0); y_q1 = T(0);
@@ -150,14 +151,18 @@ __global__ void k_dt(CtxDev c, const T* __restrict__ e, const T* __restrict__ mu
       J = Mt[4 * c.qstride + q];
       h1 = T(P.hx); h2 = T(P.hy);
     }
-    const T U1 = (y_q2 * u - x_q2 * v) / J, U2 = (-y_q1 * u + x_q1 * v) / J;
-    const T n1 = sqrt(y_q2 * y_q2 + x_q2 * x_q2) / fabs(J), n2 = sqrt(y_q1 * y_q1 + x_q1 * x_q1) / fabs(J);
-    T r = cfl * fmin(h1 / (fabs(U1) + cs * n1), h2 / (fabs(U2) + cs * n2));
-    if (mu) {  // 1/dt = 1/dt_a + mu (1/s1^2 + 1/s2^2) / cfl_mu
+    // 1/dt_a = max over k of (|U_k| + c |grad q_k|) / (cfl h_k), U_k = grad q_k . u;
+    // 1/dt = 1/dt_a + mu (1/s1^2 + 1/s2^2) / cfl_mu
+    const T iJ = T(1) / fabs(J), sJ = J < T(0) ? -iJ : iJ;
+    const T U1 = (y_q2 * u - x_q2 * v) * sJ, U2 = (-y_q1 * u + x_q1 * v) * sJ;
+    const T n1 = sqrt(y_q2 * y_q2 + x_q2 * x_q2) * iJ, n2 = sqrt(y_q1 * y_q1 + x_q1 * x_q1) * iJ;
+    T inv = fmax((fabs(U1) + cs * n1) / h1, (fabs(U2) + cs * n2) / h2) / cfl;
+    if (mu) {
       const T m = mu[inst * c.qstride + q];
-      const T s1 = h1 * sqrt(x_q1 * x_q1 + y_q1 * y_q1), s2 = h2 * sqrt(x_q2 * x_q2 + y_q2 * y_q2);
-      r = T(1) / (T(1) / r + m * (T(1) / (s1 * s1) + T(1) / (s2 * s2)) / cfl_mu);
+      const T g1 = h1 * h1 * (x_q1 * x_q1 + y_q1 * y_q1), g2 = h2 * h2 * (x_q2 * x_q2 + y_q2 * y_q2);
+      inv += m * (g1 + g2) / (g1 * g2 * cfl_mu);
     }
+    T r = T(1) / inv;
     if (!(r > T(0))) r = T(0);
     r_min = r;
   }
@@ -557,6 +562,14 @@ __global__ void k_indicator(CtxDev c, const T* __restrict__ e, signed char* tau_
 }
 
 // ============================================================ viscosity
+// |u| + c at point k of a patch whose state starts at es (np points per field)
+template <typename T>
+__device__ __forceinline__ T wave_speed(const T* es, long long np, long long k, T gam, T gm1) {
+  const T rho = es[k], mx = es[np + k], my = es[2 * np + k], En = es[3 * np + k];
+  const T p = pressure<T>(rho, mx, my, En, gm1);
+  return sqrt(mx * mx + my * my) / rho + sqrt(gam * p / rho);
+}
+
 // (a) wave speed |u| + c per point
 // mode 0: S = |u| + c;  mode 1: S = Phi = |u| sqrt(rho/(gamma p)) (classifier proxy)
 template <typename T>
@@ -571,13 +584,14 @@ __global__ void k_av_speed(CtxDev c, const T* __restrict__ e, T* S, int mode) {
   const T rho = es[0], mx = es[np], my = es[2 * np], En = es[3 * np];
   const T p = pressure<T>(rho, mx, my, En, gm1);
   const long long t = x.inst * c.qstride + P.qoff + x.lq;
-  if (mode == 0) S[t] = sqrt(mx * mx + my * my) / rho + sqrt(gam * p / rho);
+  if (mode == 0) S[t] = wave_speed<T>(es, np, 0, gam, gm1);
   else S[t] = sqrt(mx * mx + my * my) / rho * sqrt(rho / (gam * p));
 }
 
-// (b) preliminary viscosity: c_mu h_max max_{3x3}(S) w(tau), zero on fringes
+// (b) preliminary viscosity: c_mu h_max max_{3x3}(|u| + c) w(tau), zero on
+// fringes; the wave speeds are evaluated only where w(tau) > 0
 template <typename T>
-__global__ void k_av_prelim(CtxDev c, const T* __restrict__ S, const signed char* __restrict__ tau, T cmu, T* M) {
+__global__ void k_av_prelim(CtxDev c, const T* __restrict__ e, const signed char* __restrict__ tau, T cmu, T* M) {
   const long long per = c.qstride;
   const PatchDev* Pp;
   const PtIdx x = pt_index(c, &Pp);
@@ -591,14 +605,16 @@ __global__ void k_av_prelim(CtxDev c, const T* __restrict__ S, const signed char
     if (c.fringe[q]) w = T(0);
     T m = 0;
     if (w != T(0)) {
-      const T* Sp = S + inst * per + P.qoff;
+      const T* es = e + inst * c.sstride + P.soff;
+      const long long np = (long long)P.n1 * P.n2;
+      const T gam = T(c.gamma), gm1 = T(c.gamma - 1.0);
       for (int dj = -1; dj <= 1; ++dj) {
         const int jj = j + dj;
         if (jj < 0 || jj >= P.n2) continue;
         for (int di = -1; di <= 1; ++di) {
           const int ii = i + di;
           if (ii < 0 || ii >= P.n1 || !pt_active(P, ii, jj)) continue;
-          m = fmax(m, Sp[(long long)jj * P.n1 + ii]);
+          m = fmax(m, wave_speed<T>(es, np, (long long)jj * P.n1 + ii, gam, gm1));
         }
       }
     }
