@@ -69,6 +69,8 @@ struct fcs_ctx {
   void* G2 = nullptr;
   int2* tiles = nullptr;
   int2* pblk = nullptr;  // point blocks of the pointwise kernels
+  int4* btiles = nullptr;  // 32 x 32 output tiles of the viscosity blend (patch, i0, j0)
+  int nbtiles = 0;
   int4* fringe_ent = nullptr;     // copies: (dst patch, dst point, src patch, src point)
   int4* interp_ent = nullptr;     // interpolations: (dst patch, dst point, src patch, first block node)
   double* interp_w64 = nullptr;   // 36 weights per interpolation
@@ -238,6 +240,12 @@ size_t deriv_smem(const fcs_ctx* c, int n1) { return kWarps * deriv_warp_bytes<T
 template <typename T>
 size_t ypass_smem(const fcs_ctx* c, int tw, int n1) { return ypass_bytes<T>(c->n2max, tw, c->nfmax, n1, kYWarps); }
 
+constexpr int kBlendMaxR = 8;  // blend radius handled by the fused tile kernel
+size_t blend_smem(int r, size_t tsize) {
+  const size_t w = kBlendTile + 4 * r;
+  return 2 * w * w * tsize;
+}
+
 int grid_for(long long work, int per_block) {
   long long g = (work + per_block - 1) / per_block;
   if (g < 1) g = 1;
@@ -262,6 +270,8 @@ int grid_for(long long work, int per_block) {
 
 template <typename T>
 int set_smem_attrs(const fcs_ctx* c) {
+  FCS_CUDA(cudaFuncSetAttribute(k_av_blend<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)blend_smem(kBlendMaxR, sizeof(T))));
   for (int n1 : c->n1_dir[0]) {
     FCS_N1_SWITCH(n1, FCS_CUDA((prep_xpass<T, K>(xpass_smem<T>(c, n1)))); break)
   }
@@ -392,10 +402,16 @@ int av_impl(fcs_ctx* c, const void* e, const int8_t* tau, void* mu, cudaStream_t
   T* m = static_cast<T*>(mu);
   k_av_prelim<T><<<g, 256, 0, s>>>(c->dev, static_cast<const T*>(e), reinterpret_cast<const signed char*>(tau),
                                    T(c->opt.c_mu), a1);
-  k_av_boxmax<T><<<g, 256, 0, s>>>(c->dev, a1, a0, r, 0);
-  k_av_boxmax<T><<<g, 256, 0, s>>>(c->dev, a0, a1, r, 1);
-  k_av_bump<T><<<g, 256, 0, s>>>(c->dev, a1, a0, c->bump, r, 0);
-  k_av_bump<T><<<g, 256, 0, s>>>(c->dev, a0, m, c->bump, r, 1);
+  if (r <= kBlendMaxR) {
+    const size_t smem = blend_smem(r, sizeof(T));
+    k_av_blend<T><<<grid_for((long long)c->opt.instances * c->nbtiles, 1), 256, smem, s>>>(c->dev, c->btiles,
+                                                                                          c->nbtiles, a1, m, c->bump, r);
+  } else {  // wide blends: the separable kernels
+    k_av_boxmax<T><<<g, 256, 0, s>>>(c->dev, a1, a0, r, 0);
+    k_av_boxmax<T><<<g, 256, 0, s>>>(c->dev, a0, a1, r, 1);
+    k_av_bump<T><<<g, 256, 0, s>>>(c->dev, a1, a0, c->bump, r, 0);
+    k_av_bump<T><<<g, 256, 0, s>>>(c->dev, a0, m, c->bump, r, 1);
+  }
   FCS_CUDA(cudaGetLastError());
   return exchange_impl(c, mu, 1, 1, s);
 }
@@ -731,6 +747,15 @@ int fc_setup(fcs_ctx** out, int d, int C, const fcs_patch_desc* pd, int npatch, 
   std::vector<int2> pblk;
   for (int p = 0; p < npatch; ++p)
     for (int s0 = 0; s0 < pd[p].n1 * pd[p].n2; s0 += 256) pblk.push_back(make_int2(p, s0));
+  std::vector<int4> btiles;  // blend tiles holding at least one point of the patch
+  for (int p = 0; p < npatch; ++p)
+    for (int j0 = 0; j0 < pd[p].n2; j0 += kBlendTile)
+      for (int i0 = 0; i0 < pd[p].n1; i0 += kBlendTile) {
+        const PatchDev& P = c->patches[p];
+        if (i0 + kBlendTile <= P.m1 && j0 + kBlendTile <= P.m2) continue;  // inside the missing quadrant
+        btiles.push_back(make_int4(p, i0, j0, 0));
+      }
+  c->nbtiles = (int)btiles.size();
   c->sstride = soff;
   c->qstride = qoff;
   c->nwin = wins.size();
@@ -868,6 +893,7 @@ int fc_setup(fcs_ctx** out, int d, int C, const fcs_patch_desc* pd, int npatch, 
       (rc = upload(c, &c->fpairs[1], fp[1].data(), fp[1].size() * sizeof(int4))) ||
       (rc = upload(c, &c->tiles, tiles.data(), tiles.size() * sizeof(int2))) ||
       (rc = upload(c, &c->pblk, pblk.data(), pblk.size() * sizeof(int2))) ||
+      (rc = upload(c, &c->btiles, btiles.data(), btiles.size() * sizeof(int4))) ||
       (rc = upload(c, &dwin, wins.data(), wins.size() * sizeof(int4))) ||
       (rc = upload(c, &dfr, fringe.data(), fringe.size())) ||
       (rc = upload(c, &c->fringe_ent, ent.data(), ent.size() * sizeof(int4))) ||

@@ -668,6 +668,95 @@ __global__ void k_av_bump(CtxDev c, const T* __restrict__ in, T* out, const doub
   }
 }
 
+// (c+d) box maximum then bump average in one kernel, on 32 x 32 output tiles of
+// a patch (tiles: patch, i0, j0) staged with a halo of 2r points in shared
+// memory: max along i, max along j, bump along i, bump along j, each over the
+// points of the patch only and in the same order as the separable kernels
+// above, so the result is identical to theirs.
+constexpr int kBlendTile = 32;
+template <typename T>
+__global__ void __launch_bounds__(256) k_av_blend(CtxDev c, const int4* __restrict__ tiles, int ntiles,
+                                                  const T* __restrict__ mu0, T* out, const double* __restrict__ bw,
+                                                  int r) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int H = 2 * r, W = kBlendTile + 2 * H, Hh = kBlendTile + 2 * H;
+  T* A = reinterpret_cast<T*>(smem_raw);
+  T* B = A + W * Hh;
+  const long long total = (long long)c.instances * ntiles;
+  for (long long wk = blockIdx.x; wk < total; wk += gridDim.x) {
+    const int inst = (int)(wk / ntiles);
+    const int4 tl = tiles[wk % ntiles];
+    const PatchDev& P = c.patches[tl.x];
+    const int ib = tl.y - H, jb = tl.z - H;  // patch index of smem (0, 0)
+    auto valid = [&](int gi, int gj) { return gi >= 0 && gi < P.n1 && gj >= 0 && gj < P.n2 && pt_active(P, gi, gj); };
+    const T* src = mu0 + inst * c.qstride + P.qoff;
+    int nz = 0;
+    for (int t = threadIdx.x; t < W * Hh; t += blockDim.x) {
+      const int x = t % W, y = t / W, gi = ib + x, gj = jb + y;
+      const T v = valid(gi, gj) ? src[(long long)gj * P.n1 + gi] : T(0);
+      A[t] = v;
+      nz |= v != T(0);
+    }
+    T* dst = out + inst * c.qstride + P.qoff;
+    if (!__syncthreads_or(nz)) {
+      // the viscosity is localized: a tile whose halo holds no viscosity stays zero
+      for (int t = threadIdx.x; t < kBlendTile * kBlendTile; t += blockDim.x) {
+        const int gi = tl.y + t % kBlendTile, gj = tl.z + t / kBlendTile;
+        if (valid(gi, gj)) dst[(long long)gj * P.n1 + gi] = T(0);
+      }
+      continue;   // (uniform over the block: no barrier is skipped by part of it)
+    }
+    // maximum along i on x in [r, W - r), all rows
+    for (int t = threadIdx.x; t < (W - 2 * r) * Hh; t += blockDim.x) {
+      const int x = r + t % (W - 2 * r), y = t / (W - 2 * r), gi = ib + x, gj = jb + y;
+      if (!valid(gi, gj)) continue;
+      T m = A[y * W + x];
+      for (int k = -r; k <= r; ++k)
+        if (valid(gi + k, gj)) m = fmax(m, A[y * W + x + k]);
+      B[y * W + x] = m;
+    }
+    __syncthreads();
+    // maximum along j on x in [r, W - r), y in [r, Hh - r)
+    for (int t = threadIdx.x; t < (W - 2 * r) * (Hh - 2 * r); t += blockDim.x) {
+      const int x = r + t % (W - 2 * r), y = r + t / (W - 2 * r), gi = ib + x, gj = jb + y;
+      if (!valid(gi, gj)) continue;
+      T m = B[y * W + x];
+      for (int k = -r; k <= r; ++k)
+        if (valid(gi, gj + k)) m = fmax(m, B[(y + k) * W + x]);
+      A[y * W + x] = m;
+    }
+    __syncthreads();
+    // bump average along i on x in [H, W - H), y in [r, Hh - r)
+    for (int t = threadIdx.x; t < (W - 2 * H) * (Hh - 2 * r); t += blockDim.x) {
+      const int x = H + t % (W - 2 * H), y = r + t / (W - 2 * H), gi = ib + x, gj = jb + y;
+      if (!valid(gi, gj)) continue;
+      T num = 0, den = 0;
+      for (int k = -r; k <= r; ++k) {
+        if (!valid(gi + k, gj)) continue;
+        const T b = T(bw[k + r]);
+        num += b * A[y * W + x + k];
+        den += b;
+      }
+      B[y * W + x] = num / den;
+    }
+    __syncthreads();
+    // bump average along j on the output tile
+    for (int t = threadIdx.x; t < kBlendTile * kBlendTile; t += blockDim.x) {
+      const int x = H + t % kBlendTile, y = H + t / kBlendTile, gi = ib + x, gj = jb + y;
+      if (!valid(gi, gj)) continue;
+      T num = 0, den = 0;
+      for (int k = -r; k <= r; ++k) {
+        if (!valid(gi, gj + k)) continue;
+        const T b = T(bw[k + r]);
+        num += b * B[(y + k) * W + x];
+        den += b;
+      }
+      dst[(long long)gj * P.n1 + gi] = num / den;
+    }
+    __syncthreads();
+  }
+}
+
 // ============================================================ training
 constexpr int kActs = 148;  // per sample: x 16, h1 32, h2 32, dz1 32, dz2 32, dz3 4
 

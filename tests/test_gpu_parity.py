@@ -448,8 +448,11 @@ def test_indicator(dtype):
 
 
 @pytest.mark.parametrize("dtype", DTYPES)
-def test_artificial_viscosity(dtype, trained_params):
-    inst, pol, ctx = ctx_for("sod", dtype)
+@pytest.mark.parametrize("radius", [4, 10])
+def test_artificial_viscosity(dtype, radius, trained_params):
+    # radius 4: fused tile kernel of the blend; radius 10: the separable kernels
+    inst, pol = layout("sod")
+    ctx = fcsdnn.Context(inst, d=5, C=25, dtype=dtype, c_policy=pol, av_radius=radius)
     st = _shock_state(inst)
     npd = np.float32 if dtype == fcsdnn.F32 else np.float64
     st = [s.astype(npd) for s in st]
@@ -463,9 +466,9 @@ def test_artificial_viscosity(dtype, trained_params):
     ctx.av_assemble(e, t, mu)
     torch.cuda.synchronize()
     solver = euler.Solver(inst, c_policy=pol)
-    ref = sdnn.av_assemble(solver, [s.astype(np.float64) for s in st], taus)
+    ref = sdnn.av_assemble(solver, [s.astype(np.float64) for s in st], taus, radius=radius)
     err = rel_err(ctx.unpack_scalar(mu), ref)
-    print(f"viscosity dtype={dtype} err={err:.3e}")
+    print(f"viscosity radius={radius} dtype={dtype} err={err:.3e}")
     assert err < (1e-13 if dtype == fcsdnn.F64 else 1e-6)
 
 
