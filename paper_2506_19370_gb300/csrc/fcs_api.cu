@@ -240,7 +240,6 @@ size_t deriv_smem(const fcs_ctx* c, int n1) { return kWarps * deriv_warp_bytes<T
 template <typename T>
 size_t ypass_smem(const fcs_ctx* c, int tw, int n1) { return ypass_bytes<T>(c->n2max, tw, c->nfmax, n1, kYWarps); }
 
-constexpr int kBlendMaxR = 8;  // blend radius handled by the fused tile kernel
 size_t blend_smem(int r, size_t tsize) {
   const size_t w = kBlendTile + 4 * r;
   return 2 * w * w * tsize;
@@ -401,7 +400,7 @@ int av_impl(fcs_ctx* c, const void* e, const int8_t* tau, void* mu, cudaStream_t
   T* a1 = static_cast<T*>(c->av1);
   T* m = static_cast<T*>(mu);
   k_av_prelim<T><<<g, 256, 0, s>>>(c->dev, static_cast<const T*>(e), reinterpret_cast<const signed char*>(tau),
-                                   T(c->opt.c_mu), a1);
+                                   T(c->opt.c_mu), T(c->opt.gamma), T(c->opt.gamma - 1.0), a1);
   if (r <= kBlendMaxR) {
     const size_t smem = blend_smem(r, sizeof(T));
     k_av_blend<T><<<grid_for((long long)c->opt.instances * c->nbtiles, 1), 256, smem, s>>>(c->dev, c->btiles,
@@ -663,6 +662,12 @@ int fc_setup(fcs_ctx** out, int d, int C, const fcs_patch_desc* pd, int npatch, 
       if (s.back() + 16 < N) s.push_back(N - 16);
       return s;
     };
+    P.cd[PC_LX] = P.Lx;
+    P.cd[PC_LY] = P.Ly;
+    P.cd[PC_H1] = 1.0 / (q.n1 - 1);
+    P.cd[PC_H2] = 1.0 / (q.n2 - 1);
+    P.cd[PC_HMAX] = P.hmax;
+    for (int k = 0; k < 5; ++k) P.cf[k] = (float)P.cd[k];
     // windows tile each line segment (rows j < m2 and columns i < m1 of an
     // L-shaped patch are short); the list is x-lines (j outer), then y-lines
     const std::vector<int> sx = starts(q.n1), sy = starts(q.n2);
@@ -1074,12 +1079,13 @@ int fcs_time_step(fcs_ctx* c, const void* e, const void* mu, double* dt_dev, voi
   const int I = c->opt.instances;
   k_dt_init<<<(I + 127) / 128, 128, 0, s>>>(c->dtbest, I);
   const dim3 g(c->dev.npblk, I);
+  const double gam = c->opt.gamma;
   if (c->opt.dtype == FCS_F64)
     k_dt<double><<<g, 256, 0, s>>>(c->dev, static_cast<const double*>(e), static_cast<const double*>(mu), c->opt.cfl,
-                                   kCflMu, c->dtbest);
+                                   kCflMu, gam, gam - 1.0, c->dtbest);
   else
-    k_dt<float><<<g, 256, 0, s>>>(c->dev, static_cast<const float*>(e), static_cast<const float*>(mu), c->opt.cfl,
-                                  kCflMu, c->dtbest);
+    k_dt<float><<<g, 256, 0, s>>>(c->dev, static_cast<const float*>(e), static_cast<const float*>(mu),
+                                  (float)c->opt.cfl, (float)kCflMu, (float)gam, (float)(gam - 1.0), c->dtbest);
   k_dt_final<<<(I + 127) / 128, 128, 0, s>>>(c->dtbest, dt_dev, I);
   return cuda_err(cudaGetLastError());
 }
@@ -1133,11 +1139,13 @@ int sdnn_classify(fcs_ctx* c, const void* e, int8_t* tau, void* logits, void* st
   const long long nw = (long long)c->opt.instances * c->nwin;
   const dim3 gp(c->dev.npblk, c->opt.instances);
   if (c->opt.dtype == FCS_F64) {
-    k_av_speed<double><<<gp, 256, 0, s>>>(c->dev, static_cast<const double*>(e), static_cast<double*>(c->av0), 1);
+    k_av_speed<double><<<gp, 256, 0, s>>>(c->dev, static_cast<const double*>(e), static_cast<double*>(c->av0), 1, c->opt.gamma,
+                                          c->opt.gamma - 1.0);
     k_mlp64<double><<<grid_for(nw, 128), 128, 0, s>>>(c->dev, static_cast<const double*>(c->av0), c->W64, c->tau_w,
                                                       static_cast<double*>(logits));
   } else {
-    k_av_speed<float><<<gp, 256, 0, s>>>(c->dev, static_cast<const float*>(e), static_cast<float*>(c->av0), 1);
+    k_av_speed<float><<<gp, 256, 0, s>>>(c->dev, static_cast<const float*>(e), static_cast<float*>(c->av0), 1, (float)c->opt.gamma,
+                                         (float)(c->opt.gamma - 1.0));
     const long long groups = (nw + 15) / 16;
     k_mlp_bf16<<<grid_for(groups, 4), 128, 0, s>>>(c->dev, static_cast<const float*>(c->av0), c->Wb, c->bias,
                                                     c->tau_w, static_cast<float*>(logits));
@@ -1153,11 +1161,13 @@ int sdnn_indicator(fcs_ctx* c, const void* e, int8_t* tau, void* s_out, void* st
   const long long nw = (long long)c->opt.instances * c->nwin;
   const dim3 gp(c->dev.npblk, c->opt.instances);
   if (c->opt.dtype == FCS_F64) {
-    k_av_speed<double><<<gp, 256, 0, s>>>(c->dev, static_cast<const double*>(e), static_cast<double*>(c->av0), 1);
+    k_av_speed<double><<<gp, 256, 0, s>>>(c->dev, static_cast<const double*>(e), static_cast<double*>(c->av0), 1, c->opt.gamma,
+                                          c->opt.gamma - 1.0);
     k_indicator<double><<<grid_for(nw, 128), 128, 0, s>>>(c->dev, static_cast<const double*>(c->av0), c->tau_w,
                                                           static_cast<double*>(s_out));
   } else {
-    k_av_speed<float><<<gp, 256, 0, s>>>(c->dev, static_cast<const float*>(e), static_cast<float*>(c->av0), 1);
+    k_av_speed<float><<<gp, 256, 0, s>>>(c->dev, static_cast<const float*>(e), static_cast<float*>(c->av0), 1, (float)c->opt.gamma,
+                                         (float)(c->opt.gamma - 1.0));
     k_indicator<float><<<grid_for(nw, 128), 128, 0, s>>>(c->dev, static_cast<const float*>(c->av0), c->tau_w,
                                                          static_cast<float*>(s_out));
   }
@@ -1240,8 +1250,9 @@ int fcs_filter(fcs_ctx* c, void* e, void* stream) {
   cudaStream_t s = as_stream(stream);
   const dim3 g(c->dev.npblk, c->opt.instances);
   const bool f64 = c->opt.dtype == FCS_F64;
-  if (f64) k_filter_prep<double><<<g, 256, 0, s>>>(c->dev, static_cast<const double*>(e), static_cast<double*>(c->R));
-  else k_filter_prep<float><<<g, 256, 0, s>>>(c->dev, static_cast<const float*>(e), static_cast<float*>(c->R));
+  const double gm1 = c->opt.gamma - 1.0;
+  if (f64) k_filter_prep<double><<<g, 256, 0, s>>>(c->dev, static_cast<const double*>(e), static_cast<double*>(c->R), gm1);
+  else k_filter_prep<float><<<g, 256, 0, s>>>(c->dev, static_cast<const float*>(e), static_cast<float*>(c->R), (float)gm1);
   FCS_CUDA(cudaGetLastError());
   // rows R -> S, columns S -> R (order 0 of the line transform: filter)
   for (int dir = 0; dir < 2; ++dir) {
@@ -1262,8 +1273,8 @@ int fcs_filter(fcs_ctx* c, void* e, void* stream) {
       }
     }
   }
-  if (f64) k_filter_done<double><<<g, 256, 0, s>>>(c->dev, static_cast<const double*>(c->R), static_cast<double*>(e));
-  else k_filter_done<float><<<g, 256, 0, s>>>(c->dev, static_cast<const float*>(c->R), static_cast<float*>(e));
+  if (f64) k_filter_done<double><<<g, 256, 0, s>>>(c->dev, static_cast<const double*>(c->R), static_cast<double*>(e), gm1);
+  else k_filter_done<float><<<g, 256, 0, s>>>(c->dev, static_cast<const float*>(c->R), static_cast<float*>(e), (float)gm1);
   FCS_CUDA(cudaGetLastError());
   return exchange_impl(c, e, 4, 0, s);
 }

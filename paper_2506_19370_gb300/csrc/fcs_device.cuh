@@ -24,7 +24,19 @@ struct PatchDev {
   double hx, hy;        // derivative spacing along i and j (physical if Cartesian, parameter otherwise)
   double hmax;          // largest physical spacing (viscosity scale)
   double Lx, Ly;        // Cartesian box lengths (metrics x_q1, y_q2)
+  // Lx, Ly, 1/(n1 - 1), 1/(n2 - 1), hmax in both types (pointwise kernels read
+  // them per point: FP64 conversions run at 1/64 of the FP32 rate on this part)
+  double cd[5];
+  float cf[5];
 };
+
+enum { PC_LX = 0, PC_LY = 1, PC_H1 = 2, PC_H2 = 3, PC_HMAX = 4 };
+template <typename T>
+__host__ __device__ __forceinline__ T pconst(const PatchDev& P, int k);
+template <>
+__host__ __device__ __forceinline__ double pconst<double>(const PatchDev& P, int k) { return P.cd[k]; }
+template <>
+__host__ __device__ __forceinline__ float pconst<float>(const PatchDev& P, int k) { return P.cf[k]; }
 
 struct PlanDev {
   int N, C, n, nst;

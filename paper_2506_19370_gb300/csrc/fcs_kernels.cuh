@@ -78,7 +78,7 @@ __global__ void k_interp(CtxDev c, const int4* __restrict__ ent, const T* __rest
 // on W = (rho, rho u, rho v, theta), theta = p / rho; then E is rebuilt from
 // theta and the boundary conditions are imposed again.
 template <typename T>
-__global__ void k_filter_prep(CtxDev c, const T* __restrict__ e, T* W) {
+__global__ void k_filter_prep(CtxDev c, const T* __restrict__ e, T* W, T gm1) {
   const PatchDev* Pp;
   const PtIdx x = pt_index(c, &Pp);
   const PatchDev& P = *Pp;
@@ -88,12 +88,12 @@ __global__ void k_filter_prep(CtxDev c, const T* __restrict__ e, T* W) {
   W[o] = rho;
   W[o + np] = mx;
   W[o + 2 * np] = my;
-  W[o + 3 * np] = pressure<T>(rho, mx, my, En, T(c.gamma - 1.0)) / rho;
+  W[o + 3 * np] = pressure<T>(rho, mx, my, En, gm1) / rho;
 }
 
 // End of the filter: E from the filtered temperature, boundary conditions.
 template <typename T>
-__global__ void k_filter_done(CtxDev c, const T* __restrict__ W, T* e) {
+__global__ void k_filter_done(CtxDev c, const T* __restrict__ W, T* e, T gm1) {
   const PatchDev* Pp;
   const PtIdx x = pt_index(c, &Pp);
   const PatchDev& P = *Pp;
@@ -103,7 +103,7 @@ __global__ void k_filter_done(CtxDev c, const T* __restrict__ W, T* e) {
   v[0] = W[o];
   v[1] = W[o + np];
   v[2] = W[o + 2 * np];
-  v[3] = v[0] * W[o + 3 * np] / T(c.gamma - 1.0) + T(0.5) * (v[1] * v[1] + v[2] * v[2]) / v[0];
+  v[3] = v[0] * W[o + 3 * np] / gm1 + T(0.5) * (v[1] * v[1] + v[2] * v[2]) / v[0];
   apply_bc<T>(c, P, x.i, x.j, P.qoff + x.lq, v);
 #pragma unroll
   for (int f = 0; f < 4; ++f) e[o + f * np] = v[f];
@@ -121,10 +121,11 @@ __device__ __forceinline__ int find_patch(const CtxDev& c, long long q) {
 }
 
 // ============================================================ time step
+// (the constants arrive in the context's type: FP64 arithmetic and
+// conversions are slow in FP32 contexts)
 template <typename T>
-__global__ void k_dt(CtxDev c, const T* __restrict__ e, const T* __restrict__ mu, double cfl_d, double cfl_mu_d,
+__global__ void k_dt(CtxDev c, const T* __restrict__ e, const T* __restrict__ mu, T cfl, T cfl_mu, T gam, T gm1,
                      unsigned long long* best) {
-  const T cfl = T(cfl_d), cfl_mu = T(cfl_mu_d), gam = T(c.gamma), gm1 = T(c.gamma - 1.0);
   const PatchDev* Pp;
   const PtIdx x = pt_index(c, &Pp);
   const PatchDev& P = *Pp;
@@ -140,16 +141,16 @@ __global__ void k_dt(CtxDev c, const T* __restrict__ e, const T* __restrict__ mu
     const T u = mx * ir, v = my * ir;
     const T cs = sqrt(gam * pr * ir);
     T x_q1, x_q2, y_q1, y_q2, J, h1, h2;
+    h1 = pconst<T>(P, PC_H1);
+    h2 = pconst<T>(P, PC_H2);
     if (P.cart) {
-      x_q1 = T(P.Lx); y_q2 = T(P.Ly); x_q2 = T(0); y_q1 = T(0);
+      x_q1 = pconst<T>(P, PC_LX); y_q2 = pconst<T>(P, PC_LY); x_q2 = T(0); y_q1 = T(0);
       J = x_q1 * y_q2;
-      h1 = T(1) / T(P.n1 - 1); h2 = T(1) / T(P.n2 - 1);
     } else {
       const T* Mt = metrics<T>(c);
       x_q1 = Mt[q]; x_q2 = Mt[c.qstride + q];
       y_q1 = Mt[2 * c.qstride + q]; y_q2 = Mt[3 * c.qstride + q];
       J = Mt[4 * c.qstride + q];
-      h1 = T(P.hx); h2 = T(P.hy);
     }
     // 1/dt_a = max over k of (|U_k| + c |grad q_k|) / (cfl h_k), U_k = grad q_k . u;
     // 1/dt = 1/dt_a + mu (1/s1^2 + 1/s2^2) / cfl_mu
@@ -166,16 +167,17 @@ __global__ void k_dt(CtxDev c, const T* __restrict__ e, const T* __restrict__ mu
     if (!(r > T(0))) r = T(0);
     r_min = r;
   }
-  // block minimum, then one atomic per block (min of positive doubles = min of their bit patterns)
-  double rd = (double)r_min;
+  // block minimum in T, then one atomic per block on the FP64 value (min of
+  // positive doubles = min of their bit patterns)
+  T rd = r_min;
   for (int o = 16; o > 0; o >>= 1) rd = fmin(rd, __shfl_xor_sync(0xffffffffu, rd, o));
-  __shared__ double wmin[32];
+  __shared__ T wmin[32];
   if ((threadIdx.x & 31) == 0) wmin[threadIdx.x >> 5] = rd;
   __syncthreads();
   if (threadIdx.x == 0) {
-    double m = wmin[0];
+    T m = wmin[0];
     for (int k = 1; k < (int)(blockDim.x >> 5); ++k) m = fmin(m, wmin[k]);
-    if (m < INFINITY) atomicMin(best + inst, (unsigned long long)__double_as_longlong(m));
+    if (m < T(INFINITY)) atomicMin(best + inst, (unsigned long long)__double_as_longlong((double)m));
   }
 }
 
@@ -573,8 +575,7 @@ __device__ __forceinline__ T wave_speed(const T* es, long long np, long long k, 
 // (a) wave speed |u| + c per point
 // mode 0: S = |u| + c;  mode 1: S = Phi = |u| sqrt(rho/(gamma p)) (classifier proxy)
 template <typename T>
-__global__ void k_av_speed(CtxDev c, const T* __restrict__ e, T* S, int mode) {
-  const T gm1 = T(c.gamma - 1.0), gam = T(c.gamma);
+__global__ void k_av_speed(CtxDev c, const T* __restrict__ e, T* S, int mode, T gam, T gm1) {
   const PatchDev* Pp;
   const PtIdx x = pt_index(c, &Pp);
   const PatchDev& P = *Pp;
@@ -591,7 +592,8 @@ __global__ void k_av_speed(CtxDev c, const T* __restrict__ e, T* S, int mode) {
 // (b) preliminary viscosity: c_mu h_max max_{3x3}(|u| + c) w(tau), zero on
 // fringes; the wave speeds are evaluated only where w(tau) > 0
 template <typename T>
-__global__ void k_av_prelim(CtxDev c, const T* __restrict__ e, const signed char* __restrict__ tau, T cmu, T* M) {
+__global__ void k_av_prelim(CtxDev c, const T* __restrict__ e, const signed char* __restrict__ tau, T cmu, T gam,
+                            T gm1, T* M) {
   const long long per = c.qstride;
   const PatchDev* Pp;
   const PtIdx x = pt_index(c, &Pp);
@@ -607,7 +609,6 @@ __global__ void k_av_prelim(CtxDev c, const T* __restrict__ e, const signed char
     if (w != T(0)) {
       const T* es = e + inst * c.sstride + P.soff;
       const long long np = (long long)P.n1 * P.n2;
-      const T gam = T(c.gamma), gm1 = T(c.gamma - 1.0);
       for (int dj = -1; dj <= 1; ++dj) {
         const int jj = j + dj;
         if (jj < 0 || jj >= P.n2) continue;
@@ -618,7 +619,7 @@ __global__ void k_av_prelim(CtxDev c, const T* __restrict__ e, const signed char
         }
       }
     }
-    M[t] = cmu * T(P.hmax) * m * w;
+    M[t] = w != T(0) ? cmu * pconst<T>(P, PC_HMAX) * m * w : T(0);
   }
 }
 
@@ -674,6 +675,7 @@ __global__ void k_av_bump(CtxDev c, const T* __restrict__ in, T* out, const doub
 // points of the patch only and in the same order as the separable kernels
 // above, so the result is identical to theirs.
 constexpr int kBlendTile = 32;
+constexpr int kBlendMaxR = 8;  // blend radius handled by the fused tile kernel
 template <typename T>
 __global__ void __launch_bounds__(256) k_av_blend(CtxDev c, const int4* __restrict__ tiles, int ntiles,
                                                   const T* __restrict__ mu0, T* out, const double* __restrict__ bw,
@@ -682,6 +684,9 @@ __global__ void __launch_bounds__(256) k_av_blend(CtxDev c, const int4* __restri
   const int H = 2 * r, W = kBlendTile + 2 * H, Hh = kBlendTile + 2 * H;
   T* A = reinterpret_cast<T*>(smem_raw);
   T* B = A + W * Hh;
+  __shared__ T bwt[2 * kBlendMaxR + 1];
+  for (int k = threadIdx.x; k <= 2 * r; k += blockDim.x) bwt[k] = T(bw[k]);
+  __syncthreads();
   const long long total = (long long)c.instances * ntiles;
   for (long long wk = blockIdx.x; wk < total; wk += gridDim.x) {
     const int inst = (int)(wk / ntiles);
@@ -733,7 +738,7 @@ __global__ void __launch_bounds__(256) k_av_blend(CtxDev c, const int4* __restri
       T num = 0, den = 0;
       for (int k = -r; k <= r; ++k) {
         if (!valid(gi + k, gj)) continue;
-        const T b = T(bw[k + r]);
+        const T b = bwt[k + r];
         num += b * A[y * W + x + k];
         den += b;
       }
@@ -747,7 +752,7 @@ __global__ void __launch_bounds__(256) k_av_blend(CtxDev c, const int4* __restri
       T num = 0, den = 0;
       for (int k = -r; k <= r; ++k) {
         if (!valid(gi, gj + k)) continue;
-        const T b = T(bw[k + r]);
+        const T b = bwt[k + r];
         num += b * B[(y + k) * W + x];
         den += b;
       }
