@@ -36,43 +36,64 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--dtype", default="f32", choices=["f32", "f64"])
-    ap.add_argument("--instances", type=int, default=128)
+    ap.add_argument("--instances", type=int, default=None,
+                    help="independent instances (default: 128 for sod, 8 for ffs)")
+    ap.add_argument("--workload", default="sod", choices=["sod", "ffs"],
+                    help="sod: the shock-tube batch (default); ffs: the forward-facing step with corner patches")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
 
 
-def workload(instances):
+FFS_H0 = 0.002      # forward-facing step: ~1M points in 64 patches per instance
+
+
+def workload(args):
     from paper_2506_19370_gb300 import inputs as I
-    return [I.sod_instance(perturb=0.01, seed=I.SEED + k, smear=2.0) for k in range(instances)]
+    if args.workload == "ffs":
+        return [I.ffs_instance(h0=FFS_H0) for _ in range(args.instances)]
+    return [I.sod_instance(perturb=0.01, seed=I.SEED + k, smear=2.0) for k in range(args.instances)]
 
 
 def config(args, points):
-    return {"workload": f"Sod shock tube, 8 overlapping Cartesian patches of 160x40 points (overlap 10) per "
-                        f"instance, x {args.instances} independent instances; SDNN classifier + artificial "
-                        f"viscosity + CFL dt + 4 RK stages + exchange per step",
+    if args.workload == "ffs":
+        desc = (f"Mach-3 forward-facing step, channel [0,3]x[0,1], step of height 0.2 at x = 0.6; 64 overlapping "
+                f"patches of uneven resolution (48-128 points per side, non-coincident grids, interpolated "
+                f"fringes) including one L-shaped C1 corner patch and one C2 corner patch per instance, "
+                f"x {args.instances} independent instances; SDNN classifier + artificial viscosity + CFL dt + "
+                f"4 RK stages + exchange per step")
+        cdesc = "25 requested; FFT-length policy per line length (n = 96 ... 224)"
+    else:
+        desc = (f"Sod shock tube, 8 overlapping Cartesian patches of 160x40 points (overlap 10) per "
+                f"instance, x {args.instances} independent instances; SDNN classifier + artificial "
+                f"viscosity + CFL dt + 4 RK stages + exchange per step")
+        cdesc = ("25 requested; FFT-length policy gives 32 on 160-point rows (n = 192) and 24 on 40-point "
+                 "columns (n = 64)")
+    return {"workload": desc,
             "instances": args.instances, "points_per_instance": points // args.instances, "points": points,
-            "d": 5, "C": "25 requested; FFT-length policy gives 32 on 160-point rows (n = 192) and 24 on 40-point "
-                         "columns (n = 64)",
+            "d": 5, "C": cdesc,
             "classifier": "16-32-32-4 MLP trained on the device at setup (300 Adam steps, 4096 seeded windows)",
             "l2": "flushed (256 MiB write) between timed steps",
             "parallelism": f"replicas x{args.gpus}" if args.gpus > 1 else "1 GPU"}
 
 
 # ---------------------------------------------------------------- CPU oracle
-def cpu_baseline(seconds, dist_note=None):
-    """Time the oracle (single-threaded numpy) on whole steps of one instance."""
+def cpu_baseline(seconds, workload_name="sod"):
+    """Time the oracle (single-threaded numpy) on whole steps of one instance
+    (forward-facing step: the same layout at a coarser spacing, h0 = 0.005)."""
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
     code = (
         "import time, json, sys; sys.path.insert(0, %r)\n"
         "from oracle import euler, sdnn\n"
         "from paper_2506_19370_gb300 import inputs as I\n"
-        "inst = I.sod_instance(perturb=0.01, smear=2.0)\n"
+        + ("inst = I.ffs_instance(h0=0.005)\n" if workload_name == "ffs" else
+           "inst = I.sod_instance(perturb=0.01, smear=2.0)\n") +
         "s = euler.Solver(inst, c_policy=1)\n"
         "params = sdnn.init_params(0)\n"
         "st = [e.copy() for e in inst.state]\n"
         "def step(st):\n"
-        "    taus = [sdnn.classify_patch(params, e, inst.gamma)[0] for e in st]\n"
+        "    taus = [sdnn.classify_patch(params, e, inst.gamma, lcut=tuple(p.lcut) if p.is_l else (0, 0))[0]\n"
+        "            for e, p in zip(st, inst.patches)]\n"
         "    mu = sdnn.av_assemble(s, st, taus)\n"
         "    dt = s.dt(st, mu)\n"
         "    return s.step(st, dt, mu)\n"
@@ -81,7 +102,7 @@ def cpu_baseline(seconds, dist_note=None):
         "while time.perf_counter() - t0 < %f or n < 2:\n"
         "    st = step(st); n += 1\n"
         "el = time.perf_counter() - t0\n"
-        "pts = sum(p.n1 * p.n2 for p in inst.patches)\n"
+        "pts = sum(int(p.active().sum()) for p in inst.patches)\n"
         "print(json.dumps({'steps': n, 'seconds': el, 'points': pts}))\n"
     ) % (ROOT, seconds)
     r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True)
@@ -90,8 +111,9 @@ def cpu_baseline(seconds, dist_note=None):
     res = json.loads(r.stdout.strip().splitlines()[-1])
     val = res["points"] * 4 * res["steps"] / res["seconds"]
     return {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{res['steps']} full steps (classifier, viscosity, dt, 4 stages, exchange) of one Sod "
-                      f"instance ({res['points']} points) in {res['seconds']:.1f} s, FP64 numpy, 1 thread",
+            "sample": f"{res['steps']} full steps (classifier, viscosity, dt, 4 stages, exchange) of one "
+                      + ("forward-facing-step instance at h0 = 0.005" if workload_name == "ffs" else "Sod instance")
+                      + f" ({res['points']} points) in {res['seconds']:.1f} s, FP64 numpy, 1 thread",
             "seconds": res["seconds"]}
 
 
@@ -104,15 +126,18 @@ def run_reference(args):
     vals, secs = [], 0.0
     base = None
     for _ in range(args.steps):
-        b = cpu_baseline(per)
+        b = cpu_baseline(per, args.workload)
         if b["value"] is None:
             print(json.dumps({"impl": "reference", "unavailable": b["sample"]}))
             return
         vals.append(b["value"])
         secs += b["seconds"]
         base = b
-    pts = 51200
+    pts = 51200 if args.workload == "sod" else None
     value = sum(vals) / len(vals)
+    if pts is None:
+        from paper_2506_19370_gb300 import inputs as I
+        pts = sum(int(p.active().sum()) for p in I.ffs_instance(h0=FFS_H0).patches)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1000.0 * pts * 4 / value, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -225,7 +250,7 @@ def run_ours(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     dtype = fcsdnn.F64 if args.dtype == "f64" else fcsdnn.F32
-    insts = workload(args.instances)
+    insts = workload(args)
     ctx = fcsdnn.Context(insts[0], d=5, C=25, dtype=dtype, instances=args.instances, c_policy=1, autotune=1)
     from paper_2506_19370_gb300.inputs import SEED
     rng = np.random.default_rng(SEED)
@@ -248,7 +273,7 @@ def run_ours(args):
         ctx.train_step(xw_d, yw_d, 3e-3)
     host = ctx.pack_state([i.state for i in insts])
     e = ctx.to_device(host)
-    points = args.instances * sum(p.n1 * p.n2 for p in insts[0].patches)
+    points = args.instances * sum(int(p.active().sum()) for p in insts[0].patches)
     tau = ctx.new_scalar(torch.int8)
     mu = ctx.new_scalar()
     dtd = torch.zeros(args.instances, dtype=torch.float64, device=dev)
@@ -355,7 +380,16 @@ def run_ours(args):
     import math
     def per_point(N, n, C, d=5):
         return (10 * n * math.log2(n) + 2 * n + 8 * d * C) / (2 * N)
-    flops_pt = 8 * per_point(160, 192, 32) + 8 * per_point(40, 64, 24) + 70
+    # every point lies on one line segment per direction: average over the
+    # layout's segments with their own continuation lengths
+    flops_sum = 0.0
+    for p in insts[0].patches:
+        m1, m2 = p.lcut if p.is_l else (0, 0)
+        for nlines, N in ((p.n2 - m2, p.n1), (m2, p.n1 - m1), (p.n1 - m1, p.n2), (m1, p.n2 - m2)):
+            if nlines and N:
+                Cn = ctx.line_c(N)
+                flops_sum += nlines * N * 8 * per_point(N, N + Cn, Cn)
+    flops_pt = flops_sum / (points // args.instances) + 70
     stage_avg_ms = sum(stage_ms) / len(stage_ms)
     achieved_tf = flops_pt * points / (stage_avg_ms / 1000.0) / 1e12
     alu_peak = 152 * 128 * 2 * 2.07e9 / 1e12
@@ -368,7 +402,7 @@ def run_ours(args):
     alg_bytes_pt = ts * 17
     hbm_gbs = alg_bytes_pt * points / (stage_avg_ms / 1000.0) / 1e9
     peak, peak_kind = measured_peak()
-    traffic = recorded_traffic(points)
+    traffic = recorded_traffic(points) if args.workload == "sod" else None
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -387,7 +421,7 @@ def run_ours(args):
                                              "peak_gbs": peak, "frac": hbm_gbs / peak, "peak_source": peak_kind}},
                 "clocks": clocks, "status": rc, "classifier": learned}
         if not args.no_cpu_baseline and world == 1:
-            line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
+            line["cpu_baseline"] = cpu_baseline(args.cpu_seconds, args.workload)
         print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()
@@ -395,6 +429,8 @@ def run_ours(args):
 
 def main():
     args = parse()
+    if args.instances is None:
+        args.instances = 8 if args.workload == "ffs" else 128
     if args.impl == "reference":
         run_reference(args)
     else:

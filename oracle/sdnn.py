@@ -279,6 +279,16 @@ def _box_max(a, r, lcut=(0, 0)):
     """Maximum over a (2r+1) x (2r+1) box, taken separably (along the rows,
     then along the columns), each line restricted to its segment in the patch."""
     n2, n1 = a.shape
+    if not (lcut[0] > 0 and lcut[1] > 0):    # rectangle: whole lines, shifted maxima
+        tmp = a.copy()
+        for k in range(1, r + 1):
+            tmp[:, :n1 - k] = np.maximum(tmp[:, :n1 - k], a[:, k:])
+            tmp[:, k:] = np.maximum(tmp[:, k:], a[:, :n1 - k])
+        out = tmp.copy()
+        for k in range(1, r + 1):
+            out[:n2 - k, :] = np.maximum(out[:n2 - k, :], tmp[k:, :])
+            out[k:, :] = np.maximum(out[k:, :], tmp[:n2 - k, :])
+        return out
     tmp = np.zeros_like(a)
     for j in range(n2):
         s0, N = line_span(n1, n2, lcut, 0, j)
@@ -298,14 +308,14 @@ def bump_weights(r):
 
 
 def _bump_avg_line(v, r):
-    """Normalised bump average along one line segment."""
+    """Normalised bump average along the last axis (one segment per line)."""
     b = bump_weights(r)
-    n = len(v)
-    num = np.zeros(n)
+    n = v.shape[-1]
+    num = np.zeros(v.shape)
     den = np.zeros(n)
     for k in range(-r, r + 1):
         lo, hi = max(0, -k), min(n, n - k)
-        num[lo:hi] += b[k + r] * v[lo + k:hi + k]
+        num[..., lo:hi] += b[k + r] * v[..., lo + k:hi + k]
         den[lo:hi] += b[k + r]
     return num / den
 
@@ -313,6 +323,8 @@ def _bump_avg_line(v, r):
 def _bump_avg(a, r, axis, lcut=(0, 0)):
     """Bump average along rows (axis 1) or columns (axis 0), segment by segment."""
     n2, n1 = a.shape
+    if not (lcut[0] > 0 and lcut[1] > 0):    # rectangle: all lines at once
+        return np.moveaxis(_bump_avg_line(np.moveaxis(a, axis, -1), r), -1, axis)
     out = np.zeros_like(a)
     if axis == 1:
         for j in range(n2):

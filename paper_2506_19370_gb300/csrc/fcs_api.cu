@@ -952,6 +952,9 @@ int fc_setup(fcs_ctx** out, int d, int C, const fcs_patch_desc* pd, int npatch, 
   D.sstride = (long long)c->sstride;
   D.qstride = (long long)c->qstride;
   D.gamma = o.gamma;
+  D.gm1f = (float)(o.gamma - 1.0);
+  for (int k = 0; k < 4; ++k) D.inflowf[k] = (float)o.inflow[k];
+  D.p_outf = (float)o.p_out;
   for (int k = 0; k < 4; ++k) D.inflow[k] = o.inflow[k];
   D.p_out = o.p_out;
   D.ind_plan = ind;

@@ -72,6 +72,9 @@ struct CtxDev {
   int instances, d;
   long long sstride, qstride;   // per-instance element counts of state and scalar layouts
   double gamma;
+  float gm1f;             // gamma - 1 in FP32 (FP32 kernels read it per point)
+  float inflowf[4];       // inflow state and outlet pressure in FP32
+  float p_outf;
   double inflow[4];
   double p_out;
   int ind_plan;                 // plan of the indicator (n = 16 + 26)
@@ -147,6 +150,20 @@ template <>
 __device__ __forceinline__ const double* metrics<double>(const CtxDev& c) { return c.metrics64; }
 template <>
 __device__ __forceinline__ const float* metrics<float>(const CtxDev& c) { return c.metrics32; }
+
+// gamma - 1, inflow state k (k = 4: outlet pressure) in the kernel's type
+template <typename T>
+__device__ __forceinline__ T gm1_of(const CtxDev& c);
+template <>
+__device__ __forceinline__ double gm1_of<double>(const CtxDev& c) { return c.gamma - 1.0; }
+template <>
+__device__ __forceinline__ float gm1_of<float>(const CtxDev& c) { return c.gm1f; }
+template <typename T>
+__device__ __forceinline__ T bc_value(const CtxDev& c, int k);
+template <>
+__device__ __forceinline__ double bc_value<double>(const CtxDev& c, int k) { return k < 4 ? c.inflow[k] : c.p_out; }
+template <>
+__device__ __forceinline__ float bc_value<float>(const CtxDev& c, int k) { return k < 4 ? c.inflowf[k] : c.p_outf; }
 
 // ------------------------------------------------------------ FFT
 // Small DFT of radix R in registers: v[q] <- sum_r v[r] W^{rq}, W = e^{-+2 pi i/R};
@@ -398,7 +415,7 @@ __device__ __forceinline__ void wall_project(T* v, T nx, T ny) {
 // two inward edge normals grad q1 / |grad q1| + grad q2 / |grad q2|.
 template <typename T>
 __device__ __forceinline__ void apply_bc(const CtxDev& c, const PatchDev& P, int i, int j, long long q, T* v) {
-  const T gm1 = T(c.gamma - 1.0);
+  const T gm1 = gm1_of<T>(c);
   const bool on[4] = {i == 0 && j >= P.m2, i == P.n1 - 1, j == 0 && i >= P.m1, j == P.n2 - 1};
   const T* M = metrics<T>(c);
   const long long qs = c.qstride;
@@ -415,12 +432,12 @@ __device__ __forceinline__ void apply_bc(const CtxDev& c, const PatchDev& P, int
         wall_project(v, -M[2 * qs + q], M[0 * qs + q]);
       }
     } else if (code == 2) {  // inflow
-      v[0] = T(c.inflow[0]);
-      v[1] = T(c.inflow[1]);
-      v[2] = T(c.inflow[2]);
-      v[3] = T(c.inflow[3]);
+      v[0] = bc_value<T>(c, 0);
+      v[1] = bc_value<T>(c, 1);
+      v[2] = bc_value<T>(c, 2);
+      v[3] = bc_value<T>(c, 3);
     } else if (code == 3) {  // outflow pressure
-      v[3] = T(c.p_out) / gm1 + T(0.5) * (v[1] * v[1] + v[2] * v[2]) / v[0];
+      v[3] = bc_value<T>(c, 4) / gm1 + T(0.5) * (v[1] * v[1] + v[2] * v[2]) / v[0];
     }
   }
   if (P.m1 > 0) {

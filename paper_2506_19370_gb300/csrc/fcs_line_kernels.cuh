@@ -87,7 +87,7 @@ __device__ __forceinline__ void point_flux(const CtxDev& c, const PatchDev& P, l
     const int code = t == 0 ? code_lo : (t == N - 1 ? P.bc[2 * DIR + 1] : 0);
     if (code == 1 || code == 3 || code == 4) visc = false;
   }
-  const T gm1 = T(c.gamma - 1.0);
+  const T gm1 = gm1_of<T>(c);
   const T rho = v[0], mx = v[1], my = v[2], En = v[3];
   const T u = mx / rho, w = my / rho;
   const T p = pressure<T>(rho, mx, my, En, gm1);
@@ -262,7 +262,7 @@ __global__ void __launch_bounds__(kYWarps * 32, 3) k_ypass(CtxDev c, const int2*
                (size_t)warp * aux_cx(N1, c.nfmax);
   const int g = JPR == 4 ? (lane >> 3) : 0;
   Cx<T>* tile = aux + (size_t)g * 8 * (4 * N1 + 1);
-  const T gm1 = T(c.gamma - 1.0);
+  const T gm1 = gm1_of<T>(c);
   const long long total = (long long)c.instances * ntiles;
   for (long long wk = blockIdx.x; wk < total; wk += gridDim.x) {
     const int inst = (int)(wk / ntiles);

@@ -295,6 +295,10 @@ class Context:
         _check("sdnn_gradient", lib().sdnn_gradient(self.h, _ptr(x), _ptr(labels), int(x.shape[0]), _ptr(loss),
                                                     _ptr(grad), _stream(stream)))
 
+    def line_c(self, N):
+        """Continuation length the context uses on lines of N points."""
+        return int(lib().fcs_line_c(self.h, int(N)))
+
     def filter(self, e, stream=None):
         _check("fcs_filter", lib().fcs_filter(self.h, _ptr(e), _stream(stream)))
 

@@ -228,7 +228,16 @@ def annulus_ring(sizes=((64, 24), (56, 20), (72, 28)), r0=0.5, r1=1.0, overlap=0
     return patches
 
 
-def ffs_instance(h0=0.002, length=3.0, seed=SEED, delta_pts=8, jitter=0.15, mach=3.0):
+def ffs_start_factor(X, Y, ell=0.05):
+    """Smooth factor 1 - exp(-(d/ell)^2), d the distance to the step's front
+    face (x = 0.6, 0 <= y <= 0.2): the velocity of the initial state is
+    multiplied by it, so the data satisfy the wall condition on the face."""
+    dy = np.maximum(Y - 0.2, 0.0)
+    d = np.hypot(X - 0.6, dy)
+    return 1.0 - np.exp(-(d / ell) ** 2)
+
+
+def ffs_instance(h0=0.002, length=3.0, seed=SEED, delta_pts=8, jitter=0.15, mach=3.0, start="smooth"):
     """Mach-`mach` flow over a forward-facing step (§7 problem shape).
 
     Channel [0, length] x [0, 1] with a step [0.6, length] x [0, 0.2].  The
@@ -241,7 +250,11 @@ def ffs_instance(h0=0.002, length=3.0, seed=SEED, delta_pts=8, jitter=0.15, mach
     quadrant of its parameter space maps onto the step; the cell at the
     step's foot (0.6, 0) is the C2 corner patch (interior angle 90 degrees).
     Left: inflow, right: free (supersonic outflow), walls elsewhere.  Initial
-    state: the uniform Mach flow (1.4, mach, 0, 1) of §7.
+    state: the Mach flow (1.4, mach, 0, 1) of §7, its velocity brought to rest
+    smoothly at the step's front face (start="smooth", ffs_start_factor; a
+    stand-in for the localized smearing of initial data, Algorithm 4, which the
+    stage does not contain) or uniform (start="uniform": an impulsive start
+    whose wall jump the FC derivatives cannot represent).
     """
     rng = np.random.default_rng(seed)
     hmax = h0 * (1 + jitter)
@@ -290,8 +303,9 @@ def ffs_instance(h0=0.002, length=3.0, seed=SEED, delta_pts=8, jitter=0.15, mach
     patches.insert(0, c1)
     state = []
     for p in patches:
-        X, _ = p.coords()
-        state.append(conserved(np.full(X.shape, 1.4), mach, 0.0, 1.0))
+        X, Y = p.coords()
+        f = ffs_start_factor(X, Y) if start == "smooth" else 1.0
+        state.append(conserved(np.full(X.shape, 1.4), mach * f, 0.0, 1.0))
     return Instance(patches, state, inflow=tuple(float(a) for a in conserved(1.4, mach, 0.0, 1.0)), p_out=1.0,
                     name="ffs", meta=dict(h0=h0, delta=delta, length=length))
 

@@ -255,10 +255,7 @@ def test_interpolated_exchange(name, dtype):
 @pytest.mark.parametrize("dtype", DTYPES)
 @pytest.mark.parametrize("name", ["strip", "ring", "ffs", "lbox", "lcurv"])
 def test_steps_with_interpolation(name, dtype):
-    # (the impulsively started Mach-3 step flow is run for 2 steps only: without
-    # viscosity the expansion at the step corner drives the density to zero
-    # within a few more)
-    nsteps = 2 if name == "ffs" else 8
+    nsteps = 8
     inst, pol, ctx = ctx_for(name, dtype)
     solver = euler.Solver(inst, c_policy=pol)
     dt = 0.3 * solver.dt(inst.state)
