@@ -289,7 +289,8 @@ def run_ours(args):
         ctx.classify(e, tau, None, stream)
         ctx.av_assemble(e, tau, mu, stream)
         ctx.time_step(e, dtd, mu, stream)
-        launches["n"] += 3 + 6 + 3   # proxy, MLP, tau gather; 5 viscosity kernels + exchange; dt init/min/final
+        # proxy, MLP, tau gather; viscosity (preliminary, blend, exchange); dt init/min/final
+        launches["n"] += 3 + ctx.launches["av"] + 3
         for s in range(4):
             es = e if s == 0 else S
             out = e if s == 3 else S
@@ -299,7 +300,7 @@ def run_ours(args):
             if ev is not None:
                 ev[s][1].record(stream)
             ctx.patch_exchange(out, 4, stream)
-            launches["n"] += 3
+            launches["n"] += ctx.launches["stage_visc"] + ctx.launches["exchange"]
 
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):

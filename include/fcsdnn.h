@@ -139,6 +139,11 @@ typedef struct {
   const int64_t* scalar_off;  /* per patch offset in the scalar layout */
   const int64_t* window_off;  /* per patch offset of its first window */
   int tile_width;             /* columns per CTA of the pass along q2 (autotuned or widest) */
+  int launches_stage;         /* kernel launches of one rk_stage / euler_rhs call without viscosity
+                                 (one row pass and one column pass per FFT-size group) */
+  int launches_stage_visc;    /* the same with viscosity (adds the e_q2 pass of curvilinear patches) */
+  int launches_exchange;      /* kernel launches of one patch_exchange call (copies, interpolations) */
+  int launches_av;            /* kernel launches of one av_assemble call (exchange included) */
 } fcs_layout;
 
 int fcs_get_layout(const fcs_ctx* ctx, fcs_layout* out);

@@ -381,7 +381,7 @@ int exchange_impl(fcs_ctx* c, void* field, int nfields, int clamp, cudaStream_t 
     else k_exchange<float><<<g, 256, 0, s>>>(c->dev, c->fringe_ent, c->nent, static_cast<float*>(field), nfields);
   }
   if (c->ninterp) {
-    const int g = grid_for(I * c->ninterp * nfields, 256);
+    const int g = grid_for(I * c->ninterp, 256);
     if (f64)
       k_interp<double><<<g, 256, 0, s>>>(c->dev, c->interp_ent, c->interp_w64, c->ninterp,
                                          static_cast<double*>(field), nfields, clamp);
@@ -1036,6 +1036,10 @@ int fcs_get_layout(const fcs_ctx* c, fcs_layout* o) {
   o->scalar_off = c->scalar_off.data();
   o->window_off = c->window_off.data();
   o->tile_width = c->tw;
+  o->launches_stage = (int)(c->g_rows.size() + c->g_tiles.size());
+  o->launches_stage_visc = o->launches_stage + (int)c->g_vpairs.size();
+  o->launches_exchange = (c->nent > 0) + (c->ninterp > 0);
+  o->launches_av = 1 + (c->opt.av_radius <= kBlendMaxR ? 1 : 4) + o->launches_exchange;
   return FCS_OK;
 }
 

@@ -36,40 +36,43 @@ __global__ void k_exchange(CtxDev c, const int4* __restrict__ ent, int nent, T* 
 
 // Interpolated fringe points: entries (dst patch, dst point, src patch, first
 // node of the donor block); w holds the kStencil x kStencil tensor Lagrange
-// weights of each entry ([b][a], b along j).  clamp floors the result at zero
-// (viscosity).
+// weights of each entry ([b][a], b along j).  One thread per (instance,
+// entry) does all fields, so the weights are read once and the 36 x nfields
+// loads are independent.  clamp floors the result at zero (viscosity).
 template <typename T>
 __global__ void k_interp(CtxDev c, const int4* __restrict__ ent, const T* __restrict__ w, int nent, T* field,
                          int nfields, int clamp) {
   constexpr int S = 6;
-  const long long total = (long long)c.instances * nent * nfields;
+  const long long total = (long long)c.instances * nent;
   for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x) {
-    const int f = (int)(t % nfields);
-    const long long r = t / nfields;
-    const int inst = (int)(r / nent);
-    const int k = (int)(r % nent);
+    const int inst = (int)(t / nent);
+    const int k = (int)(t % nent);
     const int4 x = ent[k];
     const PatchDev& Pd = c.patches[x.x];
     const PatchDev& Ps = c.patches[x.z];
-    const T* src;
-    T* dst;
-    if (nfields == 4) {
-      src = field + inst * c.sstride + Ps.soff + (long long)f * Ps.n1 * Ps.n2 + x.w;
-      dst = field + inst * c.sstride + Pd.soff + (long long)f * Pd.n1 * Pd.n2 + x.y;
-    } else {
-      src = field + inst * c.qstride + Ps.qoff + x.w;
-      dst = field + inst * c.qstride + Pd.qoff + x.y;
-    }
+    const long long fs = nfields == 4 ? (long long)Ps.n1 * Ps.n2 : 0, fd = nfields == 4 ? (long long)Pd.n1 * Pd.n2 : 0;
+    const T* src = field + (nfields == 4 ? inst * c.sstride + Ps.soff : inst * c.qstride + Ps.qoff) + x.w;
+    T* dst = field + (nfields == 4 ? inst * c.sstride + Pd.soff : inst * c.qstride + Pd.qoff) + x.y;
     const T* wk = w + (size_t)k * S * S;
-    T acc = T(0);
+    T acc[4] = {T(0), T(0), T(0), T(0)};
 #pragma unroll
     for (int b = 0; b < S; ++b) {
-      T row = T(0);
+      T row[4] = {T(0), T(0), T(0), T(0)};
 #pragma unroll
-      for (int a = 0; a < S; ++a) row += wk[b * S + a] * src[(long long)b * Ps.n1 + a];
-      acc += row;
+      for (int a = 0; a < S; ++a) {
+        const T wv = wk[b * S + a];
+        const long long o = (long long)b * Ps.n1 + a;
+        row[0] += wv * src[o];
+        if (nfields == 4) {
+          row[1] += wv * src[fs + o];
+          row[2] += wv * src[2 * fs + o];
+          row[3] += wv * src[3 * fs + o];
+        }
+      }
+#pragma unroll
+      for (int f = 0; f < 4; ++f) acc[f] += row[f];
     }
-    *dst = clamp && acc < T(0) ? T(0) : acc;
+    for (int f = 0; f < nfields; ++f) dst[f * fd] = clamp && acc[f] < T(0) ? T(0) : acc[f];
   }
 }
 

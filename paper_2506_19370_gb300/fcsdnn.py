@@ -51,7 +51,9 @@ class Layout(ctypes.Structure):
     _fields_ = [("instances", ctypes.c_int), ("npatch", ctypes.c_int), ("dtype", ctypes.c_int), ("d", ctypes.c_int),
                 ("state_elems", ctypes.c_size_t), ("scalar_elems", ctypes.c_size_t), ("windows", ctypes.c_size_t),
                 ("state_off", ctypes.POINTER(ctypes.c_int64)), ("scalar_off", ctypes.POINTER(ctypes.c_int64)),
-                ("window_off", ctypes.POINTER(ctypes.c_int64)), ("tile_width", ctypes.c_int)]
+                ("window_off", ctypes.POINTER(ctypes.c_int64)), ("tile_width", ctypes.c_int),
+                ("launches_stage", ctypes.c_int), ("launches_stage_visc", ctypes.c_int),
+                ("launches_exchange", ctypes.c_int), ("launches_av", ctypes.c_int)]
 
 
 _lib = None
@@ -189,6 +191,8 @@ class Context:
         self.scalar_off = [lay.scalar_off[k] for k in range(self.npatch)]
         self.window_off = [lay.window_off[k] for k in range(self.npatch)]
         self.tile_width = lay.tile_width
+        self.launches = {"stage": lay.launches_stage, "stage_visc": lay.launches_stage_visc,
+                         "exchange": lay.launches_exchange, "av": lay.launches_av}
         self.dev = torch.device("cuda", torch.cuda.current_device()) if torch.cuda.is_available() else None
 
     def close(self):
