@@ -7,6 +7,9 @@ perturbations of the Sod states; per step: proxy + windows + classifier MLP,
 artificial viscosity assembly, CFL time step, four Runge-Kutta stages (FC
 derivatives of fluxes and viscous fluxes, operator, stage update, boundary
 conditions), each followed by the fringe exchange.  Inputs are synthetic.
+--workload ffs times the Mach-3 forward-facing step instead (64 patches of
+uneven resolution with interpolated fringes and the two corner patches, ~1M
+points per instance, 8 instances).
 
 Prints one JSON line (see --help).  --impl reference times the FP64 CPU
 oracle on a bounded sample of the same workload on the host cores.

@@ -19,10 +19,12 @@ template <typename T>
 __global__ void k_exchange(CtxDev c, const int4* __restrict__ ent, int nent, T* field, int nfields) {
   const long long total = (long long)c.instances * nent * nfields;
   for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x) {
-    const int f = (int)(t % nfields);
-    const long long r = t / nfields;
-    const int inst = (int)(r / nent);
-    const int4 x = ent[r % nent];
+    // entries vary fastest: neighbouring threads copy neighbouring fringe points
+    const int k = (int)(t % nent);
+    const long long r = t / nent;
+    const int f = (int)(r % nfields);
+    const int inst = (int)(r / nfields);
+    const int4 x = ent[k];
     const PatchDev& Pd = c.patches[x.x];
     const PatchDev& Ps = c.patches[x.z];
     if (nfields == 4) {
