@@ -41,8 +41,9 @@ def parse():
     ap.add_argument("--dtype", default="f32", choices=["f32", "f64"])
     ap.add_argument("--instances", type=int, default=None,
                     help="independent instances (default: 128 for sod, 8 for ffs)")
-    ap.add_argument("--workload", default="sod", choices=["sod", "ffs"],
-                    help="sod: the shock-tube batch (default); ffs: the forward-facing step with corner patches")
+    ap.add_argument("--workload", default="sod", choices=["sod", "ffs", "ensemble"],
+                    help="sod: the shock-tube batch (default); ffs: the forward-facing step with corner patches; "
+                         "ensemble: 32 step flows of seeded resolutions and Mach numbers in one layout")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
@@ -51,15 +52,35 @@ def parse():
 FFS_H0 = 0.002      # forward-facing step: ~1M points in 64 patches per instance
 
 
+def ensemble_params(n=32):
+    """Seeded resolutions (points per flow log-uniform in [0.25M, 1.1M]; the
+    corner patch of a finer flow would exceed 256 points per side) and inflow
+    Mach numbers (uniform in [2, 4]) of the step-flow ensemble."""
+    import numpy as np
+    from paper_2506_19370_gb300 import inputs as I
+    rng = np.random.default_rng(I.SEED + 5)
+    pts = np.exp(rng.uniform(np.log(0.25e6), np.log(1.1e6), n))
+    return [float(FFS_H0 * np.sqrt(880203.0 / p)) for p in pts], [float(m) for m in rng.uniform(2.0, 4.0, n)]
+
+
 def workload(args):
     from paper_2506_19370_gb300 import inputs as I
     if args.workload == "ffs":
         return [I.ffs_instance(h0=FFS_H0) for _ in range(args.instances)]
+    if args.workload == "ensemble":
+        h0s, machs = ensemble_params()
+        return [I.ffs_ensemble(h0s, machs)]
     return [I.sod_instance(perturb=0.01, seed=I.SEED + k, smear=2.0) for k in range(args.instances)]
 
 
 def config(args, points):
-    if args.workload == "ffs":
+    if args.workload == "ensemble":
+        h0s, machs = ensemble_params()
+        desc = (f"32 independent Mach 2-4 forward-facing-step flows (seeded resolutions, 0.25M-1.1M points each; "
+                f"h0 {min(h0s):.4f}-{max(h0s):.4f}) in one layout of {32 * 64} patches of uneven size with "
+                f"per-flow inflow states, one context: every launch covers all flows")
+        cdesc = "25 requested; FFT-length policy per line length"
+    elif args.workload == "ffs":
         desc = (f"Mach-3 forward-facing step, channel [0,3]x[0,1], step of height 0.2 at x = 0.6; 64 overlapping "
                 f"patches of uneven resolution (48-128 points per side, non-coincident grids, interpolated "
                 f"fringes) including one L-shaped C1 corner patch and one C2 corner patch per instance, "
@@ -89,7 +110,7 @@ def cpu_baseline(seconds, workload_name="sod"):
         "import time, json, sys; sys.path.insert(0, %r)\n"
         "from oracle import euler, sdnn\n"
         "from paper_2506_19370_gb300 import inputs as I\n"
-        + ("inst = I.ffs_instance(h0=0.005)\n" if workload_name == "ffs" else
+        + ("inst = I.ffs_instance(h0=0.005)\n" if workload_name in ("ffs", "ensemble") else
            "inst = I.sod_instance(perturb=0.01, smear=2.0)\n") +
         "s = euler.Solver(inst, c_policy=1)\n"
         "params = sdnn.init_params(0)\n"
@@ -115,7 +136,8 @@ def cpu_baseline(seconds, workload_name="sod"):
     val = res["points"] * 4 * res["steps"] / res["seconds"]
     return {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"{res['steps']} full steps (classifier, viscosity, dt, 4 stages, exchange) of one "
-                      + ("forward-facing-step instance at h0 = 0.005" if workload_name == "ffs" else "Sod instance")
+                      + ("forward-facing-step instance at h0 = 0.005" if workload_name in ("ffs", "ensemble")
+                         else "Sod instance")
                       + f" ({res['points']} points) in {res['seconds']:.1f} s, FP64 numpy, 1 thread",
             "seconds": res["seconds"]}
 
@@ -139,8 +161,7 @@ def run_reference(args):
     pts = 51200 if args.workload == "sod" else None
     value = sum(vals) / len(vals)
     if pts is None:
-        from paper_2506_19370_gb300 import inputs as I
-        pts = sum(int(p.active().sum()) for p in I.ffs_instance(h0=FFS_H0).patches)
+        pts = sum(int(p.active().sum()) for p in workload(args)[0].patches)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1000.0 * pts * 4 / value, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -434,7 +455,9 @@ def run_ours(args):
 def main():
     args = parse()
     if args.instances is None:
-        args.instances = 8 if args.workload == "ffs" else 128
+        args.instances = {"ffs": 8, "ensemble": 1}.get(args.workload, 128)
+    if args.workload == "ensemble":
+        args.instances = 1
     if args.impl == "reference":
         run_reference(args)
     else:

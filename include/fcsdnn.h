@@ -88,6 +88,8 @@ typedef struct {
   const double* x;   /* host, n1*n2, cartesian == 0 only */
   const double* y;
   int lcut[2];       /* {m1, m2}: L-shaped corner patch; {0, 0}: rectangle */
+  const double* inflow; /* host, 4 conserved values for this patch's inflow sides
+                           (copied in fc_setup); NULL: options.inflow */
 } fcs_patch_desc;
 
 typedef struct {

@@ -281,8 +281,9 @@ def apply_bc(e, geom, inst):
                 e[(1,) + idx[1:]] -= mn * nx
                 e[(2,) + idx[1:]] -= mn * ny
         elif code == I.BC_INFLOW:
+            state = geom.patch.inflow if geom.patch.inflow is not None else inst.inflow
             for c in range(4):
-                e[(c,) + idx[1:]] = inst.inflow[c]
+                e[(c,) + idx[1:]] = state[c]
         elif code == I.BC_OUTFLOW:
             rho = e[(0,) + idx[1:]]
             mx = e[(1,) + idx[1:]]
@@ -396,7 +397,9 @@ def donor_index(patch, x, y, max_iter=40):
         fj += dj_
         if not (-2.0 <= fi <= patch.n1 + 1.0 and -2.0 <= fj <= patch.n2 + 1.0):
             return None
-        if abs(di_) + abs(dj_) < 1e-12:
+        # converged well below the interpolation accuracy (index units; a tighter
+        # test can sit in the rounding noise of coordinates far from the origin)
+        if abs(di_) + abs(dj_) < 1e-10:
             return fi, fj
     return None
 
@@ -427,6 +430,14 @@ def fringe_map(patches, n_f=5):
     """
     masks = [receiver_mask(p, n_f) for p in patches]
     usable = [p.active() & ~m for p, m in zip(patches, masks)]   # possible donor nodes
+    # bounding boxes, widened generously (a curved side bulges past its nodes):
+    # only a shortcut, every patch that can contain a point passes it
+    boxes = []
+    for p in patches:
+        X, Y = p.coords()
+        wx, wy = X.max() - X.min(), Y.max() - Y.min()
+        boxes.append((X.min() - 0.05 * wx - 1e-12, X.max() + 0.05 * wx + 1e-12,
+                      Y.min() - 0.05 * wy - 1e-12, Y.max() + 0.05 * wy + 1e-12))
     copies, interp = [], []
     for p, pt in enumerate(patches):
         X, Y = pt.coords()
@@ -435,6 +446,9 @@ def fringe_map(patches, n_f=5):
             found = False
             for q, qt in enumerate(patches):
                 if q == p:
+                    continue
+                bx = boxes[q]
+                if not (bx[0] <= x <= bx[1] and bx[2] <= y <= bx[3]):
                     continue
                 loc = donor_index(qt, x, y)
                 if loc is None:

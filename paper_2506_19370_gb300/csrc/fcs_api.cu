@@ -662,6 +662,10 @@ int fc_setup(fcs_ctx** out, int d, int C, const fcs_patch_desc* pd, int npatch, 
       if (s.back() + 16 < N) s.push_back(N - 16);
       return s;
     };
+    for (int k = 0; k < 4; ++k) {
+      P.inflowd[k] = q.inflow ? q.inflow[k] : o.inflow[k];
+      P.inflowf[k] = (float)P.inflowd[k];
+    }
     P.cd[PC_LX] = P.Lx;
     P.cd[PC_LY] = P.Ly;
     P.cd[PC_H1] = 1.0 / (q.n1 - 1);
@@ -953,7 +957,6 @@ int fc_setup(fcs_ctx** out, int d, int C, const fcs_patch_desc* pd, int npatch, 
   D.qstride = (long long)c->qstride;
   D.gamma = o.gamma;
   D.gm1f = (float)(o.gamma - 1.0);
-  for (int k = 0; k < 4; ++k) D.inflowf[k] = (float)o.inflow[k];
   D.p_outf = (float)o.p_out;
   for (int k = 0; k < 4; ++k) D.inflow[k] = o.inflow[k];
   D.p_out = o.p_out;

@@ -28,6 +28,8 @@ struct PatchDev {
   // them per point: FP64 conversions run at 1/64 of the FP32 rate on this part)
   double cd[5];
   float cf[5];
+  double inflowd[4];    // conserved inflow state of the patch's inflow sides
+  float inflowf[4];
 };
 
 enum { PC_LX = 0, PC_LY = 1, PC_H1 = 2, PC_H2 = 3, PC_HMAX = 4 };
@@ -72,8 +74,7 @@ struct CtxDev {
   int instances, d;
   long long sstride, qstride;   // per-instance element counts of state and scalar layouts
   double gamma;
-  float gm1f;             // gamma - 1 in FP32 (FP32 kernels read it per point)
-  float inflowf[4];       // inflow state and outlet pressure in FP32
+  float gm1f;             // gamma - 1 and the outlet pressure in FP32 (FP32 kernels read them per point)
   float p_outf;
   double inflow[4];
   double p_out;
@@ -159,11 +160,17 @@ __device__ __forceinline__ double gm1_of<double>(const CtxDev& c) { return c.gam
 template <>
 __device__ __forceinline__ float gm1_of<float>(const CtxDev& c) { return c.gm1f; }
 template <typename T>
-__device__ __forceinline__ T bc_value(const CtxDev& c, int k);
+__device__ __forceinline__ T p_out_of(const CtxDev& c);
 template <>
-__device__ __forceinline__ double bc_value<double>(const CtxDev& c, int k) { return k < 4 ? c.inflow[k] : c.p_out; }
+__device__ __forceinline__ double p_out_of<double>(const CtxDev& c) { return c.p_out; }
 template <>
-__device__ __forceinline__ float bc_value<float>(const CtxDev& c, int k) { return k < 4 ? c.inflowf[k] : c.p_outf; }
+__device__ __forceinline__ float p_out_of<float>(const CtxDev& c) { return c.p_outf; }
+template <typename T>
+__device__ __forceinline__ T inflow_of(const PatchDev& P, int k);
+template <>
+__device__ __forceinline__ double inflow_of<double>(const PatchDev& P, int k) { return P.inflowd[k]; }
+template <>
+__device__ __forceinline__ float inflow_of<float>(const PatchDev& P, int k) { return P.inflowf[k]; }
 
 // ------------------------------------------------------------ FFT
 // Small DFT of radix R in registers: v[q] <- sum_r v[r] W^{rq}, W = e^{-+2 pi i/R};
@@ -432,12 +439,12 @@ __device__ __forceinline__ void apply_bc(const CtxDev& c, const PatchDev& P, int
         wall_project(v, -M[2 * qs + q], M[0 * qs + q]);
       }
     } else if (code == 2) {  // inflow
-      v[0] = bc_value<T>(c, 0);
-      v[1] = bc_value<T>(c, 1);
-      v[2] = bc_value<T>(c, 2);
-      v[3] = bc_value<T>(c, 3);
+      v[0] = inflow_of<T>(P, 0);
+      v[1] = inflow_of<T>(P, 1);
+      v[2] = inflow_of<T>(P, 2);
+      v[3] = inflow_of<T>(P, 3);
     } else if (code == 3) {  // outflow pressure
-      v[3] = bc_value<T>(c, 4) / gm1 + T(0.5) * (v[1] * v[1] + v[2] * v[2]) / v[0];
+      v[3] = p_out_of<T>(c) / gm1 + T(0.5) * (v[1] * v[1] + v[2] * v[2]) / v[0];
     }
   }
   if (P.m1 > 0) {

@@ -126,7 +126,9 @@ bool locate(const PatchView& P, double x, double y, double* fi, double* fj) {
     u += du;
     w += dw;
     if (u < -2.0 || u > d.n1 + 1.0 || w < -2.0 || w > d.n2 + 1.0) return false;
-    if (std::fabs(du) + std::fabs(dw) < 1e-12) {
+    // converged to well below the interpolation accuracy (index units; a tighter
+    // test can sit in the rounding noise of coordinates far from the origin)
+    if (std::fabs(du) + std::fabs(dw) < 1e-10) {
       *fi = u;
       *fj = w;
       return true;
@@ -159,6 +161,34 @@ int build_fringe(const fcs_patch_desc* pd, int npatch, int n_f, std::vector<Frin
         v.ymax = std::max(v.ymax, v.Y(i, j));
       }
   }
+  // bucket grid over the layout: each patch is listed in the buckets its
+  // widened box touches (in patch order), so a receiver only tries the
+  // patches of its bucket, lowest-numbered first
+  double gx0 = 1e300, gx1 = -1e300, gy0 = 1e300, gy1 = -1e300, wsum = 0;
+  std::vector<double> bx0(npatch), bx1(npatch), by0(npatch), by1(npatch);
+  for (int p = 0; p < npatch; ++p) {
+    const PatchView& D = V[p];
+    // generous box: a curved side bulges past its nodes' extent
+    const double mx = 0.05 * (D.xmax - D.xmin) + 1e-12, my = 0.05 * (D.ymax - D.ymin) + 1e-12;
+    bx0[p] = D.xmin - mx;
+    bx1[p] = D.xmax + mx;
+    by0[p] = D.ymin - my;
+    by1[p] = D.ymax + my;
+    gx0 = std::min(gx0, bx0[p]);
+    gx1 = std::max(gx1, bx1[p]);
+    gy0 = std::min(gy0, by0[p]);
+    gy1 = std::max(gy1, by1[p]);
+    wsum += std::max(bx1[p] - bx0[p], by1[p] - by0[p]);
+  }
+  const double cell = std::max(wsum / npatch, 1e-12);
+  const int nbx = std::max(1, std::min(4096, (int)std::ceil((gx1 - gx0) / cell)));
+  const int nby = std::max(1, std::min(4096, (int)std::ceil((gy1 - gy0) / cell)));
+  auto bxi = [&](double x) { return std::min(nbx - 1, std::max(0, (int)((x - gx0) / (gx1 - gx0 + 1e-300) * nbx))); };
+  auto byi = [&](double y) { return std::min(nby - 1, std::max(0, (int)((y - gy0) / (gy1 - gy0 + 1e-300) * nby))); };
+  std::vector<std::vector<int>> bucket((size_t)nbx * nby);
+  for (int p = 0; p < npatch; ++p)
+    for (int by = byi(by0[p]); by <= byi(by1[p]); ++by)
+      for (int bx = bxi(bx0[p]); bx <= bxi(bx1[p]); ++bx) bucket[(size_t)by * nbx + bx].push_back(p);
   for (int p = 0; p < npatch; ++p) {
     const fcs_patch_desc& q = pd[p];
     for (int j = 0; j < q.n2; ++j)
@@ -166,14 +196,13 @@ int build_fringe(const fcs_patch_desc* pd, int npatch, int n_f, std::vector<Frin
         if (!is_receiver(q, n_f, i, j)) continue;   // (only points of the patch receive)
         const double x = V[p].X(i, j), y = V[p].Y(i, j);
         bool found = false;
-        for (int r = 0; r < npatch && !found; ++r) {
+        const std::vector<int>& cand = bucket[(size_t)byi(y) * nbx + bxi(x)];
+        for (size_t ci = 0; ci < cand.size() && !found; ++ci) {
+          const int r = cand[ci];
           if (r == p) continue;
-          const PatchView& D = V[r];
-          // generous box test: a curved side bulges past its nodes' extent
-          const double mx = 0.05 * (D.xmax - D.xmin) + 1e-12, my = 0.05 * (D.ymax - D.ymin) + 1e-12;
-          if (x < D.xmin - mx || x > D.xmax + mx || y < D.ymin - my || y > D.ymax + my) continue;
+          if (x < bx0[r] || x > bx1[r] || y < by0[r] || y > by1[r]) continue;
           double fi, fj;
-          if (!locate(D, x, y, &fi, &fj)) continue;
+          if (!locate(V[r], x, y, &fi, &fj)) continue;
           const fcs_patch_desc& s = pd[r];
           if (fi < -kInsideTol || fi > s.n1 - 1 + kInsideTol || fj < -kInsideTol || fj > s.n2 - 1 + kInsideTol)
             continue;

@@ -36,7 +36,8 @@ class FcsError(RuntimeError):
 class PatchDesc(ctypes.Structure):
     _fields_ = [("n1", ctypes.c_int), ("n2", ctypes.c_int), ("bc", ctypes.c_int * 4), ("cartesian", ctypes.c_int),
                 ("box", ctypes.c_double * 4), ("x", ctypes.POINTER(ctypes.c_double)),
-                ("y", ctypes.POINTER(ctypes.c_double)), ("lcut", ctypes.c_int * 2)]
+                ("y", ctypes.POINTER(ctypes.c_double)), ("lcut", ctypes.c_int * 2),
+                ("inflow", ctypes.POINTER(ctypes.c_double))]
 
 
 class Options(ctypes.Structure):
@@ -164,6 +165,10 @@ class Context:
             descs[k].n1, descs[k].n2 = p.n1, p.n2
             if getattr(p, "is_l", False):
                 descs[k].lcut[0], descs[k].lcut[1] = int(p.lcut[0]), int(p.lcut[1])
+            if getattr(p, "inflow", None) is not None:
+                infl = np.ascontiguousarray(p.inflow, dtype=np.float64)
+                self._keep.append(infl)
+                descs[k].inflow = infl.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
             for s in range(4):
                 descs[k].bc[s] = int(p.bc[s])
             if p.cartesian:

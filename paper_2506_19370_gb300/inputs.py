@@ -50,6 +50,7 @@ class Patch:
     y: Optional[np.ndarray] = None
     lcut: Sequence[int] = (0, 0)
     kind: str = ""                                   # S, C1, C2 or I (label only)
+    inflow: Optional[Sequence[float]] = None         # conserved inflow state of this patch (None: the instance's)
 
     @property
     def cartesian(self):
@@ -308,6 +309,26 @@ def ffs_instance(h0=0.002, length=3.0, seed=SEED, delta_pts=8, jitter=0.15, mach
         state.append(conserved(np.full(X.shape, 1.4), mach * f, 0.0, 1.0))
     return Instance(patches, state, inflow=tuple(float(a) for a in conserved(1.4, mach, 0.0, 1.0)), p_out=1.0,
                     name="ffs", meta=dict(h0=h0, delta=delta, length=length))
+
+
+def ffs_ensemble(h0s, machs, length=3.0, gap=1.0):
+    """Independent step flows of different resolutions and Mach numbers in one
+    layout: flow k is moved up by k (1 + gap) so no patch of one flow meets
+    another flow, and its patches carry its own inflow state."""
+    patches, state = [], []
+    for k, (h0, M) in enumerate(zip(h0s, machs)):
+        inst = ffs_instance(h0=h0, length=length, mach=M, seed=SEED + k)
+        dy = k * (1.0 + gap)
+        for p, e in zip(inst.patches, inst.state):
+            if p.cartesian:
+                q = Patch(p.n1, p.n2, p.bc, box=(p.box[0], p.box[1], p.box[2] + dy, p.box[3] + dy), lcut=p.lcut,
+                          kind=p.kind, inflow=inst.inflow)
+            else:
+                q = Patch(p.n1, p.n2, p.bc, x=p.x, y=p.y + dy, lcut=p.lcut, kind=p.kind, inflow=inst.inflow)
+            patches.append(q)
+            state.append(e)
+    return Instance(patches, state, inflow=tuple(float(a) for a in conserved(1.4, machs[0], 0.0, 1.0)), p_out=1.0,
+                    name="ffs_ensemble", meta=dict(h0s=list(h0s), machs=list(machs)))
 
 
 def mach_flow_state(M, gamma=GAMMA):

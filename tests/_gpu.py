@@ -57,6 +57,10 @@ def layout(name):
             p = I.Patch(n1, n2, (I.BC_WALL,) * 4, x=0.9 - 1.02 * Q2, y=-0.3 + 1.2 * Q1, lcut=(m1, m2), kind="C1")
         rng = np.random.default_rng(13)
         return I.Instance([p], [I.random_state(p, rng)], name=name), 1
+    if name == "ensemble":
+        # three independent step flows of different resolutions and Mach
+        # numbers in one layout (per-patch inflow states)
+        return I.ffs_ensemble((0.006, 0.005, 0.0045), (2.0, 3.0, 4.0), length=1.4), 1
     if name == "ffs":
         # forward-facing step at Mach 3, 32 patches of uneven resolution with
         # a C1 (L-shaped) and a C2 corner patch (coarse version of the

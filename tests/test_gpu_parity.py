@@ -124,7 +124,8 @@ def rhs_bound(dtype, inst, pol, states, mus=None):
 
 
 @pytest.mark.parametrize("dtype", DTYPES)
-@pytest.mark.parametrize("name", ["vortex", "sod", "annulus", "split", "strip", "ring", "lbox", "lcurv", "ffs"])
+@pytest.mark.parametrize("name", ["vortex", "sod", "annulus", "split", "strip", "ring", "lbox", "lcurv", "ffs",
+                                  "ensemble"])
 def test_euler_rhs(name, dtype):
     inst, pol, ctx = ctx_for(name, dtype)
     st = random_states(inst, 11)
@@ -253,7 +254,7 @@ def test_interpolated_exchange(name, dtype):
 
 
 @pytest.mark.parametrize("dtype", DTYPES)
-@pytest.mark.parametrize("name", ["strip", "ring", "ffs", "lbox", "lcurv"])
+@pytest.mark.parametrize("name", ["strip", "ring", "ffs", "lbox", "lcurv", "ensemble"])
 def test_steps_with_interpolation(name, dtype):
     nsteps = 8
     inst, pol, ctx = ctx_for(name, dtype)
