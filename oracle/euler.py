@@ -329,17 +329,18 @@ def lagrange_weights(t, m=STENCIL):
 
 
 def lagrange_dweights(t, m=STENCIL):
-    """Derivatives at t of the m Lagrange basis polynomials on 0..m-1."""
+    """Derivatives at t of the m Lagrange basis polynomials on 0..m-1: the
+    product rule applied factor by factor to prod_{b != a} (t - b), divided by
+    prod_{b != a} (a - b)."""
     dw = np.zeros(m)
     for a in range(m):
-        for c in range(m):
-            if c == a:
-                continue
-            term = 1.0 / (a - c)
-            for b in range(m):
-                if b != a and b != c:
-                    term *= (t - b) / (a - b)
-            dw[a] += term
+        val, der, den = 1.0, 0.0, 1.0
+        for b in range(m):
+            if b != a:
+                der = der * (t - b) + val
+                val *= t - b
+                den *= a - b
+        dw[a] = der / den
     return dw
 
 
@@ -366,6 +367,9 @@ def stencil_block(patch, fi, fj):
     return i0, j0
 
 
+_CELL_DIAG = {}   # id(patch) -> (patch, largest cell diagonal); the patch is kept so the id stays valid
+
+
 def donor_index(patch, x, y, max_iter=40):
     """Fractional grid index (fi, fj) of the physical point (x, y) in `patch`.
 
@@ -378,7 +382,16 @@ def donor_index(patch, x, y, max_iter=40):
         x0, x1, y0, y1 = patch.box
         return (x - x0) / ((x1 - x0) / (patch.n1 - 1)), (y - y0) / ((y1 - y0) / (patch.n2 - 1))
     X, Y = patch.coords()
-    k = int(np.argmin((X - x) ** 2 + (Y - y) ** 2))
+    d2 = (X - x) ** 2 + (Y - y) ** 2
+    k = int(np.argmin(d2))
+    # a point of the patch lies within one cell diagonal of a node: farther
+    # points are outside (this only saves the Newton iterations)
+    key = id(patch)
+    if key not in _CELL_DIAG:
+        _CELL_DIAG[key] = (patch, float(np.sqrt(max(np.max(np.diff(X, axis=1) ** 2 + np.diff(Y, axis=1) ** 2),
+                                                    np.max(np.diff(X, axis=0) ** 2 + np.diff(Y, axis=0) ** 2)) * 2)))
+    if d2.flat[k] > (1.01 * _CELL_DIAG[key][1]) ** 2:
+        return None
     fj, fi = float(k // patch.n1), float(k % patch.n1)
     for _ in range(max_iter):
         i0, j0 = stencil_start(fi, patch.n1), stencil_start(fj, patch.n2)
