@@ -41,15 +41,17 @@ def parse():
     ap.add_argument("--dtype", default="f32", choices=["f32", "f64"])
     ap.add_argument("--instances", type=int, default=None,
                     help="independent instances (default: 128 for sod, 8 for ffs)")
-    ap.add_argument("--workload", default="sod", choices=["sod", "ffs", "ensemble"],
+    ap.add_argument("--workload", default="sod", choices=["sod", "ffs", "ensemble", "cylinder"],
                     help="sod: the shock-tube batch (default); ffs: the forward-facing step with corner patches; "
-                         "ensemble: 32 step flows of seeded resolutions and Mach numbers in one layout")
+                         "ensemble: 32 step flows of seeded resolutions and Mach numbers in one layout; "
+                         "cylinder: Mach-10 flow past a cylinder (annular sectors + Cartesian far field)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
 
 
 FFS_H0 = 0.002      # forward-facing step: ~1M points in 64 patches per instance
+CYL_H = 0.004       # cylinder: ~3.9M points in 260 patches
 
 
 def ensemble_params(n=32):
@@ -70,11 +72,19 @@ def workload(args):
     if args.workload == "ensemble":
         h0s, machs = ensemble_params()
         return [I.ffs_ensemble(h0s, machs)]
+    if args.workload == "cylinder":
+        return [I.cylinder_instance(h=CYL_H) for _ in range(args.instances)]
     return [I.sod_instance(perturb=0.01, seed=I.SEED + k, smear=2.0) for k in range(args.instances)]
 
 
 def config(args, points):
-    if args.workload == "ensemble":
+    if args.workload == "cylinder":
+        desc = (f"Mach-10 flow past a cylinder of radius 0.5: 16 body-fitted curvilinear annular sectors plus 244 "
+                f"Cartesian far-field patches of uneven resolution (interpolated fringes), h = {CYL_H}, "
+                f"x {args.instances} instance(s); SDNN classifier + artificial viscosity + CFL dt + 4 RK stages + "
+                f"exchange per step")
+        cdesc = "25 requested; FFT-length policy per line length"
+    elif args.workload == "ensemble":
         h0s, machs = ensemble_params()
         desc = (f"32 independent Mach 2-4 forward-facing-step flows (seeded resolutions, 0.25M-1.1M points each; "
                 f"h0 {min(h0s):.4f}-{max(h0s):.4f}) in one layout of {32 * 64} patches of uneven size with "
@@ -111,6 +121,7 @@ def cpu_baseline(seconds, workload_name="sod"):
         "from oracle import euler, sdnn\n"
         "from paper_2506_19370_gb300 import inputs as I\n"
         + ("inst = I.ffs_instance(h0=0.005)\n" if workload_name in ("ffs", "ensemble") else
+           "inst = I.cylinder_instance(h=0.02)\n" if workload_name == "cylinder" else
            "inst = I.sod_instance(perturb=0.01, smear=2.0)\n") +
         "s = euler.Solver(inst, c_policy=1)\n"
         "params = sdnn.init_params(0)\n"
@@ -137,7 +148,7 @@ def cpu_baseline(seconds, workload_name="sod"):
     return {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"{res['steps']} full steps (classifier, viscosity, dt, 4 stages, exchange) of one "
                       + ("forward-facing-step instance at h0 = 0.005" if workload_name in ("ffs", "ensemble")
-                         else "Sod instance")
+                         else "cylinder instance at h = 0.02" if workload_name == "cylinder" else "Sod instance")
                       + f" ({res['points']} points) in {res['seconds']:.1f} s, FP64 numpy, 1 thread",
             "seconds": res["seconds"]}
 
@@ -455,7 +466,7 @@ def run_ours(args):
 def main():
     args = parse()
     if args.instances is None:
-        args.instances = {"ffs": 8, "ensemble": 1}.get(args.workload, 128)
+        args.instances = {"ffs": 8, "ensemble": 1, "cylinder": 1}.get(args.workload, 128)
     if args.workload == "ensemble":
         args.instances = 1
     if args.impl == "reference":

@@ -331,6 +331,77 @@ def ffs_ensemble(h0s, machs, length=3.0, gap=1.0):
                     name="ffs_ensemble", meta=dict(h0s=list(h0s), machs=list(machs)))
 
 
+def cylinder_instance(h=0.01, R=0.5, r_out=None, box=(-3.0, 4.0, -3.0, 3.0), sectors=16, mach=10.0, delta_pts=8,
+                      seed=SEED, ell=0.15):
+    """Mach-`mach` flow past a circular cylinder of radius R at the origin.
+
+    Body-fitted curvilinear annular sectors (angle along q1, radius along q2,
+    wall at r = R) cover R <= r <= r_out and overlap by at least 24 points in
+    angle; the rest of `box` is cut into Cartesian cells, 0.25 wide within
+    [-1.5, 1.5]^2 and 0.5 wide outside.  Every cell is a patch with a seeded
+    spacing h (1 +- 0.15), extended by delta on its internal sides; cells whose
+    extended box comes closer than R + 0.1 to the centre are left out (the
+    annulus covers them: by default r_out leaves room for such a cell and the
+    annulus fringe).  Left: inflow, right: free (supersonic outflow),
+    bottom/top: walls.  Initial state: the Mach flow (1.4, mach, 0, 1) of §7
+    with the velocity brought to rest smoothly at the cylinder wall (factor
+    1 - exp(-((r - R)/ell)^2)).
+    """
+    rng = np.random.default_rng(seed)
+    hmax = h * 1.15
+    delta = delta_pts * hmax
+    r_ex = R + 0.1
+    if r_out is None:
+        r_out = max(1.2, r_ex + 0.25 * np.sqrt(2.0) + 2 * delta + 12 * hmax)
+    r_mid = 0.5 * (R + r_out)
+    patches = []
+    n2 = int(round((r_out - R) / h)) + 1
+    overlap = max(0.35, 24 * hmax / R)
+    for k in range(sectors):
+        th0 = k * 2 * np.pi / sectors - overlap / 2
+        th1 = (k + 1) * 2 * np.pi / sectors + overlap / 2
+        hs = h * (1 + 0.15 * rng.uniform(-1.0, 1.0))
+        n1 = int(round((th1 - th0) * r_mid / hs)) + 1
+        p = annulus_patch(n1, n2, R, r_out, th0, th1, bc=(BC_INTERNAL, BC_INTERNAL, BC_WALL, BC_INTERNAL))
+        p.kind = "S"
+        patches.append(p)
+    x0, x1, y0, y1 = box
+    cells = []
+    for cy0 in np.arange(y0, y1 - 1e-9, 0.5):
+        for cx0 in np.arange(x0, x1 - 1e-9, 0.5):
+            if -1.5 - 1e-9 <= cx0 < 1.5 - 1e-9 and -1.5 - 1e-9 <= cy0 < 1.5 - 1e-9:
+                cells += [(cx0 + a, cx0 + a + 0.25, cy0 + b, cy0 + b + 0.25) for b in (0.0, 0.25) for a in (0.0, 0.25)]
+            else:
+                cells.append((cx0, cx0 + 0.5, cy0, cy0 + 0.5))
+    for cx0, cx1, cy0, cy1 in cells:
+        ex0, ex1, ey0, ey1 = cx0 - delta, cx1 + delta, cy0 - delta, cy1 + delta
+        dx = 0.0 if ex0 <= 0.0 <= ex1 else min(abs(ex0), abs(ex1))
+        dy = 0.0 if ey0 <= 0.0 <= ey1 else min(abs(ey0), abs(ey1))
+        if np.hypot(dx, dy) < r_ex:
+            continue
+        bc = [BC_INTERNAL] * 4
+        if abs(cx0 - x0) < 1e-9:
+            bc[0] = BC_INFLOW
+        if abs(cx1 - x1) < 1e-9:
+            bc[1] = BC_FREE
+        if abs(cy0 - y0) < 1e-9:
+            bc[2] = BC_WALL
+        if abs(cy1 - y1) < 1e-9:
+            bc[3] = BC_WALL
+        b = (cx0 - delta * (bc[0] == BC_INTERNAL), cx1 + delta * (bc[1] == BC_INTERNAL),
+             cy0 - delta * (bc[2] == BC_INTERNAL), cy1 + delta * (bc[3] == BC_INTERNAL))
+        hh = h * (1 + 0.15 * rng.uniform(-1.0, 1.0))
+        patches.append(Patch(int(round((b[1] - b[0]) / hh)) + 1, int(round((b[3] - b[2]) / hh)) + 1, tuple(bc), box=b,
+                             kind="I" if all(c == BC_INTERNAL for c in bc) else "S"))
+    state = []
+    for p in patches:
+        X, Y = p.coords()
+        f = 1.0 - np.exp(-((np.hypot(X, Y) - R) / ell) ** 2)
+        state.append(conserved(np.full(X.shape, 1.4), mach * f, 0.0, 1.0))
+    return Instance(patches, state, inflow=tuple(float(a) for a in conserved(1.4, mach, 0.0, 1.0)), p_out=1.0,
+                    name="cylinder", meta=dict(h=h, R=R, r_out=r_out, mach=mach))
+
+
 def mach_flow_state(M, gamma=GAMMA):
     """Uniform Mach-M flow (rho, u, v, p) = (1.4, M, 0, 1) of §7 (sound speed 1)."""
     return (1.4, float(M), 0.0, 1.0)

@@ -57,6 +57,9 @@ def layout(name):
             p = I.Patch(n1, n2, (I.BC_WALL,) * 4, x=0.9 - 1.02 * Q2, y=-0.3 + 1.2 * Q1, lcut=(m1, m2), kind="C1")
         rng = np.random.default_rng(13)
         return I.Instance([p], [I.random_state(p, rng)], name=name), 1
+    if name == "cylinder":
+        # Mach-10 flow past a cylinder: annular sectors + Cartesian far field
+        return I.cylinder_instance(h=0.03), 1
     if name == "ensemble":
         # three independent step flows of different resolutions and Mach
         # numbers in one layout (per-patch inflow states)

@@ -125,7 +125,7 @@ def rhs_bound(dtype, inst, pol, states, mus=None):
 
 @pytest.mark.parametrize("dtype", DTYPES)
 @pytest.mark.parametrize("name", ["vortex", "sod", "annulus", "split", "strip", "ring", "lbox", "lcurv", "ffs",
-                                  "ensemble"])
+                                  "ensemble", "cylinder"])
 def test_euler_rhs(name, dtype):
     inst, pol, ctx = ctx_for(name, dtype)
     st = random_states(inst, 11)
@@ -254,7 +254,7 @@ def test_interpolated_exchange(name, dtype):
 
 
 @pytest.mark.parametrize("dtype", DTYPES)
-@pytest.mark.parametrize("name", ["strip", "ring", "ffs", "lbox", "lcurv", "ensemble"])
+@pytest.mark.parametrize("name", ["strip", "ring", "ffs", "lbox", "lcurv", "ensemble", "cylinder"])
 def test_steps_with_interpolation(name, dtype):
     nsteps = 8
     inst, pol, ctx = ctx_for(name, dtype)

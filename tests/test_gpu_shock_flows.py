@@ -1,9 +1,12 @@
-"""Forward-facing step at Mach 3 with corner patches: GPU (FP32, BF16
-classifier, viscosity, filter) against the FP64 oracle over many steps.
+"""Shock flows over obstacles: GPU (FP32, BF16 classifier, viscosity, filter)
+against the FP64 oracle over many steps, both sides classifying their own
+states with the same trained weights.
 
-The layout is the 32-patch coarse version of the 64-patch, ~1M-point step
-(uneven non-coincident grids, one L-shaped C1 corner patch, one C2 corner
-patch); both sides classify their own states with the same trained weights.
+  * forward-facing step at Mach 3: the 32-patch coarse version of the
+    64-patch, ~1M-point step (uneven non-coincident grids, one L-shaped C1
+    corner patch, one C2 corner patch);
+  * Mach-10 flow past a cylinder: 16 curvilinear annular sectors plus
+    Cartesian far-field patches, coarse version of the ~4M-point layout.
 """
 import json
 
@@ -17,13 +20,16 @@ from oracle import euler, sdnn  # noqa: E402
 from paper_2506_19370_gb300 import fcsdnn  # noqa: E402
 from paper_2506_19370_gb300 import inputs as I  # noqa: E402
 
-NSTEPS = 40
+CASES = {"step": (lambda: I.ffs_instance(h0=0.005, length=1.4), 40),
+         "cylinder": (lambda: I.cylinder_instance(h=0.03), 15)}
 
 
-def test_step_flow_against_oracle():
+@pytest.mark.parametrize("case", sorted(CASES))
+def test_shock_flow_against_oracle(case):
     if not torch.cuda.is_available():
         pytest.skip("no GPU")
-    inst = I.ffs_instance(h0=0.005, length=1.4)
+    make, NSTEPS = CASES[case]
+    inst = make()
     ctx = fcsdnn.Context(inst, d=5, C=25, dtype=fcsdnn.F32, c_policy=1, filter_step=1)
     xw, yw = I.classifier_windows(4096, seed=I.SEED)
     ctx.set_weights(sdnn.init_params(0).astype(np.float32))
@@ -72,7 +78,7 @@ def test_step_flow_against_oracle():
     res = {"steps": NSTEPS, "L1_rel_density": num / den, "window_mismatch": mism / tot,
            "window_mismatch_well_decided": mism_dec / max(tot_dec, 1), "well_decided": tot_dec / tot,
            "windows": tot}
-    print("step flow vs oracle", json.dumps(res))
+    print(case, "flow vs oracle", json.dumps(res))
     assert rc == 0
     # L1 density error within 1e-3 of the FP64 oracle; windows the FP64
     # network decides with a logit margin above 0.25 agree to 0.1 % (BF16
