@@ -35,6 +35,19 @@ def built():
     assert torch.cuda.is_available()
 
 
+_SOLVERS = {}
+
+
+def oracle_solver(inst, pol):
+    """The oracle's Solver of a layout, built once per layout (the donor search
+    of the large layouts takes tens of seconds)."""
+    key = (inst.name, pol, tuple((p.n1, p.n2, tuple(p.bc), None if p.box is None else tuple(p.box), tuple(p.lcut))
+                                 for p in inst.patches))
+    if key not in _SOLVERS:
+        _SOLVERS[key] = euler.Solver(inst, c_policy=pol)
+    return _SOLVERS[key]
+
+
 def ctx_for(name, dtype, instances=1):
     inst, pol = layout(name)
     return inst, pol, fcsdnn.Context(inst, d=5, C=25, dtype=dtype, instances=instances, c_policy=pol)
@@ -133,7 +146,7 @@ def test_euler_rhs(name, dtype):
     rhs = ctx.new_state()
     ctx.euler_rhs(e, rhs)
     torch.cuda.synchronize()
-    solver = euler.Solver(inst, c_policy=pol)
+    solver = oracle_solver(inst, pol)
     cast = [np.asarray(s, dtype=np.float32 if dtype == fcsdnn.F32 else np.float64).astype(np.float64) for s in st]
     ref = solver.rhs_all(cast)
     got = ctx.unpack_state(rhs)
@@ -155,7 +168,7 @@ def test_euler_rhs_with_viscosity(name, dtype):
     rhs = ctx.new_state()
     ctx.euler_rhs(e, rhs, mu=m)
     torch.cuda.synchronize()
-    solver = euler.Solver(inst, c_policy=pol)
+    solver = oracle_solver(inst, pol)
     npd = np.float32 if dtype == fcsdnn.F32 else np.float64
     cast = [np.asarray(s, dtype=npd).astype(np.float64) for s in st]
     mcast = [np.asarray(x, dtype=npd).astype(np.float64) for x in mu]
@@ -196,7 +209,7 @@ def test_vortex_100_steps(dtype):
 @pytest.mark.parametrize("dtype", DTYPES)
 def test_sod_steps_with_exchange(dtype):
     inst, pol, ctx = ctx_for("sod", dtype)
-    solver = euler.Solver(inst, c_policy=pol)
+    solver = oracle_solver(inst, pol)
     dt = 0.2 * solver.dt(inst.state)
     got = run_steps(ctx, inst.state, 10, dt)
     ref = [e.copy() for e in inst.state]
@@ -258,7 +271,7 @@ def test_interpolated_exchange(name, dtype):
 def test_steps_with_interpolation(name, dtype):
     nsteps = 8
     inst, pol, ctx = ctx_for(name, dtype)
-    solver = euler.Solver(inst, c_policy=pol)
+    solver = oracle_solver(inst, pol)
     dt = 0.3 * solver.dt(inst.state)
     got = run_steps(ctx, inst.state, nsteps, dt)
     ref = [e.copy() for e in inst.state]
@@ -278,7 +291,7 @@ def test_l_patch_time_step_and_sums(name):
     dt = torch.zeros(1, dtype=torch.float64, device="cuda")
     ctx.time_step(e, dt)
     torch.cuda.synchronize()
-    solver = euler.Solver(inst, c_policy=pol)
+    solver = oracle_solver(inst, pol)
     rtol = 1e-14 if all(p.cartesian for p in inst.patches) else 1e-10
     assert abs(dt.item() - solver.dt(st)) <= rtol * solver.dt(st)
     sums = torch.zeros(ctx.npatch * 4, dtype=torch.float64, device="cuda")
@@ -292,7 +305,7 @@ def test_l_patch_viscosity_and_indicator(name, dtype):
     inst, pol, ctx = ctx_for(name, dtype)
     npd = np.float32 if dtype == fcsdnn.F32 else np.float64
     if name == "ffs":
-        solver = euler.Solver(inst, c_policy=pol)
+        solver = oracle_solver(inst, pol)
         st = solver.step([e.copy() for e in inst.state], 0.3 * solver.dt(inst.state))
     else:
         st = random_states(inst, 17)
@@ -305,7 +318,7 @@ def test_l_patch_viscosity_and_indicator(name, dtype):
     mu = ctx.new_scalar()
     ctx.av_assemble(e, t, mu)
     torch.cuda.synchronize()
-    solver = euler.Solver(inst, c_policy=pol)
+    solver = oracle_solver(inst, pol)
     st64 = [s.astype(np.float64) for s in st]
     ref = sdnn.av_assemble(solver, st64, taus)
     got = active_only(ctx.unpack_scalar(mu), inst)
@@ -343,7 +356,7 @@ def test_time_step_and_sums(name):
     ctx.time_step(e, dt)
     ctx.conservation_sums(e, sums)
     torch.cuda.synchronize()
-    solver = euler.Solver(inst, c_policy=pol)
+    solver = oracle_solver(inst, pol)
     # Cartesian metrics are exact; curvilinear ones come from FC derivatives
     # of the coordinates (rounding as bounded in the derivative tests)
     rtol = 1e-14 if all(p.cartesian for p in inst.patches) else 1e-10
@@ -463,7 +476,7 @@ def test_artificial_viscosity(dtype, radius, trained_params):
     mu = ctx.new_scalar()
     ctx.av_assemble(e, t, mu)
     torch.cuda.synchronize()
-    solver = euler.Solver(inst, c_policy=pol)
+    solver = oracle_solver(inst, pol)
     ref = sdnn.av_assemble(solver, [s.astype(np.float64) for s in st], taus, radius=radius)
     err = rel_err(ctx.unpack_scalar(mu), ref)
     print(f"viscosity radius={radius} dtype={dtype} err={err:.3e}")
@@ -591,7 +604,7 @@ def test_spectral_filter(name, dtype):
     e = ctx.to_device(ctx.pack_state(st))
     ctx.filter(e)
     torch.cuda.synchronize()
-    solver = euler.Solver(inst, c_policy=pol)
+    solver = oracle_solver(inst, pol)
     ref = active_only(solver.filter([s.copy() for s in cast]), inst)
     got = active_only(ctx.unpack_state(e), inst)
     change = rel_err(active_only(cast, inst), ref)
@@ -605,7 +618,7 @@ def test_spectral_filter(name, dtype):
 def test_step_with_filter_option(dtype):
     inst, pol = layout("sod")
     ctx = fcsdnn.Context(inst, d=5, C=25, dtype=dtype, c_policy=pol, filter_step=1)
-    solver = euler.Solver(inst, c_policy=pol)
+    solver = oracle_solver(inst, pol)
     dt = 0.3 * solver.dt(inst.state)
     got = run_steps(ctx, inst.state, 5, dt)
     ref = [e.copy() for e in inst.state]
