@@ -366,3 +366,33 @@ def av_assemble(solver, state, taus, c_mu=1.0, radius=4):
     mus = [av_patch(e, t, g, solver.inst.gamma, solver.n_f, c_mu, radius)
            for e, t, g in zip(state, taus, solver.geoms)]
     return euler.exchange(mus, solver.fmap, clamp=True)
+
+
+# ---------------------------------------------------------------- initial smearing
+SMEAR_P = 1   # order of the stronger filter used at t = 0 (reading of "somewhat more strongly filtered":
+              # exp(-alpha (k/k_max)^2) spreads a jump over ~7 points without overshoot; orders >= 2 ring)
+
+
+def smear_weight(tau, lcut=(0, 0), radius=4):
+    """Smooth window near discontinuities: 1 where a point's tau is 1 (jump),
+    spread by the box maximum and the normalised bump average of the viscosity
+    blend (values in [0, 1])."""
+    w0 = (np.asarray(tau) == 1).astype(np.float64)
+    w0[~_active(w0.shape, lcut)] = 0.0
+    return _bump_avg(_bump_avg(_box_max(w0, radius, lcut), radius, 1, lcut), radius, 0, lcut)
+
+
+def smear_initial(solver, state, taus, p=SMEAR_P, radius=4):
+    """Localized smearing of discontinuous initial data (§5 item 3, Algorithm 4
+    at t = 0; reading of I-(33)): e' = (1 - w) e + w F_p(e), F_p the spectral
+    filter of order p, w the smooth window near the points classified as jumps;
+    then boundary conditions and the fringe exchange."""
+    out = []
+    for e, t, g in zip(state, taus, solver.geoms):
+        lc = tuple(g.patch.lcut) if g.patch.is_l else (0, 0)
+        w = smear_weight(t, lc, radius)
+        f = euler.filter_state(e, g, solver.inst.gamma, p=p)
+        out.append(np.where(g.active, (1.0 - w) * e + w * f, e))
+    for e, g in zip(out, solver.geoms):
+        euler.apply_bc(e, g, solver.inst)
+    return euler.exchange(out, solver.fmap)

@@ -133,3 +133,27 @@ def test_l_patch_windows_and_viscosity():
     g = euler.PatchGeom(p, 5, 25)
     mu = sdnn.av_patch(e, np.ones((n2, n1), dtype=np.int8), g, G, 5, c_mu=0.7)
     assert np.allclose(mu[act], 0.7 * 0.02 * 1.0, rtol=1e-13) and np.all(mu[~act] == 0.0)
+
+
+def test_initial_smearing_is_local_and_smooths_jumps():
+    from oracle import euler
+    inst = I.sod_instance()                         # sharp Sod jump at x = 0.5
+    solver = euler.Solver(inst, c_policy=1)
+    flat = [np.full((p.n2, p.n1), 4, dtype=np.int8) for p in inst.patches]
+    same = sdnn.smear_initial(solver, [e.copy() for e in inst.state], flat)
+    assert all(np.array_equal(a, b) for a, b in zip(same, inst.state))     # no jump flagged: unchanged
+    taus = []
+    for p in inst.patches:
+        X, _ = p.coords()
+        taus.append(np.where(np.abs(X - 0.5) < 0.004, 1, 4).astype(np.int8))
+    w = sdnn.smear_weight(taus[3])
+    assert w.min() >= 0.0 and w.max() <= 1.0 + 1e-15 and w.max() > 0.99
+    out = sdnn.smear_initial(solver, [e.copy() for e in inst.state], taus)
+    for a, b, p in zip(out, inst.state, inst.patches):
+        X, _ = p.coords()
+        far = np.abs(X - 0.5) > 0.05
+        assert np.array_equal(a[:, far], b[:, far])                        # local
+    jump = lambda st: max(float(np.abs(np.diff(e[0], axis=1)).max()) for e in st)
+    assert jump(out) < 0.2 * jump(inst.state)                              # the jump is spread
+    assert min(float(e[0].min()) for e in out) > 0.125 - 1e-3               # without overshoot
+    assert max(float(e[0].max()) for e in out) < 1.0 + 1e-3
