@@ -112,6 +112,7 @@ typedef struct {
   int filter_p;        /* filter order p (18) */
   int filter_step;     /* 1: fcs_step ends with fcs_filter, so every step after
                           the first starts from filtered data; 0: off (0) */
+  int smear_p;         /* order of the stronger filter of fcs_smear_initial (1) */
 } fcs_options;
 
 /* Defaults listed in the comments above. */
@@ -210,6 +211,15 @@ int fcs_time_step(fcs_ctx* ctx, const void* e_dev, const void* mu_dev, double* d
  * theta, then the boundary conditions and the fringe exchange are applied.
  * Uses the context's work buffers (not concurrently with other calls). */
 int fcs_filter(fcs_ctx* ctx, void* e_dev, void* stream);
+
+/* Localized smearing of discontinuous initial data, in place (§5 item 3,
+ * Algorithm 4 at t = 0; reading of I-(33)): e' = (1 - w) e + w F(e), with F
+ * the spectral filter of fcs_filter at order smear_p (Gaussian for 1) and w
+ * the smooth window around the points whose tau_dev (int8, scalar layout, as
+ * written by sdnn_classify or sdnn_indicator) is 1 (jump): 1 there, spread by
+ * the box maximum and the bump average of the viscosity blend (av_radius);
+ * then boundary conditions and the fringe exchange. */
+int fcs_smear_initial(fcs_ctx* ctx, void* e_dev, const int8_t* tau_dev, void* stream);
 
 /* Per instance and patch, FP64 sums of each conserved field with the FC
  * quadrature weights (tensor product along q1 and q2) times |J|:

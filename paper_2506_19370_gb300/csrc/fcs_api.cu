@@ -65,6 +65,8 @@ struct fcs_ctx {
   int4* vpairs = nullptr;  // column pairs x fields of curvilinear patches (viscous gradient e_q2)
   int4* fpairs[2] = {nullptr, nullptr};  // row / column pairs x 4 fields of every patch (filter)
   std::vector<Group> g_fpairs[2];
+  double* smr64 = nullptr;  // filter factors of the initial smearing (order smear_p), twiddle offsets
+  float* smr32 = nullptr;
   void* G1 = nullptr;      // e_q1, e_q2 of curvilinear patches (state-sized; viscous passes)
   void* G2 = nullptr;
   int2* tiles = nullptr;
@@ -524,6 +526,7 @@ void fcs_default_options(fcs_options* o) {
   o->filter_alpha = 16.0 * std::log(10.0);
   o->filter_p = 18;
   o->filter_step = 0;
+  o->smear_p = 1;
 }
 
 const char* fcs_strerror(int code) {
@@ -568,7 +571,7 @@ int fc_setup(fcs_ctx** out, int d, int C, const fcs_patch_desc* pd, int npatch, 
   else fcs_default_options(&o);
   if (o.instances < 1 || (o.dtype != FCS_F32 && o.dtype != FCS_F64) || o.n_f < 1 || o.gamma <= 1.0 ||
       o.av_radius < 0 || o.av_radius > 32 || o.train_batch_max < 1 || !(o.filter_alpha >= 0.0) || o.filter_p < 1 ||
-      o.filter_p > 64)
+      o.filter_p > 64 || o.smear_p < 1 || o.smear_p > 64)
     return FCS_EINVAL;
   for (int p = 0; p < npatch; ++p) {
     const fcs_patch_desc& q = pd[p];
@@ -817,8 +820,8 @@ int fc_setup(fcs_ctx** out, int d, int C, const fcs_patch_desc* pd, int npatch, 
   std::vector<float> thi, tlo;
   std::vector<double2> tw64;
   std::vector<float2> tw32;
-  std::vector<double> flt64;
-  std::vector<float> flt32;
+  std::vector<double> flt64, smr64;
+  std::vector<float> flt32, smr32;
   std::vector<PlanDev> plans;
   for (HostPlan& hp : c->plans) {
     hp.dev.tg_off = (int)gramT.size();
@@ -847,6 +850,9 @@ int fc_setup(fcs_ctx** out, int d, int C, const fcs_patch_desc* pd, int npatch, 
       const double sg = std::exp(-o.filter_alpha * std::pow(kk, 2.0 * o.filter_p));
       flt64.push_back(sg);
       flt32.push_back((float)sg);
+      const double si = std::exp(-o.filter_alpha * std::pow(kk, 2.0 * o.smear_p));  // smearing filter
+      smr64.push_back(si);
+      smr32.push_back((float)si);
     }
     plans.push_back(hp.dev);
   }
@@ -893,6 +899,8 @@ int fc_setup(fcs_ctx** out, int d, int C, const fcs_patch_desc* pd, int npatch, 
       (rc = upload(c, &dtw64, tw64.data(), tw64.size() * sizeof(double2))) ||
       (rc = upload(c, &dtw32, tw32.data(), tw32.size() * sizeof(float2))) ||
       (rc = upload(c, &dflt64, flt64.data(), flt64.size() * 8)) || (rc = upload(c, &dflt32, flt32.data(), flt32.size() * 4)) ||
+      (rc = upload(c, &c->smr64, smr64.data(), smr64.size() * 8)) ||
+      (rc = upload(c, &c->smr32, smr32.data(), smr32.size() * 4)) ||
       (rc = upload(c, &dl0, l0.data(), l0.size() * sizeof(LineRef))) ||
       (rc = upload(c, &dl1, l1.data(), l1.size() * sizeof(LineRef))) ||
       (rc = upload(c, &c->pairs0, p0.data(), p0.size() * sizeof(int4))) ||
@@ -1255,38 +1263,92 @@ int sdnn_train_step(fcs_ctx* c, const float* x, const int8_t* lab, int B, float 
   return cuda_err(cudaGetLastError());
 }
 
-int fcs_filter(fcs_ctx* c, void* e, void* stream) {
-  if (!c || !e) return FCS_EINVAL;
-  cudaStream_t s = as_stream(stream);
-  const dim3 g(c->dev.npblk, c->opt.instances);
+}  // extern "C"
+
+namespace {
+// Spectral filter with the factor tables of dev (the step filter or the
+// smearing filter), blended into the state by w when w is not null.
+int filter_impl(fcs_ctx* c, void* e, const CtxDev& dev, const void* w, cudaStream_t s) {
+  const dim3 g(dev.npblk, c->opt.instances);
   const bool f64 = c->opt.dtype == FCS_F64;
   const double gm1 = c->opt.gamma - 1.0;
-  if (f64) k_filter_prep<double><<<g, 256, 0, s>>>(c->dev, static_cast<const double*>(e), static_cast<double*>(c->R), gm1);
-  else k_filter_prep<float><<<g, 256, 0, s>>>(c->dev, static_cast<const float*>(e), static_cast<float*>(c->R), (float)gm1);
+  if (f64) k_filter_prep<double><<<g, 256, 0, s>>>(dev, static_cast<const double*>(e), static_cast<double*>(c->R), gm1);
+  else k_filter_prep<float><<<g, 256, 0, s>>>(dev, static_cast<const float*>(e), static_cast<float*>(c->R), (float)gm1);
   FCS_CUDA(cudaGetLastError());
   // rows R -> S, columns S -> R (order 0 of the line transform: filter)
   for (int dir = 0; dir < 2; ++dir) {
     void* src = dir == 0 ? c->R : c->S;
     void* dst = dir == 0 ? c->S : c->R;
     for (const Group& gr : c->g_fpairs[dir]) {
-      const long long work = ((long long)c->dev.instances * gr.count + jobs_per_round(gr.n1) - 1) / jobs_per_round(gr.n1);
+      const long long work = ((long long)dev.instances * gr.count + jobs_per_round(gr.n1) - 1) / jobs_per_round(gr.n1);
       if (f64) {
         const LaunchCfg lc{(unsigned)grid_for(work, kWarps), kWarps * 32, deriv_smem<double>(c, gr.n1), s};
-        FCS_N1_SWITCH(gr.n1, FCS_CUDA((run_fc_deriv<double, K>(c->dev, dir, 0, c->fpairs[dir] + gr.begin, gr.count,
+        FCS_N1_SWITCH(gr.n1, FCS_CUDA((run_fc_deriv<double, K>(dev, dir, 0, c->fpairs[dir] + gr.begin, gr.count,
                                                                static_cast<const double*>(src),
                                                                static_cast<double*>(dst), lc))); break)
       } else {
         const LaunchCfg lc{(unsigned)grid_for(work, kWarps), kWarps * 32, deriv_smem<float>(c, gr.n1), s};
-        FCS_N1_SWITCH(gr.n1, FCS_CUDA((run_fc_deriv<float, K>(c->dev, dir, 0, c->fpairs[dir] + gr.begin, gr.count,
+        FCS_N1_SWITCH(gr.n1, FCS_CUDA((run_fc_deriv<float, K>(dev, dir, 0, c->fpairs[dir] + gr.begin, gr.count,
                                                               static_cast<const float*>(src),
                                                               static_cast<float*>(dst), lc))); break)
       }
     }
   }
-  if (f64) k_filter_done<double><<<g, 256, 0, s>>>(c->dev, static_cast<const double*>(c->R), static_cast<double*>(e), gm1);
-  else k_filter_done<float><<<g, 256, 0, s>>>(c->dev, static_cast<const float*>(c->R), static_cast<float*>(e), (float)gm1);
+  if (f64)
+    k_filter_done<double><<<g, 256, 0, s>>>(dev, static_cast<const double*>(c->R), static_cast<double*>(e), gm1,
+                                            static_cast<const double*>(w));
+  else
+    k_filter_done<float><<<g, 256, 0, s>>>(dev, static_cast<const float*>(c->R), static_cast<float*>(e), (float)gm1,
+                                           static_cast<const float*>(w));
   FCS_CUDA(cudaGetLastError());
   return exchange_impl(c, e, 4, 0, s);
+}
+
+// Box maximum then bump average of a scalar field (the viscosity blend):
+// in -> out, tmp as work space (the separable kernels overwrite in).
+template <typename T>
+int blend_impl(fcs_ctx* c, T* in, T* tmp, T* out, cudaStream_t s) {
+  const int r = c->opt.av_radius;
+  if (r <= kBlendMaxR) {
+    k_av_blend<T><<<grid_for((long long)c->opt.instances * c->nbtiles, 1), 256, blend_smem(r, sizeof(T)), s>>>(
+        c->dev, c->btiles, c->nbtiles, in, out, c->bump, r);
+  } else {
+    const dim3 g(c->dev.npblk, c->opt.instances);
+    k_av_boxmax<T><<<g, 256, 0, s>>>(c->dev, in, tmp, r, 0);
+    k_av_boxmax<T><<<g, 256, 0, s>>>(c->dev, tmp, in, r, 1);
+    k_av_bump<T><<<g, 256, 0, s>>>(c->dev, in, tmp, c->bump, r, 0);
+    k_av_bump<T><<<g, 256, 0, s>>>(c->dev, tmp, out, c->bump, r, 1);
+  }
+  return cuda_err(cudaGetLastError());
+}
+}  // namespace
+
+extern "C" {
+
+int fcs_filter(fcs_ctx* c, void* e, void* stream) {
+  if (!c || !e) return FCS_EINVAL;
+  return filter_impl(c, e, c->dev, nullptr, as_stream(stream));
+}
+
+int fcs_smear_initial(fcs_ctx* c, void* e, const int8_t* tau, void* stream) {
+  if (!c || !e || !tau) return FCS_EINVAL;
+  cudaStream_t s = as_stream(stream);
+  const dim3 g(c->dev.npblk, c->opt.instances);
+  const signed char* t = reinterpret_cast<const signed char*>(tau);
+  int rc;
+  if (c->opt.dtype == FCS_F64) {
+    double *w0 = static_cast<double*>(c->av1), *tmp = static_cast<double*>(c->av0), *w = static_cast<double*>(c->mu);
+    k_smear_seed<double><<<g, 256, 0, s>>>(c->dev, t, w0);
+    if ((rc = blend_impl<double>(c, w0, tmp, w, s))) return rc;
+  } else {
+    float *w0 = static_cast<float*>(c->av1), *tmp = static_cast<float*>(c->av0), *w = static_cast<float*>(c->mu);
+    k_smear_seed<float><<<g, 256, 0, s>>>(c->dev, t, w0);
+    if ((rc = blend_impl<float>(c, w0, tmp, w, s))) return rc;
+  }
+  CtxDev dev = c->dev;  // the same context with the smearing filter's factors
+  dev.flt64 = c->smr64;
+  dev.flt32 = c->smr32;
+  return filter_impl(c, e, dev, c->mu, s);
 }
 
 int fcs_step(fcs_ctx* c, void* e, double dt, double* dt_dev, int use_av, void* stream) {

@@ -96,9 +96,11 @@ __global__ void k_filter_prep(CtxDev c, const T* __restrict__ e, T* W, T gm1) {
   W[o + 3 * np] = pressure<T>(rho, mx, my, En, gm1) / rho;
 }
 
-// End of the filter: E from the filtered temperature, boundary conditions.
+// End of the filter: E from the filtered temperature, blended with the
+// unfiltered state by the window w (smearing; nullptr: filter alone),
+// boundary conditions.
 template <typename T>
-__global__ void k_filter_done(CtxDev c, const T* __restrict__ W, T* e, T gm1) {
+__global__ void k_filter_done(CtxDev c, const T* __restrict__ W, T* e, T gm1, const T* __restrict__ w) {
   const PatchDev* Pp;
   const PtIdx x = pt_index(c, &Pp);
   const PatchDev& P = *Pp;
@@ -109,9 +111,25 @@ __global__ void k_filter_done(CtxDev c, const T* __restrict__ W, T* e, T gm1) {
   v[1] = W[o + np];
   v[2] = W[o + 2 * np];
   v[3] = v[0] * W[o + 3 * np] / gm1 + T(0.5) * (v[1] * v[1] + v[2] * v[2]) / v[0];
+  if (w) {
+    const T a = w[x.inst * c.qstride + P.qoff + x.lq];
+#pragma unroll
+    for (int f = 0; f < 4; ++f) v[f] = (T(1) - a) * e[o + f * np] + a * v[f];
+  }
   apply_bc<T>(c, P, x.i, x.j, P.qoff + x.lq, v);
 #pragma unroll
   for (int f = 0; f < 4; ++f) e[o + f * np] = v[f];
+}
+
+// Smearing window seed: 1 where tau is 1 (jump), else 0.
+template <typename T>
+__global__ void k_smear_seed(CtxDev c, const signed char* __restrict__ tau, T* w0) {
+  const PatchDev* Pp;
+  const PtIdx x = pt_index(c, &Pp);
+  const PatchDev& P = *Pp;
+  if (!x.ok) return;
+  const long long t = x.inst * c.qstride + P.qoff + x.lq;
+  w0[t] = tau[t] == 1 ? T(1) : T(0);
 }
 
 // ============================================================ point helpers

@@ -24,7 +24,7 @@ EXPORTS = ("fcs_default_options", "fc_setup", "fc_destroy", "fcs_get_layout", "f
            "fc_derivative", "euler_rhs", "rk_stage", "patch_exchange", "fcs_time_step", "fcs_conservation_sums",
            "sdnn_set_weights", "sdnn_get_weights", "sdnn_classify", "sdnn_indicator", "av_assemble",
            "sdnn_train_step", "sdnn_gradient", "sdnn_gradient_noalloc", "fcs_step", "fcs_step_graph", "fcs_status",
-           "fcs_strerror", "fcs_filter")
+           "fcs_strerror", "fcs_filter", "fcs_smear_initial")
 
 
 class FcsError(RuntimeError):
@@ -45,7 +45,7 @@ class Options(ctypes.Structure):
                 ("instances", ctypes.c_int), ("inflow", ctypes.c_double * 4), ("p_out", ctypes.c_double),
                 ("c_mu", ctypes.c_double), ("av_radius", ctypes.c_int), ("c_policy", ctypes.c_int),
                 ("train_batch_max", ctypes.c_int), ("autotune", ctypes.c_int), ("filter_alpha", ctypes.c_double),
-                ("filter_p", ctypes.c_int), ("filter_step", ctypes.c_int)]
+                ("filter_p", ctypes.c_int), ("filter_step", ctypes.c_int), ("smear_p", ctypes.c_int)]
 
 
 class Layout(ctypes.Structure):
@@ -91,6 +91,7 @@ def lib():
             "sdnn_gradient_noalloc": (i, [vp, vp, vp, i, vp, vp, vp]),
             "fcs_step": (i, [vp, vp, d, vp, i, vp]),
             "fcs_filter": (i, [vp, vp, vp]),
+            "fcs_smear_initial": (i, [vp, vp, vp, vp]),
             "fcs_step_graph": (i, [vp, vp, d, vp, i, vp]),
             "fcs_status": (i, [vp, ctypes.POINTER(ctypes.c_int)]),
             "fcs_strerror": (ctypes.c_char_p, [i]),
@@ -310,6 +311,9 @@ class Context:
 
     def filter(self, e, stream=None):
         _check("fcs_filter", lib().fcs_filter(self.h, _ptr(e), _stream(stream)))
+
+    def smear_initial(self, e, tau, stream=None):
+        _check("fcs_smear_initial", lib().fcs_smear_initial(self.h, _ptr(e), _ptr(tau), _stream(stream)))
 
     def step(self, e, dt=0.0, dt_dev=None, use_av=False, stream=None):
         _check("fcs_step", lib().fcs_step(self.h, _ptr(e), float(dt), _ptr(dt_dev), int(use_av), _stream(stream)))

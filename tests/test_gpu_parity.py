@@ -627,3 +627,32 @@ def test_step_with_filter_option(dtype):
     err = rel_err(got, ref)
     print(f"sod 5 steps with filter dtype={dtype} err={err:.3e}")
     assert err < (1e-9 if dtype == fcsdnn.F64 else 1e-4)
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("name", ["sharp_sod", "lbox"])
+def test_initial_smearing(name, dtype):
+    # Algorithm 4 at t = 0: Gaussian-order filter blended in around jump points
+    if name == "sharp_sod":
+        inst, pol = I.sod_instance(), 1
+        taus = [np.where(np.abs(p.coords()[0] - 0.5) < 0.004, 1, 4).astype(np.int8) for p in inst.patches]
+        st = [e.copy() for e in inst.state]
+    else:
+        inst, pol = layout(name)
+        rng = np.random.default_rng(41)
+        taus = [rng.choice([1, 4], p=[0.03, 0.97], size=(p.n2, p.n1)).astype(np.int8) for p in inst.patches]
+        st = random_states(inst, 43)
+    ctx = fcsdnn.Context(inst, d=5, C=25, dtype=dtype, c_policy=pol)
+    npd = np.float32 if dtype == fcsdnn.F32 else np.float64
+    cast = [np.asarray(s, dtype=npd).astype(np.float64) for s in st]
+    e = ctx.to_device(ctx.pack_state(st))
+    t = ctx.to_device(ctx.pack_scalar(taus, dtype=np.int8))
+    ctx.smear_initial(e, t)
+    torch.cuda.synchronize()
+    ref = active_only(sdnn.smear_initial(oracle_solver(inst, pol), [s.copy() for s in cast], taus), inst)
+    got = active_only(ctx.unpack_state(e), inst)
+    change = rel_err(active_only(cast, inst), ref)
+    err = rel_err(got, ref)
+    print(f"initial smearing {name} dtype={dtype} err={err:.3e} (changed the state by {change:.2e})")
+    assert change > 1e-3
+    assert err < (1e-11 if dtype == fcsdnn.F64 else 2e-5)
