@@ -329,9 +329,11 @@ __device__ __forceinline__ void continue_lines(Cx<float>* buf, const CtxDev& c, 
 
 template <typename T>
 struct Offset {
-  // FP32 lines are shifted by the mean of their end values before the FFT
-  // (the FC derivative of a constant vanishes up to the fit residual); FP64
-  // lines are transformed as they are.
+  // FP32 lines are shifted by the mean of their end values before the FFT of a
+  // derivative (the FC derivative of a constant vanishes up to the fit
+  // residual); FP64 lines, and filtered lines (the continuation of a constant
+  // is not constant, so a filter does not commute with the shift), are
+  // transformed as they are.
   static constexpr bool kShift = false;
 };
 template <>
@@ -357,7 +359,7 @@ __device__ Cx<T>* fc_deriv_pair(Cx<T>* a, Cx<T>* b, const CtxDev& c, const PlanD
                                 int lane) {
   const int N = pl.N, n = pl.n;
   T oa = T(0), ob = T(0);
-  if (Offset<T>::kShift) {
+  if (Offset<T>::kShift && order != 0) {
     const Cx<T> f0 = a[0], f1 = a[N - 1];
     oa = (f0.x + f1.x) * T(0.5);
     ob = (f0.y + f1.y) * T(0.5);
@@ -389,13 +391,7 @@ __device__ Cx<T>* fc_deriv_pair(Cx<T>* a, Cx<T>* b, const CtxDev& c, const PlanD
     r[m] = o;
   }
   __syncwarp();
-  Cx<T>* res = warp_fft<T>(r, s, c, pl, true, lane);
-  if (order == 0 && Offset<T>::kShift) {  // a filtered line keeps its offset
-    __syncwarp();
-    for (int t = lane; t < N; t += 32) res[t] = {res[t].x + oa, res[t].y + ob};
-    __syncwarp();
-  }
-  return res;
+  return warp_fft<T>(r, s, c, pl, true, lane);
 }
 
 // ------------------------------------------------------------ gas dynamics
@@ -613,7 +609,7 @@ __device__ __forceinline__ void reg_deriv_pair(const T* a, int sa, const T* b, i
                                                T scale, const LineOp<T>& op, int order, int lane) {
   const int N = op.N, n = 32 * N1;
   T offa = T(0), offb = T(0);
-  if (Offset<T>::kShift) {
+  if (Offset<T>::kShift && order != 0) {
     offa = (a[0] + a[(N - 1) * sa]) * T(0.5);
     if (b) offb = (b[0] + b[(N - 1) * sb]) * T(0.5);
   }
@@ -651,14 +647,12 @@ __device__ __forceinline__ void reg_deriv_pair(const T* a, int sa, const T* b, i
     }
   }
   reg_fft<T, N1>(x, op.tw, true, lane);
-  // a filtered line (order 0) keeps its offset
-  const T ra = order == 0 ? offa * scale : T(0), rb = order == 0 ? offb * scale : T(0);
 #pragma unroll
   for (int j1 = 0; j1 < N1; ++j1) {
     const int j = lane + 32 * j1;
     if (j < N) {
-      oa[j * soa] = x[j1].x + ra;
-      if (ob) ob[j * sob] = x[j1].y + rb;
+      oa[j * soa] = x[j1].x;
+      if (ob) ob[j * sob] = x[j1].y;
     }
   }
 }
@@ -858,7 +852,7 @@ __device__ __forceinline__ void tl_deriv_pair(const T* a, int sa, const T* b, in
   const int N = op.N, n = 8 * B, d = op.d;
   // ---- end values and continuation coefficients
   T offa = T(0), offb = T(0);
-  if (active && Offset<T>::kShift) {
+  if (active && Offset<T>::kShift && order != 0) {
     offa = (a[0] + a[(N - 1) * sa]) * T(0.5);
     if (b) offb = (b[0] + b[(N - 1) * sb]) * T(0.5);
   }
@@ -973,13 +967,12 @@ __device__ __forceinline__ void tl_deriv_pair(const T* a, int sa, const T* b, in
     });
     rdft_inv<T, 8>(v);
     if (active) {
-      const T ra = order == 0 ? offa * scale : T(0), rb = order == 0 ? offb * scale : T(0);
 #pragma unroll
       for (int aa = 0; aa < 8; ++aa) {
         const int j = bb + B * aa;
         if (j < N) {
-          oa[j * soa] = v[aa].x + ra;
-          if (ob) ob[j * sob] = v[aa].y + rb;
+          oa[j * soa] = v[aa].x;
+          if (ob) ob[j * sob] = v[aa].y;
         }
       }
     }

@@ -653,6 +653,12 @@ def test_initial_smearing(name, dtype):
     got = active_only(ctx.unpack_state(e), inst)
     change = rel_err(active_only(cast, inst), ref)
     err = rel_err(got, ref)
-    print(f"initial smearing {name} dtype={dtype} err={err:.3e} (changed the state by {change:.2e})")
+    # the Gaussian-order filter mixes the continuation region into the data
+    # near line ends, so the continuation's amplification of input rounding
+    # (table gain G, up to ~7.6e3 for C' >= 20) reaches the result there:
+    # bound 2 eps G max|e| per pass in FP32 (the FP32 path rounds its input)
+    gain = max(table_gain(5, C) for C in range(20, 49))
+    tol = 1e-11 if dtype == fcsdnn.F64 else 4 * EPS[dtype] * gain
+    print(f"initial smearing {name} dtype={dtype} err={err:.3e} tol {tol:.1e} (changed the state by {change:.2e})")
     assert change > 1e-3
-    assert err < (1e-11 if dtype == fcsdnn.F64 else 2e-5)
+    assert err < tol
