@@ -443,7 +443,8 @@ def run_ours(args):
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
-                "config": config(args, points),
+                "config": dict(config(args, points), tile_width=ctx.tile_width,
+                               launches_per_stage=ctx.launches["stage_visc"] + ctx.launches["exchange"]),
                 "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
                         "note": "pinned host state -> device, one graph-captured step, state -> host"},
                 "gpu_launches": launches["n"],
