@@ -906,12 +906,14 @@ __device__ __forceinline__ void tl_deriv_pair(const T* a, int sa, const T* b, in
     }
     return z;
   };
-  // ---- stage 1: 8-point DFTs over a for each owned b
+  // ---- stage 1: 8-point DFTs over a for each owned b (a rolled loop over
+  // the columns keeps one copy of its body: the unrolled FFT is large and
+  // instruction fetch stalls the warps)
   Cx<T> x[B];
-#pragma unroll
+#pragma unroll 1
   for (int i = 0; i < NB; ++i) {
     const int bb = t + 8 * i;
-    Cx<T>* v = x + 8 * i;
+    Cx<T> v[8];
 #pragma unroll
     for (int aa = 0; aa < 8; ++aa) v[aa] = input(bb + B * aa);
     rdft_fwd<T, 8>(v);
@@ -957,10 +959,10 @@ __device__ __forceinline__ void tl_deriv_pair(const T* a, int sa, const T* b, in
     tile[t * (B + 1) + bb] = cmul(x[bb], w);
   }
   __syncwarp();
-#pragma unroll
+#pragma unroll 1
   for (int i = 0; i < NB; ++i) {
     const int bb = t + 8 * i;
-    Cx<T>* v = x + 8 * i;
+    Cx<T> v[8];
     static_for<0, 8>([&](auto P) {
       constexpr int p = decltype(P)::value;
       v[p] = tile[Sigma<8, p>::value * (B + 1) + bb];
