@@ -242,12 +242,14 @@ __global__ void __launch_bounds__(kWarps * 32, 4) k_xpass(CtxDev c, int lbeg, in
 }
 
 // Pass along q2 on a tile of tw adjacent columns of one patch (coalesced row
-// segments staged in shared memory): L = (R - d/dq2 F2)/J, then either L
+// segments staged in shared memory; 3 blocks of 8 warps per SM up to n = 96,
+// 2 above, where the line registers of the FFT would spill at 80 registers
+// per thread): L = (R - d/dq2 F2)/J, then either L
 // (MODE_RHS) or the Runge-Kutta stage with boundary conditions (MODE_RK).
 // Curvilinear viscous columns read e_q1 from G1 (left by the row pass; rows
 // without viscosity leave stale values there, which only meet mu = 0).
 template <typename T, int MODE, int N1>
-__global__ void __launch_bounds__(kYWarps * 32, 3) k_ypass(CtxDev c, const int2* __restrict__ tiles, int ntiles,
+__global__ void __launch_bounds__(kYWarps * 32, (N1 >= 1 && N1 <= 3) ? 3 : 2) k_ypass(CtxDev c, const int2* __restrict__ tiles, int ntiles,
                                                          const T* __restrict__ e, const T* __restrict__ mu,
                                                          const T* __restrict__ R, const T* __restrict__ G1,
                                                          StageArgs<T> st) {
