@@ -127,17 +127,18 @@ class PatchGeom:
 
 def _zero_normal_viscous(V1, V2, patch):
     """Zero normal viscous flux on wall, outflow and free sides, and on the
-    inner (wall) edges of an L-shaped patch."""
+    inner (wall) edges of an L-shaped patch.  On a no-slip adiabatic wall only
+    the mass and energy fluxes vanish (impermeable, adiabatic); the momentum
+    flux, the wall shear of the viscous layer, stays."""
     noflux = (I.BC_WALL, I.BC_OUTFLOW, I.BC_FREE)
     bc = patch.bc
-    if bc[0] in noflux:
-        V1[:, :, 0] = 0.0
-    if bc[1] in noflux:
-        V1[:, :, -1] = 0.0
-    if bc[2] in noflux:
-        V2[:, 0, :] = 0.0
-    if bc[3] in noflux:
-        V2[:, -1, :] = 0.0
+    for side, V, idx in ((0, V1, (slice(None), 0)), (1, V1, (slice(None), -1)),
+                         (2, V2, (0, slice(None))), (3, V2, (-1, slice(None)))):
+        if bc[side] in noflux:
+            V[(slice(None),) + idx] = 0.0
+        elif bc[side] == I.BC_NOSLIP:
+            V[(0,) + idx] = 0.0
+            V[(3,) + idx] = 0.0
     if patch.is_l:
         m1, m2 = patch.lcut
         V1[:, :m2, m1] = 0.0
@@ -242,13 +243,65 @@ def _sides(patch):
     return out
 
 
+def neumann_weights(d):
+    """Weights w_0..w_{d-1} of the derivative at node 0 of the polynomial that
+    interpolates values on the nodes 0, 1, ..., d-1 (unit spacing):
+    p'(0) = sum_k w_k f_k.  These are the derivatives at 0 of the Lagrange
+    basis polynomials, written out as sums of products."""
+    w = np.zeros(d)
+    for k in range(d):
+        tot = 0.0
+        for j in range(d):
+            if j == k:
+                continue
+            term = 1.0 / (k - j)
+            for m in range(d):
+                if m != k and m != j:
+                    term *= (0.0 - m) / (k - m)
+            tot += term
+        w[k] = tot
+    return w
+
+
+def _inward(side, k, n1, n2):
+    """Index (rows, columns) of the points k steps inside from a side."""
+    if side == 0:
+        return (slice(None), k)
+    if side == 1:
+        return (slice(None), n1 - 1 - k)
+    if side == 2:
+        return (k, slice(None))
+    return (n2 - 1 - k, slice(None))
+
+
+def check_noslip(patch):
+    """No-slip sides are supported on rectangular patches whose adjacent sides
+    are not no-slip (each wall point's inward line then holds no other wall's
+    point)."""
+    bc = patch.bc
+    if I.BC_NOSLIP not in bc:
+        return
+    if patch.is_l:
+        raise ValueError("no-slip sides on an L-shaped patch are not supported")
+    for a, b in ((0, 2), (0, 3), (1, 2), (1, 3)):
+        if bc[a] == I.BC_NOSLIP and bc[b] == I.BC_NOSLIP:
+            raise ValueError("adjacent no-slip sides are not supported")
+
+
 def apply_bc(e, geom, inst):
     """Boundary conditions of one patch, sides in the order left, right, bottom,
     top (then the inner wall edges of an L-shaped patch).
 
     Wall: normal momentum removed (Cartesian: the normal component is set to
     zero); inflow: the prescribed conserved state; outflow: energy recomputed
-    for the prescribed pressure.  Acts in place on e (4, n2, n1).
+    for the prescribed pressure; no-slip adiabatic wall (§2, §7: zero velocity,
+    zero normal derivative of the temperature, enforced through E): momentum
+    set to zero, then, once every side's pointwise condition is in place, the
+    temperature theta = p / rho of each wall point is the value for which the
+    polynomial through theta at the d points of its inward grid line (the
+    matching points of the FC-Gram continuation there) has zero derivative
+    along that line, and E = rho theta / (gamma - 1).  Acts in place on e
+    (4, n2, n1).
     """
     gamma = inst.gamma
     for side, code, idx in _sides(geom.patch):
@@ -289,6 +342,23 @@ def apply_bc(e, geom, inst):
             mx = e[(1,) + idx[1:]]
             my = e[(2,) + idx[1:]]
             e[(3,) + idx[1:]] = inst.p_out / (gamma - 1.0) + 0.5 * (mx * mx + my * my) / rho
+        elif code == I.BC_NOSLIP:
+            e[(1,) + idx[1:]] = 0.0
+            e[(2,) + idx[1:]] = 0.0
+    if I.BC_NOSLIP in geom.patch.bc:
+        check_noslip(geom.patch)
+        w = neumann_weights(geom.d)
+        n1, n2 = geom.patch.n1, geom.patch.n2
+        for side, code in enumerate(geom.patch.bc):
+            if code != I.BC_NOSLIP:
+                continue
+            acc = 0.0
+            for k in range(1, geom.d):
+                ik = _inward(side, k, n1, n2)
+                acc = acc + w[k] * pressure(e[(slice(None),) + ik], gamma) / e[(0,) + ik]
+            i0 = _inward(side, 0, n1, n2)
+            theta0 = -acc / w[0]
+            e[(3,) + i0] = e[(0,) + i0] * theta0 / (gamma - 1.0)
     return e
 
 
@@ -542,6 +612,8 @@ class Solver:
     def __init__(self, inst, d=5, C=25, n_f=5, cfl=0.5, c_policy=0):
         self.inst = inst
         self.d, self.C, self.n_f, self.cfl = d, C, n_f, cfl
+        for p in inst.patches:
+            check_noslip(p)
         self.geoms = [PatchGeom(p, d, C, c_policy) for p in inst.patches]
         self.fmap = fringe_map(inst.patches, n_f)
 

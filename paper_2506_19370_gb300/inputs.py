@@ -30,6 +30,7 @@ BC_WALL = 1       # slip / reflecting wall: normal momentum set to zero
 BC_INFLOW = 2     # Dirichlet: all four conserved variables prescribed
 BC_OUTFLOW = 3    # pressure prescribed, energy recomputed
 BC_FREE = 4       # nothing imposed (supersonic outflow)
+BC_NOSLIP = 5     # no-slip adiabatic wall: momentum zero, zero normal temperature derivative
 
 
 @dataclass
@@ -212,20 +213,20 @@ def annulus_patch(n1=48, n2=32, r0=0.5, r1=1.0, th0=0.3, th1=1.4, bc=(BC_FREE,) 
     return Patch(n1, n2, tuple(bc), x=r * np.cos(th), y=r * np.sin(th))
 
 
-def annulus_ring(sizes=((64, 24), (56, 20), (72, 28)), r0=0.5, r1=1.0, overlap=0.9, rot=0.0):
+def annulus_ring(sizes=((64, 24), (56, 20), (72, 28)), r0=0.5, r1=1.0, overlap=0.9, rot=0.0, wall=BC_WALL):
     """Annulus r0 <= r <= r1 covered by overlapping curvilinear sectors.
 
     Sector k has sizes[k] = (n1, n2) points (angle, radius) and spans the
     angles [k 2pi/P - overlap/2, (k+1) 2pi/P + overlap/2] + rot; the sectors'
     grids differ, so their fringes are filled by interpolation.  Angle sides
-    are internal, r = r0 a wall (the cylinder), r = r1 free.
+    are internal, r = r0 a wall of kind `wall` (the cylinder), r = r1 free.
     """
     P = len(sizes)
     patches = []
     for k, (n1, n2) in enumerate(sizes):
         th0 = rot + k * 2 * np.pi / P - overlap / 2
         th1 = rot + (k + 1) * 2 * np.pi / P + overlap / 2
-        patches.append(annulus_patch(n1, n2, r0, r1, th0, th1, bc=(BC_INTERNAL, BC_INTERNAL, BC_WALL, BC_FREE)))
+        patches.append(annulus_patch(n1, n2, r0, r1, th0, th1, bc=(BC_INTERNAL, BC_INTERNAL, wall, BC_FREE)))
     return patches
 
 
@@ -332,7 +333,7 @@ def ffs_ensemble(h0s, machs, length=3.0, gap=1.0):
 
 
 def cylinder_instance(h=0.01, R=0.5, r_out=None, box=(-3.0, 4.0, -3.0, 3.0), sectors=16, mach=10.0, delta_pts=8,
-                      seed=SEED, ell=0.15):
+                      seed=SEED, ell=0.15, wall=BC_WALL):
     """Mach-`mach` flow past a circular cylinder of radius R at the origin.
 
     Body-fitted curvilinear annular sectors (angle along q1, radius along q2,
@@ -343,7 +344,8 @@ def cylinder_instance(h=0.01, R=0.5, r_out=None, box=(-3.0, 4.0, -3.0, 3.0), sec
     extended box comes closer than R + 0.1 to the centre are left out (the
     annulus covers them: by default r_out leaves room for such a cell and the
     annulus fringe).  Left: inflow, right: free (supersonic outflow),
-    bottom/top: walls.  Initial state: the Mach flow (1.4, mach, 0, 1) of §7
+    bottom/top: slip walls; the cylinder: a wall of kind `wall` (BC_WALL slip,
+    BC_NOSLIP no-slip adiabatic as in §7).  Initial state: the Mach flow (1.4, mach, 0, 1) of §7
     with the velocity brought to rest smoothly at the cylinder wall (factor
     1 - exp(-((r - R)/ell)^2)).
     """
@@ -362,7 +364,7 @@ def cylinder_instance(h=0.01, R=0.5, r_out=None, box=(-3.0, 4.0, -3.0, 3.0), sec
         th1 = (k + 1) * 2 * np.pi / sectors + overlap / 2
         hs = h * (1 + 0.15 * rng.uniform(-1.0, 1.0))
         n1 = int(round((th1 - th0) * r_mid / hs)) + 1
-        p = annulus_patch(n1, n2, R, r_out, th0, th1, bc=(BC_INTERNAL, BC_INTERNAL, BC_WALL, BC_INTERNAL))
+        p = annulus_patch(n1, n2, R, r_out, th0, th1, bc=(BC_INTERNAL, BC_INTERNAL, wall, BC_INTERNAL))
         p.kind = "S"
         patches.append(p)
     x0, x1, y0, y1 = box
@@ -399,7 +401,7 @@ def cylinder_instance(h=0.01, R=0.5, r_out=None, box=(-3.0, 4.0, -3.0, 3.0), sec
         f = 1.0 - np.exp(-((np.hypot(X, Y) - R) / ell) ** 2)
         state.append(conserved(np.full(X.shape, 1.4), mach * f, 0.0, 1.0))
     return Instance(patches, state, inflow=tuple(float(a) for a in conserved(1.4, mach, 0.0, 1.0)), p_out=1.0,
-                    name="cylinder", meta=dict(h=h, R=R, r_out=r_out, mach=mach))
+                    name="cylinder", meta=dict(h=h, R=R, r_out=r_out, mach=mach, wall=wall))
 
 
 def mach_flow_state(M, gamma=GAMMA):

@@ -366,3 +366,106 @@ def test_filter_state_keeps_uniform_and_smooth_states():
     sl = I.random_state(lp, np.random.default_rng(4))
     fl = euler.filter_state(sl, gl, G)
     assert np.abs(fl - sl).max() < 1e-8
+
+
+def test_neumann_weights_are_the_one_sided_difference_formulas():
+    # textbook one-sided first-derivative formulas on 2..6 points (unit spacing)
+    table = {2: [-1, 1], 3: [-3 / 2, 2, -1 / 2], 4: [-11 / 6, 3, -3 / 2, 1 / 3],
+             5: [-25 / 12, 4, -3, 4 / 3, -1 / 4], 6: [-137 / 60, 5, -5, 10 / 3, -5 / 4, 1 / 5]}
+    for d, w in table.items():
+        assert np.allclose(euler.neumann_weights(d), w, rtol=0, atol=1e-13)
+
+
+def _theta(e):
+    return euler.pressure(e, G) / e[0]
+
+
+def _with_theta(rho, mx, my, theta):
+    return np.stack([rho, mx, my, rho * theta / (G - 1) + 0.5 * (mx * mx + my * my) / rho])
+
+
+def test_noslip_adiabatic_wall_on_curvilinear_sector():
+    # wall at r = r0 (side 2, q2 = 0): theta along each radial line is a
+    # cubic in the index j with zero slope at the wall, so the wall value the
+    # Neumann condition gives is its value a(i) there
+    ring = I.annulus_ring(wall=I.BC_NOSLIP)
+    p = ring[0]
+    inst = I.Instance(ring, [np.zeros((4, q.n2, q.n1)) for q in ring])
+    s = euler.Solver(inst, c_policy=1)
+    rng = np.random.default_rng(3)
+    j = np.arange(p.n2)[:, None].astype(float)
+    a = 1.0 + 0.2 * rng.random(p.n1)
+    theta = a + 0.01 * j ** 2 - 0.001 * j ** 3
+    theta[0] += 0.3                                   # wall value to be replaced
+    rho = 1.0 + 0.1 * rng.random((p.n2, p.n1))
+    e = _with_theta(rho, 0.4 * rng.standard_normal((p.n2, p.n1)), 0.2 * rng.standard_normal((p.n2, p.n1)), theta)
+    before = e.copy()
+    euler.apply_bc(e, s.geoms[0], inst)
+    assert np.all(e[1:3, 0, :] == 0.0)                                      # no slip
+    assert np.abs(_theta(e[:, 0, :]) - a).max() < 1e-12                     # adiabatic
+    assert np.allclose(e[3, 0, :], e[0, 0, :] * a / (G - 1), rtol=1e-13)
+    assert np.array_equal(e[:, 1:, :], before[:, 1:, :])                    # interior untouched
+    assert np.array_equal(e[0], before[0])                                  # density free
+
+
+def test_noslip_adiabatic_walls_on_opposite_sides():
+    # left and right no-slip, bottom/top slip: theta = 1 + c i^2 (N - i)^2 has
+    # zero slope at both ends and degree 4 < d, so both wall values are 1
+    n1, n2 = 30, 12
+    p = I.Patch(n1, n2, (I.BC_NOSLIP, I.BC_NOSLIP, I.BC_WALL, I.BC_WALL), box=(0.0, 1.0, 0.0, 0.4))
+    inst = I.Instance([p], [np.zeros((4, n2, n1))])
+    s = euler.Solver(inst)
+    i = np.arange(n1)[None, :].astype(float)
+    theta = np.broadcast_to(1.0 + 1e-5 * i ** 2 * (n1 - 1 - i) ** 2, (n2, n1)).copy()
+    theta[:, 0] = theta[:, -1] = 7.0
+    e = _with_theta(np.full((n2, n1), 1.3), np.full((n2, n1), 0.5), np.full((n2, n1), -0.2), theta)
+    euler.apply_bc(e, s.geoms[0], inst)
+    for col in (0, -1):
+        assert np.all(e[1:3, :, col] == 0.0)
+        # (corner rows excluded: their inward points lie on the slip walls,
+        # whose condition removed kinetic energy and so changed theta there)
+        assert np.abs(_theta(e[:, 1:-1, col]) - 1.0).max() < 1e-12
+    assert np.all(e[2, 0, 1:-1] == 0.0) and np.all(e[2, -1, 1:-1] == 0.0)   # slip walls
+    assert np.allclose(e[1, 0, 1:-1], 0.5)
+
+
+def test_noslip_viscous_flux_keeps_wall_shear():
+    p = I.Patch(8, 8, (I.BC_INTERNAL, I.BC_FREE, I.BC_NOSLIP, I.BC_WALL), box=(0.0, 1.0, 0.0, 1.0))
+    V1, V2 = np.ones((4, 8, 8)), np.ones((4, 8, 8))
+    euler._zero_normal_viscous(V1, V2, p)
+    assert np.all(V2[[0, 3], 0, :] == 0.0) and np.all(V2[[1, 2], 0, :] == 1.0)   # no-slip: mass, energy
+    assert np.all(V2[:, -1, :] == 0.0) and np.all(V1[:, :, -1] == 0.0)            # slip wall, free side
+    assert np.all(V1[:, :, 0] == 1.0)                                             # internal side
+
+
+def test_noslip_layout_checks():
+    bad = I.Patch(8, 8, (I.BC_NOSLIP, I.BC_FREE, I.BC_NOSLIP, I.BC_FREE), box=(0.0, 1.0, 0.0, 1.0))
+    with pytest.raises(ValueError):
+        euler.Solver(I.Instance([bad], [np.zeros((4, 8, 8))]))
+    lp = _l_patch(False)
+    lp.bc = (I.BC_NOSLIP,) + tuple(lp.bc[1:])
+    with pytest.raises(ValueError):
+        euler.check_noslip(lp)
+
+
+def test_noslip_ring_steps_keep_the_wall_conditions():
+    patches = I.annulus_ring(wall=I.BC_NOSLIP)
+    state = []
+    for p in patches:
+        X, Y = p.coords()
+        r = np.hypot(X, Y)
+        f = 1.0 - np.exp(-((r - 0.5) / 0.15) ** 2)
+        state.append(I.conserved(np.full(X.shape, 1.4), 0.8 * f * (-Y / r), 0.8 * f * (X / r), 1.0))
+    inst = I.Instance(patches, state)
+    s = euler.Solver(inst, c_policy=1)
+    st = [e.copy() for e in state]
+    mu = [np.full((p.n2, p.n1), 2e-4) for p in patches]
+    for _ in range(3):
+        st = s.step(st, 2e-4, mu)
+    w = euler.neumann_weights(5)
+    for e in st:
+        inner = slice(s.n_f, e.shape[2] - s.n_f)           # wall points outside the angle fringes
+        assert np.all(e[1:3, 0, inner] == 0.0)
+        th = _theta(e[:, :5, inner])
+        assert np.abs(w @ th).max() < 1e-12 * np.abs(th).max()
+        assert np.all(np.isfinite(e))
