@@ -65,7 +65,16 @@ typedef enum {
   FCS_BC_WALL = 1,      /* slip/reflecting wall: normal momentum set to 0 */
   FCS_BC_INFLOW = 2,    /* all conserved variables set to options.inflow */
   FCS_BC_OUTFLOW = 3,   /* pressure set to options.p_out, E recomputed */
-  FCS_BC_FREE = 4       /* nothing imposed */
+  FCS_BC_FREE = 4,      /* nothing imposed */
+  FCS_BC_NOSLIP = 5     /* no-slip adiabatic wall (paper §2, §7): momentum set
+                           to 0; the temperature theta = p/rho of the wall point
+                           is the value for which the polynomial through theta at
+                           the d points of its inward grid line has zero
+                           derivative there, E = rho theta/(gamma-1).  The
+                           viscous mass and energy fluxes through the side are
+                           zero, the momentum flux (wall shear) is kept.  Only
+                           on rectangular patches, and never on two adjacent
+                           sides of one patch (FCS_EUNSUPPORTED) */
 } fcs_bc;
 
 /* One patch (paper §3.1-3.2: patches are images of Cartesian parameter
@@ -142,8 +151,10 @@ typedef struct {
   const int64_t* scalar_off;  /* per patch offset in the scalar layout */
   const int64_t* window_off;  /* per patch offset of its first window */
   int tile_width;             /* columns per CTA of the pass along q2 (autotuned or widest) */
-  int launches_stage;         /* kernel launches of one rk_stage / euler_rhs call without viscosity
-                                 (one row pass and one column pass per FFT-size group) */
+  int launches_stage;         /* kernel launches of one rk_stage call without viscosity (one row
+                                 pass and one column pass per FFT-size group, plus the no-slip
+                                 wall temperature when the layout has FCS_BC_NOSLIP sides;
+                                 euler_rhs launches that one fewer) */
   int launches_stage_visc;    /* the same with viscosity (adds the e_q2 pass of curvilinear patches) */
   int launches_exchange;      /* kernel launches of one patch_exchange call (copies, interpolations) */
   int launches_av;            /* kernel launches of one av_assemble call (exchange included) */

@@ -71,6 +71,7 @@ struct fcs_ctx {
   void* G2 = nullptr;
   int2* tiles = nullptr;
   int2* pblk = nullptr;  // point blocks of the pointwise kernels
+  int4* nsw = nullptr;   // no-slip wall points (patch, point, inward stride)
   int4* btiles = nullptr;  // 32 x 32 output tiles of the viscosity blend (patch, i0, j0)
   int nbtiles = 0;
   int4* fringe_ent = nullptr;     // copies: (dst patch, dst point, src patch, src point)
@@ -330,6 +331,10 @@ int launch_flux(fcs_ctx* c, const void* e, const void* mu, int mode, StageArgs<T
       FCS_N1_SWITCH(gr.n1, FCS_CUDA((run_ypass<T, MODE_RK, K>(c->dev, tl, gr.count, ep, mp, R, G1, st, gy))); break)
     }
   }
+  if (mode == MODE_RK && c->dev.n_nsw > 0) {  // no-slip walls: temperature after every point's stage
+    k_noslip_temperature<T><<<dim3((c->dev.n_nsw + 127) / 128, c->opt.instances), 128, 0, s>>>(c->dev, st.out);
+    FCS_CUDA(cudaGetLastError());
+  }
   return FCS_OK;
 }
 
@@ -577,7 +582,7 @@ int fc_setup(fcs_ctx** out, int d, int C, const fcs_patch_desc* pd, int npatch, 
     const fcs_patch_desc& q = pd[p];
     if (q.n1 < 16 || q.n2 < 16 || q.n1 > 256 || q.n2 > 256) return FCS_EINVAL;
     for (int s = 0; s < 4; ++s)
-      if (q.bc[s] < 0 || q.bc[s] > 4) return FCS_EINVAL;
+      if (q.bc[s] < 0 || q.bc[s] > 5) return FCS_EINVAL;
     if (q.cartesian) {
       if (!(q.box[1] > q.box[0]) || !(q.box[3] > q.box[2])) return FCS_EINVAL;
     } else {
@@ -587,6 +592,11 @@ int fc_setup(fcs_ctx** out, int d, int C, const fcs_patch_desc* pd, int npatch, 
     if (q.lcut[0] != 0 || q.lcut[1] != 0) {  // L-shaped: both cuts, segments of >= 16 points
       if (q.lcut[0] <= 0 || q.lcut[1] <= 0 || q.n1 - q.lcut[0] < 16 || q.n2 - q.lcut[1] < 16) return FCS_EINVAL;
     }
+    // no-slip walls: rectangular patches, never on two adjacent sides (a wall
+    // point's inward line must hold no other wall point)
+    const bool ns[4] = {q.bc[0] == 5, q.bc[1] == 5, q.bc[2] == 5, q.bc[3] == 5};
+    if ((ns[0] || ns[1] || ns[2] || ns[3]) && (q.lcut[0] != 0 || q.lcut[1] != 0)) return FCS_EUNSUPPORTED;
+    if ((ns[0] || ns[1]) && (ns[2] || ns[3])) return FCS_EUNSUPPORTED;
   }
   fcs_ctx* c = new fcs_ctx();
   c->opt = o;
@@ -759,6 +769,20 @@ int fc_setup(fcs_ctx** out, int d, int C, const fcs_patch_desc* pd, int npatch, 
   std::vector<int2> pblk;
   for (int p = 0; p < npatch; ++p)
     for (int s0 = 0; s0 < pd[p].n1 * pd[p].n2; s0 += 256) pblk.push_back(make_int2(p, s0));
+  // no-slip wall points: (patch, point, stride towards the interior)
+  std::vector<int4> nsw;
+  for (int p = 0; p < npatch; ++p) {
+    const int n1 = pd[p].n1, n2 = pd[p].n2;
+    for (int sd = 0; sd < 4; ++sd) {
+      if (pd[p].bc[sd] != 5) continue;
+      const int cnt = sd < 2 ? n2 : n1;
+      for (int k = 0; k < cnt; ++k) {
+        const int i = sd == 0 ? 0 : (sd == 1 ? n1 - 1 : k), j = sd == 2 ? 0 : (sd == 3 ? n2 - 1 : k);
+        const int stride = sd == 0 ? 1 : (sd == 1 ? -1 : (sd == 2 ? n1 : -n1));
+        nsw.push_back(make_int4(p, j * n1 + i, stride, 0));
+      }
+    }
+  }
   std::vector<int4> btiles;  // blend tiles holding at least one point of the patch
   for (int p = 0; p < npatch; ++p)
     for (int j0 = 0; j0 < pd[p].n2; j0 += kBlendTile)
@@ -910,6 +934,7 @@ int fc_setup(fcs_ctx** out, int d, int C, const fcs_patch_desc* pd, int npatch, 
       (rc = upload(c, &c->fpairs[1], fp[1].data(), fp[1].size() * sizeof(int4))) ||
       (rc = upload(c, &c->tiles, tiles.data(), tiles.size() * sizeof(int2))) ||
       (rc = upload(c, &c->pblk, pblk.data(), pblk.size() * sizeof(int2))) ||
+      (rc = upload(c, &c->nsw, nsw.data(), nsw.size() * sizeof(int4))) ||
       (rc = upload(c, &c->btiles, btiles.data(), btiles.size() * sizeof(int4))) ||
       (rc = upload(c, &dwin, wins.data(), wins.size() * sizeof(int4))) ||
       (rc = upload(c, &dfr, fringe.data(), fringe.size())) ||
@@ -976,6 +1001,25 @@ int fc_setup(fcs_ctx** out, int d, int C, const fcs_patch_desc* pd, int npatch, 
   D.gramT = dgt;
   D.pblk = c->pblk;
   D.npblk = (int)pblk.size();
+  D.nsw = c->nsw;
+  D.n_nsw = (int)nsw.size();
+  // derivative at node 0 of the interpolant on nodes 0..d-1: for node m > 0
+  // its basis polynomial has the root 0, so the derivative there is the rest
+  // of the product at 0 over m; node 0 takes minus the sum of the others
+  // (a constant has zero derivative)
+  {
+    double w0 = 0.0;
+    for (int m = 1; m < d; ++m) {
+      double pr = 1.0 / m;
+      for (int r = 1; r < d; ++r)
+        if (r != m) pr *= (double)(-r) / (double)(m - r);
+      D.nsw64[m] = pr;
+      D.nsw32[m] = (float)pr;
+      w0 -= pr;
+    }
+    D.nsw64[0] = w0;
+    D.nsw32[0] = (float)w0;
+  }
   D.tw = c->tw;
   D.n2max = c->n2max;
   if ((rc = (o.dtype == FCS_F64 ? set_smem_attrs<double>(c) : set_smem_attrs<float>(c)))) return fail(rc);
@@ -1047,7 +1091,7 @@ int fcs_get_layout(const fcs_ctx* c, fcs_layout* o) {
   o->scalar_off = c->scalar_off.data();
   o->window_off = c->window_off.data();
   o->tile_width = c->tw;
-  o->launches_stage = (int)(c->g_rows.size() + c->g_tiles.size());
+  o->launches_stage = (int)(c->g_rows.size() + c->g_tiles.size()) + (c->dev.n_nsw > 0);
   o->launches_stage_visc = o->launches_stage + (int)c->g_vpairs.size();
   o->launches_exchange = (c->nent > 0) + (c->ninterp > 0);
   o->launches_av = 1 + (c->opt.av_radius <= kBlendMaxR ? 1 : 4) + o->launches_exchange;
@@ -1301,6 +1345,12 @@ int filter_impl(fcs_ctx* c, void* e, const CtxDev& dev, const void* w, cudaStrea
     k_filter_done<float><<<g, 256, 0, s>>>(dev, static_cast<const float*>(c->R), static_cast<float*>(e), (float)gm1,
                                            static_cast<const float*>(w));
   FCS_CUDA(cudaGetLastError());
+  if (dev.n_nsw > 0) {  // no-slip walls: temperature from the filtered interior
+    const dim3 gw((dev.n_nsw + 127) / 128, c->opt.instances);
+    if (f64) k_noslip_temperature<double><<<gw, 128, 0, s>>>(dev, static_cast<double*>(e));
+    else k_noslip_temperature<float><<<gw, 128, 0, s>>>(dev, static_cast<float*>(e));
+    FCS_CUDA(cudaGetLastError());
+  }
   return exchange_impl(c, e, 4, 0, s);
 }
 

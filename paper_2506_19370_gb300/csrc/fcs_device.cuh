@@ -88,6 +88,10 @@ struct CtxDev {
   const float* gramT;           // Gram blend tables of all plans (FP32)
   const int2* pblk;             // point blocks of 256 points: (patch, first point), one instance
   int npblk;
+  const int4* nsw;              // no-slip wall points: (patch, point, inward stride in points, 0)
+  int n_nsw;
+  double nsw64[8];              // d weights of the derivative at node 0 on nodes 0..d-1
+  float nsw32[8];
 };
 
 // Point handled by this thread in a pointwise kernel launched on
@@ -441,6 +445,9 @@ __device__ __forceinline__ void apply_bc(const CtxDev& c, const PatchDev& P, int
       v[3] = inflow_of<T>(P, 3);
     } else if (code == 3) {  // outflow pressure
       v[3] = p_out_of<T>(c) / gm1 + T(0.5) * (v[1] * v[1] + v[2] * v[2]) / v[0];
+    } else if (code == 5) {  // no-slip wall: momentum (its temperature: k_noslip_temperature)
+      v[1] = T(0);
+      v[2] = T(0);
     }
   }
   if (P.m1 > 0) {

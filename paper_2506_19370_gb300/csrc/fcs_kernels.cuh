@@ -121,6 +121,37 @@ __global__ void k_filter_done(CtxDev c, const T* __restrict__ W, T* e, T gm1, co
   for (int f = 0; f < 4; ++f) e[o + f * np] = v[f];
 }
 
+// No-slip adiabatic wall (FCS_BC_NOSLIP): the temperature theta = p / rho of
+// a wall point is the value for which the polynomial through theta at the d
+// points of its inward grid line has zero derivative at the wall,
+// sum_m w_m theta_m = 0 with w the derivative weights at node 0; momentum is
+// zero there (set by apply_bc), so E = rho theta / (gamma - 1).  Thread per
+// wall point (x) and instance (y).  A wall point's line holds no other wall
+// point (no two adjacent sides are no-slip), so reads and writes never meet.
+template <typename T>
+__global__ void k_noslip_temperature(CtxDev c, T* __restrict__ e) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= c.n_nsw) return;
+  const int4 w = c.nsw[k];
+  const PatchDev& P = c.patches[w.x];
+  const int np = P.n1 * P.n2;
+  T* s = e + blockIdx.y * c.sstride + P.soff;
+  const T gm1 = gm1_of<T>(c);
+  T acc = T(0);
+#pragma unroll
+  for (int m = 1; m < 8; ++m) {
+    if (m >= c.d) break;
+    const int q = w.y + m * w.z;
+    const T rho = s[q];
+    const T th = pressure<T>(rho, s[q + np], s[q + 2 * np], s[q + 3 * np], gm1) / rho;
+    acc += (sizeof(T) == 8 ? T(c.nsw64[m]) : T(c.nsw32[m])) * th;
+  }
+  const T theta0 = -acc / (sizeof(T) == 8 ? T(c.nsw64[0]) : T(c.nsw32[0]));
+  s[w.y + np] = T(0);
+  s[w.y + 2 * np] = T(0);
+  s[w.y + 3 * np] = s[w.y] * theta0 / gm1;
+}
+
 // Smearing window seed: 1 where tau is 1 (jump), else 0.
 template <typename T>
 __global__ void k_smear_seed(CtxDev c, const signed char* __restrict__ tau, T* w0) {

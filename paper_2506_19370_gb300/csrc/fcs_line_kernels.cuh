@@ -83,9 +83,13 @@ __global__ void __launch_bounds__(kWarps * 32) k_fc_deriv(CtxDev c, int dir, int
 template <typename T, int DIR>
 __device__ __forceinline__ void point_flux(const CtxDev& c, const PatchDev& P, long long q, const T* v, const T* dv,
                                            const T* dvo, T mu, bool visc, T* F, int t, int N, int code_lo) {
+  // fields whose viscous flux this point keeps: none on the closed end points
+  // (wall, outflow, free), momentum only on a no-slip wall
+  int vmask = 15;
   if (visc) {
     const int code = t == 0 ? code_lo : (t == N - 1 ? P.bc[2 * DIR + 1] : 0);
     if (code == 1 || code == 3 || code == 4) visc = false;
+    if (code == 5) vmask = 6;
   }
   const T gm1 = gm1_of<T>(c);
   const T rho = v[0], mx = v[1], my = v[2], En = v[3];
@@ -99,7 +103,8 @@ __device__ __forceinline__ void point_flux(const CtxDev& c, const PatchDev& P, l
     }
     if (visc) {
 #pragma unroll
-      for (int f = 0; f < 4; ++f) F[f] -= mu * dv[f];
+      for (int f = 0; f < 4; ++f)
+        if (vmask >> f & 1) F[f] -= mu * dv[f];
     }
   } else {
     const T* Mt = metrics<T>(c);
@@ -119,7 +124,7 @@ __device__ __forceinline__ void point_flux(const CtxDev& c, const PatchDev& P, l
       for (int f = 0; f < 4; ++f) {
         const T d1 = DIR == 0 ? dv[f] : dvo[f], d2 = DIR == 0 ? dvo[f] : dv[f];
         const T ex = (y_q2 * d1 - y_q1 * d2) * invJ, ey = (-x_q2 * d1 + x_q1 * d2) * invJ;
-        F[f] -= mu * (ca * ex + cb * ey);
+        if (vmask >> f & 1) F[f] -= mu * (ca * ex + cb * ey);
       }
     }
   }

@@ -46,6 +46,29 @@ def layout(name):
             st.append(I.conserved(1.4 * (1 + 0.05 * np.sin(a * X + b * Y)), 0.4 + 0.05 * np.cos(b * X), 0.2,
                                   1.0 + 0.05 * np.cos(a * Y)))
         return I.Instance(pts, st, name="ring"), 1
+    if name == "ringns":
+        # the ring with a no-slip adiabatic wall at r = 0.5 and a swirling
+        # flow brought to rest smoothly at the wall
+        pts = I.annulus_ring(sizes=((64, 24), (100, 30), (72, 28)), wall=I.BC_NOSLIP)
+        st = []
+        for p in pts:
+            X, Y = p.coords()
+            r = np.hypot(X, Y)
+            f = 1.0 - np.exp(-((r - 0.5) / 0.15) ** 2)
+            st.append(I.conserved(1.4 * (1 + 0.05 * np.sin(3 * X + Y)), 0.6 * f * (-Y / r) + 0.1 * f,
+                                  0.6 * f * (X / r), 1.0 + 0.05 * np.cos(2 * Y)))
+        return I.Instance(pts, st, name="ringns"), 1
+    if name == "splitns":
+        # the four-patch split layout with no-slip adiabatic walls on the left
+        # and right outer sides (slip walls at the bottom and top)
+        inst, pol = layout("split")
+        for p in inst.patches:
+            p.bc = tuple(I.BC_NOSLIP if (k < 2 and b == I.BC_WALL) else b for k, b in enumerate(p.bc))
+        inst.name = "splitns"
+        return inst, pol
+    if name == "cylns":
+        # the Mach-10 cylinder with the paper's no-slip adiabatic body wall
+        return I.cylinder_instance(h=0.03, wall=I.BC_NOSLIP), 1
     if name in ("lbox", "lcurv"):
         # one L-shaped corner patch (60 x 52 grid, points i < 24, j < 20
         # missing), as a box or on a grid rotated by 90 degrees, walls around

@@ -157,7 +157,7 @@ def test_euler_rhs(name, dtype):
 
 
 @pytest.mark.parametrize("dtype", DTYPES)
-@pytest.mark.parametrize("name", ["sod", "annulus", "ring", "lbox", "lcurv"])
+@pytest.mark.parametrize("name", ["sod", "annulus", "ring", "lbox", "lcurv", "ringns", "splitns"])
 def test_euler_rhs_with_viscosity(name, dtype):
     inst, pol, ctx = ctx_for(name, dtype)
     st = random_states(inst, 12)
@@ -267,7 +267,8 @@ def test_interpolated_exchange(name, dtype):
 
 
 @pytest.mark.parametrize("dtype", DTYPES)
-@pytest.mark.parametrize("name", ["strip", "ring", "ffs", "lbox", "lcurv", "ensemble", "cylinder"])
+@pytest.mark.parametrize("name", ["strip", "ring", "ffs", "lbox", "lcurv", "ensemble", "cylinder", "ringns", "splitns",
+                                  "cylns"])
 def test_steps_with_interpolation(name, dtype):
     nsteps = 8
     inst, pol, ctx = ctx_for(name, dtype)
@@ -565,6 +566,14 @@ def test_invalid_arguments_rejected():
     with pytest.raises(fcsdnn.FcsError) as ei:
         fcsdnn.Context(bad, c_policy=1)
     assert ei.value.code == -2
+    # no-slip walls on two adjacent sides, or on an L-shaped patch: unsupported
+    adj = I.Instance([I.Patch(40, 40, (I.BC_NOSLIP, I.BC_WALL, I.BC_NOSLIP, I.BC_WALL), box=(0, 1, 0, 1))],
+                     [np.ones((4, 40, 40))])
+    lpt = I.Patch(60, 52, (I.BC_NOSLIP, I.BC_WALL, I.BC_WALL, I.BC_WALL), box=(0, 1, 0, 1), lcut=(24, 20), kind="C1")
+    for inst_bad in (adj, I.Instance([lpt], [np.ones((4, 52, 60))])):
+        with pytest.raises(fcsdnn.FcsError) as ei:
+            fcsdnn.Context(inst_bad, c_policy=1)
+        assert ei.value.code == -3
 
 
 @pytest.mark.parametrize("dtype", DTYPES)
@@ -587,7 +596,7 @@ def test_autotuned_tile_width_gives_identical_results(dtype):
 
 
 @pytest.mark.parametrize("dtype", DTYPES)
-@pytest.mark.parametrize("name", ["sod", "lbox", "lcurv", "ring"])
+@pytest.mark.parametrize("name", ["sod", "lbox", "lcurv", "ring", "ringns"])
 def test_spectral_filter(name, dtype):
     # filter of (rho, rho u, rho v, theta) along q1 then q2, E rebuilt, BCs,
     # exchange; the state carries seeded grid-scale noise so the filter acts
@@ -662,3 +671,46 @@ def test_initial_smearing(name, dtype):
     print(f"initial smearing {name} dtype={dtype} err={err:.3e} tol {tol:.1e} (changed the state by {change:.2e})")
     assert change > 1e-3
     assert err < tol
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("name", ["ringns", "splitns"])
+def test_noslip_stages_with_viscosity(name, dtype):
+    # two steps of four rk_stage + patch_exchange calls with a given viscosity:
+    # no-slip momentum and the wall temperature after every stage, the wall
+    # shear kept in the viscous fluxes
+    inst, pol, ctx = ctx_for(name, dtype)
+    solver = oracle_solver(inst, pol)
+    rng = np.random.default_rng(21)
+    mu = [2e-3 * rng.uniform(0.5, 1) * (1 + np.sin(p.coords()[0] * 5)) for p in inst.patches]
+    npd = np.float32 if dtype == fcsdnn.F32 else np.float64
+    mcast = [np.asarray(x, dtype=npd).astype(np.float64) for x in mu]
+    dt = 0.3 * solver.dt(inst.state, mcast)
+    e = ctx.to_device(ctx.pack_state(inst.state))
+    m = ctx.to_device(ctx.pack_scalar(mu))
+    S, A = ctx.new_state(), ctx.new_state()
+    ref = [x.copy() for x in inst.state]
+    for _ in range(2):
+        for s in range(4):
+            ctx.rk_stage(s, dt, e, e if s == 0 else S, A, e if s == 3 else S, mu=m)
+            ctx.patch_exchange(e if s == 3 else S, 4)
+        ref = solver.step(ref, dt, mcast)
+    torch.cuda.synchronize()
+    got = ctx.unpack_state(e)
+    err = rel_err(got, ref)
+    print(f"{name} 2 steps with viscosity dtype={dtype} err={err:.3e}")
+    assert err < (1e-9 if dtype == fcsdnn.F64 else 1e-4)
+    # the wall conditions hold on the GPU state (wall points outside fringes)
+    w = euler.neumann_weights(5)
+    for a, p in zip(got, inst.patches):
+        for side, code in enumerate(p.bc):
+            if code != I.BC_NOSLIP:
+                continue
+            line = np.moveaxis(a, 2, 1) if side < 2 else a          # (4, along the wall normal, along the wall)
+            if side in (1, 3):
+                line = line[:, ::-1]
+            line = line[:, :5, 5:-5]
+            assert np.all(line[1:3, 0] == 0.0)
+            th = euler.pressure(line, 1.4) / line[0]
+            tol = 1e-12 if dtype == fcsdnn.F64 else 1e-5
+            assert np.abs(w @ th).max() < tol * np.abs(th).max()
