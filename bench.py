@@ -73,14 +73,15 @@ def workload(args):
         h0s, machs = ensemble_params()
         return [I.ffs_ensemble(h0s, machs)]
     if args.workload == "cylinder":
-        return [I.cylinder_instance(h=CYL_H) for _ in range(args.instances)]
+        return [I.cylinder_instance(h=CYL_H, wall=I.BC_NOSLIP) for _ in range(args.instances)]
     return [I.sod_instance(perturb=0.01, seed=I.SEED + k, smear=2.0) for k in range(args.instances)]
 
 
 def config(args, points):
     if args.workload == "cylinder":
         desc = (f"Mach-10 flow past a cylinder of radius 0.5: 16 body-fitted curvilinear annular sectors plus 244 "
-                f"Cartesian far-field patches of uneven resolution (interpolated fringes), h = {CYL_H}, "
+                f"Cartesian far-field patches of uneven resolution (interpolated fringes), no-slip adiabatic "
+                f"cylinder wall, h = {CYL_H}, "
                 f"x {args.instances} instance(s); SDNN classifier + artificial viscosity + CFL dt + 4 RK stages + "
                 f"exchange per step")
         cdesc = "25 requested; FFT-length policy per line length"
@@ -121,7 +122,7 @@ def cpu_baseline(seconds, workload_name="sod"):
         "from oracle import euler, sdnn\n"
         "from paper_2506_19370_gb300 import inputs as I\n"
         + ("inst = I.ffs_instance(h0=0.005)\n" if workload_name in ("ffs", "ensemble") else
-           "inst = I.cylinder_instance(h=0.02)\n" if workload_name == "cylinder" else
+           "inst = I.cylinder_instance(h=0.02, wall=I.BC_NOSLIP)\n" if workload_name == "cylinder" else
            "inst = I.sod_instance(perturb=0.01, smear=2.0)\n") +
         "s = euler.Solver(inst, c_policy=1)\n"
         "params = sdnn.init_params(0)\n"

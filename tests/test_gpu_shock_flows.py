@@ -7,7 +7,8 @@ identical inputs (the GPU's state) at every step.
     64-patch, ~1M-point step (uneven non-coincident grids, one L-shaped C1
     corner patch, one C2 corner patch);
   * Mach-10 flow past a cylinder: 16 curvilinear annular sectors plus
-    Cartesian far-field patches, coarse version of the ~4M-point layout.
+    Cartesian far-field patches, coarse version of the ~4M-point layout, with
+    the no-slip adiabatic body wall of §7.
 """
 import json
 
@@ -24,7 +25,7 @@ from paper_2506_19370_gb300 import inputs as I  # noqa: E402
 # (layout, steps, bound on the trajectories' window mismatch, on the classifier
 # mismatch among well-decided windows of the same state)
 CASES = {"step": (lambda: I.ffs_instance(h0=0.005, length=1.4), 40, 1e-2, 1e-3),
-         "cylinder": (lambda: I.cylinder_instance(h=0.03), 15, 2e-2, 1e-2)}
+         "cylinder": (lambda: I.cylinder_instance(h=0.03, wall=I.BC_NOSLIP), 15, 2e-2, 1e-2)}
 
 
 @pytest.mark.parametrize("case", sorted(CASES))
