@@ -32,7 +32,7 @@ __host__ __device__ inline size_t align16(size_t r) { return (r + 15) & ~size_t(
 constexpr int kRowsPerWarp = 2;  // rows a warp of the pass along q1 handles together
 template <typename T>
 __host__ __device__ inline size_t xpass_warp_bytes(int nmax, int nfmax, int N1) {
-  return align16((size_t)kRowsPerWarp * 9 * nmax * sizeof(T)) + aux_cx(N1, nfmax) * 2 * sizeof(T);
+  return align16((size_t)kRowsPerWarp * 5 * nmax * sizeof(T)) + aux_cx(N1, nfmax) * 2 * sizeof(T);
 }
 template <typename T>
 __host__ __device__ inline size_t deriv_warp_bytes(int nmax, int nfmax, int N1) {

@@ -131,10 +131,12 @@ __device__ __forceinline__ void point_flux(const CtxDev& c, const PatchDev& P, l
 }
 
 // Pass along q1 (rows lbeg .. lbeg + lcnt - 1 of the row list, one FFT-size
-// group): R = -d/dq1 F1; a warp takes kRowsPerWarp rows.  Jobs of a phase:
-// (row, field pair); phase 0 (viscous only) W = d e/dq1, phase 1 R = -d F/dq1
-// with F formed in W.  Curvilinear viscous rows read e_q2 from G2 (computed
-// before this pass) and leave e_q1 in G1 for the pass along q2.
+// group): R = -d/dq1 F1; a warp takes kRowsPerWarp rows, staged in shared
+// memory.  Jobs of a phase: (row, field pair); phase 0 (rows with viscosity
+// only) G1 = d e/dq1 in global memory, phase 1 R = -d F/dq1 with F formed in
+// place of the staged state (so a warp stages 5 values per point, not 9: four
+// blocks of 4 warps fit an SM).  Curvilinear viscous rows read e_q2 from G2
+// (computed before this pass); the pass along q2 reads e_q1 from G1.
 template <typename T, int N1>
 __global__ void __launch_bounds__(kWarps * 32, 4) k_xpass(CtxDev c, int lbeg, int lcnt, const T* __restrict__ e,
                                                         const T* __restrict__ mu, T* __restrict__ R,
@@ -145,10 +147,9 @@ __global__ void __launch_bounds__(kWarps * 32, 4) k_xpass(CtxDev c, int lbeg, in
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nmax = c.nmax;
   unsigned char* base = smem_raw + (size_t)warp * xpass_warp_bytes<T>(nmax, c.nfmax, N1);
-  T* E = reinterpret_cast<T*>(base);   // [RW][4][nmax]
-  T* W = E + RW * 4 * nmax;            // [RW][4][nmax]
-  T* M = W + RW * 4 * nmax;            // [RW][nmax]
-  Cx<T>* aux = reinterpret_cast<Cx<T>*>(base + align16((size_t)RW * 9 * nmax * sizeof(T)));
+  T* E = reinterpret_cast<T*>(base);   // [RW][4][nmax]: state, then flux
+  T* M = E + RW * 4 * nmax;            // [RW][nmax]
+  Cx<T>* aux = reinterpret_cast<Cx<T>*>(base + align16((size_t)RW * 5 * nmax * sizeof(T)));
   const int g = JPR == 4 ? (lane >> 3) : 0;
   Cx<T>* tile = aux + (size_t)g * 8 * (4 * N1 + 1);
   const long long groups = ((long long)lcnt + RW - 1) / RW;   // row groups per instance
@@ -204,13 +205,12 @@ __global__ void __launch_bounds__(kWarps * 32, 4) k_xpass(CtxDev c, int lbeg, in
 #pragma unroll
             for (int f = 0; f < 4; ++f) {
               v[f] = E[(k * 4 + f) * nmax + t];
-              dv[f] = visc ? W[(k * 4 + f) * nmax + t] : T(0);
+              dv[f] = visc ? G1[s0 + f * np + t] : T(0);
               dvo[f] = curv ? G2[s0 + f * np + t] : T(0);
-              if (curv) G1[s0 + f * np + t] = dv[f];
             }
             point_flux<T, 0>(c, P, q0 + t, v, dv, dvo, visc ? M[k * nmax + t] : T(0), visc, F, t, N, code_lo);
 #pragma unroll
-            for (int f = 0; f < 4; ++f) W[(k * 4 + f) * nmax + t] = F[f];
+            for (int f = 0; f < 4; ++f) E[(k * 4 + f) * nmax + t] = F[f];
           }
         }
         __syncwarp();
@@ -228,16 +228,11 @@ __global__ void __launch_bounds__(kWarps * 32, 4) k_xpass(CtxDev c, int lbeg, in
         const PlanDev& pl = c.plans[line_plan(P, 0, rowk)];
         if (phase == 0 && !(kk ? vrow[1] : vrow[0])) active = false;
         const long long np = (long long)P.n1 * P.n2;
-        const T* src = (phase == 0 ? E : W) + (kk * 4 + 2 * pr) * nmax;
-        T* oa;
-        T* ob;
-        if (phase == 0) {
-          oa = W + (kk * 4 + 2 * pr) * nmax;
-          ob = oa + nmax;
-        } else {
-          oa = R + inst * c.sstride + P.soff + (long long)rowk * P.n1 + line_start(P, 0, rowk) + (2 * pr) * np;
-          ob = oa + np;
-        }
+        const T* src = E + (kk * 4 + 2 * pr) * nmax;
+        const long long orow = inst * c.sstride + P.soff + (long long)rowk * P.n1 + line_start(P, 0, rowk) +
+                               (2 * pr) * np;
+        T* oa = (phase == 0 ? G1 : R) + orow;
+        T* ob = oa + np;
         line_deriv_pair<T, N1>(src, 1, src + nmax, 1, oa, 1, ob, 1, phase == 0 ? T(1) : T(-1), c, pl, T(P.hx), 1, lane,
                                aux, aux + c.nfmax, tile, active);
       }
