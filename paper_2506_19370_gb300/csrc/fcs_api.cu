@@ -67,7 +67,7 @@ struct fcs_ctx {
   std::vector<Group> g_fpairs[2];
   double* smr64 = nullptr;  // filter factors of the initial smearing (order smear_p), twiddle offsets
   float* smr32 = nullptr;
-  void* G1 = nullptr;      // e_q1 of rows with viscosity; e_q2 of curvilinear patches (state-sized)
+  void* G1 = nullptr;      // e_q1, e_q2 of the lines with viscosity (state-sized)
   void* G2 = nullptr;
   int2* tiles = nullptr;
   int2* pblk = nullptr;  // point blocks of the pointwise kernels
@@ -326,9 +326,9 @@ int launch_flux(fcs_ctx* c, const void* e, const void* mu, int mode, StageArgs<T
     const LaunchCfg gy{(unsigned)grid_for(w1, 1), kYWarps * 32, ypass_smem<T>(c, c->tw, gr.n1), s};
     const int2* tl = c->tiles + gr.begin;
     if (mode == MODE_RHS) {
-      FCS_N1_SWITCH(gr.n1, FCS_CUDA((run_ypass<T, MODE_RHS, K>(c->dev, tl, gr.count, ep, mp, R, G1, st, gy))); break)
+      FCS_N1_SWITCH(gr.n1, FCS_CUDA((run_ypass<T, MODE_RHS, K>(c->dev, tl, gr.count, ep, mp, R, G1, G2, st, gy))); break)
     } else {
-      FCS_N1_SWITCH(gr.n1, FCS_CUDA((run_ypass<T, MODE_RK, K>(c->dev, tl, gr.count, ep, mp, R, G1, st, gy))); break)
+      FCS_N1_SWITCH(gr.n1, FCS_CUDA((run_ypass<T, MODE_RK, K>(c->dev, tl, gr.count, ep, mp, R, G1, G2, st, gy))); break)
     }
   }
   if (mode == MODE_RK && c->dev.n_nsw > 0) {  // no-slip walls: temperature after every point's stage
@@ -961,9 +961,8 @@ int fc_setup(fcs_ctx** out, int d, int C, const fcs_patch_desc* pd, int npatch, 
       (rc = dalloc(c, &c->gpart, (size_t)((o.train_batch_max + kGradChunk - 1) / kGradChunk) * kNParams * 8)) || (rc = dalloc(c, &m64, 5 * c->qstride * 8)) ||
       (rc = dalloc(c, &m32, 5 * c->qstride * 4)))
     return fail(rc);
-  // G1: e_q1 of the rows with viscosity (every layout); G2: e_q2 of curvilinear patches
-  if ((rc = dalloc(c, &c->G1, I * c->sstride * ts)) ||
-      (!vp.empty() && (rc = dalloc(c, &c->G2, I * c->sstride * ts))))
+  // G1, G2: e_q1, e_q2 of the lines with viscosity (viscous fluxes of both passes)
+  if ((rc = dalloc(c, &c->G1, I * c->sstride * ts)) || (rc = dalloc(c, &c->G2, I * c->sstride * ts)))
     return fail(rc);
   c->W64 = dW64;
   D.patches = dpatch;

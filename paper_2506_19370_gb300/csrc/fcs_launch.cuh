@@ -40,7 +40,7 @@ __host__ __device__ inline size_t deriv_warp_bytes(int nmax, int nfmax, int N1) 
 }
 template <typename T>
 __host__ __device__ inline size_t ypass_bytes(int n2max, int tw, int nfmax, int N1, int warps) {
-  return align16((size_t)9 * n2max * (tw + 1) * sizeof(T)) + (size_t)warps * aux_cx(N1, nfmax) * 2 * sizeof(T);
+  return align16((size_t)5 * n2max * (tw + 1) * sizeof(T)) + (size_t)warps * aux_cx(N1, nfmax) * 2 * sizeof(T);
 }
 constexpr int kYWarps = 8;
 
@@ -67,6 +67,6 @@ cudaError_t run_xpass(const CtxDev& c, int lbeg, int lcnt, const T* e, const T* 
                       LaunchCfg g);
 template <typename T, int MODE, int N1>
 cudaError_t run_ypass(const CtxDev& c, const int2* tiles, int ntiles, const T* e, const T* mu, const T* R,
-                      const T* G1, StageArgs<T> st, LaunchCfg g);
+                      const T* G1, T* G2, StageArgs<T> st, LaunchCfg g);
 
 }  // namespace fcs

@@ -36,8 +36,8 @@ cudaError_t run_xpass(const CtxDev& c, int lbeg, int lcnt, const T* e, const T* 
 }
 template <typename T, int MODE, int N1>
 cudaError_t run_ypass(const CtxDev& c, const int2* tiles, int ntiles, const T* e, const T* mu, const T* R,
-                      const T* G1, StageArgs<T> st, LaunchCfg g) {
-  k_ypass<T, MODE, N1><<<g.grid, g.block, g.smem, g.stream>>>(c, tiles, ntiles, e, mu, R, G1, st);
+                      const T* G1, T* G2, StageArgs<T> st, LaunchCfg g) {
+  k_ypass<T, MODE, N1><<<g.grid, g.block, g.smem, g.stream>>>(c, tiles, ntiles, e, mu, R, G1, G2, st);
   return cudaGetLastError();
 }
 
@@ -52,8 +52,8 @@ cudaError_t run_ypass(const CtxDev& c, const int2* tiles, int ntiles, const T* e
   template cudaError_t fcs::run_xpass<T, N1>(const CtxDev&, int, int, const T*, const T*, T*, T*, const T*,    \
                                              LaunchCfg);                                                      \
   template cudaError_t fcs::run_ypass<T, fcs::MODE_RHS, N1>(const CtxDev&, const int2*, int, const T*,       \
-                                                            const T*, const T*, const T*, StageArgs<T>,       \
+                                                            const T*, const T*, const T*, T*, StageArgs<T>,   \
                                                             LaunchCfg);                                       \
   template cudaError_t fcs::run_ypass<T, fcs::MODE_RK, N1>(const CtxDev&, const int2*, int, const T*,        \
-                                                           const T*, const T*, const T*, StageArgs<T>,        \
+                                                           const T*, const T*, const T*, T*, StageArgs<T>,    \
                                                            LaunchCfg);

@@ -242,25 +242,28 @@ __global__ void __launch_bounds__(kWarps * 32, 4) k_xpass(CtxDev c, int lbeg, in
 }
 
 // Pass along q2 on a tile of tw adjacent columns of one patch (coalesced row
-// segments staged in shared memory; 3 blocks of 8 warps per SM up to n = 96,
-// 2 above, where the line registers of the FFT would spill at 80 registers
-// per thread): L = (R - d/dq2 F2)/J, then either L
+// segments staged in shared memory; blocks of 8 warps per SM: 4 for n = 64
+// (64 registers, a few spilled; measured faster than 3), 3 for n = 96, 2
+// above, where the line registers of the FFT would spill at 80 registers per
+// thread): L = (R - d/dq2 F2)/J, then either L
 // (MODE_RHS) or the Runge-Kutta stage with boundary conditions (MODE_RK).
-// Curvilinear viscous columns read e_q1 from G1 (left by the row pass; rows
-// without viscosity leave stale values there, which only meet mu = 0).
+// The tile stages 5 values per point (state, then flux in its place, and mu).
+// Viscous columns take e_q2 from G2: on curvilinear patches from the e_q2
+// pass before the row pass, on Cartesian ones from this pass's phase 0;
+// curvilinear viscous columns also read e_q1 from G1 (left by the row pass;
+// rows without viscosity leave stale values there, which only meet mu = 0).
 template <typename T, int MODE, int N1>
-__global__ void __launch_bounds__(kYWarps * 32, (N1 >= 1 && N1 <= 3) ? 3 : 2) k_ypass(CtxDev c, const int2* __restrict__ tiles, int ntiles,
+__global__ void __launch_bounds__(kYWarps * 32, (N1 >= 1 && N1 <= 2) ? 4 : ((N1 >= 1 && N1 <= 3) ? 3 : 2)) k_ypass(CtxDev c, const int2* __restrict__ tiles, int ntiles,
                                                          const T* __restrict__ e, const T* __restrict__ mu,
                                                          const T* __restrict__ R, const T* __restrict__ G1,
-                                                         StageArgs<T> st) {
+                                                         T* __restrict__ G2, StageArgs<T> st) {
   constexpr int JPR = jobs_per_round(N1);
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int tw = c.tw, ld = c.tw + 1, n2m = c.n2max;
-  T* E = reinterpret_cast<T*>(smem_raw);           // [4][n2m][ld]
-  T* D = E + 4 * n2m * ld;                         // [4][n2m][ld]
-  T* M = D + 4 * n2m * ld;                         // [n2m][ld]
-  Cx<T>* aux = reinterpret_cast<Cx<T>*>(smem_raw + align16((size_t)9 * n2m * ld * sizeof(T))) +
+  T* E = reinterpret_cast<T*>(smem_raw);           // [4][n2m][ld]: state, flux, d flux/dq2
+  T* M = E + 4 * n2m * ld;                         // [n2m][ld]
+  Cx<T>* aux = reinterpret_cast<Cx<T>*>(smem_raw + align16((size_t)5 * n2m * ld * sizeof(T))) +
                (size_t)warp * aux_cx(N1, c.nfmax);
   const int g = JPR == 4 ? (lane >> 3) : 0;
   Cx<T>* tile = aux + (size_t)g * 8 * (4 * N1 + 1);
@@ -310,8 +313,9 @@ __global__ void __launch_bounds__(kYWarps * 32, (N1 >= 1 && N1 <= 3) ? 3 : 2) k_
     }
     __syncthreads();
     const T h = T(P.hy);
-    // phase 0 (viscous columns only): D = d e/dy; phase 1: E = d F2/dq2 with F2 formed in D
-    for (int phase = (visc && nact > 0) ? 0 : 1; phase < 2; ++phase) {
+    // phase 0 (viscous columns of Cartesian patches only): G2 = d e/dq2; phase
+    // 1: F2 formed in place of the state, then E = d F2/dq2 in place
+    for (int phase = (visc && nact > 0 && P.cart) ? 0 : 1; phase < 2; ++phase) {
       if (phase == 1) {
         for (int j = jr; colok && j < N; j += js) {
           T v[4], dv[4], dvo[4], F[4];
@@ -320,27 +324,30 @@ __global__ void __launch_bounds__(kYWarps * 32, (N1 >= 1 && N1 <= 3) ? 3 : 2) k_
 #pragma unroll
           for (int f = 0; f < 4; ++f) {
             v[f] = E[(f * n2m + j) * ld + cc];
-            dv[f] = vc ? D[(f * n2m + j) * ld + cc] : T(0);
+            dv[f] = vc ? G2[sbase + f * np + (long long)j * P.n1 + cc] : T(0);
             dvo[f] = curv ? G1[sbase + f * np + (long long)j * P.n1 + cc] : T(0);
           }
           point_flux<T, 1>(c, P, qbase + (long long)j * P.n1 + cc, v, dv, dvo, vc ? M[j * ld + cc] : T(0), vc, F, j, N,
                            code_lo);
 #pragma unroll
-          for (int f = 0; f < 4; ++f) D[(f * n2m + j) * ld + cc] = F[f];
+          for (int f = 0; f < 4; ++f) E[(f * n2m + j) * ld + cc] = F[f];
         }
         __syncthreads();
       }
-      const T* src = phase == 0 ? E : D;
-      T* dst = phase == 0 ? D : E;
-      // jobs (column, field pair): phase 0 over the viscous columns only
+      // jobs (column, field pair): phase 0 over the viscous columns only (a
+      // line pair's values are all read before any is written, so phase 1
+      // differentiates in place)
       const int ncol = phase == 0 ? nact : width;
       for (int u0 = warp * JPR; u0 < 2 * ncol; u0 += kYWarps * JPR) {
         const int u = u0 + g;
         const bool active = u < 2 * ncol;
         const int cc = active ? (phase == 0 ? act[u >> 1] : (u >> 1)) : 0, pr = u & 1;
-        line_deriv_pair<T, N1>(src + (2 * pr) * n2m * ld + cc, ld, src + (2 * pr + 1) * n2m * ld + cc, ld,
-                               dst + (2 * pr) * n2m * ld + cc, ld, dst + (2 * pr + 1) * n2m * ld + cc, ld, T(1), c, pl,
-                               h, 1, lane, aux, aux + c.nfmax, tile, active);
+        T* src = E + (2 * pr) * n2m * ld + cc;
+        T* oa = phase == 0 ? G2 + sbase + (2 * pr) * np + cc : src;
+        const int so = phase == 0 ? P.n1 : ld;
+        const long long fo = phase == 0 ? np : (long long)n2m * ld;
+        line_deriv_pair<T, N1>(src, ld, src + n2m * ld, ld, oa, so, oa + fo, so, T(1), c, pl, h, 1, lane, aux,
+                               aux + c.nfmax, tile, active);
       }
       __syncthreads();
     }
