@@ -183,6 +183,58 @@ def rhs(e, geom, d, C, gamma, mu=None):
     return np.where(geom.active, -div / geom.J, 0.0)
 
 
+def chain_variables(e, gamma):
+    """w = (rho, rho u, rho v, theta = p / rho): the variables the chain-rule
+    form of the operator differentiates (Algorithm 5: density, momenta and
+    temperature)."""
+    e = np.asarray(e, dtype=np.float64)
+    return np.stack([e[0], e[1], e[2], pressure(e, gamma) / e[0]])
+
+
+def flux_jacobians(w, gamma):
+    """A[i][k] = d f_i / d w_k and B[i][k] = d g_i / d w_k at w = (rho, m, n,
+    theta), m = rho u, n = rho v, for f, g of Eq. (1) written in w:
+    p = rho theta, E = rho theta / (gamma - 1) + (m^2 + n^2) / (2 rho)."""
+    rho, m, n, th = w
+    u, v = m / rho, n / rho
+    q2 = u * u + v * v
+    gg = gamma / (gamma - 1.0)
+    z, one = np.zeros_like(rho), np.ones_like(rho)
+    A = [[z, one, z, z],
+         [th - u * u, 2.0 * u, z, rho],
+         [-u * v, v, u, z],
+         [-u * q2, gg * th + 0.5 * (3.0 * u * u + v * v), u * v, gg * rho * u]]
+    B = [[z, z, one, z],
+         [-u * v, v, u, z],
+         [th - v * v, z, 2.0 * v, rho],
+         [-v * q2, u * v, gg * th + 0.5 * (u * u + 3.0 * v * v), gg * rho * v]]
+    return np.array(A), np.array(B)
+
+
+def rhs_chain(e, geom, gamma):
+    """L(e) on one patch in the chain-rule form of Algorithm 5 (inviscid):
+    FC derivatives of w = (rho, rho u, rho v, theta) along q1 and q2, physical
+    derivatives through the inverse Jacobian of the patch map, w_x = (y_q2
+    w_q1 - y_q1 w_q2) / J, w_y = (-x_q2 w_q1 + x_q1 w_q2) / J, and the flux
+    divergence by the product rule, f_x + g_y = A(w) w_x + B(w) w_y.
+    Cartesian patches differentiate at the physical spacings directly."""
+    e = np.asarray(e, dtype=np.float64)
+    if geom.patch.is_l:
+        e = np.where(geom.active, e, np.array([1.0, 0.0, 0.0, 2.5])[:, None, None])
+    w = chain_variables(e, gamma)
+    A, B = flux_jacobians(w, gamma)
+    if geom.patch.cartesian:
+        wx = geom.D(w, 0, geom.hx)
+        wy = geom.D(w, 1, geom.hy)
+    else:
+        w1 = geom.D(w, 0, geom.h1)
+        w2 = geom.D(w, 1, geom.h2)
+        wx = (geom.y_q2 * w1 - geom.y_q1 * w2) / geom.J
+        wy = (-geom.x_q2 * w1 + geom.x_q1 * w2) / geom.J
+    L = -(np.einsum("ik...,k...->i...", A, wx) + np.einsum("ik...,k...->i...", B, wy))
+    return np.where(geom.active, L, 0.0)
+
+
 def filter_state(e, geom, gamma, alpha=fcgram.FILTER_ALPHA, p=fcgram.FILTER_P):
     """Spectral filter of one patch's state (§5 item 3, Algorithm 4, t > 0).
 
@@ -609,15 +661,20 @@ def max_wave_speed(state, gamma):
 class Solver:
     """Multi-patch FC-SDNN stepping on one instance (Algorithms 1 and 5)."""
 
-    def __init__(self, inst, d=5, C=25, n_f=5, cfl=0.5, c_policy=0):
+    def __init__(self, inst, d=5, C=25, n_f=5, cfl=0.5, c_policy=0, chain=False):
         self.inst = inst
         self.d, self.C, self.n_f, self.cfl = d, C, n_f, cfl
+        self.chain = chain      # operator in the chain-rule form (inviscid only)
         for p in inst.patches:
             check_noslip(p)
         self.geoms = [PatchGeom(p, d, C, c_policy) for p in inst.patches]
         self.fmap = fringe_map(inst.patches, n_f)
 
     def rhs_all(self, state, mu=None):
+        if self.chain:
+            if mu is not None:
+                raise ValueError("the chain-rule operator form is inviscid")
+            return [rhs_chain(e, g, self.inst.gamma) for e, g in zip(state, self.geoms)]
         return [rhs(e, g, self.d, self.C, self.inst.gamma, None if mu is None else mu[k])
                 for k, (e, g) in enumerate(zip(state, self.geoms))]
 

@@ -469,3 +469,72 @@ def test_noslip_ring_steps_keep_the_wall_conditions():
         th = _theta(e[:, :5, inner])
         assert np.abs(w @ th).max() < 1e-12 * np.abs(th).max()
         assert np.all(np.isfinite(e))
+
+
+def _conserved_of_w(w):
+    rho, m, n, th = w
+    return np.stack([rho, m, n, rho * th / (G - 1) + 0.5 * (m * m + n * n) / rho])
+
+
+def test_flux_jacobians_match_finite_differences():
+    rng = np.random.default_rng(5)
+    w = np.stack([rng.uniform(0.5, 2, 50), rng.uniform(-2, 2, 50), rng.uniform(-2, 2, 50), rng.uniform(0.3, 3, 50)])
+    A, B = euler.flux_jacobians(w, G)
+    for k in range(4):
+        dw = np.zeros_like(w)
+        dw[k] = 1e-6 * np.maximum(np.abs(w[k]), 1.0)
+        fp, gp = euler.fluxes(_conserved_of_w(w + dw), G)
+        fm, gm = euler.fluxes(_conserved_of_w(w - dw), G)
+        dfa = (fp - fm) / (2 * dw[k])
+        dga = (gp - gm) / (2 * dw[k])
+        scale = 1.0 + np.abs(dfa) + np.abs(dga)
+        assert np.abs(A[:, k] - dfa).max() / scale.max() < 1e-7
+        assert np.abs(B[:, k] - dga).max() / scale.max() < 1e-7
+
+
+def _exact_divergence():
+    """-(f_x + g_y) of a smooth analytic state, differentiated symbolically."""
+    sympy = pytest.importorskip("sympy")
+    x, y = sympy.symbols("x y")
+    rho = 1.2 + 0.2 * sympy.sin(2 * x + 1) * sympy.cos(y)
+    u = 0.6 + 0.2 * sympy.cos(3 * x - y)
+    v = -0.3 + 0.2 * sympy.sin(x + 2 * y)
+    p = 1.0 + 0.3 * sympy.cos(x) * sympy.sin(2 * y + 0.5)
+    E = p / (G - 1) + rho * (u * u + v * v) / 2
+    f = [rho * u, rho * u * u + p, rho * u * v, (E + p) * u]
+    g = [rho * v, rho * u * v, rho * v * v + p, (E + p) * v]
+    L = [-(sympy.diff(f[i], x) + sympy.diff(g[i], y)) for i in range(4)]
+    state = sympy.lambdify((x, y), [rho, rho * u, rho * v, E], "numpy")
+    div = sympy.lambdify((x, y), L, "numpy")
+    return state, div
+
+
+def _chain_error(patch, state, div, cart=True):
+    inst = I.Instance([patch], [np.zeros((4, patch.n2, patch.n1))])
+    s = euler.Solver(inst, c_policy=1, chain=True)
+    X, Y = patch.coords()
+    e = np.array([np.broadcast_to(a, X.shape) for a in state(X, Y)], dtype=np.float64)
+    L = s.rhs_all([e])[0]
+    ex = np.array([np.broadcast_to(a, X.shape) for a in div(X, Y)])
+    return np.abs(L - ex).max() / np.abs(ex).max()
+
+
+def test_chain_form_converges_to_the_exact_divergence_cartesian():
+    state, div = _exact_divergence()
+    errs = [_chain_error(I.Patch(n, n, (I.BC_FREE,) * 4, box=(0.0, 1.0, 0.0, 1.0)), state, div) for n in (24, 48, 96)]
+    assert errs[-1] < 1e-6
+    assert errs[0] / errs[1] > 6 and errs[1] / errs[2] > 6      # at least third order
+
+
+def test_chain_form_converges_to_the_exact_divergence_curvilinear():
+    state, div = _exact_divergence()
+    errs = [_chain_error(I.annulus_patch(n, n, bc=(I.BC_FREE,) * 4), state, div) for n in (24, 48, 96)]
+    assert errs[-1] < 1e-5
+    assert errs[0] / errs[1] > 6 and errs[1] / errs[2] > 6
+
+
+def test_chain_form_is_inviscid_only():
+    inst = I.vortex_instance(21)
+    s = euler.Solver(inst, chain=True)
+    with pytest.raises(ValueError):
+        s.rhs_all(inst.state, [np.zeros((21, 21))])
