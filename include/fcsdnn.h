@@ -122,6 +122,14 @@ typedef struct {
   int filter_step;     /* 1: fcs_step ends with fcs_filter, so every step after
                           the first starts from filtered data; 0: off (0) */
   int smear_p;         /* order of the stronger filter of fcs_smear_initial (1) */
+  int op_form;         /* form of the operator L(e): 0 conservative contravariant
+                          flux form (0, the default); 1 chain-rule form of
+                          Algorithm 5: FC derivatives of rho, rho u, rho v and
+                          theta = p / rho along q1 and q2, physical derivatives
+                          through the inverse Jacobian of the patch map, flux
+                          divergence by the product rule (f_x + g_y = A w_x +
+                          B w_y, A = df/dw, B = dg/dw).  Form 1 is inviscid:
+                          calls with a viscosity return FCS_EUNSUPPORTED */
 } fcs_options;
 
 /* Defaults listed in the comments above. */

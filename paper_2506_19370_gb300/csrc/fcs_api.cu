@@ -304,6 +304,7 @@ int launch_deriv(fcs_ctx* c, const void* in, void* out, int dir, int order, cuda
 // per FFT-size group; every row pass precedes every column pass in the stream.
 template <typename T>
 int launch_flux(fcs_ctx* c, const void* e, const void* mu, int mode, StageArgs<T> st, cudaStream_t s) {
+  if (mu && c->opt.op_form == 1) return FCS_EUNSUPPORTED;  // the chain-rule form is inviscid
   const T* ep = static_cast<const T*>(e);
   const T* mp = static_cast<const T*>(mu);
   T* R = static_cast<T*>(c->R);
@@ -319,16 +320,24 @@ int launch_flux(fcs_ctx* c, const void* e, const void* mu, int mode, StageArgs<T
   for (const Group& gr : c->g_rows) {
     const long long w0 = (long long)c->opt.instances * ((gr.count + kRowsPerWarp - 1) / kRowsPerWarp);
     const LaunchCfg gx{(unsigned)grid_for(w0, kWarps), kWarps * 32, xpass_smem<T>(c, gr.n1), s};
-    FCS_N1_SWITCH(gr.n1, FCS_CUDA((run_xpass<T, K>(c->dev, gr.begin, gr.count, ep, mp, R, G1, G2, gx))); break)
+    FCS_N1_SWITCH(gr.n1, FCS_CUDA((run_xpass<T, K>(c->dev, gr.begin, gr.count, ep, mp, R, G1, G2, c->opt.op_form, gx)));
+                  break)
   }
   for (const Group& gr : c->g_tiles) {
     const long long w1 = (long long)c->opt.instances * gr.count;
     const LaunchCfg gy{(unsigned)grid_for(w1, 1), kYWarps * 32, ypass_smem<T>(c, c->tw, gr.n1), s};
     const int2* tl = c->tiles + gr.begin;
-    if (mode == MODE_RHS) {
+    const bool ch = c->opt.op_form == 1;
+    if (mode == MODE_RHS && !ch) {
       FCS_N1_SWITCH(gr.n1, FCS_CUDA((run_ypass<T, MODE_RHS, K>(c->dev, tl, gr.count, ep, mp, R, G1, G2, st, gy))); break)
-    } else {
+    } else if (mode == MODE_RHS) {
+      FCS_N1_SWITCH(gr.n1, FCS_CUDA((run_ypass<T, MODE_RHS | MODE_CHAIN, K>(c->dev, tl, gr.count, ep, mp, R, G1, G2, st,
+                                                                            gy))); break)
+    } else if (!ch) {
       FCS_N1_SWITCH(gr.n1, FCS_CUDA((run_ypass<T, MODE_RK, K>(c->dev, tl, gr.count, ep, mp, R, G1, G2, st, gy))); break)
+    } else {
+      FCS_N1_SWITCH(gr.n1, FCS_CUDA((run_ypass<T, MODE_RK | MODE_CHAIN, K>(c->dev, tl, gr.count, ep, mp, R, G1, G2, st,
+                                                                           gy))); break)
     }
   }
   if (mode == MODE_RK && c->dev.n_nsw > 0) {  // no-slip walls: temperature after every point's stage
@@ -532,6 +541,7 @@ void fcs_default_options(fcs_options* o) {
   o->filter_p = 18;
   o->filter_step = 0;
   o->smear_p = 1;
+  o->op_form = 0;
 }
 
 const char* fcs_strerror(int code) {
@@ -576,7 +586,7 @@ int fc_setup(fcs_ctx** out, int d, int C, const fcs_patch_desc* pd, int npatch, 
   else fcs_default_options(&o);
   if (o.instances < 1 || (o.dtype != FCS_F32 && o.dtype != FCS_F64) || o.n_f < 1 || o.gamma <= 1.0 ||
       o.av_radius < 0 || o.av_radius > 32 || o.train_batch_max < 1 || !(o.filter_alpha >= 0.0) || o.filter_p < 1 ||
-      o.filter_p > 64 || o.smear_p < 1 || o.smear_p > 64)
+      o.filter_p > 64 || o.smear_p < 1 || o.smear_p > 64 || o.op_form < 0 || o.op_form > 1)
     return FCS_EINVAL;
   for (int p = 0; p < npatch; ++p) {
     const fcs_patch_desc& q = pd[p];

@@ -10,7 +10,7 @@
 
 namespace fcs {
 
-enum { MODE_RHS = 1, MODE_RK = 2 };
+enum { MODE_RHS = 1, MODE_RK = 2, MODE_CHAIN = 4 };  // column-pass epilogue; MODE_CHAIN: chain-rule form
 
 template <typename T>
 struct StageArgs {
@@ -64,7 +64,7 @@ cudaError_t run_fc_deriv(const CtxDev& c, int dir, int order, const int4* pairs,
                          LaunchCfg g);
 template <typename T, int N1>
 cudaError_t run_xpass(const CtxDev& c, int lbeg, int lcnt, const T* e, const T* mu, T* R, T* G1, const T* G2,
-                      LaunchCfg g);
+                      int chain, LaunchCfg g);
 template <typename T, int MODE, int N1>
 cudaError_t run_ypass(const CtxDev& c, const int2* tiles, int ntiles, const T* e, const T* mu, const T* R,
                       const T* G1, T* G2, StageArgs<T> st, LaunchCfg g);

@@ -130,6 +130,26 @@ __device__ __forceinline__ void point_flux(const CtxDev& c, const PatchDev& P, l
   }
 }
 
+// Chain-rule form of the operator (Algorithm 5): with w = (rho, m, n, theta),
+// m = rho u, n = rho v, theta = p / rho, the flux divergence is
+// f_x + g_y = A(w) w_x + B(w) w_y, A = df/dw, B = dg/dw.  The derivative of w
+// along one parameter direction enters with the weight ca A + cb B (Cartesian
+// rows: A, columns: B; curvilinear rows: y_q2 A - x_q2 B, columns:
+// -y_q1 A + x_q1 B, the rest of the inverse Jacobian, 1/J, comes at the end).
+// out_i = sum_k (ca A_ik + cb B_ik) dw_k at the state v (conserved).
+template <typename T>
+__device__ __forceinline__ void chain_contract(const T* v, const T* dw, T ca, T cb, T gm1, T gg, T* out) {
+  const T rho = v[0], u = v[1] / rho, vv = v[2] / rho;
+  const T th = pressure<T>(v[0], v[1], v[2], v[3], gm1) / rho;
+  const T q2 = u * u + vv * vv, uv = u * vv;
+  out[0] = ca * dw[1] + cb * dw[2];
+  out[1] = ca * ((th - u * u) * dw[0] + T(2) * u * dw[1] + rho * dw[3]) + cb * (-uv * dw[0] + vv * dw[1] + u * dw[2]);
+  out[2] = ca * (-uv * dw[0] + vv * dw[1] + u * dw[2]) + cb * ((th - vv * vv) * dw[0] + T(2) * vv * dw[2] + rho * dw[3]);
+  out[3] = ca * (-u * q2 * dw[0] + (gg * th + T(0.5) * (T(3) * u * u + vv * vv)) * dw[1] + uv * dw[2] + gg * rho * u * dw[3]) +
+           cb * (-vv * q2 * dw[0] + uv * dw[1] + (gg * th + T(0.5) * (u * u + T(3) * vv * vv)) * dw[2] +
+                 gg * rho * vv * dw[3]);
+}
+
 // Pass along q1 (rows lbeg .. lbeg + lcnt - 1 of the row list, one FFT-size
 // group): R = -d/dq1 F1; a warp takes kRowsPerWarp rows, staged in shared
 // memory.  Jobs of a phase: (row, field pair); phase 0 (rows with viscosity
@@ -137,7 +157,9 @@ __device__ __forceinline__ void point_flux(const CtxDev& c, const PatchDev& P, l
 // place of the staged state (so a warp stages 5 values per point, not 9: four
 // blocks of 4 warps fit an SM).  Curvilinear viscous rows read e_q2 from G2
 // (computed before this pass); the pass along q2 reads e_q1 from G1.
-template <typename T, int N1>
+// CH = 1: chain-rule form (inviscid): w is staged and differentiated in
+// place, then R = -(ca A + cb B) w_q1 point by point.
+template <typename T, int N1, int CH>
 __global__ void __launch_bounds__(kWarps * 32, 4) k_xpass(CtxDev c, int lbeg, int lcnt, const T* __restrict__ e,
                                                         const T* __restrict__ mu, T* __restrict__ R,
                                                         T* __restrict__ G1, const T* __restrict__ G2) {
@@ -173,8 +195,18 @@ __global__ void __launch_bounds__(kWarps * 32, 4) k_xpass(CtxDev c, int lbeg, in
       bool any_mu = false;
       if (has[k])
         for (int t = lane; t < N; t += 32) {
+          if (CH) {
+            T v[4];
 #pragma unroll
-          for (int f = 0; f < 4; ++f) E[(k * 4 + f) * nmax + t] = es[f * np + t];
+            for (int f = 0; f < 4; ++f) v[f] = es[f * np + t];
+            E[(k * 4 + 0) * nmax + t] = v[0];
+            E[(k * 4 + 1) * nmax + t] = v[1];
+            E[(k * 4 + 2) * nmax + t] = v[2];
+            E[(k * 4 + 3) * nmax + t] = pressure<T>(v[0], v[1], v[2], v[3], gm1_of<T>(c)) / v[0];
+          } else {
+#pragma unroll
+            for (int f = 0; f < 4; ++f) E[(k * 4 + f) * nmax + t] = es[f * np + t];
+          }
           if (visc) {
             const T m = mu[inst * c.qstride + P.qoff + (long long)lr.line * P.n1 + s0 + t];
             M[k * nmax + t] = m;
@@ -188,7 +220,7 @@ __global__ void __launch_bounds__(kWarps * 32, 4) k_xpass(CtxDev c, int lbeg, in
     __syncwarp();
     const bool visc_any = vrow[0] || vrow[1];
     for (int phase = visc_any ? 0 : 1; phase < 2; ++phase) {
-      if (phase == 1) {
+      if (phase == 1 && !CH) {
 #pragma unroll
         for (int k = 0; k < RW; ++k) {
           if (!has[k]) continue;
@@ -228,13 +260,42 @@ __global__ void __launch_bounds__(kWarps * 32, 4) k_xpass(CtxDev c, int lbeg, in
         const PlanDev& pl = c.plans[line_plan(P, 0, rowk)];
         if (phase == 0 && !(kk ? vrow[1] : vrow[0])) active = false;
         const long long np = (long long)P.n1 * P.n2;
-        const T* src = E + (kk * 4 + 2 * pr) * nmax;
+        T* src = E + (kk * 4 + 2 * pr) * nmax;
         const long long orow = inst * c.sstride + P.soff + (long long)rowk * P.n1 + line_start(P, 0, rowk) +
                                (2 * pr) * np;
-        T* oa = (phase == 0 ? G1 : R) + orow;
-        T* ob = oa + np;
-        line_deriv_pair<T, N1>(src, 1, src + nmax, 1, oa, 1, ob, 1, phase == 0 ? T(1) : T(-1), c, pl, T(P.hx), 1, lane,
-                               aux, aux + c.nfmax, tile, active);
+        // chain-rule form: w_q1 in place of w (a pair's values are all read
+        // before any is written)
+        T* oa = CH ? src : (phase == 0 ? G1 : R) + orow;
+        const long long ob_off = CH ? (long long)nmax : np;
+        line_deriv_pair<T, N1>(src, 1, src + nmax, 1, oa, 1, oa + ob_off, 1, (phase == 0 || CH) ? T(1) : T(-1), c, pl,
+                               T(P.hx), 1, lane, aux, aux + c.nfmax, tile, active);
+      }
+      __syncwarp();
+    }
+    if (CH) {   // R = -(ca A + cb B) w_q1 at every point of the rows
+      const T gm1 = gm1_of<T>(c), gg = T(c.gamma) / gm1;
+#pragma unroll
+      for (int k = 0; k < RW; ++k) {
+        if (!has[k]) continue;
+        const PatchDev& P = c.patches[pid[k]];
+        const int a0 = line_start(P, 0, row[k]), N = P.n1 - a0;
+        const long long np = (long long)P.n1 * P.n2;
+        const long long s0 = inst * c.sstride + P.soff + (long long)row[k] * P.n1 + a0;
+        const long long q0 = P.qoff + (long long)row[k] * P.n1 + a0;
+        const T* Mt = metrics<T>(c);
+        for (int t = lane; t < N; t += 32) {
+          T v[4], dw[4], out[4];
+#pragma unroll
+          for (int f = 0; f < 4; ++f) {
+            v[f] = e[s0 + f * np + t];
+            dw[f] = E[(k * 4 + f) * nmax + t];
+          }
+          const T ca = P.cart ? T(1) : Mt[3 * c.qstride + q0 + t];
+          const T cb = P.cart ? T(0) : -Mt[c.qstride + q0 + t];
+          chain_contract<T>(v, dw, ca, cb, gm1, gg, out);
+#pragma unroll
+          for (int f = 0; f < 4; ++f) R[s0 + f * np + t] = -out[f];
+        }
       }
       __syncwarp();
     }
@@ -252,6 +313,8 @@ __global__ void __launch_bounds__(kWarps * 32, 4) k_xpass(CtxDev c, int lbeg, in
 // pass before the row pass, on Cartesian ones from this pass's phase 0;
 // curvilinear viscous columns also read e_q1 from G1 (left by the row pass;
 // rows without viscosity leave stale values there, which only meet mu = 0).
+// MODE_CHAIN (or-ed into MODE): chain-rule form (inviscid): w is staged and
+// differentiated in place, and the epilogue forms (ca A + cb B) w_q2.
 template <typename T, int MODE, int N1>
 __global__ void __launch_bounds__(kYWarps * 32, (N1 >= 1 && N1 <= 2) ? 4 : ((N1 >= 1 && N1 <= 3) ? 3 : 2)) k_ypass(CtxDev c, const int2* __restrict__ tiles, int ntiles,
                                                          const T* __restrict__ e, const T* __restrict__ mu,
@@ -267,6 +330,7 @@ __global__ void __launch_bounds__(kYWarps * 32, (N1 >= 1 && N1 <= 2) ? 4 : ((N1 
                (size_t)warp * aux_cx(N1, c.nfmax);
   const int g = JPR == 4 ? (lane >> 3) : 0;
   Cx<T>* tile = aux + (size_t)g * 8 * (4 * N1 + 1);
+  constexpr bool CH = (MODE & MODE_CHAIN) != 0;
   const T gm1 = gm1_of<T>(c);
   const long long total = (long long)c.instances * ntiles;
   for (long long wk = blockIdx.x; wk < total; wk += gridDim.x) {
@@ -294,8 +358,17 @@ __global__ void __launch_bounds__(kYWarps * 32, (N1 >= 1 && N1 <= 2) ? 4 : ((N1 
     if (colok) {
       bool any_mu = false;
       for (int j = jr; j < N; j += js) {
+        if (CH) {
+          T v[4];
 #pragma unroll
-        for (int f = 0; f < 4; ++f) E[(f * n2m + j) * ld + cc] = e[sbase + f * np + (long long)j * P.n1 + cc];
+          for (int f = 0; f < 4; ++f) v[f] = e[sbase + f * np + (long long)j * P.n1 + cc];
+#pragma unroll
+          for (int f = 0; f < 3; ++f) E[(f * n2m + j) * ld + cc] = v[f];
+          E[(3 * n2m + j) * ld + cc] = pressure<T>(v[0], v[1], v[2], v[3], gm1) / v[0];
+        } else {
+#pragma unroll
+          for (int f = 0; f < 4; ++f) E[(f * n2m + j) * ld + cc] = e[sbase + f * np + (long long)j * P.n1 + cc];
+        }
         if (visc) {
           const T m = mu[inst * c.qstride + qbase + (long long)j * P.n1 + cc];
           M[j * ld + cc] = m;
@@ -316,7 +389,7 @@ __global__ void __launch_bounds__(kYWarps * 32, (N1 >= 1 && N1 <= 2) ? 4 : ((N1 
     // phase 0 (viscous columns of Cartesian patches only): G2 = d e/dq2; phase
     // 1: F2 formed in place of the state, then E = d F2/dq2 in place
     for (int phase = (visc && nact > 0 && P.cart) ? 0 : 1; phase < 2; ++phase) {
-      if (phase == 1) {
+      if (phase == 1 && !CH) {
         for (int j = jr; colok && j < N; j += js) {
           T v[4], dv[4], dvo[4], F[4];
           const bool vc = visc && colv[cc];
@@ -357,9 +430,24 @@ __global__ void __launch_bounds__(kYWarps * 32, (N1 >= 1 && N1 <= 2) ? 4 : ((N1 
       const long long q = qbase + (long long)j * P.n1 + cc;
       const T invJ = P.cart ? T(1) : T(1) / metrics<T>(c)[4 * c.qstride + q];
       T kv[4];
+      if (CH) {   // (ca A + cb B) w_q2 at the stage's input state
+        T v[4], dw[4], out[4];
 #pragma unroll
-      for (int f = 0; f < 4; ++f) kv[f] = (R[off + f * np] - E[(f * n2m + j) * ld + cc]) * invJ;
-      if (MODE == MODE_RHS) {
+        for (int f = 0; f < 4; ++f) {
+          v[f] = e[off + f * np];
+          dw[f] = E[(f * n2m + j) * ld + cc];
+        }
+        const T* Mt = metrics<T>(c);
+        const T ca = P.cart ? T(0) : -Mt[2 * c.qstride + q];
+        const T cb = P.cart ? T(1) : Mt[q];
+        chain_contract<T>(v, dw, ca, cb, gm1, T(c.gamma) / gm1, out);
+#pragma unroll
+        for (int f = 0; f < 4; ++f) kv[f] = (R[off + f * np] - out[f]) * invJ;
+      } else {
+#pragma unroll
+        for (int f = 0; f < 4; ++f) kv[f] = (R[off + f * np] - E[(f * n2m + j) * ld + cc]) * invJ;
+      }
+      if ((MODE & 3) == MODE_RHS) {
 #pragma unroll
         for (int f = 0; f < 4; ++f) st.out[off + f * np] = kv[f];
         continue;

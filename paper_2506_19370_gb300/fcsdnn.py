@@ -45,7 +45,8 @@ class Options(ctypes.Structure):
                 ("instances", ctypes.c_int), ("inflow", ctypes.c_double * 4), ("p_out", ctypes.c_double),
                 ("c_mu", ctypes.c_double), ("av_radius", ctypes.c_int), ("c_policy", ctypes.c_int),
                 ("train_batch_max", ctypes.c_int), ("autotune", ctypes.c_int), ("filter_alpha", ctypes.c_double),
-                ("filter_p", ctypes.c_int), ("filter_step", ctypes.c_int), ("smear_p", ctypes.c_int)]
+                ("filter_p", ctypes.c_int), ("filter_step", ctypes.c_int), ("smear_p", ctypes.c_int),
+                ("op_form", ctypes.c_int)]
 
 
 class Layout(ctypes.Structure):
@@ -139,7 +140,8 @@ class Context:
     """An fcs_ctx for one patch layout (an ``inputs.Instance``) and its options."""
 
     def __init__(self, inst, d=5, C=25, dtype=F32, instances=1, cfl=0.5, n_f=5, c_mu=1.0, av_radius=4,
-                 c_policy=0, train_batch_max=4096, autotune=0, filter_step=0, filter_p=None, filter_alpha=None):
+                 c_policy=0, train_batch_max=4096, autotune=0, filter_step=0, filter_p=None, filter_alpha=None,
+                 op_form=0):
         import torch  # device memory and streams
         self.torch = torch
         L = lib()
@@ -156,6 +158,7 @@ class Context:
         opt.train_batch_max = train_batch_max
         opt.autotune = autotune
         opt.filter_step = filter_step
+        opt.op_form = op_form
         if filter_p is not None:
             opt.filter_p = filter_p
         if filter_alpha is not None:

@@ -714,3 +714,79 @@ def test_noslip_stages_with_viscosity(name, dtype):
             th = euler.pressure(line, 1.4) / line[0]
             tol = 1e-12 if dtype == fcsdnn.F64 else 1e-5
             assert np.abs(w @ th).max() < tol * np.abs(th).max()
+
+
+def chain_bound(dtype, inst, pol, states):
+    """Per patch rounding bound of the chain-rule form: the derivative bound of
+    each w_k (theta with the magnitude of its own rounding, p being a
+    difference of E and the kinetic energy) weighted by the largest flux
+    Jacobian entries and metric factors, plus the rounding of the pointwise
+    products (coefficients and derivatives of the context's type)."""
+    out = []
+    fill = np.array([1.0, 0.0, 0.0, 2.5])[:, None, None]
+    for e, p in zip(states, inst.patches):
+        g = euler.PatchGeom(p, 5, 25, pol)
+        act = p.active()
+        e = np.where(act, e, fill)
+        w = euler.chain_variables(e, inst.gamma)
+        A, B = euler.flux_jacobians(w, inst.gamma)
+        if p.cartesian:
+            dirs = ((g.hx, p.n1 + g.C1, 1.0, 0.0), (g.hy, p.n2 + g.C2, 0.0, 1.0))
+            jmin = 1.0
+        else:
+            m = [float(np.abs(x).max()) for x in (g.x_q1, g.x_q2, g.y_q1, g.y_q2)]
+            dirs = ((g.h1, p.n1 + g.C1, m[3], m[1]), (g.h2, p.n2 + g.C2, m[2], m[0]))
+            jmin = float(np.abs(g.J).min())
+        gain = max(table_gain(5, g.C_of(N)) for dirn in (0, 1) for _, N in g.segments(dirn))
+        wmag = [float(np.abs(w[k][act]).max()) for k in range(4)]
+        wmag[3] = float(((inst.gamma - 1) * (np.abs(e[3]) + (e[1] ** 2 + e[2] ** 2) / e[0]) / e[0])[act].max())
+        Am = np.abs(A * act).reshape(4, 4, -1).max(-1)
+        Bm = np.abs(B * act).reshape(4, 4, -1).max(-1)
+        b = np.zeros(4)
+        for dirn, (h, n, ca, cb) in enumerate(dirs):
+            c = ca * Am + cb * Bm
+            wq = [float(np.abs(g.D(w[k], dirn, h) * act).max()) for k in range(4)]
+            db = np.array([deriv_bound(dtype, wmag[k], h, n, 1, gain) for k in range(4)])
+            b += c @ db + 8 * EPS[dtype] * (c @ np.array(wq))
+        out.append(float(b.max()) / jmin)
+    return out
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("name", ["vortex", "sod", "annulus", "ring", "lcurv", "ffs"])
+def test_chain_form_rhs(name, dtype):
+    # the operator in the chain-rule form of Algorithm 5 against the oracle's
+    inst, pol = layout(name)
+    ctx = fcsdnn.Context(inst, d=5, C=25, dtype=dtype, c_policy=pol, op_form=1)
+    st = random_states(inst, 11)
+    e = ctx.to_device(ctx.pack_state(st))
+    rhs = ctx.new_state()
+    ctx.euler_rhs(e, rhs)
+    torch.cuda.synchronize()
+    solver = oracle_solver(inst, pol)
+    cast = [np.asarray(s, dtype=np.float32 if dtype == fcsdnn.F32 else np.float64).astype(np.float64) for s in st]
+    ref = [euler.rhs_chain(s, g, inst.gamma) for s, g in zip(cast, solver.geoms)]
+    got = active_only(ctx.unpack_state(rhs), inst)
+    bounds = chain_bound(dtype, inst, pol, cast)
+    ratios = [float(np.abs(a - b).max()) / bd for a, b, bd in zip(got, ref, bounds)]
+    print(f"chain-form rhs {name} dtype={dtype} rel={rel_err(got, ref):.3e} err/bound={max(ratios):.2e}")
+    assert max(ratios) <= 1.0
+    with pytest.raises(fcsdnn.FcsError) as ei:      # inviscid form: a viscosity is refused
+        ctx.euler_rhs(e, rhs, mu=ctx.new_scalar())
+    assert ei.value.code == -3
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("name", ["ring", "splitns"])
+def test_chain_form_steps(name, dtype):
+    inst, pol = layout(name)
+    ctx = fcsdnn.Context(inst, d=5, C=25, dtype=dtype, c_policy=pol, op_form=1)
+    solver = euler.Solver(inst, c_policy=pol, chain=True)
+    dt = 0.3 * solver.dt(inst.state)
+    got = run_steps(ctx, inst.state, 6, dt)
+    ref = [x.copy() for x in inst.state]
+    for _ in range(6):
+        ref = solver.step(ref, dt)
+    err = rel_err(active_only(got, inst), active_only(ref, inst))
+    print(f"chain-form {name} 6 steps dtype={dtype} err={err:.3e}")
+    assert err < (1e-9 if dtype == fcsdnn.F64 else 1e-4)
