@@ -47,9 +47,11 @@ def parse():
                          "cylinder: Mach-10 flow past a cylinder (annular sectors + Cartesian far field)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--e2e-chunks", type=int, default=4,
+    ap.add_argument("--e2e-chunks", type=int, default=None,
                     help="end-to-end run: instances split into this many contexts on their own streams, so the "
-                         "copies of one chunk overlap the step of another (1: one context, no overlap)")
+                         "copies of one chunk overlap the step of another (1: one context, no overlap; default 4 "
+                         "for the Sod batch, 1 for the multi-patch flows, whose smaller per-context launches "
+                         "measured slower than the copies they hide)")
     return ap.parse_args()
 
 
@@ -395,7 +397,8 @@ def run_ours(args):
     # each on its own stream: chunk k's host->device copy overlaps chunk k-1's
     # step, and its device->host copy chunk k+1's (copy engines and SMs work
     # at once).  Every step copies the whole state in and out.
-    K = args.e2e_chunks if args.e2e_chunks > 0 and args.instances % args.e2e_chunks == 0 else 1
+    K = args.e2e_chunks if args.e2e_chunks is not None else (4 if args.workload == "sod" else 1)
+    K = K if K > 0 and args.instances % K == 0 else 1
     m = args.instances // K
     wts = ctx.get_weights()
     chunks = []
