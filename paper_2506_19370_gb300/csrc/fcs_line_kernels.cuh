@@ -8,6 +8,17 @@
 
 namespace fcs {
 
+// Asynchronous copy of one element global -> shared (cp.async): a thread
+// issues all its staging copies before waiting once, so their latencies
+// overlap without holding registers.
+template <typename T>
+__device__ __forceinline__ void cp_async_elem(T* dst, const T* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  if constexpr (sizeof(T) == 4) asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
+  else asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
 // ============================================================ FC derivative
 // FC derivative (with respect to the patch parameter, spacing 1/(n1 - 1) or
 // 1/(n2 - 1) also on the short lines of an L-shaped patch) of a scalar field:
@@ -179,7 +190,7 @@ __global__ void __launch_bounds__(kWarps * 32, 4) k_xpass(CtxDev c, int lbeg, in
   for (long long w = (long long)blockIdx.x * kWarps + warp; w < total; w += (long long)gridDim.x * kWarps) {
     const int inst = (int)(w / groups);
     const int l0 = lbeg + (int)(w % groups) * RW;
-    int pid[RW], row[RW];
+    int pid[RW], row[RW], nk[RW];
     bool has[RW], vrow[RW];
 #pragma unroll
     for (int k = 0; k < RW; ++k) {
@@ -191,28 +202,25 @@ __global__ void __launch_bounds__(kWarps * 32, 4) k_xpass(CtxDev c, int lbeg, in
       const long long np = (long long)P.n1 * P.n2;
       const int s0 = line_start(P, 0, lr.line), N = P.n1 - s0;
       const T* es = e + inst * c.sstride + P.soff + (long long)lr.line * P.n1 + s0;
-      const bool visc = mu != nullptr;
+      const T* ms = mu ? mu + inst * c.qstride + P.qoff + (long long)lr.line * P.n1 + s0 : nullptr;
+      nk[k] = has[k] ? N : 0;
+      for (int t = lane; t < nk[k]; t += 32) {
+#pragma unroll
+        for (int f = 0; f < 4; ++f) cp_async_elem(&E[(k * 4 + f) * nmax + t], es + f * np + t);
+        if (ms) cp_async_elem(&M[k * nmax + t], ms + t);
+      }
+    }
+    cp_async_wait_all();
+#pragma unroll
+    for (int k = 0; k < RW; ++k) {   // the lane's own staged points
       bool any_mu = false;
-      if (has[k])
-        for (int t = lane; t < N; t += 32) {
-          if (CH) {
-            T v[4];
-#pragma unroll
-            for (int f = 0; f < 4; ++f) v[f] = es[f * np + t];
-            E[(k * 4 + 0) * nmax + t] = v[0];
-            E[(k * 4 + 1) * nmax + t] = v[1];
-            E[(k * 4 + 2) * nmax + t] = v[2];
-            E[(k * 4 + 3) * nmax + t] = pressure<T>(v[0], v[1], v[2], v[3], gm1_of<T>(c)) / v[0];
-          } else {
-#pragma unroll
-            for (int f = 0; f < 4; ++f) E[(k * 4 + f) * nmax + t] = es[f * np + t];
-          }
-          if (visc) {
-            const T m = mu[inst * c.qstride + P.qoff + (long long)lr.line * P.n1 + s0 + t];
-            M[k * nmax + t] = m;
-            any_mu |= m != T(0);
-          }
+      for (int t = lane; t < nk[k]; t += 32) {
+        if (CH) {
+          const T* v = E + k * 4 * nmax + t;
+          E[(k * 4 + 3) * nmax + t] = pressure<T>(v[0], v[nmax], v[2 * nmax], v[3 * nmax], gm1_of<T>(c)) / v[0];
         }
+        if (mu) any_mu |= M[k * nmax + t] != T(0);
+      }
       // the viscous flux of a row with mu == 0 everywhere vanishes: skip its
       // derivatives (localized viscosity)
       vrow[k] = __any_sync(0xffffffffu, any_mu);
@@ -355,25 +363,23 @@ __global__ void __launch_bounds__(kYWarps * 32, (N1 >= 1 && N1 <= 2) ? 4 : ((N1 
     __shared__ int nact;
     if (threadIdx.x < 32) colv[threadIdx.x] = 0;
     __syncthreads();
-    if (colok) {
+    if (colok)
+      for (int j = jr; j < N; j += js) {
+#pragma unroll
+        for (int f = 0; f < 4; ++f)
+          cp_async_elem(&E[(f * n2m + j) * ld + cc], e + sbase + f * np + (long long)j * P.n1 + cc);
+        if (visc) cp_async_elem(&M[j * ld + cc], mu + inst * c.qstride + qbase + (long long)j * P.n1 + cc);
+      }
+    cp_async_wait_all();
+    if (colok) {   // the thread's own staged points
       bool any_mu = false;
       for (int j = jr; j < N; j += js) {
         if (CH) {
-          T v[4];
-#pragma unroll
-          for (int f = 0; f < 4; ++f) v[f] = e[sbase + f * np + (long long)j * P.n1 + cc];
-#pragma unroll
-          for (int f = 0; f < 3; ++f) E[(f * n2m + j) * ld + cc] = v[f];
-          E[(3 * n2m + j) * ld + cc] = pressure<T>(v[0], v[1], v[2], v[3], gm1) / v[0];
-        } else {
-#pragma unroll
-          for (int f = 0; f < 4; ++f) E[(f * n2m + j) * ld + cc] = e[sbase + f * np + (long long)j * P.n1 + cc];
+          const T* v = E + j * ld + cc;
+          const int fs = n2m * ld;
+          E[(3 * n2m + j) * ld + cc] = pressure<T>(v[0], v[fs], v[2 * fs], v[3 * fs], gm1) / v[0];
         }
-        if (visc) {
-          const T m = mu[inst * c.qstride + qbase + (long long)j * P.n1 + cc];
-          M[j * ld + cc] = m;
-          any_mu |= m != T(0);
-        }
+        if (visc) any_mu |= M[j * ld + cc] != T(0);
       }
       if (any_mu) atomicOr(&colv[cc], 1);
     }
