@@ -397,7 +397,7 @@ int exchange_impl(fcs_ctx* c, void* field, int nfields, int clamp, cudaStream_t 
     else k_exchange<float><<<g, 256, 0, s>>>(c->dev, c->fringe_ent, c->nent, static_cast<float*>(field), nfields);
   }
   if (c->ninterp) {
-    const int g = grid_for(I * c->ninterp, 256);
+    const int g = grid_for(I * c->ninterp, 32);   // 4 entries per warp, 8 warps per block
     if (f64)
       k_interp<double><<<g, 256, 0, s>>>(c->dev, c->interp_ent, c->interp_w64, c->ninterp,
                                          static_cast<double*>(field), nfields, clamp);

@@ -38,43 +38,56 @@ __global__ void k_exchange(CtxDev c, const int4* __restrict__ ent, int nent, T* 
 
 // Interpolated fringe points: entries (dst patch, dst point, src patch, first
 // node of the donor block); w holds the kStencil x kStencil tensor Lagrange
-// weights of each entry ([b][a], b along j).  One thread per (instance,
-// entry) does all fields, so the weights are read once and the 36 x nfields
-// loads are independent.  clamp floors the result at zero (viscosity).
+// weights of each entry ([b][a], b along j).  A group of 8 lanes takes one
+// (instance, entry), 4 per warp: lane a < 6 of the group sums the stencil
+// column a over the rows b (its loads of one row are adjacent to the other
+// lanes', so a warp load touches 4 short segments instead of 32 scattered
+// points), then the group adds its lanes' sums by shuffles.  Every field of
+// the entry is done at once.  clamp floors the result at zero (viscosity).
 template <typename T>
 __global__ void k_interp(CtxDev c, const int4* __restrict__ ent, const T* __restrict__ w, int nent, T* field,
                          int nfields, int clamp) {
   constexpr int S = 6;
+  const int lane = threadIdx.x & 31, a = lane & 7, grp = lane >> 3;
   const long long total = (long long)c.instances * nent;
-  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x) {
-    const int inst = (int)(t / nent);
-    const int k = (int)(t % nent);
-    const int4 x = ent[k];
-    const PatchDev& Pd = c.patches[x.x];
-    const PatchDev& Ps = c.patches[x.z];
-    const long long fs = nfields == 4 ? (long long)Ps.n1 * Ps.n2 : 0, fd = nfields == 4 ? (long long)Pd.n1 * Pd.n2 : 0;
-    const T* src = field + (nfields == 4 ? inst * c.sstride + Ps.soff : inst * c.qstride + Ps.qoff) + x.w;
-    T* dst = field + (nfields == 4 ? inst * c.sstride + Pd.soff : inst * c.qstride + Pd.qoff) + x.y;
-    const T* wk = w + (size_t)k * S * S;
+  const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
+  for (long long base = ((long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 4; base < total;
+       base += nwarps * 4) {
+    const long long t = base + grp;
+    const bool ok = t < total;
     T acc[4] = {T(0), T(0), T(0), T(0)};
+    long long dbase = 0, fd = 0;
+    if (ok) {
+      const int inst = (int)(t / nent);
+      const int k = (int)(t % nent);
+      const int4 x = ent[k];
+      const PatchDev& Pd = c.patches[x.x];
+      const PatchDev& Ps = c.patches[x.z];
+      const long long fs = nfields == 4 ? (long long)Ps.n1 * Ps.n2 : 0;
+      fd = nfields == 4 ? (long long)Pd.n1 * Pd.n2 : 0;
+      dbase = (nfields == 4 ? inst * c.sstride + Pd.soff : inst * c.qstride + Pd.qoff) + x.y;
+      if (a < S) {
+        const T* src = field + (nfields == 4 ? inst * c.sstride + Ps.soff : inst * c.qstride + Ps.qoff) + x.w + a;
+        const T* wk = w + (size_t)k * S * S + a;
 #pragma unroll
-    for (int b = 0; b < S; ++b) {
-      T row[4] = {T(0), T(0), T(0), T(0)};
-#pragma unroll
-      for (int a = 0; a < S; ++a) {
-        const T wv = wk[b * S + a];
-        const long long o = (long long)b * Ps.n1 + a;
-        row[0] += wv * src[o];
-        if (nfields == 4) {
-          row[1] += wv * src[fs + o];
-          row[2] += wv * src[2 * fs + o];
-          row[3] += wv * src[3 * fs + o];
+        for (int b = 0; b < S; ++b) {
+          const T wv = wk[b * S];
+          const long long o = (long long)b * Ps.n1;
+          acc[0] += wv * src[o];
+          if (nfields == 4) {
+            acc[1] += wv * src[fs + o];
+            acc[2] += wv * src[2 * fs + o];
+            acc[3] += wv * src[3 * fs + o];
+          }
         }
       }
-#pragma unroll
-      for (int f = 0; f < 4; ++f) acc[f] += row[f];
     }
-    for (int f = 0; f < nfields; ++f) dst[f * fd] = clamp && acc[f] < T(0) ? T(0) : acc[f];
+#pragma unroll
+    for (int f = 0; f < 4; ++f)
+#pragma unroll
+      for (int off = 4; off > 0; off >>= 1) acc[f] += __shfl_down_sync(0xffffffffu, acc[f], off, 8);
+    if (ok && a == 0)
+      for (int f = 0; f < nfields; ++f) field[dbase + f * fd] = clamp && acc[f] < T(0) ? T(0) : acc[f];
   }
 }
 
