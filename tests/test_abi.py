@@ -60,3 +60,32 @@ def test_errors_are_reported(lib):
     assert lib.fcs_build_table(1, 25, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))) == -1
     h = ctypes.c_void_p()
     assert lib.fc_setup(ctypes.byref(h), 5, 25, None, 0, None) == -1
+
+
+def _setup_rc(lib, bc, lcut=(0, 0), op_form=0):
+    """fc_setup return code for one 40 x 40 Cartesian patch; every case here is
+    refused by the host-side validation, before any CUDA call."""
+    from paper_2506_19370_gb300 import fcsdnn
+    desc = (fcsdnn.PatchDesc * 1)()
+    desc[0].n1 = desc[0].n2 = 40
+    desc[0].cartesian = 1
+    desc[0].lcut[0], desc[0].lcut[1] = lcut
+    for k in range(4):
+        desc[0].bc[k] = bc[k]
+    desc[0].box[0], desc[0].box[1], desc[0].box[2], desc[0].box[3] = 0.0, 1.0, 0.0, 1.0
+    opt = fcsdnn.Options()
+    lib.fcs_default_options(ctypes.byref(opt))
+    opt.op_form = op_form
+    h = ctypes.c_void_p()
+    rc = lib.fc_setup(ctypes.byref(h), 5, 25, desc, 1, ctypes.byref(opt))
+    assert not h.value
+    return rc
+
+
+def test_setup_refuses_unsupported_wall_layouts_on_the_host(lib):
+    NOSLIP, WALL, FREE = 5, 1, 4
+    assert _setup_rc(lib, (NOSLIP, WALL, NOSLIP, WALL)) == -3         # adjacent no-slip sides
+    assert _setup_rc(lib, (WALL, NOSLIP, WALL, NOSLIP)) == -3
+    assert _setup_rc(lib, (NOSLIP, WALL, WALL, WALL), lcut=(20, 20)) == -3   # no-slip side on an L-shaped patch
+    assert _setup_rc(lib, (6, WALL, WALL, WALL)) == -1                 # unknown side code
+    assert _setup_rc(lib, (FREE, FREE, FREE, FREE), op_form=2) == -1   # unknown operator form
