@@ -29,7 +29,21 @@ module follows this reading of the FC(Gram) method of Bruno and Lyon:
 
 The fit is solved at 40 significant digits (mpmath) so that the FP64 tables
 are correct to the last bit despite the ill-conditioning of Fourier
-extension.  Derivative: FFT of the continued line, multiply mode k by
+extension.
+
+Continuation in the Gram form of FC(Gram): the d end values are projected
+on the Gram basis (coefficients a = Q^T f_end) and the appended values are
+sum_k T_k a_k for the right end plus the same for the reflected left end.
+The projection cancels: for smooth data the high-degree coefficients are
+small differences of values of size |f|, while their blend values T_k reach
+~3e3 for d = 5, so an FP64 projection would leave rounding of ~1e-12 |f| in
+the continuation.  The oracle therefore evaluates the projection in extended
+precision (numpy longdouble: 64-bit significand on x86, IEEE binary128 on
+Arm) with the 40-digit basis Q held as a double-double pair, rounds the
+coefficients to FP64 once, and sums T a in FP64 (the terms T_k a_k are small
+where T_k is large, so that sum keeps ~1 ulp of |f|).
+
+Derivative: FFT of the continued line, multiply mode k by
 (i 2 pi k / beta)^order, inverse FFT, keep the first N values.  For even n the
 Nyquist mode is zeroed for odd orders and kept, times -(pi n/beta)^2, for the
 second derivative (reading of a point the paper leaves open).
@@ -170,11 +184,48 @@ def continuation_tables(d, C, use_store=True):
     return A_R, A_L
 
 
+@functools.lru_cache(maxsize=None)
+def gram_tables(d, C, use_store=True):
+    """Gram form of the continuation (FC-Gram, §2): (Q_hi, Q_lo, T).
+
+    Q = Q_hi + Q_lo (d x d, double-double of the 40-digit Gram basis: column
+    k holds p_k at the matching points s = 0..d-1); T (C x d, FP64): T[c, k]
+    = blend-to-zero continuation of p_k at s = d + c.  A_R = T Q^T.
+    """
+    Q, _ = gram_basis(d)
+    with mp.workdps(DIGITS):
+        Qhi = np.array([[float(Q[i, k]) for k in range(d)] for i in range(d)], dtype=np.float64)
+        Qlo = np.array([[float(Q[i, k] - mp.mpf(Qhi[i, k])) for k in range(d)] for i in range(d)],
+                       dtype=np.float64)
+    key = f"T_d{d}_C{C}"
+    if use_store and key in _stored():
+        T = _stored()[key].copy()
+    else:
+        Tm, _ = blend_fit(d, C)
+        T = np.array([[float(Tm[c, k]) for k in range(d)] for c in range(C)], dtype=np.float64)
+    return Qhi, Qlo, T
+
+
+def gram_coefficients(f_end, d):
+    """a = Q^T f_end over the last axis (d values at s = 0..d-1), evaluated
+    in extended precision with the double-double basis, rounded to FP64."""
+    Qhi, Qlo, _ = gram_tables(d, 2 * d)
+    Qx = Qhi.astype(np.longdouble) + Qlo.astype(np.longdouble)
+    return (np.asarray(f_end, dtype=np.longdouble) @ Qx).astype(np.float64)
+
+
 def continue_lines(f, d, C):
-    """Append the C FC-Gram continuation values to each line (last axis)."""
+    """Append the C FC-Gram continuation values to each line (last axis).
+
+    Right end: the Gram coefficients of the last d values (s = m at point
+    N-d+m) continued by T; left end by reflection: the first d values read
+    backwards (s = m at point d-1-m), continued by T read backwards.
+    """
     f = np.asarray(f, dtype=np.float64)
-    A_R, A_L = continuation_tables(d, C)
-    ext = f[..., -d:] @ A_R.T + f[..., :d] @ A_L.T
+    _, _, T = gram_tables(d, C)
+    a_right = gram_coefficients(f[..., -d:], d)
+    a_left = gram_coefficients(f[..., d - 1::-1], d)
+    ext = a_right @ T.T + a_left @ T[::-1].T
     return np.concatenate([f, ext], axis=-1)
 
 
@@ -188,10 +239,12 @@ def spectral_multiplier(n, h, order):
     return mult
 
 
-def fc_derivative(f, h, d, C, order=1):
+def fc_derivative(f, h, d, C, order=1, extended=False):
     """FC derivative of every line of f along the last axis (Algorithm 5).
 
-    f: (..., N) samples at spacing h (parameter space); returns (..., N).
+    f: (..., N) samples at spacing h (parameter space); returns (..., N), or
+    with extended=True the derivative of the continued line at all n = N + C
+    points of its period (the first N are the derivative values).
     """
     f = np.asarray(f, dtype=np.float64)
     N = f.shape[-1]
@@ -199,7 +252,7 @@ def fc_derivative(f, h, d, C, order=1):
     n = y.shape[-1]
     Y = np.fft.fft(y, axis=-1)
     dy = np.fft.ifft(Y * spectral_multiplier(n, h, order), axis=-1).real
-    return dy[..., :N]
+    return dy if extended else dy[..., :N]
 
 
 def fc_derivative_axis(f, h, d, C, axis, order=1):

@@ -126,6 +126,38 @@ def test_stored_tables_match_fresh_fits():
         stored, _ = fcgram.continuation_tables(5, C)
         fresh, _ = fcgram.continuation_tables(5, C, use_store=False)
         assert np.array_equal(stored, fresh)
+        assert np.array_equal(fcgram.gram_tables(5, C)[2], fcgram.gram_tables(5, C, use_store=False)[2])
+
+
+@pytest.mark.parametrize("d,C", [(5, 25), (2, 25)])
+def test_continuation_matches_exact_40_digit_evaluation(d, C):
+    # FC-Gram (§2): the appended values are A_R f_right + A_L f_left with
+    # A_R = T Q^T.  Evaluated exactly (40 digits, the fit's own T and Q) on
+    # smooth lines, lines offset by a large constant and a rough line, the
+    # oracle's continuation is correct to a few ulps of the line's values;
+    # a plain FP64 sum with the combined table (entries ~2e3) is not
+    T_mp, _ = fcgram.blend_fit(d, C)
+    Q_mp, _ = fcgram.gram_basis(d)
+    rng = np.random.default_rng(11)
+    N = 64
+    x = np.linspace(0, 1, N)
+    lines = [np.sin(3 * x + 1), 116.0 + 0.01 * np.cos(2 * x), np.exp(x) * np.cos(5 * x),
+             rng.standard_normal(N)]
+    A_R, A_L = fcgram.continuation_tables(d, C)
+    worst_plain = 0.0
+    for f in lines:
+        got = fcgram.continue_lines(f, d, C)[N:]
+        with mp.workdps(40):
+            AR = T_mp * Q_mp.T
+            exact = [mp.fsum(AR[c, m] * mp.mpf(f[N - d + m]) + AR[C - 1 - c, m] * mp.mpf(f[d - 1 - m])
+                             for m in range(d)) for c in range(C)]
+        ex = np.array([float(v) for v in exact])
+        scale = np.abs(f).max()
+        assert np.abs(got - ex).max() <= 8 * 2.0 ** -53 * max(scale, np.abs(ex).max()), f[:3]
+        plain = f[-d:] @ A_R.T + f[:d] @ A_L.T
+        worst_plain = max(worst_plain, np.abs(plain - ex).max() / scale)
+    if d == 5:
+        assert worst_plain > 1e-15   # the cancellation the Gram form avoids is real
 
 
 def test_filter_factors_on_single_modes():
