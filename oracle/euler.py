@@ -713,14 +713,36 @@ class Solver:
     def dt(self, state, mu=None):
         return time_step(state, self.geoms, self.inst.gamma, self.cfl, mu)
 
+    def quadrature_weights(self, g):
+        """Per-point weights of the FC quadrature over the patch's parameter
+        space (times |J|: the integral over the patch in physical space; §7
+        energy test).  Rectangles: tensor product of the FC quadratures of
+        the rows and the columns.  L-shaped parameter space (reading): the
+        union of the upper rectangle, rows j >= m2 (full rows), and the lower
+        right one, rows j <= m2 and columns i >= m1, which share the segment
+        of row m2 to the right of i = m1; each is integrated by the tensor
+        product of the FC quadratures of its own line segments (every
+        integrand is smooth on each rectangle, while the row integral of the
+        whole L has a kink at row m2)."""
+        d = self.d
+        n1, n2 = g.n1, g.n2
+
+        def W(N, length):
+            return fcgram.fc_quadrature_weights(N, d, g.C_of(N)) * length
+
+        if not g.patch.is_l:
+            w = np.outer(W(n2, 1.0), W(n1, 1.0))
+        else:
+            m1, m2 = g.patch.lcut
+            w = np.zeros((n2, n1))
+            w[m2:, :] += np.outer(W(n2 - m2, (n2 - 1 - m2) / (n2 - 1)), W(n1, 1.0))
+            w[:m2 + 1, m1:] += np.outer(W(m2 + 1, m2 / (n2 - 1)), W(n1 - m1, (n1 - 1 - m1) / (n1 - 1)))
+        return w * np.abs(g.J)
+
     def conservation_sums(self, state):
         """Per patch: FC quadrature of each conserved field times |J| (4 sums)."""
         out = []
         for e, g in zip(state, self.geoms):
-            if g.patch.is_l:
-                raise NotImplementedError("quadrature on L-shaped patches")
-            W1 = fcgram.fc_quadrature_weights(g.n1, self.d, g.C1)
-            W2 = fcgram.fc_quadrature_weights(g.n2, self.d, g.C2)
-            w = np.outer(W2, W1) * np.abs(g.J)
+            w = self.quadrature_weights(g)
             out.append(np.array([np.sum(w * e[c]) for c in range(4)]))
         return np.array(out)
