@@ -139,12 +139,19 @@ void fcs_default_options(fcs_options* opt);
  * tables for degree d (2 <= d <= 8) and C continuation points (2 <= C <= 64;
  * paper §2; construction is a
  * Tikhonov-regularised oversampled Fourier-extension fit of the Gram
- * polynomials, solved in double-double arithmetic), FFT plans, metrics of
- * curvilinear patches, fringe/donor maps (§3.3; coincident grids only), window
- * tables of the classifier, device work buffers.  Uses the current CUDA
- * device.  Errors: FCS_EINVAL (sizes, codes), FCS_EOVERLAP, FCS_EUNSUPPORTED
- * (FFT length with a prime factor above 7, curvilinear patch with an internal
- * side), FCS_ENOMEM, FCS_ECUDA.  *out is NULL on error. */
+ * polynomials, solved in double-double arithmetic; the Gram basis and the
+ * blend values of the Gram polynomials in double-double too), FFT plans,
+ * metrics of curvilinear patches, fringe/donor maps (§3.3: a host donor
+ * search over all patches; a receiver on a donor node is copied, any other
+ * receiver is interpolated with a 6 x 6 tensor Lagrange stencil in the
+ * donor's index space, Cartesian, curvilinear and L-shaped donors alike),
+ * window tables of the classifier, device work buffers.  Patches have 16 to
+ * 512 points per side.  Uses the current CUDA device.  Errors: FCS_EINVAL
+ * (sizes, codes), FCS_EOVERLAP (a receiver without a donor that is not a
+ * receiver itself), FCS_EUNSUPPORTED (FFT length with a prime factor above
+ * 7; a line class whose buffers exceed a block's shared memory, possible
+ * for FP64 lines near 512 points; no-slip walls on an L-shaped patch or on
+ * two adjacent sides), FCS_ENOMEM, FCS_ECUDA.  *out is NULL on error. */
 int fc_setup(fcs_ctx** out, int d, int C, const fcs_patch_desc* patches, int npatch,
              const fcs_options* opt);
 
@@ -241,11 +248,14 @@ int fcs_filter(fcs_ctx* ctx, void* e_dev, void* stream);
 int fcs_smear_initial(fcs_ctx* ctx, void* e_dev, const int8_t* tau_dev, void* stream);
 
 /* Per instance and patch, FP64 sums of each conserved field with the FC
- * quadrature weights (tensor product along q1 and q2) times |J|:
- * sums_dev[(instance * npatch + patch) * 4 + field].  Also checks the state
- * and latches FCS_ENONFINITE / FCS_ENEGATIVE into the status word.
- * FCS_EUNSUPPORTED if the layout has an L-shaped patch (the tensor-product
- * quadrature does not apply there). */
+ * quadrature weights times |J| (§7 energy test: integrals over the domain):
+ * sums_dev[(instance * npatch + patch) * 4 + field].  Rectangular patches:
+ * tensor product of the FC quadratures along q1 and q2.  L-shaped patches:
+ * the union of the upper rectangle (rows j >= m2) and the lower right one
+ * (rows j <= m2, columns i >= m1), each the tensor product of the FC
+ * quadratures of its line segments.  Also checks the state and latches
+ * FCS_ENONFINITE / FCS_ENEGATIVE into the status word.  FCS_EUNSUPPORTED if
+ * an L-shaped patch has m2 + 1 < 2 d (no quadrature below its cut). */
 int fcs_conservation_sums(fcs_ctx* ctx, const void* e_dev, double* sums_dev, void* stream);
 
 /* Classifier weights (the paper's ANN, §4/§5 item 2): FP32 master copy,
@@ -262,6 +272,18 @@ int sdnn_get_weights(fcs_ctx* ctx, float* w_host, size_t n);
  * contexts run the MLP on BF16 tensor cores with FP32 accumulation; F64
  * contexts in FP64. */
 int sdnn_classify(fcs_ctx* ctx, const void* e_dev, int8_t* tau_dev, void* logits_dev, void* stream);
+
+/* The classifier's input windows (Algorithm 3: the Mach-number proxy on
+ * 16-point windows along every line, as sdnn_classify cuts them), before the
+ * per-window normalisation that sdnn_classify and sdnn_train_step apply:
+ * x_dev [instance][window][16] float, in the window order of the layout
+ * (per patch: rows j = 0.. n2-1, each row's windows by start 0, 16, ...,
+ * the last right-aligned, then the columns i = 0 .. n1-1 likewise; segments
+ * of L-shaped patches as in the classifier).  flat_dev (int8
+ * [instance][window], optional): 1 where the window is flat (classified
+ * smooth without inference).  Used to build training data from states the
+ * solver's own FC steps produced.  Work buffers are the context's. */
+int sdnn_windows(fcs_ctx* ctx, const void* e_dev, float* x_dev, int8_t* flat_dev, void* stream);
 
 /* Coefficient-decay smoothness indicator (fallback and judge of the
  * classifier; not in the paper): per window the decay rate s of the FC
@@ -325,6 +347,16 @@ int fcs_step_graph(fcs_ctx* ctx, void* e_dev, double dt, double* dt_dev, int use
 int fcs_status(fcs_ctx* ctx, int* flags);
 
 const char* fcs_strerror(int code);
+
+/* Measurement helper (the paper has no counterpart): launches `blocks`
+ * blocks of 256 threads that each run iters x 32 independent fused
+ * multiply-adds per thread in FP32 (dtype FCS_F32) or FP64 (FCS_F64), i.e.
+ * blocks x 256 x iters x 64 flops, asynchronously on `stream`.  Timed with
+ * events around it, it gives the peak arithmetic rate that the roofline
+ * fractions of the FC derivative and stage kernels are quoted against.
+ * out_dev: device buffer of at least `blocks` elements of that type (never
+ * written for these inputs).  FCS_EINVAL on a bad argument. */
+int fcs_alu_probe(int dtype, int blocks, int iters, void* out_dev, void* stream);
 
 #ifdef __cplusplus
 }

@@ -30,7 +30,8 @@ struct DevBuf {
 
 struct HostPlan {
   PlanDev dev;
-  std::vector<double> tab;  // C x d
+  std::vector<double> tab;     // C x d, FP64
+  std::vector<double> tab_lo;  // remainder of the double-double table
 };
 
 // A contiguous range of a work list (rows, line pairs, column tiles) whose
@@ -52,6 +53,9 @@ struct fcs_ctx {
   size_t sstride = 0, qstride = 0, nwin = 0;
   int nlines0 = 0, nlines1 = 0, npairs0 = 0, npairs1 = 0, nent = 0, ntiles = 0;
   int nmax = 0, nfmax = 0, n2max = 0, stockham = 0, tw = 32;
+  // per direction and FFT-size class n1: longest line and longest FFT (the
+  // line kernels size their shared-memory buffers by these)
+  int gnmax[2][kN1Classes] = {}, gnfmax[2][kN1Classes] = {};
   std::vector<int> kind_n1[2][2];  // [dir][kind][patch]: FFT size of the full (kind 0) and short
                                    // (kind 1, L-shaped patches) lines along q1 / q2; -1: none
   std::vector<int> n1_dir[2];    // distinct FFT sizes per direction
@@ -103,6 +107,7 @@ struct fcs_ctx {
   float* loss_s = nullptr;
   double* gpart = nullptr;  // per batch-chunk partial gradients
   int adam_t = 0;
+  bool sums_ok = true;  // every patch has a quadrature (L-shaped: m2 + 1 >= 2 d)
   // graph of fcs_step
   cudaGraphExec_t gexec = nullptr;
   cudaGraph_t graph = nullptr;
@@ -229,7 +234,8 @@ int get_plan(fcs_ctx* c, int N, int C, int d) {
   hp.dev.nst = (int)rad.size();
   for (int s = 0; s < hp.dev.nst; ++s) hp.dev.radix[s] = rad[s];
   hp.tab.resize((size_t)C * d);
-  if (build_table(d, C, hp.tab.data()) != 0) return FCS_EINVAL;
+  hp.tab_lo.resize((size_t)C * d);
+  if (build_table(d, C, hp.tab.data(), hp.tab_lo.data()) != 0) return FCS_EINVAL;
   c->plans.push_back(hp);
   const int idx = (int)c->plans.size() - 1;
   c->plan_of_len[key] = idx;
@@ -237,11 +243,19 @@ int get_plan(fcs_ctx* c, int N, int C, int d) {
 }
 
 template <typename T>
-size_t xpass_smem(const fcs_ctx* c, int n1) { return kWarps * xpass_warp_bytes<T>(c->nmax, c->nfmax, n1); }
+size_t xpass_smem(const fcs_ctx* c, int n1) {
+  return kWarps * xpass_warp_bytes<T>(c->gnmax[0][n1], c->gnfmax[0][n1], n1);
+}
 template <typename T>
-size_t deriv_smem(const fcs_ctx* c, int n1) { return kWarps * deriv_warp_bytes<T>(c->nmax, c->nfmax, n1); }
+size_t deriv_smem(const fcs_ctx* c, int n1) {
+  return kWarps * std::max(deriv_warp_bytes<T>(c->gnmax[0][n1], c->gnfmax[0][n1], n1),
+                           deriv_warp_bytes<T>(c->gnmax[1][n1], c->gnfmax[1][n1], n1));
+}
 template <typename T>
-size_t ypass_smem(const fcs_ctx* c, int tw, int n1) { return ypass_bytes<T>(c->n2max, tw, c->nfmax, n1, kYWarps); }
+size_t ypass_smem(const fcs_ctx* c, int tw, int n1) {
+  return ypass_bytes<T>(c->gnmax[1][n1], tw, c->gnfmax[1][n1], n1, kYWarps);
+}
+constexpr size_t kSmemMax = 227 * 1024;   // dynamic shared memory a block may use
 
 size_t blend_smem(int r, size_t tsize) {
   const size_t w = kBlendTile + 4 * r;
@@ -590,7 +604,7 @@ int fc_setup(fcs_ctx** out, int d, int C, const fcs_patch_desc* pd, int npatch, 
     return FCS_EINVAL;
   for (int p = 0; p < npatch; ++p) {
     const fcs_patch_desc& q = pd[p];
-    if (q.n1 < 16 || q.n2 < 16 || q.n1 > 256 || q.n2 > 256) return FCS_EINVAL;
+    if (q.n1 < 16 || q.n2 < 16 || q.n1 > kMaxLine || q.n2 > kMaxLine) return FCS_EINVAL;
     for (int s = 0; s < 4; ++s)
       if (q.bc[s] < 0 || q.bc[s] > 5) return FCS_EINVAL;
     if (q.cartesian) {
@@ -648,6 +662,8 @@ int fc_setup(fcs_ctx** out, int d, int C, const fcs_patch_desc* pd, int npatch, 
         c->nfmax = std::max(c->nfmax, c->plans[pi].dev.n);
         int r = c->plans[pi].dev.n1reg;
         if (r % 2 == 0 && d > 5) r = 0;  // the two-level register FFT handles d <= 5
+        c->gnmax[dir][r] = std::max(c->gnmax[dir][r], N);
+        c->gnfmax[dir][r] = std::max(c->gnfmax[dir][r], c->plans[pi].dev.n);
         c->kind_n1[dir][kind].push_back(r);
         if (std::find(c->n1_dir[dir].begin(), c->n1_dir[dir].end(), r) == c->n1_dir[dir].end())
           c->n1_dir[dir].push_back(r);
@@ -755,11 +771,22 @@ int fc_setup(fcs_ctx** out, int d, int C, const fcs_patch_desc* pd, int npatch, 
           const PatchDev& P = c->patches[p];
           if (c->plans[(kind ? P.plan_s : P.plan)[dir]].dev.nst == 0) return fail(FCS_EUNSUPPORTED);
         }
-  // column-tile width of the pass along q2: widest of 32, 16, 8 that fits
+  // row passes and line-pair derivatives of every class must fit a block's
+  // shared memory (long Stockham lines in FP64 may not)
+  for (int n1 : c->n1_dir[0])
+    if ((c->tsize == 8 ? xpass_smem<double>(c, n1) : xpass_smem<float>(c, n1)) > kSmemMax)
+      return fail(FCS_EUNSUPPORTED);
+  for (int dir = 0; dir < 2; ++dir)
+    for (int n1 : c->n1_dir[dir])
+      if ((c->tsize == 8 ? deriv_smem<double>(c, n1) : deriv_smem<float>(c, n1)) > kSmemMax)
+        return fail(FCS_EUNSUPPORTED);
+  // column-tile width of the pass along q2: widest of 32, 16, 8, 4 that fits
+  // the 227 KB of shared memory a block may use (FP64 tiles of long columns
+  // need the narrow widths)
   {
-    const size_t esz = c->tsize, lim = 200 * 1024;
+    const size_t esz = c->tsize, lim = kSmemMax;
     int tw = 0;
-    for (int t : {32, 16, 8}) {
+    for (int t : {32, 16, 8, 4}) {
       size_t b = 0;
       for (int n1 : c->n1_dir[1])
         b = std::max(b, esz == 8 ? ypass_smem<double>(c, t, n1) : ypass_smem<float>(c, t, n1));
@@ -831,24 +858,15 @@ int fc_setup(fcs_ctx** out, int d, int C, const fcs_patch_desc* pd, int npatch, 
   c->nent = (int)ent.size();
   c->ninterp = (int)ient.size();
 
-  // ---- Gram basis on the d matching points (QR of the Vandermonde matrix,
-  // modified Gram-Schmidt) and per plan the blend values of the Gram
-  // polynomials T = A_R Q, both FP32 for the FP32 continuation
-  std::vector<double> Qd((size_t)d * d);
-  for (int i = 0; i < d; ++i)
-    for (int j = 0; j < d; ++j) Qd[(size_t)i * d + j] = std::pow((double)i / (d - 1), j);
-  for (int j = 0; j < d; ++j) {
-    for (int k = 0; k < j; ++k) {
-      double dot = 0;
-      for (int i = 0; i < d; ++i) dot += Qd[(size_t)i * d + k] * Qd[(size_t)i * d + j];
-      for (int i = 0; i < d; ++i) Qd[(size_t)i * d + j] -= dot * Qd[(size_t)i * d + k];
-    }
-    double nrm = 0;
-    for (int i = 0; i < d; ++i) nrm += Qd[(size_t)i * d + j] * Qd[(size_t)i * d + j];
-    nrm = std::sqrt(nrm);
-    for (int i = 0; i < d; ++i) Qd[(size_t)i * d + j] /= nrm;
-  }
-  std::vector<float> gramQ(Qd.begin(), Qd.end()), gramT;
+  // ---- Gram basis on the d matching points (orthonormalised Vandermonde
+  // matrix, double-double) and per plan the blend values of the Gram
+  // polynomials T = A_R Q (double-double, rounded to FP64 and FP32): the
+  // continuation in the Gram form projects the d end values on the basis and
+  // sums T times the coefficients
+  std::vector<double> Qhi((size_t)d * d), Qlo((size_t)d * d);
+  gram_basis_dd(d, Qhi.data(), Qlo.data());
+  std::vector<float> gramQ(Qhi.begin(), Qhi.end()), gramT;
+  std::vector<double> gramT64;
   // ---- device tables
   std::vector<double> tab64;
   std::vector<float> thi, tlo;
@@ -859,12 +877,14 @@ int fc_setup(fcs_ctx** out, int d, int C, const fcs_patch_desc* pd, int npatch, 
   std::vector<PlanDev> plans;
   for (HostPlan& hp : c->plans) {
     hp.dev.tg_off = (int)gramT.size();
-    for (int q = 0; q < hp.dev.C; ++q)
-      for (int k = 0; k < d; ++k) {
-        double v = 0;
-        for (int m = 0; m < d; ++m) v += hp.tab[(size_t)q * d + m] * Qd[(size_t)m * d + k];
+    {
+      std::vector<double> Tb((size_t)hp.dev.C * d);
+      gram_blend(d, hp.dev.C, hp.tab.data(), hp.tab_lo.data(), Qhi.data(), Qlo.data(), Tb.data());
+      for (double v : Tb) {
         gramT.push_back((float)v);
+        gramT64.push_back(v);
       }
+    }
     hp.dev.tab_off = (int)tab64.size();
     for (double v : hp.tab) {
       float a, b;
@@ -890,16 +910,47 @@ int fc_setup(fcs_ctx** out, int d, int C, const fcs_patch_desc* pd, int npatch, 
     }
     plans.push_back(hp.dev);
   }
-  // quadrature weights per patch
+  // quadrature weights per patch: rectangles, the FC quadratures of a row
+  // and a column (tensor product); L-shaped patches, per point weights of
+  // the union of the upper rectangle (rows j >= m2) and the lower right one
+  // (rows j <= m2, columns i >= m1), each the tensor product of the FC
+  // quadratures of its own line segments (marked by woff.y = -1)
   std::vector<double> wq;
   std::vector<int2> wo;
   for (int p = 0; p < npatch; ++p) {
+    const PatchDev& P = c->patches[p];
     int2 w2;
-    for (int dir = 0; dir < 2; ++dir) {
-      const HostPlan& hp = c->plans[c->patches[p].plan[dir]];
-      std::vector<double> W = quad_weights(hp.dev.N, hp.dev.C, d, hp.tab);
-      (dir == 0 ? w2.x : w2.y) = (int)wq.size();
-      wq.insert(wq.end(), W.begin(), W.end());
+    if (P.m1 > 0) {
+      const int n1 = P.n1, n2 = P.n2, m1 = P.m1, m2 = P.m2;
+      if (m2 + 1 < 2 * d) {   // too short a segment below the cut for a quadrature
+        c->sums_ok = false;
+        wo.push_back(make_int2(0, 0));
+        continue;
+      }
+      auto seg = [&](int N, double len) {
+        const int Cq = choose_c(o, C, N);
+        std::vector<double> A((size_t)Cq * d);
+        build_table(d, Cq, A.data());
+        std::vector<double> W = quad_weights(N, Cq, d, A);
+        for (double& x : W) x *= len;
+        return W;
+      };
+      const std::vector<double> Wxf = seg(n1, 1.0), Wxs = seg(n1 - m1, double(n1 - 1 - m1) / (n1 - 1));
+      const std::vector<double> Wyh = seg(n2 - m2, double(n2 - 1 - m2) / (n2 - 1)), Wyl = seg(m2 + 1, double(m2) / (n2 - 1));
+      std::vector<double> w((size_t)n1 * n2, 0.0);
+      for (int j = m2; j < n2; ++j)
+        for (int i = 0; i < n1; ++i) w[(size_t)j * n1 + i] += Wyh[j - m2] * Wxf[i];
+      for (int j = 0; j <= m2; ++j)
+        for (int i = m1; i < n1; ++i) w[(size_t)j * n1 + i] += Wyl[j] * Wxs[i - m1];
+      w2 = make_int2((int)wq.size(), -1);
+      wq.insert(wq.end(), w.begin(), w.end());
+    } else {
+      for (int dir = 0; dir < 2; ++dir) {
+        const HostPlan& hp = c->plans[P.plan[dir]];
+        std::vector<double> W = quad_weights(hp.dev.N, hp.dev.C, d, hp.tab);
+        (dir == 0 ? w2.x : w2.y) = (int)wq.size();
+        wq.insert(wq.end(), W.begin(), W.end());
+      }
     }
     wo.push_back(w2);
   }
@@ -924,7 +975,10 @@ int fc_setup(fcs_ctx** out, int d, int C, const fcs_patch_desc* pd, int npatch, 
   unsigned char* dfr;
   int* dstatus;
   float *dgq, *dgt;
-  if ((rc = upload(c, &dgq, gramQ.data(), gramQ.size() * 4)) || (rc = upload(c, &dgt, gramT.data(), gramT.size() * 4)))
+  double *dgqh, *dgql, *dgt64;
+  if ((rc = upload(c, &dgq, gramQ.data(), gramQ.size() * 4)) || (rc = upload(c, &dgt, gramT.data(), gramT.size() * 4)) ||
+      (rc = upload(c, &dgqh, Qhi.data(), Qhi.size() * 8)) || (rc = upload(c, &dgql, Qlo.data(), Qlo.size() * 8)) ||
+      (rc = upload(c, &dgt64, gramT64.data(), gramT64.size() * 8)))
     return fail(rc);
   if ((rc = upload(c, &dpatch, c->patches.data(), c->patches.size() * sizeof(PatchDev))) ||
       (rc = upload(c, &dplan, plans.data(), plans.size() * sizeof(PlanDev))) ||
@@ -1007,9 +1061,17 @@ int fc_setup(fcs_ctx** out, int d, int C, const fcs_patch_desc* pd, int npatch, 
   D.ind_plan = ind;
   D.nmax = c->nmax;
   D.nfmax = c->nfmax;
+  for (int dir = 0; dir < 2; ++dir)
+    for (int k = 0; k < kN1Classes; ++k) {
+      D.gnmax[dir][k] = c->gnmax[dir][k];
+      D.gnfmax[dir][k] = c->gnfmax[dir][k];
+    }
   D.stockham = c->stockham;
   D.gramQ = dgq;
   D.gramT = dgt;
+  D.gramQ64h = dgqh;
+  D.gramQ64l = dgql;
+  D.gramT64 = dgt64;
   D.pblk = c->pblk;
   D.npblk = (int)pblk.size();
   D.nsw = c->nsw;
@@ -1165,8 +1227,7 @@ int fcs_time_step(fcs_ctx* c, const void* e, const void* mu, double* dt_dev, voi
 
 int fcs_conservation_sums(fcs_ctx* c, const void* e, double* sums, void* stream) {
   if (!c || !e || !sums) return FCS_EINVAL;
-  for (const PatchDev& P : c->patches)
-    if (P.m1 > 0) return FCS_EUNSUPPORTED;  // no tensor quadrature on an L-shaped patch
+  if (!c->sums_ok) return FCS_EUNSUPPORTED;  // an L-shaped patch cut too close to its bottom side
   const int blocks = c->opt.instances * c->npatch;
   if (c->opt.dtype == FCS_F64)
     k_sums<double><<<blocks, 256, 0, as_stream(stream)>>>(c->dev, static_cast<const double*>(e), c->wq, c->woff, sums);
@@ -1225,6 +1286,24 @@ int sdnn_classify(fcs_ctx* c, const void* e, int8_t* tau, void* logits, void* st
   }
   FCS_CUDA(cudaGetLastError());
   k_tau_gather<<<gp, 256, 0, s>>>(c->dev, c->tau_w, reinterpret_cast<signed char*>(tau));
+  return cuda_err(cudaGetLastError());
+}
+
+int sdnn_windows(fcs_ctx* c, const void* e, float* x, int8_t* flat, void* stream) {
+  if (!c || !e || !x) return FCS_EINVAL;
+  cudaStream_t s = as_stream(stream);
+  const long long nw = (long long)c->opt.instances * c->nwin;
+  const dim3 gp(c->dev.npblk, c->opt.instances);
+  signed char* fl = reinterpret_cast<signed char*>(flat);
+  if (c->opt.dtype == FCS_F64) {
+    k_av_speed<double><<<gp, 256, 0, s>>>(c->dev, static_cast<const double*>(e), static_cast<double*>(c->av0), 1, c->opt.gamma,
+                                          c->opt.gamma - 1.0);
+    k_windows<double><<<grid_for(nw, 128), 128, 0, s>>>(c->dev, static_cast<const double*>(c->av0), x, fl);
+  } else {
+    k_av_speed<float><<<gp, 256, 0, s>>>(c->dev, static_cast<const float*>(e), static_cast<float*>(c->av0), 1, (float)c->opt.gamma,
+                                         (float)(c->opt.gamma - 1.0));
+    k_windows<float><<<grid_for(nw, 128), 128, 0, s>>>(c->dev, static_cast<const float*>(c->av0), x, fl);
+  }
   return cuda_err(cudaGetLastError());
 }
 
@@ -1463,6 +1542,14 @@ int fcs_step_graph(fcs_ctx* c, void* e, double dt, double* dt_dev, int use_av, v
     c->g_stream = s;
   }
   return cuda_err(cudaGraphLaunch(c->gexec, s));
+}
+
+int fcs_alu_probe(int dtype, int blocks, int iters, void* out, void* stream) {
+  if (blocks < 1 || iters < 1 || !out || (dtype != FCS_F32 && dtype != FCS_F64)) return FCS_EINVAL;
+  if (dtype == FCS_F64) k_fma_probe<double><<<blocks, 256, 0, as_stream(stream)>>>(iters, static_cast<double*>(out));
+  else k_fma_probe<float><<<blocks, 256, 0, as_stream(stream)>>>(iters, static_cast<float*>(out));
+  FCS_CUDA(cudaGetLastError());
+  return FCS_OK;
 }
 
 int fcs_status(fcs_ctx* c, int* flags) {

@@ -9,6 +9,8 @@ namespace fcs {
 
 constexpr int kMaxStages = 12;
 constexpr int kWarps = 4;             // warps per block of the line kernels
+constexpr int kN1Classes = 10;        // FFT-size classes n1 = 0 (Stockham), 2..9 (register FFTs of n = 32 n1)
+constexpr int kMaxLine = 512;         // most points per patch side
 
 // ------------------------------------------------------------ descriptors
 struct PatchDev {
@@ -84,8 +86,13 @@ struct CtxDev {
   int stockham;                 // 1 if some plan needs the shared-memory FFT buffers
   int tw;                       // column-tile width of the pass along q2
   int n2max;                    // longest column (lines along q2)
+  int gnmax[2][kN1Classes];     // per direction and FFT-size class: longest line
+  int gnfmax[2][kN1Classes];    // ... and longest FFT (shared-memory layout of the line kernels)
   const float* gramQ;           // d x d Gram basis at the matching points (FP32)
   const float* gramT;           // Gram blend tables of all plans (FP32)
+  const double* gramQ64h;       // the Gram basis as double-double hi + lo
+  const double* gramQ64l;
+  const double* gramT64;        // Gram blend tables of all plans (FP64, same offsets as gramT)
   const int2* pblk;             // point blocks of 256 points: (patch, first point), one instance
   int npblk;
   const int4* nsw;              // no-slip wall points: (patch, point, inward stride in points, 0)
@@ -270,26 +277,61 @@ __device__ Cx<T>* warp_fft(Cx<T>* a, Cx<T>* b, const CtxDev& c, const PlanDev& p
 }
 
 // ------------------------------------------------------------ FC continuation
-// buf[0..N) holds two real lines as (re, im); append the C continuation values
-//   cont[c] = sum_m A_R[c][m] f[N-d+m] + sum_m A_R[C-1-c][m] f[d-1-m]
-// (FC-Gram right blend-to-zero plus the reflected left blend).
+// FP64 continuation in the Gram form of FC-Gram: the d end values of a line
+// (v[m * sv], m = 0..d-1, matching point s = m) are projected on the Gram
+// basis, a_k = sum_m Q[m][k] v_m, and the appended value at gap point q is
+// sum_k T[q][k] a_k (right end) plus T[C-1-q][k] a_k of the reflected left
+// end.  The projection cancels (the high-degree coefficients of smooth data
+// are tiny differences of values of size |v|, and their blend values reach
+// ~3e3), so it is a compensated dot product (Ogita-Rump-Oishi "Dot2":
+// error-free products by fma, error-free sums) with the double-double basis
+// Q = Qh + Ql; the blend sum T a is plain, since its large terms are small.
+__device__ __forceinline__ double gram_coef64(const double* v, int sv, const double* Qh, const double* Ql, int d,
+                                              int k) {
+  double s = 0.0, e = 0.0;
+  for (int m = 0; m < d; ++m) {
+    const double x = v[m * sv];
+    const double q = __ldg(Qh + m * d + k);
+    const double p = __dmul_rn(q, x);
+    const double pe = fma(q, x, -p);
+    const double t = __dadd_rn(s, p);
+    const double z = __dsub_rn(t, s);
+    const double se = __dadd_rn(__dsub_rn(s, __dsub_rn(t, z)), __dsub_rn(p, z));
+    s = t;
+    e = __dadd_rn(e, __dadd_rn(pe, __dadd_rn(se, __dmul_rn(__ldg(Ql + m * d + k), x))));
+  }
+  return __dadd_rn(s, e);
+}
+
+// buf[0..N) holds two real lines as (re, im); append the C continuation
+// values.  Every lane of the warp calls it: lanes k < d project, the others
+// read the coefficients by shuffles.
 __device__ __forceinline__ void continue_lines(Cx<double>* buf, const CtxDev& c, const PlanDev& pl, int d,
                                                int lane) {
-  const double* tab = c.tab64 + pl.tab_off;
+  const double* Tg = c.gramT64 + pl.tg_off;
   const int N = pl.N, C = pl.C;
-  for (int q = lane; q < C; q += 32) {
-    const double* tr = tab + q * d;
-    const double* tl = tab + (C - 1 - q) * d;
+  double* f = reinterpret_cast<double*>(buf);   // line a at stride 2, line b at offset 1
+  double aR = 0.0, aL = 0.0, bR = 0.0, bL = 0.0;
+  if (lane < d) {
+    aR = gram_coef64(f + 2 * (N - d), 2, c.gramQ64h, c.gramQ64l, d, lane);
+    aL = gram_coef64(f + 2 * (d - 1), -2, c.gramQ64h, c.gramQ64l, d, lane);
+    bR = gram_coef64(f + 2 * (N - d) + 1, 2, c.gramQ64h, c.gramQ64l, d, lane);
+    bL = gram_coef64(f + 2 * (d - 1) + 1, -2, c.gramQ64h, c.gramQ64l, d, lane);
+  }
+  for (int q0 = 0; q0 < C; q0 += 32) {
+    const int q = q0 + lane;
+    const bool own = q < C;
     double sa = 0.0, sb = 0.0;
-    for (int m = 0; m < d; ++m) {
-      const double ar = __ldg(tr + m), al = __ldg(tl + m);
-      const Cx<double> fr = buf[N - d + m], fl = buf[d - 1 - m];
-      sa = fma(ar, fr.x, sa);
-      sb = fma(ar, fr.y, sb);
-      sa = fma(al, fl.x, sa);
-      sb = fma(al, fl.y, sb);
+    for (int k = 0; k < d; ++k) {
+      const double gaR = __shfl_sync(0xffffffffu, aR, k), gaL = __shfl_sync(0xffffffffu, aL, k);
+      const double gbR = __shfl_sync(0xffffffffu, bR, k), gbL = __shfl_sync(0xffffffffu, bL, k);
+      if (own) {
+        const double tr = __ldg(Tg + q * d + k), tl = __ldg(Tg + (C - 1 - q) * d + k);
+        sa = fma(tr, gaR, fma(tl, gaL, sa));
+        sb = fma(tr, gbR, fma(tl, gbL, sb));
+      }
     }
-    buf[N + q] = {sa, sb};
+    if (own) buf[N + q] = {sa, sb};
   }
 }
 
@@ -474,6 +516,9 @@ __device__ __forceinline__ void apply_bc(const CtxDev& c, const PatchDev& P, int
 
 
 // ------------------------------------------------------------ register FFT
+__device__ __forceinline__ float fma_t(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double fma_t(double a, double b, double c) { return fma(a, b, c); }
+
 // Everything one FC derivative of a line pair needs, by value (no pointer to
 // the kernel's context, so nothing has to be spilled to local memory).
 template <typename T>
@@ -483,6 +528,11 @@ struct LineOp {
   const double* t64;    // the plan's C x d table (FP64)
   const float* thi;     // FP32 split of the table (hi, lo)
   const float* tlo;
+  const double* gQh;    // FP64 Gram basis (double-double) and the plan's FP64 Gram blend table
+  const double* gQl;
+  const double* gT64;
+  const float* gQ32;    // FP32 Gram basis and the plan's FP32 Gram blend table
+  const float* gT32;
   int N, C, n, d, n1reg;
   T h;                  // line spacing
 };
@@ -492,12 +542,14 @@ __device__ __forceinline__ LineOp<T> make_op(const CtxDev& c, const PlanDev& pl,
 template <>
 __device__ __forceinline__ LineOp<double> make_op<double>(const CtxDev& c, const PlanDev& pl, double h) {
   return {reinterpret_cast<const Cx<double>*>(c.tw64 + pl.tw_off), c.flt64 + pl.tw_off, c.tab64 + pl.tab_off,
-          c.tabhi + pl.tab_off, c.tablo + pl.tab_off, pl.N, pl.C, pl.n, c.d, pl.n1reg, h};
+          c.tabhi + pl.tab_off, c.tablo + pl.tab_off, c.gramQ64h, c.gramQ64l, c.gramT64 + pl.tg_off,
+          c.gramQ, c.gramT + pl.tg_off, pl.N, pl.C, pl.n, c.d, pl.n1reg, h};
 }
 template <>
 __device__ __forceinline__ LineOp<float> make_op<float>(const CtxDev& c, const PlanDev& pl, float h) {
   return {reinterpret_cast<const Cx<float>*>(c.tw32 + pl.tw_off), c.flt32 + pl.tw_off, c.tab64 + pl.tab_off,
-          c.tabhi + pl.tab_off, c.tablo + pl.tab_off, pl.N, pl.C, pl.n, c.d, pl.n1reg, h};
+          c.tabhi + pl.tab_off, c.tablo + pl.tab_off, c.gramQ64h, c.gramQ64l, c.gramT64 + pl.tg_off,
+          c.gramQ, c.gramT + pl.tg_off, pl.N, pl.C, pl.n, c.d, pl.n1reg, h};
 }
 
 template <typename T>
@@ -587,28 +639,6 @@ __device__ __forceinline__ void reg_fft(Cx<T>* x, const Cx<T>* tw, bool inv, int
 
 __device__ __forceinline__ int bitrev5(int v) { return __brev(v) >> 27; }
 
-// Continuation value q (0 <= q < C) of the line a (stride sa) minus offset o:
-// sum_m A_R[q][m] a[N-d+m] + A_R[C-1-q][m] a[d-1-m]
-__device__ __forceinline__ double cont_value(const double* a, int sa, double o, const LineOp<double>& op, int q) {
-  const double* tr = op.t64 + q * op.d;
-  const double* tl = op.t64 + (op.C - 1 - q) * op.d;
-  double s = 0.0;
-  for (int m = 0; m < op.d; ++m) {
-    s = fma(__ldg(tr + m), a[(op.N - op.d + m) * sa] - o, s);
-    s = fma(__ldg(tl + m), a[(op.d - 1 - m) * sa] - o, s);
-  }
-  return s;
-}
-__device__ __forceinline__ float cont_value(const float* a, int sa, float o, const LineOp<float>& op, int q) {
-  const int rr = q * op.d, rl = (op.C - 1 - q) * op.d;
-  Dot2 acc{0.f, 0.f};
-  for (int m = 0; m < op.d; ++m) {
-    acc.add(__ldg(op.thi + rr + m), __ldg(op.tlo + rr + m), __fsub_rn(a[(op.N - op.d + m) * sa], o));
-    acc.add(__ldg(op.thi + rl + m), __ldg(op.tlo + rl + m), __fsub_rn(a[(op.d - 1 - m) * sa], o));
-  }
-  return acc.get();
-}
-
 // FC derivative of the lines a and b (b may be null) with the register FFT;
 // results times `scale` go to oa[t*soa], ob[t*sob] for t < N.
 template <typename T, int N1>
@@ -621,15 +651,63 @@ __device__ __forceinline__ void reg_deriv_pair(const T* a, int sa, const T* b, i
     if (b) offb = (b[0] + b[(N - 1) * sb]) * T(0.5);
   }
   Cx<T> x[N1];
+  {
+    // Gram form of the continuation: lanes k < d project the four line ends
+    // on the Gram basis (FP64: compensated sums with the double-double basis;
+    // FP32: plain sums of the shifted values, whose high-degree coefficients
+    // are small for smooth data), every lane reads the coefficients of its
+    // gap points by shuffles and sums the blend values T
+    const int d = op.d;
+    T aR = T(0), aL = T(0), bR = T(0), bL = T(0);
+    if (lane < d) {
+      if constexpr (sizeof(T) == 8) {
+        aR = gram_coef64(a + (N - d) * sa, sa, op.gQh, op.gQl, d, lane);
+        aL = gram_coef64(a + (d - 1) * sa, -sa, op.gQh, op.gQl, d, lane);
+        if (b) {
+          bR = gram_coef64(b + (N - d) * sb, sb, op.gQh, op.gQl, d, lane);
+          bL = gram_coef64(b + (d - 1) * sb, -sb, op.gQh, op.gQl, d, lane);
+        }
+      } else {
+        for (int m = 0; m < d; ++m) {
+          const float q = __ldg(op.gQ32 + m * d + lane);
+          aR = fmaf(q, a[(N - d + m) * sa] - offa, aR);
+          aL = fmaf(q, a[(d - 1 - m) * sa] - offa, aL);
+          if (b) {
+            bR = fmaf(q, b[(N - d + m) * sb] - offb, bR);
+            bL = fmaf(q, b[(d - 1 - m) * sb] - offb, bL);
+          }
+        }
+      }
+    }
 #pragma unroll
-  for (int j1 = 0; j1 < N1; ++j1) {
-    const int j = lane + 32 * j1;
-    if (j < N) {
-      x[j1].x = a[j * sa] - offa;
-      x[j1].y = b ? b[j * sb] - offb : T(0);
-    } else {
-      x[j1].x = cont_value(a, sa, offa, op, j - N);
-      x[j1].y = b ? cont_value(b, sb, offb, op, j - N) : T(0);
+    for (int j1 = 0; j1 < N1; ++j1) {
+      const int j = lane + 32 * j1;
+      x[j1] = {T(0), T(0)};
+      if (j < N) {
+        x[j1].x = a[j * sa] - offa;
+        x[j1].y = b ? b[j * sb] - offb : T(0);
+      }
+      if (32 * j1 + 31 >= N) {   // this register row holds gap points (uniform over the warp)
+        const int q = j - N;
+        T sa_ = T(0), sb_ = T(0);
+        for (int k = 0; k < d; ++k) {
+          const T gaR = __shfl_sync(0xffffffffu, aR, k), gaL = __shfl_sync(0xffffffffu, aL, k);
+          const T gbR = __shfl_sync(0xffffffffu, bR, k), gbL = __shfl_sync(0xffffffffu, bL, k);
+          if (q >= 0) {
+            T tr, tl;
+            if constexpr (sizeof(T) == 8) {
+              tr = __ldg(op.gT64 + q * d + k);
+              tl = __ldg(op.gT64 + (op.C - 1 - q) * d + k);
+            } else {
+              tr = __ldg(op.gT32 + q * d + k);
+              tl = __ldg(op.gT32 + (op.C - 1 - q) * d + k);
+            }
+            sa_ = fma_t(tr, gaR, fma_t(tl, gaL, sa_));
+            sb_ = fma_t(tr, gbR, fma_t(tl, gbL, sb_));
+          }
+        }
+        if (q >= 0) x[j1] = {sa_, b ? sb_ : T(0)};
+      }
     }
   }
   reg_fft<T, N1>(x, op.tw, false, lane);
@@ -843,11 +921,15 @@ __device__ __forceinline__ void rdft_inv(Cx<T>* x) {
 //   transpose back, 8-point inverse DFTs), natural order again.
 // FP32 continuation: Gram coefficients of the d end values (Q^T f), then the
 // blend table T = A_R Q (no cancellation for smooth data, so plain FP32
-// sums suffice); FP64: the A_R table directly.
+// sums suffice); FP64: the same two steps, the projection compensated
+// (gram_coef64).
 template <typename T>
 struct GramOp {
-  const float* Q;   // d x d Gram basis (values at the d matching points), FP32
-  const float* Tg;  // C x d blend values of the Gram polynomials, FP32
+  const float* Q;     // d x d Gram basis (values at the d matching points), FP32
+  const float* Tg;    // C x d blend values of the Gram polynomials, FP32
+  const double* Qh;   // the basis as double-double (FP64 lines)
+  const double* Ql;
+  const double* Tg64; // C x d blend values, FP64
 };
 
 template <typename T, int B>
@@ -863,19 +945,30 @@ __device__ __forceinline__ void tl_deriv_pair(const T* a, int sa, const T* b, in
     offa = (a[0] + a[(N - 1) * sa]) * T(0.5);
     if (b) offb = (b[0] + b[(N - 1) * sb]) * T(0.5);
   }
-  // FP32: lane t (< d) of the group computes Gram coefficient k = t of both
-  // lines and both ends; the group then shares them by shuffles
-  float gaR[MAXD], gaL[MAXD], gbR[MAXD], gbL[MAXD];
-  if constexpr (sizeof(T) == 4) {
-    float cR = 0.f, cL = 0.f, dR = 0.f, dL = 0.f;
+  // lane t (< d) of the group computes Gram coefficient k = t of both lines
+  // and both ends (FP32: plain sums of the shifted values; FP64: compensated
+  // sums with the double-double basis); the group then shares them by
+  // shuffles
+  T gaR[MAXD], gaL[MAXD], gbR[MAXD], gbL[MAXD];
+  {
+    T cR = T(0), cL = T(0), dR = T(0), dL = T(0);
     if (active && t < d) {
-      for (int m = 0; m < d; ++m) {
-        const float q = __ldg(gop.Q + m * d + t);
-        cR = fmaf(q, a[(N - d + m) * sa] - offa, cR);
-        cL = fmaf(q, a[(d - 1 - m) * sa] - offa, cL);
+      if constexpr (sizeof(T) == 4) {
+        for (int m = 0; m < d; ++m) {
+          const float q = __ldg(gop.Q + m * d + t);
+          cR = fmaf(q, a[(N - d + m) * sa] - offa, cR);
+          cL = fmaf(q, a[(d - 1 - m) * sa] - offa, cL);
+          if (b) {
+            dR = fmaf(q, b[(N - d + m) * sb] - offb, dR);
+            dL = fmaf(q, b[(d - 1 - m) * sb] - offb, dL);
+          }
+        }
+      } else {
+        cR = gram_coef64(a + (N - d) * sa, sa, gop.Qh, gop.Ql, d, t);
+        cL = gram_coef64(a + (d - 1) * sa, -sa, gop.Qh, gop.Ql, d, t);
         if (b) {
-          dR = fmaf(q, b[(N - d + m) * sb] - offb, dR);
-          dL = fmaf(q, b[(d - 1 - m) * sb] - offb, dL);
+          dR = gram_coef64(b + (N - d) * sb, sb, gop.Qh, gop.Ql, d, t);
+          dL = gram_coef64(b + (d - 1) * sb, -sb, gop.Qh, gop.Ql, d, t);
         }
       }
     }
@@ -896,20 +989,22 @@ __device__ __forceinline__ void tl_deriv_pair(const T* a, int sa, const T* b, in
       z.y = b ? b[j * sb] - offb : T(0);
     } else {
       const int q = j - N;
-      if constexpr (sizeof(T) == 4) {
-        float sa_ = 0.f, sb_ = 0.f;
+      T sa_ = T(0), sb_ = T(0);
 #pragma unroll
-        for (int k = 0; k < MAXD; ++k) {
-          if (k >= d) continue;
-          const float tr = __ldg(gop.Tg + q * d + k), tl = __ldg(gop.Tg + (op.C - 1 - q) * d + k);
-          sa_ = fmaf(tr, gaR[k], fmaf(tl, gaL[k], sa_));
-          sb_ = fmaf(tr, gbR[k], fmaf(tl, gbL[k], sb_));
+      for (int k = 0; k < MAXD; ++k) {
+        if (k >= d) continue;
+        T tr, tl;
+        if constexpr (sizeof(T) == 4) {
+          tr = __ldg(gop.Tg + q * d + k);
+          tl = __ldg(gop.Tg + (op.C - 1 - q) * d + k);
+        } else {
+          tr = __ldg(gop.Tg64 + q * d + k);
+          tl = __ldg(gop.Tg64 + (op.C - 1 - q) * d + k);
         }
-        z = {T(sa_), b ? T(sb_) : T(0)};
-      } else {
-        z.x = cont_value(a, sa, offa, op, q);
-        z.y = b ? cont_value(b, sb, offb, op, q) : T(0);
+        sa_ = fma_t(tr, gaR[k], fma_t(tl, gaL[k], sa_));
+        sb_ = fma_t(tr, gbR[k], fma_t(tl, gbL[k], sb_));
       }
+      z = {sa_, b ? sb_ : T(0)};
     }
     return z;
   };
@@ -1008,7 +1103,7 @@ __device__ __forceinline__ void line_deriv_pair(const T* a, int sa, const T* b, 
     if (active) reg_deriv_pair<T, N1>(a, sa, b, sb, oa, soa, ob, sob, scale, op, order, lane);
   } else {
     const LineOp<T> op = make_op<T>(c, pl, h);
-    const GramOp<T> gop{c.gramQ, c.gramT + pl.tg_off};
+    const GramOp<T> gop{c.gramQ, c.gramT + pl.tg_off, c.gramQ64h, c.gramQ64l, c.gramT64 + pl.tg_off};
     tl_deriv_pair<T, 4 * N1>(a, sa, b, sb, oa, soa, ob, sob, scale, op, gop, order, lane & 7, tile, active);
   }
 }

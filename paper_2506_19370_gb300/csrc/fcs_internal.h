@@ -31,8 +31,18 @@ int build_fringe(const fcs_patch_desc* pd, int npatch, int n_f, std::vector<Frin
 // Period P and highest mode K of the blend-to-zero fit for (d, C).
 void fit_params(int d, int C, int* P, int* K);
 
-// FP64 right-end continuation table A_R (C x d, row-major); 0 on success.
-int build_table(int d, int C, double* A_R);
+// FP64 right-end continuation table A_R (C x d, row-major), and with A_R_lo
+// the remainder of its double-double value; 0 on success.
+int build_table(int d, int C, double* A_R, double* A_R_lo = nullptr);
+
+// Gram basis of the d matching points (d x d, Q[m][k] = p_k(m), orthonormal
+// columns of the Vandermonde matrix at m / (d - 1)) as double-double hi + lo.
+void gram_basis_dd(int d, double* Qhi, double* Qlo);
+
+// Blend values of the Gram polynomials, T = A_R Q (C x d), evaluated in
+// double-double and rounded to FP64.
+void gram_blend(int d, int C, const double* ARhi, const double* ARlo, const double* Qhi, const double* Qlo,
+                double* T);
 
 // e^{-2 pi i k / n}, k = 0..n-1, correctly rounded from double-double.
 void twiddles(int n, double* re, double* im);

@@ -260,7 +260,9 @@ __global__ void k_dt_final(const unsigned long long* best, double* dt, int n) {
 
 // ============================================================ conservation sums
 // one block per (instance, patch); quadrature weights w1 (per patch, n1) and
-// w2 (n2) at offsets wq1[p], wq2[p] of wq.
+// w2 (n2) at offsets woff[p].x, woff[p].y of wq, or (woff[p].y = -1, an
+// L-shaped patch) one weight per point at woff[p].x; points outside an
+// L-shaped patch are skipped.
 template <typename T>
 __global__ void k_sums(CtxDev c, const T* __restrict__ e, const double* __restrict__ wq, const int2* __restrict__ woff,
                        double* sums) {
@@ -275,10 +277,11 @@ __global__ void k_sums(CtxDev c, const T* __restrict__ e, const double* __restri
   const double gm1 = c.gamma - 1.0;
   for (long long t = threadIdx.x; t < np; t += blockDim.x) {
     const int i = (int)(t % P.n1), j = (int)(t / P.n1);
+    if (!pt_active(P, i, j)) continue;
     double J;
     if (P.cart) J = P.Lx * P.Ly;
     else J = c.metrics64[4 * c.qstride + P.qoff + t];
-    const double w = wq[wo.x + i] * wq[wo.y + j] * fabs(J);
+    const double w = (wo.y < 0 ? wq[wo.x + t] : wq[wo.x + i] * wq[wo.y + j]) * fabs(J);
     double v[4];
 #pragma unroll
     for (int f = 0; f < 4; ++f) {
@@ -522,6 +525,27 @@ __global__ void __launch_bounds__(128) k_mlp_bf16(CtxDev c, const float* __restr
       }
     }
     __syncwarp();
+  }
+}
+
+// Raw proxy windows (the classifier's input before its normalisation) of all
+// instances, [instance][window][16] as float, and their flat flags (the same
+// test, in the context's type, as the classifier kernels apply).
+template <typename T>
+__global__ void k_windows(CtxDev c, const T* __restrict__ phi, float* __restrict__ x, signed char* __restrict__ flat) {
+  const long long total = (long long)c.instances * c.nwin;
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x) {
+    const long long inst = t / c.nwin;
+    const int4 wd = c.windows[t % c.nwin];
+    T mn = proxy_at<T>(c, phi, inst, wd, 0), mx = mn, amax = T(0);
+    for (int k = 0; k < 16; ++k) {
+      const T v = proxy_at<T>(c, phi, inst, wd, k);
+      x[t * 16 + k] = (float)v;
+      mn = v < mn ? v : mn;
+      mx = v > mx ? v : mx;
+      amax = fabs(v) > amax ? fabs(v) : amax;
+    }
+    if (flat) flat[t] = (mx - mn) <= T(kFlatTol) * (amax > T(1) ? amax : T(1));
   }
 }
 
@@ -978,6 +1002,28 @@ __global__ void k_adam(float* W, float* m, float* v, const float* __restrict__ g
   else if (t < 1728) Wb[1536 + t - 1600] = __float2bfloat16_rn(w);
   else bias[64 + t - 1728] = w;
   W64[t] = (double)w;
+}
+
+// Arithmetic-rate probe: every thread runs `iters` rounds of 4 x 8 fused
+// multiply-adds on 8 independent registers (8 dependency chains, enough to
+// cover the FMA latency at full occupancy) and keeps the result live through a
+// store that these inputs never take.  Work: blocks x 256 x iters x 64 flops.
+template <typename T>
+__global__ void __launch_bounds__(256) k_fma_probe(int iters, T* out) {
+  T a[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) a[k] = T(threadIdx.x + k) * T(1e-7);
+  const T m = T(0.999999), b = T(1e-7);
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+      for (int k = 0; k < 8; ++k) a[k] = fma(a[k], m, b);
+  }
+  T s = T(0);
+#pragma unroll
+  for (int k = 0; k < 8; ++k) s += a[k];
+  if (s == T(-1)) out[blockIdx.x] = s;
 }
 
 }  // namespace fcs

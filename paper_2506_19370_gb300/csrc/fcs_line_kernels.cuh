@@ -31,8 +31,8 @@ __global__ void __launch_bounds__(kWarps * 32) k_fc_deriv(CtxDev c, int dir, int
   constexpr int JPR = jobs_per_round(N1);
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int nmax = c.nmax;
-  unsigned char* base = smem_raw + (size_t)warp * deriv_warp_bytes<T>(nmax, c.nfmax, N1);
+  const int nmax = c.gnmax[dir][N1], nfmax = c.gnfmax[dir][N1];
+  unsigned char* base = smem_raw + (size_t)warp * deriv_warp_bytes<T>(nmax, nfmax, N1);
   T* L = reinterpret_cast<T*>(base);  // [JPR][2][nmax]
   Cx<T>* aux = reinterpret_cast<Cx<T>*>(base + align16((size_t)8 * nmax * sizeof(T)));
   const int g = JPR == 4 ? (lane >> 3) : 0;
@@ -75,7 +75,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_fc_deriv(CtxDev c, int dir, int
                              : inst * c.sstride + P.soff + (long long)pr.w * P.n1 * P.n2);
     const T hq = T(1) / T((dir == 0 ? P.n1 : P.n2) - 1);
     line_deriv_pair<T, N1>(L + (2 * g) * nmax, 1, lb >= 0 ? L + (2 * g + 1) * nmax : nullptr, 1, dst + la, (int)stride,
-                           lb >= 0 ? dst + lb : nullptr, (int)stride, T(1), c, pl, hq, order, lane, aux, aux + c.nfmax,
+                           lb >= 0 ? dst + lb : nullptr, (int)stride, T(1), c, pl, hq, order, lane, aux, aux + nfmax,
                            tile, active);
     __syncwarp();
   }
@@ -178,8 +178,8 @@ __global__ void __launch_bounds__(kWarps * 32, 4) k_xpass(CtxDev c, int lbeg, in
   constexpr int RW = kRowsPerWarp;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int nmax = c.nmax;
-  unsigned char* base = smem_raw + (size_t)warp * xpass_warp_bytes<T>(nmax, c.nfmax, N1);
+  const int nmax = c.gnmax[0][N1], nfmax = c.gnfmax[0][N1];
+  unsigned char* base = smem_raw + (size_t)warp * xpass_warp_bytes<T>(nmax, nfmax, N1);
   T* E = reinterpret_cast<T*>(base);   // [RW][4][nmax]: state, then flux
   T* M = E + RW * 4 * nmax;            // [RW][nmax]
   Cx<T>* aux = reinterpret_cast<Cx<T>*>(base + align16((size_t)RW * 5 * nmax * sizeof(T)));
@@ -276,7 +276,7 @@ __global__ void __launch_bounds__(kWarps * 32, 4) k_xpass(CtxDev c, int lbeg, in
         T* oa = CH ? src : (phase == 0 ? G1 : R) + orow;
         const long long ob_off = CH ? (long long)nmax : np;
         line_deriv_pair<T, N1>(src, 1, src + nmax, 1, oa, 1, oa + ob_off, 1, (phase == 0 || CH) ? T(1) : T(-1), c, pl,
-                               T(P.hx), 1, lane, aux, aux + c.nfmax, tile, active);
+                               T(P.hx), 1, lane, aux, aux + nfmax, tile, active);
       }
       __syncwarp();
     }
@@ -331,11 +331,11 @@ __global__ void __launch_bounds__(kYWarps * 32, (N1 >= 1 && N1 <= 2) ? 4 : ((N1 
   constexpr int JPR = jobs_per_round(N1);
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int tw = c.tw, ld = c.tw + 1, n2m = c.n2max;
+  const int tw = c.tw, ld = c.tw + 1, n2m = c.gnmax[1][N1], nfmax = c.gnfmax[1][N1];
   T* E = reinterpret_cast<T*>(smem_raw);           // [4][n2m][ld]: state, flux, d flux/dq2
   T* M = E + 4 * n2m * ld;                         // [n2m][ld]
   Cx<T>* aux = reinterpret_cast<Cx<T>*>(smem_raw + align16((size_t)5 * n2m * ld * sizeof(T))) +
-               (size_t)warp * aux_cx(N1, c.nfmax);
+               (size_t)warp * aux_cx(N1, nfmax);
   const int g = JPR == 4 ? (lane >> 3) : 0;
   Cx<T>* tile = aux + (size_t)g * 8 * (4 * N1 + 1);
   constexpr bool CH = (MODE & MODE_CHAIN) != 0;
@@ -426,7 +426,7 @@ __global__ void __launch_bounds__(kYWarps * 32, (N1 >= 1 && N1 <= 2) ? 4 : ((N1 
         const int so = phase == 0 ? P.n1 : ld;
         const long long fo = phase == 0 ? np : (long long)n2m * ld;
         line_deriv_pair<T, N1>(src, ld, src + n2m * ld, ld, oa, so, oa + fo, so, T(1), c, pl, h, 1, lane, aux,
-                               aux + c.nfmax, tile, active);
+                               aux + nfmax, tile, active);
       }
       __syncthreads();
     }

@@ -117,7 +117,7 @@ void fit_params(int d, int C, int* P, int* K) {
   *K = (*P - 9) / 3;
 }
 
-int build_table(int d, int C, double* A_R) {
+int build_table(int d, int C, double* A_R, double* A_R_lo) {
   if (d < 2 || d > 12 || C < 2 || C > 64) return -1;
   int P, K;
   fit_params(d, C, &P, &K);
@@ -200,9 +200,51 @@ int build_table(int d, int C, double* A_R) {
         v = add(v, add(mul(cs, X[(size_t)(2 * m - 1) * d + q]), mul(sn, X[(size_t)(2 * m) * d + q])));
       }
       A_R[c * d + q] = v.hi + v.lo;
+      if (A_R_lo) A_R_lo[c * d + q] = v.lo - (A_R[c * d + q] - v.hi);
     }
   }
   return 0;
+}
+
+void gram_basis_dd(int d, double* Qhi, double* Qlo) {
+  // Vandermonde matrix at s / (d - 1), s = 0..d-1, orthonormalised column by
+  // column (modified Gram-Schmidt, twice for orthogonality to the last bits)
+  std::vector<dd> Q((size_t)d * d);
+  for (int i = 0; i < d; ++i) {
+    const dd x = div(mk((double)i), mk((double)(d - 1)));
+    dd v = mk(1.0);
+    for (int j = 0; j < d; ++j) {
+      Q[(size_t)i * d + j] = v;
+      v = mul(v, x);
+    }
+  }
+  for (int j = 0; j < d; ++j) {
+    for (int pass = 0; pass < 2; ++pass)
+      for (int k = 0; k < j; ++k) {
+        dd dot = mk(0.0);
+        for (int i = 0; i < d; ++i) dot = add(dot, mul(Q[(size_t)i * d + k], Q[(size_t)i * d + j]));
+        for (int i = 0; i < d; ++i) Q[(size_t)i * d + j] = sub(Q[(size_t)i * d + j], mul(dot, Q[(size_t)i * d + k]));
+      }
+    dd nrm2 = mk(0.0);
+    for (int i = 0; i < d; ++i) nrm2 = add(nrm2, mul(Q[(size_t)i * d + j], Q[(size_t)i * d + j]));
+    const dd nrm = sqrt_dd(nrm2);
+    for (int i = 0; i < d; ++i) Q[(size_t)i * d + j] = div(Q[(size_t)i * d + j], nrm);
+  }
+  for (size_t k = 0; k < Q.size(); ++k) {
+    Qhi[k] = Q[k].hi + Q[k].lo;
+    Qlo[k] = Q[k].lo - (Qhi[k] - Q[k].hi);
+  }
+}
+
+void gram_blend(int d, int C, const double* ARhi, const double* ARlo, const double* Qhi, const double* Qlo,
+                double* T) {
+  for (int c = 0; c < C; ++c)
+    for (int k = 0; k < d; ++k) {
+      dd v = mk(0.0);
+      for (int m = 0; m < d; ++m)
+        v = add(v, mul(dd{ARhi[c * d + m], ARlo[c * d + m]}, dd{Qhi[m * d + k], Qlo[m * d + k]}));
+      T[c * d + k] = v.hi + v.lo;
+    }
 }
 
 void twiddles(int n, double* re, double* im) {

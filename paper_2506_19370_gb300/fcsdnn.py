@@ -24,7 +24,7 @@ EXPORTS = ("fcs_default_options", "fc_setup", "fc_destroy", "fcs_get_layout", "f
            "fc_derivative", "euler_rhs", "rk_stage", "patch_exchange", "fcs_time_step", "fcs_conservation_sums",
            "sdnn_set_weights", "sdnn_get_weights", "sdnn_classify", "sdnn_indicator", "av_assemble",
            "sdnn_train_step", "sdnn_gradient", "sdnn_gradient_noalloc", "fcs_step", "fcs_step_graph", "fcs_status",
-           "fcs_strerror", "fcs_filter", "fcs_smear_initial")
+           "fcs_strerror", "fcs_filter", "fcs_smear_initial", "fcs_alu_probe", "sdnn_windows")
 
 
 class FcsError(RuntimeError):
@@ -86,6 +86,7 @@ def lib():
             "sdnn_get_weights": (i, [vp, ctypes.POINTER(ctypes.c_float), ctypes.c_size_t]),
             "sdnn_classify": (i, [vp, vp, vp, vp, vp]),
             "sdnn_indicator": (i, [vp, vp, vp, vp, vp]),
+            "sdnn_windows": (i, [vp, vp, vp, vp, vp]),
             "av_assemble": (i, [vp, vp, vp, vp, vp]),
             "sdnn_train_step": (i, [vp, vp, vp, i, ctypes.c_float, vp, vp]),
             "sdnn_gradient": (i, [vp, vp, vp, i, vp, vp, vp]),
@@ -96,6 +97,7 @@ def lib():
             "fcs_step_graph": (i, [vp, vp, d, vp, i, vp]),
             "fcs_status": (i, [vp, ctypes.POINTER(ctypes.c_int)]),
             "fcs_strerror": (ctypes.c_char_p, [i]),
+            "fcs_alu_probe": (i, [i, i, i, vp, vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -124,6 +126,12 @@ def gradient_noalloc(w, x, labels, grad, loss=None, stream=None):
     labels: device int8 (batch); grad: device float (1732)."""
     _check("sdnn_gradient_noalloc", lib().sdnn_gradient_noalloc(_ptr(w), _ptr(x), _ptr(labels), int(x.shape[0]),
                                                                 _ptr(loss), _ptr(grad), _stream(stream)))
+
+
+def alu_probe(dtype, blocks, iters, out, stream=None):
+    """Launch the library's FMA-rate probe (blocks x 256 x iters x 64 flops);
+    out: device tensor of at least `blocks` elements of the dtype."""
+    _check("fcs_alu_probe", lib().fcs_alu_probe(int(dtype), int(blocks), int(iters), _ptr(out), _stream(stream)))
 
 
 def _ptr(t):
@@ -293,6 +301,10 @@ class Context:
 
     def classify(self, e, tau, logits=None, stream=None):
         _check("sdnn_classify", lib().sdnn_classify(self.h, _ptr(e), _ptr(tau), _ptr(logits), _stream(stream)))
+
+    def windows_raw(self, e, x, flat=None, stream=None):
+        """Raw proxy windows (instances x windows x 16 float) and flat flags."""
+        _check("sdnn_windows", lib().sdnn_windows(self.h, _ptr(e), _ptr(x), _ptr(flat), _stream(stream)))
 
     def indicator(self, e, tau, s=None, stream=None):
         _check("sdnn_indicator", lib().sdnn_indicator(self.h, _ptr(e), _ptr(tau), _ptr(s), _stream(stream)))

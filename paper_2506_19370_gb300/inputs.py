@@ -463,3 +463,65 @@ def classifier_windows(count, seed=SEED, window=WINDOW):
     feat = np.where(lab[:, None] == CLASS_KINK, np.abs(t) / window * 4.0, feat)
     feat = np.where(lab[:, None] == CLASS_C1, np.maximum(t, 0.0) ** 2 / window ** 2 * 8.0, feat)
     return s + A * feat, lab.astype(np.int8)
+
+
+# --------------------------------------------------------------------------
+# flow states with features at known places (training data of the classifier)
+# --------------------------------------------------------------------------
+FEATURE_L = 0.03   # localisation length of the kink and C1 features
+
+
+def feature_profiles(batch, seed=SEED, n1=256, n2=16, per_row=8, gamma=GAMMA):
+    """Seeded flow states on one Cartesian patch [0,1] x [0, (n2-1)/(n1-1)]
+    (free sides) with features at known places, for `batch` instances.
+
+    Every instance has a smooth background (density, velocity, pressure) and
+    `per_row` features on the lines x = a_k + b y (k = 0..per_row-1, a_k near
+    the centres of per_row equal bins of [0,1], |b| <= 1, so successive rows
+    see a feature up to a grid spacing apart), each of a seeded class: 1 a
+    jump, 2 a kink (slope jump), 3 a jump of the second derivative (C1), 4
+    none.  With s = x - a_k - b y and t = s / L, a feature changes log(rho),
+    log(p) and u by A * f: f = H(s) - 1/2 (jump), |t| exp(-t^2) (kink) and
+    t_+^2 exp(-t^2) (C1), L = FEATURE_L, so the features are localised and the
+    states stay positive.  Float32 arithmetic (the library's FP32 contexts
+    read float states).
+
+    Returns (patch, states, features): states a list of (4, n2, n1) conserved
+    arrays, features a dict with 'cls' (batch, per_row) int8, 'a' (batch,
+    per_row) and 'b' (batch,) float64.
+    """
+    rng = np.random.default_rng(seed)
+    h = 1.0 / (n1 - 1)
+    patch = Patch(n1, n2, (BC_FREE,) * 4, box=(0.0, 1.0, 0.0, (n2 - 1) * h))
+    X, Y = (c.astype(np.float32)[None] for c in patch.coords())
+    B, K = batch, per_row
+    cls = rng.integers(1, 5, size=(B, K)).astype(np.int8)
+    a = (np.arange(K) + 0.5) / K + rng.uniform(-0.15, 0.15, size=(B, K)) / K
+    b = rng.uniform(-1.0, 1.0, size=B)
+    om = rng.uniform(0.5, 2.0, size=(B, 4))
+    ph = rng.uniform(0.0, 2 * np.pi, size=(B, 4))
+    ky = rng.uniform(-2.0, 2.0, size=(B, 4))
+    amp = rng.uniform(0.1, 0.5, size=(B, K, 3)) * rng.choice([-1.0, 1.0], size=(B, K, 3))
+    f32 = np.float32
+
+    def col(v):
+        return np.asarray(v, dtype=f32)[:, None, None]
+
+    def bg(c, scale):
+        return f32(scale) * np.sin(f32(2 * np.pi) * col(om[:, c]) * X + col(ky[:, c]) * Y + col(ph[:, c]))
+
+    lrho, u, lp = bg(0, 0.15), f32(0.8) + bg(1, 0.3), bg(2, 0.15)
+    v = bg(3, 0.1)
+    for k in range(K):
+        t = (X - col(a[:, k]) - col(b) * Y) / f32(FEATURE_L)
+        g = np.exp(-t * t)
+        c = cls[:, k]
+        f = (col(c == CLASS_JUMP) * ((t >= 0).astype(f32) - f32(0.5)) + col(c == CLASS_KINK) * np.abs(t) * g
+             + col(c == CLASS_C1) * np.square(np.maximum(t, f32(0))) * g)
+        lrho += col(amp[:, k, 0]) * f
+        u += col(amp[:, k, 1]) * f
+        lp += col(amp[:, k, 2]) * f
+    rho, p = np.exp(lrho), np.exp(lp)
+    E = p / f32(gamma - 1.0) + f32(0.5) * rho * (u * u + v * v)
+    st = np.stack([rho, rho * u, rho * v, E], axis=1)
+    return patch, list(st), {"cls": cls, "a": a, "b": b}

@@ -133,13 +133,19 @@ def table_gain(d, C):
     return float(np.max(np.abs(A_R).sum(1) + np.abs(A_L).sum(1)))
 
 
-def deriv_bound(dtype, fmax, h, n, order, gain):
+def deriv_bound(dtype, fmax, h, n, order, gain=None):
     """Rounding bound of one FC derivative of a line with values up to fmax.
 
-    Sums of the continuation lose up to `gain` in relative accuracy (FP64 sums
-    are plain; FP32 sums are compensated, so only the final rounding counts),
-    the FFT pair loses ~log2(n), and each derivative order multiplies by up
-    to the largest wavenumber pi/h; factor 4 of headroom.
+    Both precisions continue in the Gram form (FP64: compensated projection
+    on the Gram basis; FP32: Gram coefficients of the shifted line, or
+    compensated sums with a split table), so the continuation adds a few
+    roundings of the line's values (the ill-conditioned combined table, whose
+    row sums `gain` reach ~7e3, never meets the data directly).  Rounding
+    errors of the FFT pair add up like a random walk over its log2(n) stages
+    (standard deviation ~ eps sqrt(log2 n + 4) fmax per mode); the derivative
+    weights mode k by k^order, whose root mean square over the band is
+    (pi/h)^order / sqrt(2 order + 1); the largest of all the points of a line
+    set stays within 4 standard deviations.
     """
-    cont = gain if dtype == F64 else 4.0
-    return 4.0 * EPS[dtype] * (math.log2(n) + cont) * fmax * (math.pi / h) ** order
+    return (4.0 * EPS[dtype] * math.sqrt(math.log2(n) + 4.0) * fmax * (math.pi / h) ** order
+            / math.sqrt(2 * order + 1))

@@ -95,7 +95,15 @@ def test_trained_network_beats_no_viscosity_and_viscosity_everywhere():
         state = "broke down" if rc != 0 else "completed"
         print(f"  {m:10s} {state} after {steps:4d} steps  L1(rho) {l1:.3e}  overshoot {over:.3e}")
     assert loss.item() < 0.5 * l0 and acc > 0.85
-    # the trained network's run completes; the inviscid FP32 run may break down
+    # the trained network's run completes and is closer to the exact solution
+    # than viscosity everywhere (which smears the waves)
     assert res["trained"][0] == 0 and res["everywhere"][0] == 0
-    assert res["trained"][1] < res["none"][1] and res["trained"][1] < res["everywhere"][1]
-    assert res["trained"][2] < 0.1 * res["none"][2]
+    assert np.isfinite(res["trained"][1]) and res["trained"][1] < res["everywhere"][1]
+    # without viscosity the FP32 run either breaks down (Gibbs oscillations at
+    # the shock drive the pressure negative: the gain is that the trained run
+    # completes at all) or completes with a larger error and overshoot
+    if res["none"][0] == 0:
+        assert np.isfinite(res["none"][1])
+        assert res["trained"][1] < res["none"][1] and res["trained"][2] < 0.1 * res["none"][2]
+    else:
+        assert res["none"][3] < res["trained"][3]   # it broke down before the end time
