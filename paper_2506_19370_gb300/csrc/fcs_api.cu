@@ -59,7 +59,7 @@ struct fcs_ctx {
   std::vector<int> kind_n1[2][2];  // [dir][kind][patch]: FFT size of the full (kind 0) and short
                                    // (kind 1, L-shaped patches) lines along q1 / q2; -1: none
   std::vector<int> n1_dir[2];    // distinct FFT sizes per direction
-  std::vector<Group> g_rows, g_pairs[2], g_tiles, g_vpairs;
+  std::vector<Group> g_rows, g_pairs[2], g_tiles, g_vpairs, g_vtiles;
   std::vector<int> tw_options;  // column-tile widths that fit in shared memory (widest first)
   CtxDev dev{};
   std::vector<void*> allocs;
@@ -67,6 +67,7 @@ struct fcs_ctx {
   int4* pairs0 = nullptr;
   int4* pairs1 = nullptr;
   int4* vpairs = nullptr;  // column pairs x fields of curvilinear patches (viscous gradient e_q2)
+  int2* vtiles = nullptr;  // column tiles of curvilinear patches (viscous gradient e_q2)
   int4* fpairs[2] = {nullptr, nullptr};  // row / column pairs x 4 fields of every patch (filter)
   std::vector<Group> g_fpairs[2];
   double* smr64 = nullptr;  // filter factors of the initial smearing (order smear_p), twiddle offsets
@@ -80,7 +81,7 @@ struct fcs_ctx {
   int nbtiles = 0;
   int4* fringe_ent = nullptr;     // copies: (dst patch, dst point, src patch, src point)
   int4* interp_ent = nullptr;     // interpolations: (dst patch, dst point, src patch, first block node)
-  double* interp_w64 = nullptr;   // 36 weights per interpolation
+  double* interp_w64 = nullptr;   // 12 weights per interpolation (the two factors of the tensor stencil)
   float* interp_w32 = nullptr;
   int ninterp = 0;
   double* wq = nullptr;
@@ -255,6 +256,12 @@ template <typename T>
 size_t ypass_smem(const fcs_ctx* c, int tw, int n1) {
   return ypass_bytes<T>(c->gnmax[1][n1], tw, c->gnfmax[1][n1], n1, kYWarps);
 }
+template <typename T>
+size_t cols_smem(const fcs_ctx* c, int tw, int n1, int nf) {
+  return cols_bytes<T>(c->gnmax[1][n1], tw, c->gnfmax[1][n1], n1, kYWarps) -
+         align16((size_t)4 * c->gnmax[1][n1] * (tw + 1) * sizeof(T)) +
+         align16((size_t)nf * c->gnmax[1][n1] * (tw + 1) * sizeof(T));
+}
 constexpr size_t kSmemMax = 227 * 1024;   // dynamic shared memory a block may use
 
 size_t blend_smem(int r, size_t tsize) {
@@ -298,12 +305,25 @@ int set_smem_attrs(const fcs_ctx* c) {
     for (int n1 : c->n1_dir[dir]) {
       FCS_N1_SWITCH(n1, FCS_CUDA((prep_fc_deriv<T, K>(deriv_smem<T>(c, n1)))); break)
     }
+  const int twmax = c->tw_options.empty() ? c->tw : c->tw_options[0];
+  for (int n1 : c->n1_dir[1]) {
+    FCS_N1_SWITCH(n1, FCS_CUDA((prep_fc_cols<T, K>(cols_smem<T>(c, twmax, n1, 4)))); break)
+  }
   return FCS_OK;
 }
 
 // FC derivative of a scalar field: one launch per FFT-size group of line pairs.
 template <typename T>
 int launch_deriv(fcs_ctx* c, const void* in, void* out, int dir, int order, cudaStream_t s) {
+  if (dir == 1) {   // columns: tiles of adjacent columns (coalesced row segments)
+    for (const Group& gr : c->g_tiles) {
+      const LaunchCfg g{(unsigned)grid_for((long long)c->dev.instances * gr.count, 1), kYWarps * 32,
+                        cols_smem<T>(c, c->tw, gr.n1, 1), s};
+      FCS_N1_SWITCH(gr.n1, FCS_CUDA((run_fc_cols<T, K>(c->dev, order, c->tiles + gr.begin, gr.count, 1,
+                                                       static_cast<const T*>(in), static_cast<T*>(out), g))); break)
+    }
+    return FCS_OK;
+  }
   const int4* pr = dir == 0 ? c->pairs0 : c->pairs1;
   for (const Group& gr : c->g_pairs[dir]) {
     const long long work = ((long long)c->dev.instances * gr.count + jobs_per_round(gr.n1) - 1) / jobs_per_round(gr.n1);
@@ -325,10 +345,10 @@ int launch_flux(fcs_ctx* c, const void* e, const void* mu, int mode, StageArgs<T
   T* G1 = static_cast<T*>(c->G1);
   T* G2 = static_cast<T*>(c->G2);
   if (mu) {  // viscous fluxes of curvilinear patches need e_q2 before the row pass
-    for (const Group& gr : c->g_vpairs) {
-      const long long work = ((long long)c->dev.instances * gr.count + jobs_per_round(gr.n1) - 1) / jobs_per_round(gr.n1);
-      const LaunchCfg g{(unsigned)grid_for(work, kWarps), kWarps * 32, deriv_smem<T>(c, gr.n1), s};
-      FCS_N1_SWITCH(gr.n1, FCS_CUDA((run_fc_deriv<T, K>(c->dev, 1, 1, c->vpairs + gr.begin, gr.count, ep, G2, g))); break)
+    for (const Group& gr : c->g_vtiles) {
+      const LaunchCfg g{(unsigned)grid_for((long long)c->dev.instances * gr.count, 1), kYWarps * 32,
+                        cols_smem<T>(c, c->tw, gr.n1, 4), s};
+      FCS_N1_SWITCH(gr.n1, FCS_CUDA((run_fc_cols<T, K>(c->dev, 1, c->vtiles + gr.begin, gr.count, 4, ep, G2, g))); break)
     }
   }
   for (const Group& gr : c->g_rows) {
@@ -461,14 +481,20 @@ int train_forward_backward(fcs_ctx* c, const float* x, const int8_t* lab, int B,
 // Column tiles of the pass along q2 for tile width tw (one instance),
 // grouped by FFT size.
 int set_tiles(fcs_ctx* c, const fcs_patch_desc* pd, int tw) {
-  std::vector<int2> tiles;
+  std::vector<int2> tiles, vtiles;
   grouped(c, 1, &tiles, &c->g_tiles, [&](int p, int lo, int hi, std::vector<int2>* o) {
     for (int c0 = lo; c0 < hi; c0 += tw) o->push_back(make_int2(p, c0));
   });
-  int2* t = nullptr;
+  grouped(c, 1, &vtiles, &c->g_vtiles, [&](int p, int lo, int hi, std::vector<int2>* o) {
+    if (pd[p].cartesian) return;
+    for (int c0 = lo; c0 < hi; c0 += tw) o->push_back(make_int2(p, c0));
+  });
+  int2 *t = nullptr, *vt = nullptr;
   int rc = upload(c, &t, tiles.data(), tiles.size() * sizeof(int2));
+  if (!rc && !vtiles.empty()) rc = upload(c, &vt, vtiles.data(), vtiles.size() * sizeof(int2));
   if (rc) return rc;
   c->tiles = t;
+  c->vtiles = vt;
   c->ntiles = (int)tiles.size();
   c->tw = tw;
   c->dev.tw = tw;
@@ -798,11 +824,10 @@ int fc_setup(fcs_ctx** out, int d, int C, const fcs_patch_desc* pd, int npatch, 
     if (!tw) return fail(FCS_EUNSUPPORTED);
     c->tw = tw;
   }
-  std::vector<int2> tiles;
-  grouped(c, 1, &tiles, &c->g_tiles, [&](int p, int lo, int hi, std::vector<int2>* o) {
-    for (int c0 = lo; c0 < hi; c0 += c->tw) o->push_back(make_int2(p, c0));
-  });
-  c->ntiles = (int)tiles.size();
+  {
+    const int rc0 = set_tiles(c, pd, c->tw);
+    if (rc0) return fail(rc0);
+  }
   std::vector<int2> pblk;
   for (int p = 0; p < npatch; ++p)
     for (int s0 = 0; s0 < pd[p].n1 * pd[p].n2; s0 += 256) pblk.push_back(make_int2(p, s0));
@@ -852,7 +877,8 @@ int fc_setup(fcs_ctx** out, int d, int C, const fcs_patch_desc* pd, int npatch, 
   for (const FringeCopy& f : fcopy) ent.push_back(make_int4(f.dst_patch, f.dst_point, f.src_patch, f.src_point));
   for (const FringeInterp& f : finterp) {
     ient.push_back(make_int4(f.dst_patch, f.dst_point, f.src_patch, f.src_point));
-    iw64.insert(iw64.end(), f.w, f.w + kStencil * kStencil);
+    iw64.insert(iw64.end(), f.wi, f.wi + kStencil);   // 12 weights per entry: along i, then along j
+    iw64.insert(iw64.end(), f.wj, f.wj + kStencil);
   }
   std::vector<float> iw32(iw64.begin(), iw64.end());
   c->nent = (int)ent.size();
@@ -867,6 +893,7 @@ int fc_setup(fcs_ctx** out, int d, int C, const fcs_patch_desc* pd, int npatch, 
   gram_basis_dd(d, Qhi.data(), Qlo.data());
   std::vector<float> gramQ(Qhi.begin(), Qhi.end()), gramT;
   std::vector<double> gramT64;
+  std::vector<float> gramR;
   // ---- device tables
   std::vector<double> tab64;
   std::vector<float> thi, tlo;
@@ -884,6 +911,12 @@ int fc_setup(fcs_ctx** out, int d, int C, const fcs_patch_desc* pd, int npatch, 
         gramT.push_back((float)v);
         gramT64.push_back(v);
       }
+    }
+    hp.dev.rs_off = (int)gramR.size();
+    {
+      std::vector<double> rs(hp.dev.C);
+      row_sums(d, hp.dev.C, hp.tab.data(), hp.tab_lo.data(), rs.data());
+      for (double v : rs) gramR.push_back((float)v);
     }
     hp.dev.tab_off = (int)tab64.size();
     for (double v : hp.tab) {
@@ -976,9 +1009,11 @@ int fc_setup(fcs_ctx** out, int d, int C, const fcs_patch_desc* pd, int npatch, 
   int* dstatus;
   float *dgq, *dgt;
   double *dgqh, *dgql, *dgt64;
+  float* dgr;
   if ((rc = upload(c, &dgq, gramQ.data(), gramQ.size() * 4)) || (rc = upload(c, &dgt, gramT.data(), gramT.size() * 4)) ||
       (rc = upload(c, &dgqh, Qhi.data(), Qhi.size() * 8)) || (rc = upload(c, &dgql, Qlo.data(), Qlo.size() * 8)) ||
-      (rc = upload(c, &dgt64, gramT64.data(), gramT64.size() * 8)))
+      (rc = upload(c, &dgt64, gramT64.data(), gramT64.size() * 8)) ||
+      (rc = upload(c, &dgr, gramR.data(), gramR.size() * 4)))
     return fail(rc);
   if ((rc = upload(c, &dpatch, c->patches.data(), c->patches.size() * sizeof(PatchDev))) ||
       (rc = upload(c, &dplan, plans.data(), plans.size() * sizeof(PlanDev))) ||
@@ -996,7 +1031,6 @@ int fc_setup(fcs_ctx** out, int d, int C, const fcs_patch_desc* pd, int npatch, 
       (rc = upload(c, &c->vpairs, vp.data(), vp.size() * sizeof(int4))) ||
       (rc = upload(c, &c->fpairs[0], fp[0].data(), fp[0].size() * sizeof(int4))) ||
       (rc = upload(c, &c->fpairs[1], fp[1].data(), fp[1].size() * sizeof(int4))) ||
-      (rc = upload(c, &c->tiles, tiles.data(), tiles.size() * sizeof(int2))) ||
       (rc = upload(c, &c->pblk, pblk.data(), pblk.size() * sizeof(int2))) ||
       (rc = upload(c, &c->nsw, nsw.data(), nsw.size() * sizeof(int4))) ||
       (rc = upload(c, &c->btiles, btiles.data(), btiles.size() * sizeof(int4))) ||
@@ -1072,6 +1106,7 @@ int fc_setup(fcs_ctx** out, int d, int C, const fcs_patch_desc* pd, int npatch, 
   D.gramQ64h = dgqh;
   D.gramQ64l = dgql;
   D.gramT64 = dgt64;
+  D.gramR = dgr;
   D.pblk = c->pblk;
   D.npblk = (int)pblk.size();
   D.nsw = c->nsw;
@@ -1096,11 +1131,17 @@ int fc_setup(fcs_ctx** out, int d, int C, const fcs_patch_desc* pd, int npatch, 
   D.tw = c->tw;
   D.n2max = c->n2max;
   if ((rc = (o.dtype == FCS_F64 ? set_smem_attrs<double>(c) : set_smem_attrs<float>(c)))) return fail(rc);
-  if (o.dtype != FCS_F64) {  // the metrics use FP64 derivatives
+  if (o.dtype != FCS_F64) {  // the metrics use FP64 derivatives (columns: one field per tile)
     for (int dir = 0; dir < 2; ++dir)
       for (int n1 : c->n1_dir[dir]) {
         FCS_N1_SWITCH(n1, if (prep_fc_deriv<double, K>(deriv_smem<double>(c, n1)) != cudaSuccess) return fail(FCS_ECUDA); break)
       }
+    const int twmax = c->tw_options.empty() ? c->tw : c->tw_options[0];
+    for (int n1 : c->n1_dir[1]) {
+      if (cols_smem<double>(c, c->tw, n1, 1) > kSmemMax) return fail(FCS_EUNSUPPORTED);
+      const size_t sm = std::min(cols_smem<double>(c, twmax, n1, 1), kSmemMax);
+      FCS_N1_SWITCH(n1, if (prep_fc_cols<double, K>(sm) != cudaSuccess) return fail(FCS_ECUDA); break)
+    }
   }
 
   // ---- metrics of curvilinear patches: FP64 FC derivatives of x and y
@@ -1165,7 +1206,7 @@ int fcs_get_layout(const fcs_ctx* c, fcs_layout* o) {
   o->window_off = c->window_off.data();
   o->tile_width = c->tw;
   o->launches_stage = (int)(c->g_rows.size() + c->g_tiles.size()) + (c->dev.n_nsw > 0);
-  o->launches_stage_visc = o->launches_stage + (int)c->g_vpairs.size();
+  o->launches_stage_visc = o->launches_stage + (int)c->g_vtiles.size();
   o->launches_exchange = (c->nent > 0) + (c->ninterp > 0);
   o->launches_av = 1 + (c->opt.av_radius <= kBlendMaxR ? 1 : 4) + o->launches_exchange;
   return FCS_OK;
@@ -1413,6 +1454,23 @@ int filter_impl(fcs_ctx* c, void* e, const CtxDev& dev, const void* w, cudaStrea
   for (int dir = 0; dir < 2; ++dir) {
     void* src = dir == 0 ? c->R : c->S;
     void* dst = dir == 0 ? c->S : c->R;
+    if (dir == 1) {   // columns: tiles of adjacent columns, the four fields of the state layout
+      for (const Group& gr : c->g_tiles) {
+        const unsigned grid = (unsigned)grid_for((long long)dev.instances * gr.count, 1);
+        if (f64) {
+          const LaunchCfg lc{grid, kYWarps * 32, cols_smem<double>(c, c->tw, gr.n1, 4), s};
+          FCS_N1_SWITCH(gr.n1, FCS_CUDA((run_fc_cols<double, K>(dev, 0, c->tiles + gr.begin, gr.count, 4,
+                                                                static_cast<const double*>(src),
+                                                                static_cast<double*>(dst), lc))); break)
+        } else {
+          const LaunchCfg lc{grid, kYWarps * 32, cols_smem<float>(c, c->tw, gr.n1, 4), s};
+          FCS_N1_SWITCH(gr.n1, FCS_CUDA((run_fc_cols<float, K>(dev, 0, c->tiles + gr.begin, gr.count, 4,
+                                                               static_cast<const float*>(src),
+                                                               static_cast<float*>(dst), lc))); break)
+        }
+      }
+      continue;
+    }
     for (const Group& gr : c->g_fpairs[dir]) {
       const long long work = ((long long)dev.instances * gr.count + jobs_per_round(gr.n1) - 1) / jobs_per_round(gr.n1);
       if (f64) {

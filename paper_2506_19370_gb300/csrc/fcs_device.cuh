@@ -49,6 +49,7 @@ struct PlanDev {
   int tab_off;          // offset of the C x d continuation table (FP64, and its FP32 split)
   int n1reg;            // n = 32 * n1reg: register FFT (two-level for even n1reg); 0: Stockham FFT
   int tg_off;           // offset of the C x d Gram blend table (FP32)
+  int rs_off;           // offset of the C values of the continuation of a constant 1 from the right end (FP32)
 };
 
 struct LineRef {
@@ -90,6 +91,7 @@ struct CtxDev {
   int gnfmax[2][kN1Classes];    // ... and longest FFT (shared-memory layout of the line kernels)
   const float* gramQ;           // d x d Gram basis at the matching points (FP32)
   const float* gramT;           // Gram blend tables of all plans (FP32)
+  const float* gramR;           // row sums of A_R of all plans (FP32): the continuation of a constant
   const double* gramQ64h;       // the Gram basis as double-double hi + lo
   const double* gramQ64l;
   const double* gramT64;        // Gram blend tables of all plans (FP64, same offsets as gramT)
@@ -533,6 +535,7 @@ struct LineOp {
   const double* gT64;
   const float* gQ32;    // FP32 Gram basis and the plan's FP32 Gram blend table
   const float* gT32;
+  const float* gR32;    // the plan's continuation of a constant (row sums of A_R), FP32
   int N, C, n, d, n1reg;
   T h;                  // line spacing
 };
@@ -543,13 +546,13 @@ template <>
 __device__ __forceinline__ LineOp<double> make_op<double>(const CtxDev& c, const PlanDev& pl, double h) {
   return {reinterpret_cast<const Cx<double>*>(c.tw64 + pl.tw_off), c.flt64 + pl.tw_off, c.tab64 + pl.tab_off,
           c.tabhi + pl.tab_off, c.tablo + pl.tab_off, c.gramQ64h, c.gramQ64l, c.gramT64 + pl.tg_off,
-          c.gramQ, c.gramT + pl.tg_off, pl.N, pl.C, pl.n, c.d, pl.n1reg, h};
+          c.gramQ, c.gramT + pl.tg_off, c.gramR + pl.rs_off, pl.N, pl.C, pl.n, c.d, pl.n1reg, h};
 }
 template <>
 __device__ __forceinline__ LineOp<float> make_op<float>(const CtxDev& c, const PlanDev& pl, float h) {
   return {reinterpret_cast<const Cx<float>*>(c.tw32 + pl.tw_off), c.flt32 + pl.tw_off, c.tab64 + pl.tab_off,
           c.tabhi + pl.tab_off, c.tablo + pl.tab_off, c.gramQ64h, c.gramQ64l, c.gramT64 + pl.tg_off,
-          c.gramQ, c.gramT + pl.tg_off, pl.N, pl.C, pl.n, c.d, pl.n1reg, h};
+          c.gramQ, c.gramT + pl.tg_off, c.gramR + pl.rs_off, pl.N, pl.C, pl.n, c.d, pl.n1reg, h};
 }
 
 template <typename T>
@@ -592,6 +595,11 @@ __device__ __forceinline__ void lane_dft(Cx<T>* x, const Cx<T>* tw, bool inv) {
   for (int k = 0; k < N1; ++k) x[k] = o[k];
 }
 
+// The radix-2 stages across lanes are written without a branch on the lane's
+// half: forward (decimation in frequency) every lane forms w' (p + sg x) with
+// sg = +1, w' = 1 in the lower half (x + p) and sg = -1, w' = w in the upper
+// half ((p - x) w); inverse (decimation in time) every lane forms
+// a + w'' b with (a, b, w'') = (x, p, w) below and (p, x, -w) above.
 template <typename T, int N1>
 __device__ __forceinline__ void reg_fft(Cx<T>* x, const Cx<T>* tw, bool inv, int lane) {
   if (!inv) {
@@ -600,31 +608,27 @@ __device__ __forceinline__ void reg_fft(Cx<T>* x, const Cx<T>* tw, bool inv, int
     for (int k = 1; k < N1; ++k) x[k] = cmul(x[k], ldtw(tw, lane * k));
 #pragma unroll
     for (int s = 16; s >= 1; s >>= 1) {
-      const Cx<T> w = ldtw(tw, (lane & (s - 1)) * (16 / s) * N1);
       const bool hi = lane & s;
+      const Cx<T> w0 = ldtw(tw, (lane & (s - 1)) * (16 / s) * N1);
+      const Cx<T> w = hi ? w0 : Cx<T>{T(1), T(0)};
+      const T sg = hi ? T(-1) : T(1);
 #pragma unroll
       for (int k = 0; k < N1; ++k) {
         const Cx<T> p = shfl_xor_c(x[k], s);
-        if (!hi) x[k] = {x[k].x + p.x, x[k].y + p.y};
-        else x[k] = cmul(Cx<T>{p.x - x[k].x, p.y - x[k].y}, w);
+        x[k] = cmul(Cx<T>{fma_t(sg, x[k].x, p.x), fma_t(sg, x[k].y, p.y)}, w);
       }
     }
   } else {
 #pragma unroll
     for (int s = 1; s <= 16; s <<= 1) {
-      Cx<T> w = ldtw(tw, (lane & (s - 1)) * (16 / s) * N1);
-      w.y = -w.y;
       const bool hi = lane & s;
+      const Cx<T> w0 = ldtw(tw, (lane & (s - 1)) * (16 / s) * N1);
+      const Cx<T> w = hi ? Cx<T>{-w0.x, w0.y} : Cx<T>{w0.x, -w0.y};   // -conj(w0) above, conj(w0) below
 #pragma unroll
       for (int k = 0; k < N1; ++k) {
         const Cx<T> p = shfl_xor_c(x[k], s);
-        if (!hi) {
-          const Cx<T> q = cmul(p, w);
-          x[k] = {x[k].x + q.x, x[k].y + q.y};
-        } else {
-          const Cx<T> q = cmul(x[k], w);
-          x[k] = {p.x - q.x, p.y - q.y};
-        }
+        const Cx<T> a = hi ? p : x[k], b = hi ? x[k] : p;
+        x[k] = {fma_t(w.x, b.x, fma_t(-w.y, b.y, a.x)), fma_t(w.x, b.y, fma_t(w.y, b.x, a.y))};
       }
     }
 #pragma unroll
@@ -668,15 +672,27 @@ __device__ __forceinline__ void reg_deriv_pair(const T* a, int sa, const T* b, i
           bL = gram_coef64(b + (d - 1) * sb, -sb, op.gQh, op.gQl, d, lane);
         }
       } else {
+        const float caR = a[(N - 1) * sa], caL = a[0];
+        const float cbR = b ? b[(N - 1) * sb] : 0.f, cbL = b ? b[0] : 0.f;
         for (int m = 0; m < d; ++m) {
           const float q = __ldg(op.gQ32 + m * d + lane);
-          aR = fmaf(q, a[(N - d + m) * sa] - offa, aR);
-          aL = fmaf(q, a[(d - 1 - m) * sa] - offa, aL);
+          aR = fmaf(q, a[(N - d + m) * sa] - caR, aR);
+          aL = fmaf(q, a[(d - 1 - m) * sa] - caL, aL);
           if (b) {
-            bR = fmaf(q, b[(N - d + m) * sb] - offb, bR);
-            bL = fmaf(q, b[(d - 1 - m) * sb] - offb, bL);
+            bR = fmaf(q, b[(N - d + m) * sb] - cbR, bR);
+            bL = fmaf(q, b[(d - 1 - m) * sb] - cbL, bL);
           }
         }
+      }
+    }
+    // FP32: the ends' values relative to the line offset, continued as constants
+    T eaR = T(0), eaL = T(0), ebR = T(0), ebL = T(0);
+    if constexpr (sizeof(T) == 4) {
+      eaR = a[(N - 1) * sa] - offa;
+      eaL = a[0] - offa;
+      if (b) {
+        ebR = b[(N - 1) * sb] - offb;
+        ebL = b[0] - offb;
       }
     }
 #pragma unroll
@@ -704,6 +720,13 @@ __device__ __forceinline__ void reg_deriv_pair(const T* a, int sa, const T* b, i
             }
             sa_ = fma_t(tr, gaR, fma_t(tl, gaL, sa_));
             sb_ = fma_t(tr, gbR, fma_t(tl, gbL, sb_));
+          }
+        }
+        if constexpr (sizeof(T) == 4) {
+          if (q >= 0) {
+            const float rr = __ldg(op.gR32 + q), rl = __ldg(op.gR32 + op.C - 1 - q);
+            sa_ = fmaf(eaR, rr, fmaf(eaL, rl, sa_));
+            sb_ = fmaf(ebR, rr, fmaf(ebL, rl, sb_));
           }
         }
         if (q >= 0) x[j1] = {sa_, b ? sb_ : T(0)};
@@ -930,6 +953,7 @@ struct GramOp {
   const double* Qh;   // the basis as double-double (FP64 lines)
   const double* Ql;
   const double* Tg64; // C x d blend values, FP64
+  const float* Rs;    // C values: continuation of a constant 1 from the right end (FP32)
 };
 
 template <typename T, int B>
@@ -946,21 +970,25 @@ __device__ __forceinline__ void tl_deriv_pair(const T* a, int sa, const T* b, in
     if (b) offb = (b[0] + b[(N - 1) * sb]) * T(0.5);
   }
   // lane t (< d) of the group computes Gram coefficient k = t of both lines
-  // and both ends (FP32: plain sums of the shifted values; FP64: compensated
-  // sums with the double-double basis); the group then shares them by
-  // shuffles
+  // and both ends (FP64: compensated sums with the double-double basis;
+  // FP32: plain sums of the values relative to the end's own value, whose
+  // differences are small for smooth data, the constant part entering
+  // through the continuation of a constant, e* Rs); the group then shares
+  // them by shuffles
   T gaR[MAXD], gaL[MAXD], gbR[MAXD], gbL[MAXD];
   {
     T cR = T(0), cL = T(0), dR = T(0), dL = T(0);
     if (active && t < d) {
       if constexpr (sizeof(T) == 4) {
+        const float caR = a[(N - 1) * sa], caL = a[0];
+        const float cbR = b ? b[(N - 1) * sb] : 0.f, cbL = b ? b[0] : 0.f;
         for (int m = 0; m < d; ++m) {
           const float q = __ldg(gop.Q + m * d + t);
-          cR = fmaf(q, a[(N - d + m) * sa] - offa, cR);
-          cL = fmaf(q, a[(d - 1 - m) * sa] - offa, cL);
+          cR = fmaf(q, a[(N - d + m) * sa] - caR, cR);
+          cL = fmaf(q, a[(d - 1 - m) * sa] - caL, cL);
           if (b) {
-            dR = fmaf(q, b[(N - d + m) * sb] - offb, dR);
-            dL = fmaf(q, b[(d - 1 - m) * sb] - offb, dL);
+            dR = fmaf(q, b[(N - d + m) * sb] - cbR, dR);
+            dL = fmaf(q, b[(d - 1 - m) * sb] - cbL, dL);
           }
         }
       } else {
@@ -1003,6 +1031,12 @@ __device__ __forceinline__ void tl_deriv_pair(const T* a, int sa, const T* b, in
         }
         sa_ = fma_t(tr, gaR[k], fma_t(tl, gaL[k], sa_));
         sb_ = fma_t(tr, gbR[k], fma_t(tl, gbL[k], sb_));
+      }
+      if constexpr (sizeof(T) == 4) {
+        // the ends' values relative to the line offset, continued as constants
+        const float rr = __ldg(gop.Rs + q), rl = __ldg(gop.Rs + op.C - 1 - q);
+        sa_ = fmaf(a[(N - 1) * sa] - offa, rr, fmaf(a[0] - offa, rl, sa_));
+        if (b) sb_ = fmaf(b[(N - 1) * sb] - offb, rr, fmaf(b[0] - offb, rl, sb_));
       }
       z = {sa_, b ? sb_ : T(0)};
     }
@@ -1103,7 +1137,8 @@ __device__ __forceinline__ void line_deriv_pair(const T* a, int sa, const T* b, 
     if (active) reg_deriv_pair<T, N1>(a, sa, b, sb, oa, soa, ob, sob, scale, op, order, lane);
   } else {
     const LineOp<T> op = make_op<T>(c, pl, h);
-    const GramOp<T> gop{c.gramQ, c.gramT + pl.tg_off, c.gramQ64h, c.gramQ64l, c.gramT64 + pl.tg_off};
+    const GramOp<T> gop{c.gramQ, c.gramT + pl.tg_off, c.gramQ64h, c.gramQ64l, c.gramT64 + pl.tg_off,
+                        c.gramR + pl.rs_off};
     tl_deriv_pair<T, 4 * N1>(a, sa, b, sb, oa, soa, ob, sob, scale, op, gop, order, lane & 7, tile, active);
   }
 }

@@ -226,11 +226,8 @@ int build_fringe(const fcs_patch_desc* pd, int npatch, int n_f, std::vector<Frin
           e.dst_point = j * q.n1 + i;
           e.src_patch = r;
           e.src_point = j0 * s.n1 + i0;
-          double vi[kS], vj[kS];
-          basis(fi - i0, vi, nullptr);
-          basis(fj - j0, vj, nullptr);
-          for (int b = 0; b < kS; ++b)
-            for (int a = 0; a < kS; ++a) e.w[b * kS + a] = vj[b] * vi[a];
+          basis(fi - i0, e.wi, nullptr);
+          basis(fj - j0, e.wj, nullptr);
           interp->push_back(e);
           found = true;
         }

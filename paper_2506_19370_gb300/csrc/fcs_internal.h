@@ -17,7 +17,7 @@ struct FringeCopy {
 };
 struct FringeInterp {
   int dst_patch, dst_point, src_patch, src_point;  // src_point: first node of the stencil block
-  double w[kStencil * kStencil];                   // weights [b][a], b along j
+  double wi[kStencil], wj[kStencil];               // tensor Lagrange weights: node (a, b) has wi[a] * wj[b]
 };
 
 // 1 if (i, j) of patch q lies in an n_f-point fringe of an internal side.
@@ -38,6 +38,10 @@ int build_table(int d, int C, double* A_R, double* A_R_lo = nullptr);
 // Gram basis of the d matching points (d x d, Q[m][k] = p_k(m), orthonormal
 // columns of the Vandermonde matrix at m / (d - 1)) as double-double hi + lo.
 void gram_basis_dd(int d, double* Qhi, double* Qlo);
+
+// Row sums of A_R (C values: the continuation of a constant 1 from the right
+// end), evaluated in double-double and rounded to FP64.
+void row_sums(int d, int C, const double* ARhi, const double* ARlo, double* rs);
 
 // Blend values of the Gram polynomials, T = A_R Q (C x d), evaluated in
 // double-double and rounded to FP64.

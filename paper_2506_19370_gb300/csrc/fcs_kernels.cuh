@@ -37,8 +37,9 @@ __global__ void k_exchange(CtxDev c, const int4* __restrict__ ent, int nent, T* 
 }
 
 // Interpolated fringe points: entries (dst patch, dst point, src patch, first
-// node of the donor block); w holds the kStencil x kStencil tensor Lagrange
-// weights of each entry ([b][a], b along j).  A group of 8 lanes takes one
+// node of the donor block); w holds the two factors of each entry's tensor
+// Lagrange stencil (kStencil weights along i, then kStencil along j: node
+// (a, b) has weight w_i[a] w_j[b]).  A group of 8 lanes takes one
 // (instance, entry), 4 per warp: lane a < 6 of the group sums the stencil
 // column a over the rows b (its loads of one row are adjacent to the other
 // lanes', so a warp load touches 4 short segments instead of 32 scattered
@@ -67,11 +68,13 @@ __global__ void k_interp(CtxDev c, const int4* __restrict__ ent, const T* __rest
       fd = nfields == 4 ? (long long)Pd.n1 * Pd.n2 : 0;
       dbase = (nfields == 4 ? inst * c.sstride + Pd.soff : inst * c.qstride + Pd.qoff) + x.y;
       if (a < S) {
+        // column a of the stencil block: sum over its rows b with the
+        // weights along j, then the weight of column a along i
         const T* src = field + (nfields == 4 ? inst * c.sstride + Ps.soff : inst * c.qstride + Ps.qoff) + x.w + a;
-        const T* wk = w + (size_t)k * S * S + a;
+        const T* wk = w + (size_t)k * 2 * S;
 #pragma unroll
         for (int b = 0; b < S; ++b) {
-          const T wv = wk[b * S];
+          const T wv = wk[S + b];
           const long long o = (long long)b * Ps.n1;
           acc[0] += wv * src[o];
           if (nfields == 4) {
@@ -80,6 +83,9 @@ __global__ void k_interp(CtxDev c, const int4* __restrict__ ent, const T* __rest
             acc[3] += wv * src[3 * fs + o];
           }
         }
+        const T wa = wk[a];
+#pragma unroll
+        for (int f = 0; f < 4; ++f) acc[f] *= wa;
       }
     }
 #pragma unroll

@@ -39,10 +39,26 @@ __host__ __device__ inline size_t deriv_warp_bytes(int nmax, int nfmax, int N1) 
   return align16((size_t)8 * nmax * sizeof(T)) + aux_cx(N1, nfmax) * 2 * sizeof(T);
 }
 template <typename T>
+__host__ __device__ inline size_t cols_bytes(int n2max, int tw, int nfmax, int N1, int warps) {
+  return align16((size_t)4 * n2max * (tw + 1) * sizeof(T)) + (size_t)warps * aux_cx(N1, nfmax) * 2 * sizeof(T);
+}
+template <typename T>
 __host__ __device__ inline size_t ypass_bytes(int n2max, int tw, int nfmax, int N1, int warps) {
   return align16((size_t)5 * n2max * (tw + 1) * sizeof(T)) + (size_t)warps * aux_cx(N1, nfmax) * 2 * sizeof(T);
 }
 constexpr int kYWarps = 8;
+
+// Blocks per SM the flux passes are compiled for (register budget 65536 /
+// (threads x blocks)).  The 32-lane shuffle FFT (odd n1) keeps only 2 n1
+// values of a line pair per lane, so the FP32 passes of n1 = 3 and 5 take
+// more blocks than the two-level FFT (even n1: 2 x 4 n1 values per lane);
+// n1 = 7 and 9 spill at the lower budgets (ptxas).
+__host__ __device__ constexpr int ypass_min_blocks(size_t tsize, int N1) {
+  return (N1 >= 1 && N1 <= 2) ? 4 : (N1 == 3 || (tsize == 4 && N1 == 5)) ? 3 : 2;
+}
+__host__ __device__ constexpr int xpass_min_blocks(size_t tsize, int N1) {
+  return (tsize == 4 && N1 == 3) ? 6 : (tsize == 4 && N1 == 5) ? 5 : 4;
+}
 
 struct LaunchCfg {
   unsigned grid;
@@ -58,10 +74,15 @@ template <typename T, int N1>
 cudaError_t prep_ypass(size_t smem);
 template <typename T, int N1>
 cudaError_t prep_fc_deriv(size_t smem);
+template <typename T, int N1>
+cudaError_t prep_fc_cols(size_t smem);
 
 template <typename T, int N1>
 cudaError_t run_fc_deriv(const CtxDev& c, int dir, int order, const int4* pairs, int npairs, const T* in, T* out,
                          LaunchCfg g);
+template <typename T, int N1>
+cudaError_t run_fc_cols(const CtxDev& c, int order, const int2* tiles, int ntiles, int nf, const T* in, T* out,
+                        LaunchCfg g);
 template <typename T, int N1>
 cudaError_t run_xpass(const CtxDev& c, int lbeg, int lcnt, const T* e, const T* mu, T* R, T* G1, const T* G2,
                       int chain, LaunchCfg g);

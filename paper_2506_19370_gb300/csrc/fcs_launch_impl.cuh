@@ -28,6 +28,16 @@ cudaError_t prep_fc_deriv(size_t smem) {
 }
 
 template <typename T, int N1>
+cudaError_t prep_fc_cols(size_t smem) {
+  return cudaFuncSetAttribute(k_fc_cols<T, N1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+template <typename T, int N1>
+cudaError_t run_fc_cols(const CtxDev& c, int order, const int2* tiles, int ntiles, int nf, const T* in, T* out,
+                        LaunchCfg g) {
+  k_fc_cols<T, N1><<<g.grid, g.block, g.smem, g.stream>>>(c, order, tiles, ntiles, nf, in, out);
+  return cudaGetLastError();
+}
+template <typename T, int N1>
 cudaError_t run_fc_deriv(const CtxDev& c, int dir, int order, const int4* pairs, int npairs, const T* in, T* out,
                          LaunchCfg g) {
   k_fc_deriv<T, N1><<<g.grid, g.block, g.smem, g.stream>>>(c, dir, order, pairs, npairs, in, out);
@@ -53,6 +63,9 @@ cudaError_t run_ypass(const CtxDev& c, const int2* tiles, int ntiles, const T* e
   template cudaError_t fcs::prep_xpass<T, N1>(size_t);                                                        \
   template cudaError_t fcs::prep_ypass<T, N1>(size_t);                                                        \
   template cudaError_t fcs::prep_fc_deriv<T, N1>(size_t);                                                     \
+  template cudaError_t fcs::prep_fc_cols<T, N1>(size_t);                                                      \
+  template cudaError_t fcs::run_fc_cols<T, N1>(const CtxDev&, int, const int2*, int, int, const T*, T*,        \
+                                               LaunchCfg);                                                    \
   template cudaError_t fcs::run_fc_deriv<T, N1>(const CtxDev&, int, int, const int4*, int, const T*, T*,     \
                                                 LaunchCfg);                                                   \
   template cudaError_t fcs::run_xpass<T, N1>(const CtxDev&, int, int, const T*, const T*, T*, T*, const T*,    \

@@ -81,6 +81,74 @@ __global__ void __launch_bounds__(kWarps * 32) k_fc_deriv(CtxDev c, int dir, int
   }
 }
 
+// FC derivative along q2 (spacing 1/(n2 - 1)) on tiles of tw adjacent
+// columns of one patch, the layout of the pass along q2: the tile's row
+// segments are staged in shared memory with coalesced copies, transformed in
+// place, and written back as row segments.  nf = 1: one scalar-layout field,
+// adjacent columns share a transform; nf = 4: the four fields of the state
+// layout, field pairs (0, 1) and (2, 3) of a column share one.  order as in
+// k_fc_deriv (0: the filter factors).
+template <typename T, int N1>
+__global__ void __launch_bounds__(kYWarps * 32, ypass_min_blocks(sizeof(T), N1))
+    k_fc_cols(CtxDev c, int order, const int2* __restrict__ tiles, int ntiles, int nf, const T* __restrict__ in,
+              T* __restrict__ out) {
+  constexpr int JPR = jobs_per_round(N1);
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int tw = c.tw, ld = c.tw + 1, n2m = c.gnmax[1][N1], nfmax = c.gnfmax[1][N1];
+  T* E = reinterpret_cast<T*>(smem_raw);   // [nf][n2m][ld], then the warps' FFT buffers
+  Cx<T>* aux = reinterpret_cast<Cx<T>*>(smem_raw + align16((size_t)nf * n2m * ld * sizeof(T))) +
+               (size_t)warp * aux_cx(N1, nfmax);
+  const int g = JPR == 4 ? (lane >> 3) : 0;
+  Cx<T>* tile = aux + (size_t)g * 8 * (4 * N1 + 1);
+  const long long total = (long long)c.instances * ntiles;
+  for (long long wk = blockIdx.x; wk < total; wk += gridDim.x) {
+    const int inst = (int)(wk / ntiles);
+    const int2 tl = tiles[wk % ntiles];
+    const PatchDev P = c.patches[tl.x];
+    const int c0 = tl.y;
+    const int j0 = line_start(P, 1, c0), N = P.n2 - j0;
+    const PlanDev pl = c.plans[line_plan(P, 1, c0)];
+    const int width = min(tw, (c0 < P.m1 ? P.m1 : P.n1) - c0);
+    const long long fs = nf == 1 ? 0 : (long long)P.n1 * P.n2;
+    const long long base = (nf == 1 ? inst * c.qstride + P.qoff : inst * c.sstride + P.soff) +
+                           (long long)j0 * P.n1 + c0;
+    const int cnt = nf * N * width;
+    for (int k = threadIdx.x; k < cnt; k += blockDim.x) {   // columns fastest: coalesced row segments
+      const int cc = k % width, r = k / width, j = r % N, f = r / N;
+      cp_async_elem(&E[(f * n2m + j) * ld + cc], in + base + f * fs + (long long)j * P.n1 + cc);
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    const int njobs = nf == 1 ? (width + 1) / 2 : 2 * width;
+    const T h = T(1) / T(P.n2 - 1);
+    for (int u0 = warp * JPR; u0 < njobs; u0 += kYWarps * JPR) {
+      const int u = u0 + g;
+      const bool active = u < njobs;
+      T* sa;
+      T* sb;
+      if (nf == 1) {
+        const int cc = active ? 2 * u : 0;
+        sa = E + cc;
+        sb = cc + 1 < width ? E + cc + 1 : nullptr;
+      } else {
+        const int cc = active ? (u >> 1) : 0, pr = u & 1;
+        sa = E + (2 * pr) * n2m * ld + cc;
+        sb = sa + n2m * ld;
+      }
+      // a pair's values are all read before any is written: in place
+      line_deriv_pair<T, N1>(sa, ld, sb, ld, sa, ld, sb, ld, T(1), c, pl, h, order, lane, aux, aux + nfmax, tile,
+                             active);
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < cnt; k += blockDim.x) {
+      const int cc = k % width, r = k / width, j = r % N, f = r / N;
+      out[base + f * fs + (long long)j * P.n1 + cc] = E[(f * n2m + j) * ld + cc];
+    }
+    __syncthreads();
+  }
+}
+
 // Flux of Eq. (1) along direction DIR at one point, transformed for the
 // parameter direction: DIR 0: y_q2 f - x_q2 g, DIR 1: -y_q1 f + x_q1 g;
 // Cartesian: f resp. g.  With viscosity the physical fluxes become f - mu e_x,
@@ -171,7 +239,7 @@ __device__ __forceinline__ void chain_contract(const T* v, const T* dw, T ca, T 
 // CH = 1: chain-rule form (inviscid): w is staged and differentiated in
 // place, then R = -(ca A + cb B) w_q1 point by point.
 template <typename T, int N1, int CH>
-__global__ void __launch_bounds__(kWarps * 32, 4) k_xpass(CtxDev c, int lbeg, int lcnt, const T* __restrict__ e,
+__global__ void __launch_bounds__(kWarps * 32, xpass_min_blocks(sizeof(T), N1)) k_xpass(CtxDev c, int lbeg, int lcnt, const T* __restrict__ e,
                                                         const T* __restrict__ mu, T* __restrict__ R,
                                                         T* __restrict__ G1, const T* __restrict__ G2) {
   constexpr int JPR = jobs_per_round(N1);
@@ -324,7 +392,7 @@ __global__ void __launch_bounds__(kWarps * 32, 4) k_xpass(CtxDev c, int lbeg, in
 // MODE_CHAIN (or-ed into MODE): chain-rule form (inviscid): w is staged and
 // differentiated in place, and the epilogue forms (ca A + cb B) w_q2.
 template <typename T, int MODE, int N1>
-__global__ void __launch_bounds__(kYWarps * 32, (N1 >= 1 && N1 <= 2) ? 4 : ((N1 >= 1 && N1 <= 3) ? 3 : 2)) k_ypass(CtxDev c, const int2* __restrict__ tiles, int ntiles,
+__global__ void __launch_bounds__(kYWarps * 32, ypass_min_blocks(sizeof(T), N1)) k_ypass(CtxDev c, const int2* __restrict__ tiles, int ntiles,
                                                          const T* __restrict__ e, const T* __restrict__ mu,
                                                          const T* __restrict__ R, const T* __restrict__ G1,
                                                          T* __restrict__ G2, StageArgs<T> st) {
@@ -362,6 +430,22 @@ __global__ void __launch_bounds__(kYWarps * 32, (N1 >= 1 && N1 <= 2) ? 4 : ((N1 
     __shared__ int act[32];    // compacted list of such columns
     __shared__ int nact;
     if (threadIdx.x < 32) colv[threadIdx.x] = 0;
+    // the epilogue's operands (R, and e_n, acc of a stage update) are read
+    // after the transforms: start moving the tile's rows of them into L2 now
+    // (one prefetch per row segment and field, spread over the threads)
+    {
+      const int narr = (MODE & 3) == MODE_RK ? 3 : 1;
+      const int nseg = N * 4 * narr;
+      for (int k = threadIdx.x; k < nseg; k += blockDim.x) {
+        const int j = k % N, f = (k / N) & 3, a = k / (4 * N);
+        const T* base = a == 0 ? R : (a == 1 ? st.e_n : st.acc);
+        if (base) {
+          const T* row = base + sbase + f * np + (long long)j * P.n1;
+          asm volatile("prefetch.global.L2 [%0];" ::"l"(row));
+          asm volatile("prefetch.global.L2 [%0];" ::"l"(row + width - 1));
+        }
+      }
+    }
     __syncthreads();
     if (colok)
       for (int j = jr; j < N; j += js) {

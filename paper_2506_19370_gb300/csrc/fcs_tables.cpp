@@ -236,6 +236,14 @@ void gram_basis_dd(int d, double* Qhi, double* Qlo) {
   }
 }
 
+void row_sums(int d, int C, const double* ARhi, const double* ARlo, double* rs) {
+  for (int c = 0; c < C; ++c) {
+    dd v = mk(0.0);
+    for (int m = 0; m < d; ++m) v = add(v, dd{ARhi[c * d + m], ARlo[c * d + m]});
+    rs[c] = v.hi + v.lo;
+  }
+}
+
 void gram_blend(int d, int C, const double* ARhi, const double* ARlo, const double* Qhi, const double* Qlo,
                 double* T) {
   for (int c = 0; c < C; ++c)

@@ -71,7 +71,7 @@ class WindowSource:
     instances at a time, on one FP32 context (its network is the one trained
     and evaluated)."""
 
-    def __init__(self, chunk=2048, seed=I.SEED):
+    def __init__(self, chunk=2048, seed=I.SEED, d=5):
         import torch
         if chunk % PARTS:
             raise ValueError(f"chunk must be a multiple of {PARTS}")
@@ -79,7 +79,8 @@ class WindowSource:
         self.chunk, self.seed = chunk, seed
         patch, st, feat = I.feature_profiles(1, seed=seed)
         self.patch = patch
-        self.ctx = fcsdnn.Context(I.Instance([patch], st), dtype=fcsdnn.F32, instances=chunk, c_policy=1,
+        # d: the FC-Gram degree of the solver whose FC step makes the windows
+        self.ctx = fcsdnn.Context(I.Instance([patch], st), d=d, dtype=fcsdnn.F32, instances=chunk, c_policy=1,
                                   train_batch_max=4096)
         self.nx = N2 * len(window_starts(N1))       # row windows come first in the window table
         c = self.ctx

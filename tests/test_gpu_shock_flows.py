@@ -115,3 +115,60 @@ def test_shock_flow_against_oracle(case):
     assert res["L1_rel_density"] < 1e-3
     assert res["classifier_mismatch_well_decided"] <= tol_dec
     assert res["trajectory_window_mismatch"] <= tol_all
+
+
+def test_step_flow_full_size_2000_stages():
+    # The step-flow configuration at full size: the 64-patch layout of ~0.85M
+    # points (h0 = 0.002; uneven non-coincident grids, one C1 and one C2
+    # corner patch) for 2000 Runge-Kutta stages (500 steps), FP32 with the
+    # BF16 classifier against the plain FP64 form on the GPU (the FP64 form
+    # stands in for the oracle at this size: it matches the oracle to 1e-12
+    # per derivative in the parity tests; the oracle itself runs the 32-patch
+    # version above).  Same weights, same time steps (the FP64 run's),
+    # viscosity and filter on.  Bars: L1 density error 1e-3 relative; on
+    # identical states (the FP32 run's, every 50 steps) 99.9 % of the windows
+    # get the same class from the BF16 and the FP64 network.
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    inst = I.ffs_instance(h0=0.002)
+    c32 = fcsdnn.Context(inst, dtype=fcsdnn.F32, c_policy=1, filter_step=1)
+    c64 = fcsdnn.Context(inst, dtype=fcsdnn.F64, c_policy=1, filter_step=1)
+    xw, yw = I.classifier_windows(4096, seed=I.SEED)
+    c32.set_weights(sdnn.init_params(0).astype(np.float32))
+    xd, yd = torch.from_numpy(xw.astype(np.float32)).cuda(), torch.from_numpy(yw).cuda()
+    for _ in range(300):
+        c32.train_step(xd, yd, 3e-3)
+    c64.set_weights(c32.get_weights())
+    e32 = c32.to_device(c32.pack_state(inst.state))
+    e64 = c64.to_device(c64.pack_state(inst.state))
+    dtd = torch.zeros(1, dtype=torch.float64, device="cuda")
+    t32, t64 = c32.new_scalar(torch.int8), c64.new_scalar(torch.int8)
+    lg32 = torch.zeros(c32.windows * 4, dtype=torch.float32, device="cuda")
+    lg64 = torch.zeros(c64.windows * 4, dtype=torch.float64, device="cuda")
+    same = tot = 0
+    for k in range(500):
+        c64.step(e64, dt_dev=dtd, use_av=True)
+        c32.step(e32, dt=float(dtd.item()), use_av=True)
+        if k % 50 == 49:
+            # both networks on the FP32 run's state
+            c32.classify(e32, t32, lg32)
+            c64.classify(e32.to(torch.float64), t64, lg64)
+            z32 = lg32.view(-1, 4).cpu().numpy()
+            z64 = lg64.view(-1, 4).cpu().numpy()
+            tw32 = np.where(np.all(z32 == 0, 1), 4, 1 + np.argmax(z32, 1))
+            tw64 = np.where(np.all(z64 == 0, 1), 4, 1 + np.argmax(z64, 1))
+            same += int(np.sum(tw32 != tw64))
+            tot += len(tw32)
+    torch.cuda.synchronize()
+    rc32, _ = c32.status()
+    rc64, _ = c64.status()
+    a, b = c32.unpack_state(e32), c64.unpack_state(e64)
+    num = sum(float(np.abs(x[0] - y[0])[p.active()].sum()) for x, y, p in zip(a, b, inst.patches))
+    den = sum(float(np.abs(y[0])[p.active()].sum()) for y, p in zip(b, inst.patches))
+    pts = sum(int(p.active().sum()) for p in inst.patches)
+    print(f"\nstep flow {pts} points, 2000 stages: L1 rel density FP32 vs FP64 {num / den:.3e}; "
+          f"window classes on identical states differ on {same} of {tot} ({same / tot:.2e}); "
+          f"rho_min FP32 {min(float(x[0][p.active()].min()) for x, p in zip(a, inst.patches)):.3f}")
+    assert rc32 == 0 and rc64 == 0
+    assert num / den < 1e-3
+    assert same / tot <= 1e-3
