@@ -555,6 +555,7 @@ def run_ours(args):
     xs = ctx.to_device(ctx.pack_scalar([rng.standard_normal((p.n2, p.n1)) for p in inst0.patches]))
     ys = ctx.new_scalar()
     fcd = {}
+    torch.cuda.nvtx.range_push("fcs_fcderiv")
     for direction in (0, 1):
         with torch.cuda.stream(stream):
             ctx.fc_derivative(xs, ys, direction, 1, stream)
@@ -570,6 +571,7 @@ def run_ours(args):
             ts_.append(a.elapsed_time(b))
         ts_.sort()
         fcd[direction] = ts_[len(ts_) // 2]
+    torch.cuda.nvtx.range_pop()
     fcd_bytes = 2.0 * 4 * points
     fcd_gbs = [fcd_bytes / (fcd[k] / 1000.0) / 1e9 for k in (0, 1)]
     fc_derivative = {"kernel": "k_fc_deriv (FP32, all FFT-size groups of one direction)",

@@ -170,7 +170,7 @@ typedef struct {
                                  pass and one column pass per FFT-size group, plus the no-slip
                                  wall temperature when the layout has FCS_BC_NOSLIP sides;
                                  euler_rhs launches that one fewer) */
-  int launches_stage_visc;    /* the same with viscosity (adds the e_q2 pass of curvilinear patches) */
+  int launches_stage_visc;    /* the same with viscosity (adds the e_q1 pass of curvilinear patches) */
   int launches_exchange;      /* kernel launches of one patch_exchange call (copies, interpolations) */
   int launches_av;            /* kernel launches of one av_assemble call (exchange included) */
 } fcs_layout;

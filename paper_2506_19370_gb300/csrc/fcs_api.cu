@@ -59,15 +59,14 @@ struct fcs_ctx {
   std::vector<int> kind_n1[2][2];  // [dir][kind][patch]: FFT size of the full (kind 0) and short
                                    // (kind 1, L-shaped patches) lines along q1 / q2; -1: none
   std::vector<int> n1_dir[2];    // distinct FFT sizes per direction
-  std::vector<Group> g_rows, g_pairs[2], g_tiles, g_vpairs, g_vtiles;
+  std::vector<Group> g_rows, g_pairs[2], g_tiles, g_vpairs;
   std::vector<int> tw_options;  // column-tile widths that fit in shared memory (widest first)
   CtxDev dev{};
   std::vector<void*> allocs;
   // device arrays
   int4* pairs0 = nullptr;
   int4* pairs1 = nullptr;
-  int4* vpairs = nullptr;  // column pairs x fields of curvilinear patches (viscous gradient e_q2)
-  int2* vtiles = nullptr;  // column tiles of curvilinear patches (viscous gradient e_q2)
+  int4* vpairs = nullptr;  // row pairs x fields of curvilinear patches (viscous gradient e_q1)
   int4* fpairs[2] = {nullptr, nullptr};  // row / column pairs x 4 fields of every patch (filter)
   std::vector<Group> g_fpairs[2];
   double* smr64 = nullptr;  // filter factors of the initial smearing (order smear_p), twiddle offsets
@@ -79,8 +78,8 @@ struct fcs_ctx {
   int4* nsw = nullptr;   // no-slip wall points (patch, point, inward stride)
   int4* btiles = nullptr;  // 32 x 32 output tiles of the viscosity blend (patch, i0, j0)
   int nbtiles = 0;
-  int4* fringe_ent = nullptr;     // copies: (dst patch, dst point, src patch, src point)
-  int4* interp_ent = nullptr;     // interpolations: (dst patch, dst point, src patch, first block node)
+  int4* fringe_ent[2] = {nullptr, nullptr};   // copies, resolved for the state [0] and scalar [1] layouts
+  int4* interp_ent[2] = {nullptr, nullptr};   // interpolations (src: first node of the donor block), likewise
   double* interp_w64 = nullptr;   // 12 weights per interpolation (the two factors of the tensor stencil)
   float* interp_w32 = nullptr;
   int ninterp = 0;
@@ -312,18 +311,11 @@ int set_smem_attrs(const fcs_ctx* c) {
   return FCS_OK;
 }
 
-// FC derivative of a scalar field: one launch per FFT-size group of line pairs.
+// FC derivative of a scalar field: one launch per FFT-size group of line pairs
+// (rows or columns; the column-tile kernel leaves most of its warps idle on a
+// single field, whose adjacent columns share one transform).
 template <typename T>
 int launch_deriv(fcs_ctx* c, const void* in, void* out, int dir, int order, cudaStream_t s) {
-  if (dir == 1) {   // columns: tiles of adjacent columns (coalesced row segments)
-    for (const Group& gr : c->g_tiles) {
-      const LaunchCfg g{(unsigned)grid_for((long long)c->dev.instances * gr.count, 1), kYWarps * 32,
-                        cols_smem<T>(c, c->tw, gr.n1, 1), s};
-      FCS_N1_SWITCH(gr.n1, FCS_CUDA((run_fc_cols<T, K>(c->dev, order, c->tiles + gr.begin, gr.count, 1,
-                                                       static_cast<const T*>(in), static_cast<T*>(out), g))); break)
-    }
-    return FCS_OK;
-  }
   const int4* pr = dir == 0 ? c->pairs0 : c->pairs1;
   for (const Group& gr : c->g_pairs[dir]) {
     const long long work = ((long long)c->dev.instances * gr.count + jobs_per_round(gr.n1) - 1) / jobs_per_round(gr.n1);
@@ -334,8 +326,9 @@ int launch_deriv(fcs_ctx* c, const void* in, void* out, int dir, int order, cuda
   return FCS_OK;
 }
 
-// The operator (and stage): row passes, then column-tile passes, one launch
-// per FFT-size group; every row pass precedes every column pass in the stream.
+// The operator (and stage): column-tile passes (partial operator R), then
+// row passes (L, and the stage update), one launch per FFT-size group; every
+// column pass precedes every row pass in the stream.
 template <typename T>
 int launch_flux(fcs_ctx* c, const void* e, const void* mu, int mode, StageArgs<T> st, cudaStream_t s) {
   if (mu && c->opt.op_form == 1) return FCS_EUNSUPPORTED;  // the chain-rule form is inviscid
@@ -344,34 +337,36 @@ int launch_flux(fcs_ctx* c, const void* e, const void* mu, int mode, StageArgs<T
   T* R = static_cast<T*>(c->R);
   T* G1 = static_cast<T*>(c->G1);
   T* G2 = static_cast<T*>(c->G2);
-  if (mu) {  // viscous fluxes of curvilinear patches need e_q2 before the row pass
-    for (const Group& gr : c->g_vtiles) {
-      const LaunchCfg g{(unsigned)grid_for((long long)c->dev.instances * gr.count, 1), kYWarps * 32,
-                        cols_smem<T>(c, c->tw, gr.n1, 4), s};
-      FCS_N1_SWITCH(gr.n1, FCS_CUDA((run_fc_cols<T, K>(c->dev, 1, c->vtiles + gr.begin, gr.count, 4, ep, G2, g))); break)
+  if (mu) {  // viscous fluxes of curvilinear patches need e_q1 before the column pass
+    for (const Group& gr : c->g_vpairs) {
+      const long long work =
+          ((long long)c->dev.instances * gr.count + jobs_per_round(gr.n1) - 1) / jobs_per_round(gr.n1);
+      const LaunchCfg g{(unsigned)grid_for(work, kWarps), kWarps * 32, deriv_smem<T>(c, gr.n1), s};
+      FCS_N1_SWITCH(gr.n1, FCS_CUDA((run_fc_deriv<T, K>(c->dev, 0, 1, c->vpairs + gr.begin, gr.count, ep, G1, g)));
+                    break)
     }
+  }
+  const bool ch = c->opt.op_form == 1;
+  for (const Group& gr : c->g_tiles) {
+    const long long w1 = (long long)c->opt.instances * gr.count;
+    const LaunchCfg gy{(unsigned)grid_for(w1, 1), kYWarps * 32, ypass_smem<T>(c, c->tw, gr.n1), s};
+    FCS_N1_SWITCH(gr.n1, FCS_CUDA((run_ypass<T, K>(c->dev, c->tiles + gr.begin, gr.count, ep, mp, R, G1, G2, ch, gy)));
+                  break)
   }
   for (const Group& gr : c->g_rows) {
     const long long w0 = (long long)c->opt.instances * ((gr.count + kRowsPerWarp - 1) / kRowsPerWarp);
     const LaunchCfg gx{(unsigned)grid_for(w0, kWarps), kWarps * 32, xpass_smem<T>(c, gr.n1), s};
-    FCS_N1_SWITCH(gr.n1, FCS_CUDA((run_xpass<T, K>(c->dev, gr.begin, gr.count, ep, mp, R, G1, G2, c->opt.op_form, gx)));
-                  break)
-  }
-  for (const Group& gr : c->g_tiles) {
-    const long long w1 = (long long)c->opt.instances * gr.count;
-    const LaunchCfg gy{(unsigned)grid_for(w1, 1), kYWarps * 32, ypass_smem<T>(c, c->tw, gr.n1), s};
-    const int2* tl = c->tiles + gr.begin;
-    const bool ch = c->opt.op_form == 1;
+    const int b = gr.begin, n = gr.count;
     if (mode == MODE_RHS && !ch) {
-      FCS_N1_SWITCH(gr.n1, FCS_CUDA((run_ypass<T, MODE_RHS, K>(c->dev, tl, gr.count, ep, mp, R, G1, G2, st, gy))); break)
+      FCS_N1_SWITCH(gr.n1, FCS_CUDA((run_xpass<T, MODE_RHS, K>(c->dev, b, n, ep, mp, R, G1, G2, st, gx))); break)
     } else if (mode == MODE_RHS) {
-      FCS_N1_SWITCH(gr.n1, FCS_CUDA((run_ypass<T, MODE_RHS | MODE_CHAIN, K>(c->dev, tl, gr.count, ep, mp, R, G1, G2, st,
-                                                                            gy))); break)
+      FCS_N1_SWITCH(gr.n1, FCS_CUDA((run_xpass<T, MODE_RHS | MODE_CHAIN, K>(c->dev, b, n, ep, mp, R, G1, G2, st, gx)));
+                    break)
     } else if (!ch) {
-      FCS_N1_SWITCH(gr.n1, FCS_CUDA((run_ypass<T, MODE_RK, K>(c->dev, tl, gr.count, ep, mp, R, G1, G2, st, gy))); break)
+      FCS_N1_SWITCH(gr.n1, FCS_CUDA((run_xpass<T, MODE_RK, K>(c->dev, b, n, ep, mp, R, G1, G2, st, gx))); break)
     } else {
-      FCS_N1_SWITCH(gr.n1, FCS_CUDA((run_ypass<T, MODE_RK | MODE_CHAIN, K>(c->dev, tl, gr.count, ep, mp, R, G1, G2, st,
-                                                                           gy))); break)
+      FCS_N1_SWITCH(gr.n1, FCS_CUDA((run_xpass<T, MODE_RK | MODE_CHAIN, K>(c->dev, b, n, ep, mp, R, G1, G2, st, gx)));
+                    break)
     }
   }
   if (mode == MODE_RK && c->dev.n_nsw > 0) {  // no-slip walls: temperature after every point's stage
@@ -427,16 +422,17 @@ int exchange_impl(fcs_ctx* c, void* field, int nfields, int clamp, cudaStream_t 
   const bool f64 = c->opt.dtype == FCS_F64;
   if (c->nent) {
     const int g = grid_for(I * c->nent * nfields, 256);
-    if (f64) k_exchange<double><<<g, 256, 0, s>>>(c->dev, c->fringe_ent, c->nent, static_cast<double*>(field), nfields);
-    else k_exchange<float><<<g, 256, 0, s>>>(c->dev, c->fringe_ent, c->nent, static_cast<float*>(field), nfields);
+    const int4* en = c->fringe_ent[nfields == 4 ? 0 : 1];
+    if (f64) k_exchange<double><<<g, 256, 0, s>>>(c->dev, en, c->nent, static_cast<double*>(field), nfields);
+    else k_exchange<float><<<g, 256, 0, s>>>(c->dev, en, c->nent, static_cast<float*>(field), nfields);
   }
   if (c->ninterp) {
     const int g = grid_for(I * c->ninterp, 32);   // 4 entries per warp, 8 warps per block
     if (f64)
-      k_interp<double><<<g, 256, 0, s>>>(c->dev, c->interp_ent, c->interp_w64, c->ninterp,
+      k_interp<double><<<g, 256, 0, s>>>(c->dev, c->interp_ent[nfields == 4 ? 0 : 1], c->interp_w64, c->ninterp,
                                          static_cast<double*>(field), nfields, clamp);
     else
-      k_interp<float><<<g, 256, 0, s>>>(c->dev, c->interp_ent, c->interp_w32, c->ninterp,
+      k_interp<float><<<g, 256, 0, s>>>(c->dev, c->interp_ent[nfields == 4 ? 0 : 1], c->interp_w32, c->ninterp,
                                         static_cast<float*>(field), nfields, clamp);
   }
   return cuda_err(cudaGetLastError());
@@ -480,21 +476,15 @@ int train_forward_backward(fcs_ctx* c, const float* x, const int8_t* lab, int B,
 
 // Column tiles of the pass along q2 for tile width tw (one instance),
 // grouped by FFT size.
-int set_tiles(fcs_ctx* c, const fcs_patch_desc* pd, int tw) {
-  std::vector<int2> tiles, vtiles;
+int set_tiles(fcs_ctx* c, int tw) {
+  std::vector<int2> tiles;
   grouped(c, 1, &tiles, &c->g_tiles, [&](int p, int lo, int hi, std::vector<int2>* o) {
     for (int c0 = lo; c0 < hi; c0 += tw) o->push_back(make_int2(p, c0));
   });
-  grouped(c, 1, &vtiles, &c->g_vtiles, [&](int p, int lo, int hi, std::vector<int2>* o) {
-    if (pd[p].cartesian) return;
-    for (int c0 = lo; c0 < hi; c0 += tw) o->push_back(make_int2(p, c0));
-  });
-  int2 *t = nullptr, *vt = nullptr;
+  int2* t = nullptr;
   int rc = upload(c, &t, tiles.data(), tiles.size() * sizeof(int2));
-  if (!rc && !vtiles.empty()) rc = upload(c, &vt, vtiles.data(), vtiles.size() * sizeof(int2));
   if (rc) return rc;
   c->tiles = t;
-  c->vtiles = vt;
   c->ntiles = (int)tiles.size();
   c->tw = tw;
   c->dev.tw = tw;
@@ -543,7 +533,7 @@ int autotune_tile_width(fcs_ctx* c, const fcs_patch_desc* pd) {
   float best = 1e30f;
   int best_tw = c->tw;
   for (int tw : c->tw_options) {
-    int rc = set_tiles(c, pd, tw);
+    int rc = set_tiles(c, tw);
     if (rc) return rc;
     float ms = 0.f;
     rc = c->tsize == 8 ? time_rhs<double>(c, &ms) : time_rhs<float>(c, &ms);
@@ -553,7 +543,7 @@ int autotune_tile_width(fcs_ctx* c, const fcs_patch_desc* pd) {
       best_tw = tw;
     }
   }
-  return set_tiles(c, pd, best_tw);
+  return set_tiles(c, best_tw);
 }
 
 // =====================================================================
@@ -779,8 +769,8 @@ int fc_setup(fcs_ctx** out, int d, int C, const fcs_patch_desc* pd, int npatch, 
       for (int f = 0; f < 4; ++f)
         for (int l = lo; l < hi; l += 2) o->push_back(make_int4(p, l, l + 1 < hi ? l + 1 : -1, f));
     });
-  std::vector<int4> vp;  // state-layout column pairs of curvilinear patches, 4 fields
-  grouped(c, 1, &vp, &c->g_vpairs, [&](int p, int lo, int hi, std::vector<int4>* o) {
+  std::vector<int4> vp;  // state-layout row pairs of curvilinear patches, 4 fields
+  grouped(c, 0, &vp, &c->g_vpairs, [&](int p, int lo, int hi, std::vector<int4>* o) {
     if (pd[p].cartesian) return;
     for (int f = 0; f < 4; ++f)
       for (int i = lo; i < hi; i += 2) o->push_back(make_int4(p, i, i + 1 < hi ? i + 1 : -1, f));
@@ -825,7 +815,7 @@ int fc_setup(fcs_ctx** out, int d, int C, const fcs_patch_desc* pd, int npatch, 
     c->tw = tw;
   }
   {
-    const int rc0 = set_tiles(c, pd, c->tw);
+    const int rc0 = set_tiles(c, c->tw);
     if (rc0) return fail(rc0);
   }
   std::vector<int2> pblk;
@@ -872,17 +862,29 @@ int fc_setup(fcs_ctx** out, int d, int C, const fcs_patch_desc* pd, int npatch, 
   std::vector<FringeCopy> fcopy;
   std::vector<FringeInterp> finterp;
   if (build_fringe(pd, npatch, o.n_f, &fcopy, &finterp) != 0) return fail(FCS_EOVERLAP);
-  std::vector<int4> ent, ient;
+  // entries resolved for the state layout (fields 4) and the scalar layout:
+  // offsets within one instance (32-bit), field strides, the donor's row pitch
+  if (soff > (size_t)INT32_MAX) return fail(FCS_EUNSUPPORTED);
+  std::vector<int4> ent[2], ient[2];
   std::vector<double> iw64;
-  for (const FringeCopy& f : fcopy) ent.push_back(make_int4(f.dst_patch, f.dst_point, f.src_patch, f.src_point));
+  auto resolved = [&](int lay, int dp, int dpt, int sp, int spt) {
+    const long long dnp = (long long)pd[dp].n1 * pd[dp].n2, snp = (long long)pd[sp].n1 * pd[sp].n2;
+    const int64_t* off = lay == 0 ? c->state_off.data() : c->scalar_off.data();
+    return make_int4((int)(off[dp] + dpt), (int)(off[sp] + spt), (int)((lay == 0 ? dnp : 0) | ((long long)pd[sp].n1 << 19)),
+                     (int)(lay == 0 ? snp : 0));
+  };
+  for (int lay = 0; lay < 2; ++lay) {
+    for (const FringeCopy& f : fcopy) ent[lay].push_back(resolved(lay, f.dst_patch, f.dst_point, f.src_patch, f.src_point));
+    for (const FringeInterp& f : finterp)
+      ient[lay].push_back(resolved(lay, f.dst_patch, f.dst_point, f.src_patch, f.src_point));
+  }
   for (const FringeInterp& f : finterp) {
-    ient.push_back(make_int4(f.dst_patch, f.dst_point, f.src_patch, f.src_point));
     iw64.insert(iw64.end(), f.wi, f.wi + kStencil);   // 12 weights per entry: along i, then along j
     iw64.insert(iw64.end(), f.wj, f.wj + kStencil);
   }
   std::vector<float> iw32(iw64.begin(), iw64.end());
-  c->nent = (int)ent.size();
-  c->ninterp = (int)ient.size();
+  c->nent = (int)ent[0].size();
+  c->ninterp = (int)ient[0].size();
 
   // ---- Gram basis on the d matching points (orthonormalised Vandermonde
   // matrix, double-double) and per plan the blend values of the Gram
@@ -1036,8 +1038,10 @@ int fc_setup(fcs_ctx** out, int d, int C, const fcs_patch_desc* pd, int npatch, 
       (rc = upload(c, &c->btiles, btiles.data(), btiles.size() * sizeof(int4))) ||
       (rc = upload(c, &dwin, wins.data(), wins.size() * sizeof(int4))) ||
       (rc = upload(c, &dfr, fringe.data(), fringe.size())) ||
-      (rc = upload(c, &c->fringe_ent, ent.data(), ent.size() * sizeof(int4))) ||
-      (rc = upload(c, &c->interp_ent, ient.data(), ient.size() * sizeof(int4))) ||
+      (rc = upload(c, &c->fringe_ent[0], ent[0].data(), ent[0].size() * sizeof(int4))) ||
+      (rc = upload(c, &c->fringe_ent[1], ent[1].data(), ent[1].size() * sizeof(int4))) ||
+      (rc = upload(c, &c->interp_ent[0], ient[0].data(), ient[0].size() * sizeof(int4))) ||
+      (rc = upload(c, &c->interp_ent[1], ient[1].data(), ient[1].size() * sizeof(int4))) ||
       (rc = upload(c, &c->interp_w64, iw64.data(), iw64.size() * 8)) ||
       (rc = upload(c, &c->interp_w32, iw32.data(), iw32.size() * 4)) ||
       (rc = upload(c, &c->wq, wq.data(), wq.size() * 8)) || (rc = upload(c, &c->woff, wo.data(), wo.size() * sizeof(int2))) ||
@@ -1131,17 +1135,11 @@ int fc_setup(fcs_ctx** out, int d, int C, const fcs_patch_desc* pd, int npatch, 
   D.tw = c->tw;
   D.n2max = c->n2max;
   if ((rc = (o.dtype == FCS_F64 ? set_smem_attrs<double>(c) : set_smem_attrs<float>(c)))) return fail(rc);
-  if (o.dtype != FCS_F64) {  // the metrics use FP64 derivatives (columns: one field per tile)
+  if (o.dtype != FCS_F64) {  // the metrics use FP64 derivatives
     for (int dir = 0; dir < 2; ++dir)
       for (int n1 : c->n1_dir[dir]) {
         FCS_N1_SWITCH(n1, if (prep_fc_deriv<double, K>(deriv_smem<double>(c, n1)) != cudaSuccess) return fail(FCS_ECUDA); break)
       }
-    const int twmax = c->tw_options.empty() ? c->tw : c->tw_options[0];
-    for (int n1 : c->n1_dir[1]) {
-      if (cols_smem<double>(c, c->tw, n1, 1) > kSmemMax) return fail(FCS_EUNSUPPORTED);
-      const size_t sm = std::min(cols_smem<double>(c, twmax, n1, 1), kSmemMax);
-      FCS_N1_SWITCH(n1, if (prep_fc_cols<double, K>(sm) != cudaSuccess) return fail(FCS_ECUDA); break)
-    }
   }
 
   // ---- metrics of curvilinear patches: FP64 FC derivatives of x and y
@@ -1206,7 +1204,7 @@ int fcs_get_layout(const fcs_ctx* c, fcs_layout* o) {
   o->window_off = c->window_off.data();
   o->tile_width = c->tw;
   o->launches_stage = (int)(c->g_rows.size() + c->g_tiles.size()) + (c->dev.n_nsw > 0);
-  o->launches_stage_visc = o->launches_stage + (int)c->g_vtiles.size();
+  o->launches_stage_visc = o->launches_stage + (int)c->g_vpairs.size();
   o->launches_exchange = (c->nent > 0) + (c->ninterp > 0);
   o->launches_av = 1 + (c->opt.av_radius <= kBlendMaxR ? 1 : 4) + o->launches_exchange;
   return FCS_OK;

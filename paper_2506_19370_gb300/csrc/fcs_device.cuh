@@ -464,12 +464,12 @@ __device__ __forceinline__ void wall_project(T* v, T nx, T ny) {
 // for an L-shaped patch its inner wall edges i = m1 (j < m2) and j = m2
 // (i < m1) and the corner node (m1, m2), a wall along the bisector of the
 // two inward edge normals grad q1 / |grad q1| + grad q2 / |grad q2|.
+// The work at a boundary point is out of line (called only there), so the
+// inlined check keeps the update loops of the stage kernels short.
 template <typename T>
-__device__ __forceinline__ void apply_bc(const CtxDev& c, const PatchDev& P, int i, int j, long long q, T* v) {
-  const T gm1 = gm1_of<T>(c);
+__device__ __noinline__ void apply_bc_edge(const T* M, long long qs, T gm1, T pout, const PatchDev& P, int i, int j,
+                                           long long q, T* v) {
   const bool on[4] = {i == 0 && j >= P.m2, i == P.n1 - 1, j == 0 && i >= P.m1, j == P.n2 - 1};
-  const T* M = metrics<T>(c);
-  const long long qs = c.qstride;
 #pragma unroll
   for (int s = 0; s < 4; ++s) {
     if (!on[s]) continue;
@@ -488,7 +488,7 @@ __device__ __forceinline__ void apply_bc(const CtxDev& c, const PatchDev& P, int
       v[2] = inflow_of<T>(P, 2);
       v[3] = inflow_of<T>(P, 3);
     } else if (code == 3) {  // outflow pressure
-      v[3] = p_out_of<T>(c) / gm1 + T(0.5) * (v[1] * v[1] + v[2] * v[2]) / v[0];
+      v[3] = pout / gm1 + T(0.5) * (v[1] * v[1] + v[2] * v[2]) / v[0];
     } else if (code == 5) {  // no-slip wall: momentum (its temperature: k_noslip_temperature)
       v[1] = T(0);
       v[2] = T(0);
@@ -514,6 +514,12 @@ __device__ __forceinline__ void apply_bc(const CtxDev& c, const PatchDev& P, int
       wall_project(v, ax / na + bx / nb, ay / na + by / nb);
     }
   }
+}
+template <typename T>
+__device__ __forceinline__ void apply_bc(const CtxDev& c, const PatchDev& P, int i, int j, long long q, T* v) {
+  const bool edge = i == 0 || j == 0 || i == P.n1 - 1 || j == P.n2 - 1 ||
+                    (P.m1 > 0 && ((i == P.m1 && j <= P.m2) || (j == P.m2 && i <= P.m1)));
+  if (edge) apply_bc_edge<T>(metrics<T>(c), c.qstride, gm1_of<T>(c), p_out_of<T>(c), P, i, j, q, v);
 }
 
 

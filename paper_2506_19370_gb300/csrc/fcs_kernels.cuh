@@ -14,10 +14,19 @@ namespace fcs {
 constexpr double kFlatTol = 1e-4;
 
 // ============================================================ exchange
-// entries: (dst patch, dst point, src patch, src point) of one instance.
+// Fringe entries are layout-resolved on the host: (dst offset, src offset,
+// dst field stride | src row pitch << 19, src field stride), the offsets
+// within one instance of the state layout (nfields = 4) or of the scalar
+// layout (nfields = 1; field strides 0), so a thread needs no patch
+// descriptor (the field strides are at most 512 x 512 = 2^18 elements).
+__device__ __forceinline__ int ent_dnp(const int4& x) { return x.z & 0x7ffff; }
+__device__ __forceinline__ int ent_pitch(const int4& x) { return x.z >> 19; }
+
+// Copies (donor node on the receiver): entries as above, src = the donor node.
 template <typename T>
 __global__ void k_exchange(CtxDev c, const int4* __restrict__ ent, int nent, T* field, int nfields) {
   const long long total = (long long)c.instances * nent * nfields;
+  const long long istride = nfields == 4 ? c.sstride : c.qstride;
   for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x) {
     // entries vary fastest: neighbouring threads copy neighbouring fringe points
     const int k = (int)(t % nent);
@@ -25,19 +34,12 @@ __global__ void k_exchange(CtxDev c, const int4* __restrict__ ent, int nent, T* 
     const int f = (int)(r % nfields);
     const int inst = (int)(r / nfields);
     const int4 x = ent[k];
-    const PatchDev& Pd = c.patches[x.x];
-    const PatchDev& Ps = c.patches[x.z];
-    if (nfields == 4) {
-      const long long pd = (long long)Pd.n1 * Pd.n2, ps = (long long)Ps.n1 * Ps.n2;
-      field[inst * c.sstride + Pd.soff + f * pd + x.y] = field[inst * c.sstride + Ps.soff + f * ps + x.w];
-    } else {
-      field[inst * c.qstride + Pd.qoff + x.y] = field[inst * c.qstride + Ps.qoff + x.w];
-    }
+    field[inst * istride + x.x + (long long)f * ent_dnp(x)] = field[inst * istride + x.y + (long long)f * x.w];
   }
 }
 
-// Interpolated fringe points: entries (dst patch, dst point, src patch, first
-// node of the donor block); w holds the two factors of each entry's tensor
+// Interpolated fringe points: entries as for the copies, src = the first
+// node of the donor block; w holds the two factors of each entry's tensor
 // Lagrange stencil (kStencil weights along i, then kStencil along j: node
 // (a, b) has weight w_i[a] w_j[b]).  A group of 8 lanes takes one
 // (instance, entry), 4 per warp: lane a < 6 of the group sums the stencil
@@ -51,6 +53,7 @@ __global__ void k_interp(CtxDev c, const int4* __restrict__ ent, const T* __rest
   constexpr int S = 6;
   const int lane = threadIdx.x & 31, a = lane & 7, grp = lane >> 3;
   const long long total = (long long)c.instances * nent;
+  const long long istride = nfields == 4 ? c.sstride : c.qstride;
   const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
   for (long long base = ((long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 4; base < total;
        base += nwarps * 4) {
@@ -62,20 +65,19 @@ __global__ void k_interp(CtxDev c, const int4* __restrict__ ent, const T* __rest
       const int inst = (int)(t / nent);
       const int k = (int)(t % nent);
       const int4 x = ent[k];
-      const PatchDev& Pd = c.patches[x.x];
-      const PatchDev& Ps = c.patches[x.z];
-      const long long fs = nfields == 4 ? (long long)Ps.n1 * Ps.n2 : 0;
-      fd = nfields == 4 ? (long long)Pd.n1 * Pd.n2 : 0;
-      dbase = (nfields == 4 ? inst * c.sstride + Pd.soff : inst * c.qstride + Pd.qoff) + x.y;
+      const T* wk = w + (size_t)k * 2 * S;   // independent of the entry record: both loads in flight together
+      const long long fs = x.w;
+      fd = ent_dnp(x);
+      dbase = inst * istride + x.x;
       if (a < S) {
         // column a of the stencil block: sum over its rows b with the
         // weights along j, then the weight of column a along i
-        const T* src = field + (nfields == 4 ? inst * c.sstride + Ps.soff : inst * c.qstride + Ps.qoff) + x.w + a;
-        const T* wk = w + (size_t)k * 2 * S;
+        const T* src = field + inst * istride + x.y + a;
+        const long long pitch = ent_pitch(x);
 #pragma unroll
         for (int b = 0; b < S; ++b) {
-          const T wv = wk[S + b];
-          const long long o = (long long)b * Ps.n1;
+          const T wv = __ldg(wk + S + b);
+          const long long o = (long long)b * pitch;
           acc[0] += wv * src[o];
           if (nfields == 4) {
             acc[1] += wv * src[fs + o];
@@ -83,7 +85,7 @@ __global__ void k_interp(CtxDev c, const int4* __restrict__ ent, const T* __rest
             acc[3] += wv * src[3 * fs + o];
           }
         }
-        const T wa = wk[a];
+        const T wa = __ldg(wk + a);
 #pragma unroll
         for (int f = 0; f < 4; ++f) acc[f] *= wa;
       }
@@ -92,8 +94,11 @@ __global__ void k_interp(CtxDev c, const int4* __restrict__ ent, const T* __rest
     for (int f = 0; f < 4; ++f)
 #pragma unroll
       for (int off = 4; off > 0; off >>= 1) acc[f] += __shfl_down_sync(0xffffffffu, acc[f], off, 8);
-    if (ok && a == 0)
-      for (int f = 0; f < nfields; ++f) field[dbase + f * fd] = clamp && acc[f] < T(0) ? T(0) : acc[f];
+    if (ok && a == 0) {
+#pragma unroll
+      for (int f = 0; f < 4; ++f)   // unrolled: acc stays in registers
+        if (f < nfields) field[dbase + f * fd] = clamp && acc[f] < T(0) ? T(0) : acc[f];
+    }
   }
 }
 

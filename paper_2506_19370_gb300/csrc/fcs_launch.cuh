@@ -10,7 +10,7 @@
 
 namespace fcs {
 
-enum { MODE_RHS = 1, MODE_RK = 2, MODE_CHAIN = 4 };  // column-pass epilogue; MODE_CHAIN: chain-rule form
+enum { MODE_RHS = 1, MODE_RK = 2, MODE_CHAIN = 4 };  // row-pass epilogue; MODE_CHAIN: chain-rule form
 
 template <typename T>
 struct StageArgs {
@@ -83,11 +83,13 @@ cudaError_t run_fc_deriv(const CtxDev& c, int dir, int order, const int4* pairs,
 template <typename T, int N1>
 cudaError_t run_fc_cols(const CtxDev& c, int order, const int2* tiles, int ntiles, int nf, const T* in, T* out,
                         LaunchCfg g);
-template <typename T, int N1>
-cudaError_t run_xpass(const CtxDev& c, int lbeg, int lcnt, const T* e, const T* mu, T* R, T* G1, const T* G2,
-                      int chain, LaunchCfg g);
+// The operator is the pass along q2 (writes R) followed by the pass along q1
+// (completes L and takes the stage).
 template <typename T, int MODE, int N1>
-cudaError_t run_ypass(const CtxDev& c, const int2* tiles, int ntiles, const T* e, const T* mu, const T* R,
-                      const T* G1, T* G2, StageArgs<T> st, LaunchCfg g);
+cudaError_t run_xpass(const CtxDev& c, int lbeg, int lcnt, const T* e, const T* mu, const T* R, T* G1, const T* G2,
+                      StageArgs<T> st, LaunchCfg g);
+template <typename T, int N1>
+cudaError_t run_ypass(const CtxDev& c, const int2* tiles, int ntiles, const T* e, const T* mu, T* R, const T* G1,
+                      T* G2, int chain, LaunchCfg g);
 
 }  // namespace fcs

@@ -9,18 +9,18 @@ namespace fcs {
 
 template <typename T, int N1>
 cudaError_t prep_xpass(size_t smem) {
-  cudaError_t e = cudaFuncSetAttribute(k_xpass<T, N1, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_xpass<T, N1, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
+  cudaError_t e = cudaFuncSetAttribute(k_xpass<T, MODE_RHS, N1>, a, (int)smem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_xpass<T, MODE_RK, N1>, a, (int)smem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_xpass<T, MODE_RHS | MODE_CHAIN, N1>, a, (int)smem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_xpass<T, MODE_RK | MODE_CHAIN, N1>, a, (int)smem);
+  return e;
 }
 template <typename T, int N1>
 cudaError_t prep_ypass(size_t smem) {
-  const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
-  cudaError_t e = cudaFuncSetAttribute(k_ypass<T, MODE_RHS, N1>, a, (int)smem);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_ypass<T, MODE_RK, N1>, a, (int)smem);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_ypass<T, MODE_RHS | MODE_CHAIN, N1>, a, (int)smem);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_ypass<T, MODE_RK | MODE_CHAIN, N1>, a, (int)smem);
-  return e;
+  cudaError_t e = cudaFuncSetAttribute(k_ypass<T, 0, N1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_ypass<T, 1, N1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 template <typename T, int N1>
 cudaError_t prep_fc_deriv(size_t smem) {
@@ -43,17 +43,17 @@ cudaError_t run_fc_deriv(const CtxDev& c, int dir, int order, const int4* pairs,
   k_fc_deriv<T, N1><<<g.grid, g.block, g.smem, g.stream>>>(c, dir, order, pairs, npairs, in, out);
   return cudaGetLastError();
 }
-template <typename T, int N1>
-cudaError_t run_xpass(const CtxDev& c, int lbeg, int lcnt, const T* e, const T* mu, T* R, T* G1, const T* G2,
-                      int chain, LaunchCfg g) {
-  if (chain) k_xpass<T, N1, 1><<<g.grid, g.block, g.smem, g.stream>>>(c, lbeg, lcnt, e, mu, R, G1, G2);
-  else k_xpass<T, N1, 0><<<g.grid, g.block, g.smem, g.stream>>>(c, lbeg, lcnt, e, mu, R, G1, G2);
+template <typename T, int MODE, int N1>
+cudaError_t run_xpass(const CtxDev& c, int lbeg, int lcnt, const T* e, const T* mu, const T* R, T* G1, const T* G2,
+                      StageArgs<T> st, LaunchCfg g) {
+  k_xpass<T, MODE, N1><<<g.grid, g.block, g.smem, g.stream>>>(c, lbeg, lcnt, e, mu, R, G1, G2, st);
   return cudaGetLastError();
 }
-template <typename T, int MODE, int N1>
-cudaError_t run_ypass(const CtxDev& c, const int2* tiles, int ntiles, const T* e, const T* mu, const T* R,
-                      const T* G1, T* G2, StageArgs<T> st, LaunchCfg g) {
-  k_ypass<T, MODE, N1><<<g.grid, g.block, g.smem, g.stream>>>(c, tiles, ntiles, e, mu, R, G1, G2, st);
+template <typename T, int N1>
+cudaError_t run_ypass(const CtxDev& c, const int2* tiles, int ntiles, const T* e, const T* mu, T* R, const T* G1,
+                      T* G2, int chain, LaunchCfg g) {
+  if (chain) k_ypass<T, 1, N1><<<g.grid, g.block, g.smem, g.stream>>>(c, tiles, ntiles, e, mu, R, G1, G2);
+  else k_ypass<T, 0, N1><<<g.grid, g.block, g.smem, g.stream>>>(c, tiles, ntiles, e, mu, R, G1, G2);
   return cudaGetLastError();
 }
 
@@ -68,15 +68,13 @@ cudaError_t run_ypass(const CtxDev& c, const int2* tiles, int ntiles, const T* e
                                                LaunchCfg);                                                    \
   template cudaError_t fcs::run_fc_deriv<T, N1>(const CtxDev&, int, int, const int4*, int, const T*, T*,     \
                                                 LaunchCfg);                                                   \
-  template cudaError_t fcs::run_xpass<T, N1>(const CtxDev&, int, int, const T*, const T*, T*, T*, const T*,    \
-                                             int, LaunchCfg);                                                 \
-  template cudaError_t fcs::run_ypass<T, fcs::MODE_RHS, N1>(const CtxDev&, const int2*, int, const T*,       \
-                                                            const T*, const T*, const T*, T*, StageArgs<T>,   \
-                                                            LaunchCfg);                                       \
-  template cudaError_t fcs::run_ypass<T, fcs::MODE_RK, N1>(const CtxDev&, const int2*, int, const T*,        \
-                                                           const T*, const T*, const T*, T*, StageArgs<T>,    \
-                                                           LaunchCfg);                                        \
-  template cudaError_t fcs::run_ypass<T, fcs::MODE_RHS | fcs::MODE_CHAIN, N1>(                                \
-      const CtxDev&, const int2*, int, const T*, const T*, const T*, const T*, T*, StageArgs<T>, LaunchCfg);   \
-  template cudaError_t fcs::run_ypass<T, fcs::MODE_RK | fcs::MODE_CHAIN, N1>(                                 \
-      const CtxDev&, const int2*, int, const T*, const T*, const T*, const T*, T*, StageArgs<T>, LaunchCfg);
+  template cudaError_t fcs::run_ypass<T, N1>(const CtxDev&, const int2*, int, const T*, const T*, T*, const T*, \
+                                             T*, int, LaunchCfg);                                             \
+  template cudaError_t fcs::run_xpass<T, fcs::MODE_RHS, N1>(const CtxDev&, int, int, const T*, const T*,     \
+                                                            const T*, T*, const T*, StageArgs<T>, LaunchCfg);  \
+  template cudaError_t fcs::run_xpass<T, fcs::MODE_RK, N1>(const CtxDev&, int, int, const T*, const T*,      \
+                                                           const T*, T*, const T*, StageArgs<T>, LaunchCfg);   \
+  template cudaError_t fcs::run_xpass<T, fcs::MODE_RHS | fcs::MODE_CHAIN, N1>(                                \
+      const CtxDev&, int, int, const T*, const T*, const T*, T*, const T*, StageArgs<T>, LaunchCfg);           \
+  template cudaError_t fcs::run_xpass<T, fcs::MODE_RK | fcs::MODE_CHAIN, N1>(                                 \
+      const CtxDev&, int, int, const T*, const T*, const T*, T*, const T*, StageArgs<T>, LaunchCfg);

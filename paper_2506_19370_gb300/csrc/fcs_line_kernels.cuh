@@ -40,7 +40,8 @@ __global__ void __launch_bounds__(kWarps * 32) k_fc_deriv(CtxDev c, int dir, int
   const long long total = (long long)c.instances * npairs;
   const long long rounds = (total + JPR - 1) / JPR;
   for (long long r = (long long)blockIdx.x * kWarps + warp; r < rounds; r += (long long)gridDim.x * kWarps) {
-    // stage the JPR line pairs of this round
+    // stage the JPR line pairs of this round (asynchronous copies: all of a
+    // lane's loads are in flight together)
     for (int k = 0; k < JPR; ++k) {
       const long long w = r * JPR + k;
       if (w >= total) break;
@@ -55,10 +56,11 @@ __global__ void __launch_bounds__(kWarps * 32) k_fc_deriv(CtxDev c, int dir, int
       const T* src = in + (pr.w < 0 ? inst * c.qstride + P.qoff
                                     : inst * c.sstride + P.soff + (long long)pr.w * P.n1 * P.n2);
       for (int t = lane; t < N; t += 32) {
-        L[(2 * k) * nmax + t] = src[la + t * stride];
-        L[(2 * k + 1) * nmax + t] = lb >= 0 ? src[lb + t * stride] : T(0);
+        cp_async_elem(&L[(2 * k) * nmax + t], src + la + t * stride);
+        if (lb >= 0) cp_async_elem(&L[(2 * k + 1) * nmax + t], src + lb + t * stride);
       }
     }
+    cp_async_wait_all();
     __syncwarp();
     const long long w = r * JPR + g;
     const bool active = w < total;
@@ -229,37 +231,236 @@ __device__ __forceinline__ void chain_contract(const T* v, const T* dw, T ca, T 
                  gg * rho * vv * dw[3]);
 }
 
-// Pass along q1 (rows lbeg .. lbeg + lcnt - 1 of the row list, one FFT-size
-// group): R = -d/dq1 F1; a warp takes kRowsPerWarp rows, staged in shared
-// memory.  Jobs of a phase: (row, field pair); phase 0 (rows with viscosity
-// only) G1 = d e/dq1 in global memory, phase 1 R = -d F/dq1 with F formed in
-// place of the staged state (so a warp stages 5 values per point, not 9: four
-// blocks of 4 warps fit an SM).  Curvilinear viscous rows read e_q2 from G2
-// (computed before this pass); the pass along q2 reads e_q1 from G1.
+// Pass along q2, the first of the operator: a tile of tw adjacent columns of
+// one patch (coalesced row segments staged in shared memory; blocks of 8
+// warps per SM: 4 for n = 64 (64 registers, a few spilled; measured faster
+// than 3), 3 for n = 96, 2 above, where the line registers of the FFT would
+// spill at 80 registers per thread) writes the partial operator
+// R = -d/dq2 F2 that the pass along q1 completes.
+// The tile stages 5 values per point (state, then flux in its place, and mu).
+// Viscous columns (mu != 0 somewhere on them) first take e_q2 into G2 (phase
+// 0), which the pass along q1 reads on curvilinear patches; curvilinear
+// viscous columns also read e_q1 from G1 (the row transform of those patches
+// before this pass).
 // CH = 1: chain-rule form (inviscid): w is staged and differentiated in
-// place, then R = -(ca A + cb B) w_q1 point by point.
-template <typename T, int N1, int CH>
-__global__ void __launch_bounds__(kWarps * 32, xpass_min_blocks(sizeof(T), N1)) k_xpass(CtxDev c, int lbeg, int lcnt, const T* __restrict__ e,
-                                                        const T* __restrict__ mu, T* __restrict__ R,
-                                                        T* __restrict__ G1, const T* __restrict__ G2) {
+// place, and R = -(ca A + cb B) w_q2.
+template <typename T, int CH, int N1>
+__global__ void __launch_bounds__(kYWarps * 32, ypass_min_blocks(sizeof(T), N1))
+    k_ypass(CtxDev c, const int2* __restrict__ tiles, int ntiles, const T* __restrict__ e, const T* __restrict__ mu,
+            T* __restrict__ R, const T* __restrict__ G1, T* __restrict__ G2) {
+  constexpr int JPR = jobs_per_round(N1);
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int tw = c.tw, ld = c.tw + 1, n2m = c.gnmax[1][N1], nfmax = c.gnfmax[1][N1];
+  T* E = reinterpret_cast<T*>(smem_raw);           // [4][n2m][ld]: state, flux, d flux/dq2
+  T* M = E + 4 * n2m * ld;                         // [n2m][ld]
+  Cx<T>* aux = reinterpret_cast<Cx<T>*>(smem_raw + align16((size_t)5 * n2m * ld * sizeof(T))) +
+               (size_t)warp * aux_cx(N1, nfmax);
+  const int g = JPR == 4 ? (lane >> 3) : 0;
+  Cx<T>* tile = aux + (size_t)g * 8 * (4 * N1 + 1);
+  const T gm1 = gm1_of<T>(c);
+  const long long total = (long long)c.instances * ntiles;
+  for (long long wk = blockIdx.x; wk < total; wk += gridDim.x) {
+    const int inst = (int)(wk / ntiles);
+    const int2 tl = tiles[wk % ntiles];
+    const PatchDev P = c.patches[tl.x];
+    const int c0 = tl.y;
+    // all columns of a tile share their segment (tiles never straddle i = m1)
+    const int j0 = line_start(P, 1, c0), N = P.n2 - j0;
+    const PlanDev pl = c.plans[line_plan(P, 1, c0)];
+    const int code_lo = j0 ? 1 : P.bc[2];
+    const int width = min(tw, (c0 < P.m1 ? P.m1 : P.n1) - c0);
+    const long long np = (long long)P.n1 * P.n2;
+    const long long sbase = inst * c.sstride + P.soff + (long long)j0 * P.n1 + c0;   // row j0 of the tile
+    const long long qbase = P.qoff + (long long)j0 * P.n1 + c0;
+    const bool visc = mu != nullptr;
+    // each thread keeps one column cc of the tile and strides over rows
+    const int cc = threadIdx.x % tw, jr = threadIdx.x / tw, js = blockDim.x / tw;
+    const bool colok = cc < width && jr < js;
+    __shared__ int colv[32];   // column has mu != 0 somewhere (tw <= 32)
+    __shared__ int act[32];    // compacted list of such columns
+    __shared__ int nact;
+    if (threadIdx.x < 32) colv[threadIdx.x] = 0;
+    __syncthreads();
+    if (colok)
+      for (int j = jr; j < N; j += js) {
+#pragma unroll
+        for (int f = 0; f < 4; ++f)
+          cp_async_elem(&E[(f * n2m + j) * ld + cc], e + sbase + f * np + (long long)j * P.n1 + cc);
+        if (visc) cp_async_elem(&M[j * ld + cc], mu + inst * c.qstride + qbase + (long long)j * P.n1 + cc);
+      }
+    cp_async_wait_all();
+    if (colok) {   // the thread's own staged points
+      bool any_mu = false;
+      for (int j = jr; j < N; j += js) {
+        if (CH) {
+          const T* v = E + j * ld + cc;
+          const int fs = n2m * ld;
+          E[(3 * n2m + j) * ld + cc] = pressure<T>(v[0], v[fs], v[2 * fs], v[3 * fs], gm1) / v[0];
+        }
+        if (visc) any_mu |= M[j * ld + cc] != T(0);
+      }
+      if (any_mu) atomicOr(&colv[cc], 1);
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {   // warp 0 compacts the viscous columns
+      const bool v = threadIdx.x < width && colv[threadIdx.x];
+      const unsigned bal = __ballot_sync(0xffffffffu, v);
+      if (v) act[__popc(bal & ((1u << threadIdx.x) - 1u))] = threadIdx.x;
+      if (threadIdx.x == 0) nact = __popc(bal);
+    }
+    __syncthreads();
+    const T h = T(P.hy);
+    // phase 0 (viscous columns only): G2 = d e/dq2; phase 1: F2 formed in
+    // place of the state, then -d F2/dq2 (chain-rule form: +d w/dq2) in place
+    for (int phase = (visc && nact > 0) ? 0 : 1; phase < 2; ++phase) {
+      if (phase == 1 && !CH) {
+        for (int j = jr; colok && j < N; j += js) {
+          T v[4], dv[4], dvo[4], F[4];
+          const bool vc = visc && colv[cc];
+          const bool curv = vc && !P.cart;
+#pragma unroll
+          for (int f = 0; f < 4; ++f) {
+            v[f] = E[(f * n2m + j) * ld + cc];
+            dv[f] = vc ? G2[sbase + f * np + (long long)j * P.n1 + cc] : T(0);
+            dvo[f] = curv ? G1[sbase + f * np + (long long)j * P.n1 + cc] : T(0);
+          }
+          point_flux<T, 1>(c, P, qbase + (long long)j * P.n1 + cc, v, dv, dvo, vc ? M[j * ld + cc] : T(0), vc, F, j, N,
+                           code_lo);
+#pragma unroll
+          for (int f = 0; f < 4; ++f) E[(f * n2m + j) * ld + cc] = F[f];
+        }
+        __syncthreads();
+      }
+      // jobs (column, field pair): phase 0 over the viscous columns only (a
+      // line pair's values are all read before any is written, so phase 1
+      // differentiates in place)
+      const int ncol = phase == 0 ? nact : width;
+      for (int u0 = warp * JPR; u0 < 2 * ncol; u0 += kYWarps * JPR) {
+        const int u = u0 + g;
+        const bool active = u < 2 * ncol;
+        const int cc = active ? (phase == 0 ? act[u >> 1] : (u >> 1)) : 0, pr = u & 1;
+        T* src = E + (2 * pr) * n2m * ld + cc;
+        T* oa = phase == 0 ? G2 + sbase + (2 * pr) * np + cc : src;
+        const int so = phase == 0 ? P.n1 : ld;
+        const long long fo = phase == 0 ? np : (long long)n2m * ld;
+        line_deriv_pair<T, N1>(src, ld, src + n2m * ld, ld, oa, so, oa + fo, so, (phase == 0 || CH) ? T(1) : T(-1), c,
+                               pl, h, 1, lane, aux, aux + nfmax, tile, active);
+      }
+      __syncthreads();
+    }
+    for (int j = jr; colok && j < N; j += js) {
+      const long long off = sbase + (long long)j * P.n1 + cc;
+      if (CH) {   // -(ca A + cb B) w_q2 at the stage's input state
+        const long long q = qbase + (long long)j * P.n1 + cc;
+        T v[4], dw[4], out[4];
+#pragma unroll
+        for (int f = 0; f < 4; ++f) {
+          v[f] = e[off + f * np];
+          dw[f] = E[(f * n2m + j) * ld + cc];
+        }
+        const T* Mt = metrics<T>(c);
+        const T ca = P.cart ? T(0) : -Mt[2 * c.qstride + q];
+        const T cb = P.cart ? T(1) : Mt[q];
+        chain_contract<T>(v, dw, ca, cb, gm1, T(c.gamma) / gm1, out);
+#pragma unroll
+        for (int f = 0; f < 4; ++f) R[off + f * np] = -out[f];
+      } else {
+#pragma unroll
+        for (int f = 0; f < 4; ++f) R[off + f * np] = E[(f * n2m + j) * ld + cc];
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Stage update of one point from its operator value kv = L(e_s): MODE_RHS
+// stores kv; MODE_RK takes stage st.stage of the classical 4-stage
+// Runge-Kutta scheme (acc collects e_n + dt/6 (k1 + 2 k2 + 2 k3) on the way,
+// out = the next stage's input, or e_{n+1} after the fourth), then the
+// boundary conditions and the state check (non-finite: status bit 1,
+// density or pressure not positive: bit 2).  en, ac: the point's e_n (stages
+// 0-2) and acc (stages 1-3), loaded by the caller; (i, j) is the point, q
+// its scalar-layout offset, off its state-layout offset, np the field stride.
+template <typename T, int MODE>
+__device__ __forceinline__ void stage_point(const CtxDev& c, const PatchDev& P, const StageArgs<T>& st, T dtv,
+                                            long long off, long long np, long long q, int i, int j, const T* kv,
+                                            const T* en, const T* ac) {
+  if ((MODE & 3) == MODE_RHS) {
+#pragma unroll
+    for (int f = 0; f < 4; ++f) st.out[off + f * np] = kv[f];
+    return;
+  }
+  T v[4];
+  const int s = st.stage;
+  if (s == 0) {
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+      st.acc[off + f * np] = en[f] + (dtv / T(6)) * kv[f];
+      v[f] = en[f] + (dtv / T(2)) * kv[f];
+    }
+  } else if (s < 3) {
+    const T a = s == 1 ? dtv / T(2) : dtv;
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+      st.acc[off + f * np] = ac[f] + (dtv / T(3)) * kv[f];
+      v[f] = en[f] + a * kv[f];
+    }
+  } else {
+#pragma unroll
+    for (int f = 0; f < 4; ++f) v[f] = ac[f] + (dtv / T(6)) * kv[f];
+  }
+  apply_bc<T>(c, P, i, j, q, v);
+  const T pr = pressure<T>(v[0], v[1], v[2], v[3], gm1_of<T>(c));
+  int flag = 0;
+  if (!(isfinite(v[0]) && isfinite(v[1]) && isfinite(v[2]) && isfinite(v[3]))) flag |= 1;
+  else if (!(v[0] > T(0)) || !(pr > T(0))) flag |= 2;
+  if (flag) atomicOr(c.status, flag);
+#pragma unroll
+  for (int f = 0; f < 4; ++f) st.out[off + f * np] = v[f];
+}
+
+// Pass along q1, the second of the operator (rows lbeg .. lbeg + lcnt - 1 of
+// the row list, one FFT-size group), with the stage epilogue: a warp takes
+// kRowsPerWarp rows, staged in shared memory (5 values per point, so four
+// blocks of 4 warps fit an SM), forms d/dq1 F1 in place and completes
+// L = (R - d/dq1 F1)/J with the partial operator R = -d/dq2 F2 of the pass
+// along q2, then stores L (MODE_RHS) or takes the Runge-Kutta stage
+// (MODE_RK): each warp updates its own rows with coalesced loads and stores.
+// Jobs of a phase: (row, field pair); phase 0 (viscous rows of Cartesian
+// patches) G1 = d e/dq1 in global memory (curvilinear patches have it from
+// their row transform before the pass along q2); phase 1 the flux in place of
+// the staged state, then its derivative in place.  Curvilinear viscous rows
+// read e_q2 from G2 (the pass along q2).
+// MODE_CHAIN (or-ed into MODE): chain-rule form (inviscid): w is staged and
+// differentiated in place, and the epilogue forms (ca A + cb B) w_q1.
+template <typename T, int MODE, int N1>
+__global__ void __launch_bounds__(kWarps * 32, xpass_min_blocks(sizeof(T), N1))
+    k_xpass(CtxDev c, int lbeg, int lcnt, const T* __restrict__ e, const T* __restrict__ mu, const T* __restrict__ R,
+            T* __restrict__ G1, const T* __restrict__ G2, StageArgs<T> st) {
+  constexpr bool CH = (MODE & MODE_CHAIN) != 0;
   constexpr int JPR = jobs_per_round(N1);
   constexpr int RW = kRowsPerWarp;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nmax = c.gnmax[0][N1], nfmax = c.gnfmax[0][N1];
   unsigned char* base = smem_raw + (size_t)warp * xpass_warp_bytes<T>(nmax, nfmax, N1);
-  T* E = reinterpret_cast<T*>(base);   // [RW][4][nmax]: state, then flux
+  T* E = reinterpret_cast<T*>(base);   // [RW][4][nmax]: state, then flux, then its derivative
   T* M = E + RW * 4 * nmax;            // [RW][nmax]
   Cx<T>* aux = reinterpret_cast<Cx<T>*>(base + align16((size_t)RW * 5 * nmax * sizeof(T)));
   const int g = JPR == 4 ? (lane >> 3) : 0;
   Cx<T>* tile = aux + (size_t)g * 8 * (4 * N1 + 1);
+  const T gm1 = gm1_of<T>(c);
+  // the epilogue's operands: R always; e_n in stages 0-2, acc in stages 1-3
+  constexpr bool rk = (MODE & 3) == MODE_RK;
+  const unsigned arrs = 1u | (rk && st.stage < 3 ? 2u : 0u) | (rk && st.stage > 0 ? 4u : 0u);
   const long long groups = ((long long)lcnt + RW - 1) / RW;   // row groups per instance
   const long long total = (long long)c.instances * groups;
   for (long long w = (long long)blockIdx.x * kWarps + warp; w < total; w += (long long)gridDim.x * kWarps) {
     const int inst = (int)(w / groups);
     const int l0 = lbeg + (int)(w % groups) * RW;
     int pid[RW], row[RW], nk[RW];
-    bool has[RW], vrow[RW];
+    bool has[RW], vrow[RW], cart[RW];
 #pragma unroll
     for (int k = 0; k < RW; ++k) {
       has[k] = l0 + k < lbeg + lcnt;
@@ -267,15 +468,27 @@ __global__ void __launch_bounds__(kWarps * 32, xpass_min_blocks(sizeof(T), N1)) 
       pid[k] = lr.patch;
       row[k] = lr.line;
       const PatchDev& P = c.patches[lr.patch];
+      cart[k] = P.cart;
       const long long np = (long long)P.n1 * P.n2;
       const int s0 = line_start(P, 0, lr.line), N = P.n1 - s0;
-      const T* es = e + inst * c.sstride + P.soff + (long long)lr.line * P.n1 + s0;
+      const long long so = inst * c.sstride + P.soff + (long long)lr.line * P.n1 + s0;
+      const T* es = e + so;
       const T* ms = mu ? mu + inst * c.qstride + P.qoff + (long long)lr.line * P.n1 + s0 : nullptr;
       nk[k] = has[k] ? N : 0;
       for (int t = lane; t < nk[k]; t += 32) {
 #pragma unroll
         for (int f = 0; f < 4; ++f) cp_async_elem(&E[(k * 4 + f) * nmax + t], es + f * np + t);
         if (ms) cp_async_elem(&M[k * nmax + t], ms + t);
+      }
+      // start moving the row's segments of the epilogue's operands into L2
+      // while the row is transformed (one prefetch per 128-byte line)
+      const int nl = nk[k] ? (nk[k] * (int)sizeof(T) + 127) / 128 + 1 : 0;
+      for (int u = lane; u < 12 * nl; u += 32) {
+        const int a = u / (4 * nl), f = (u / nl) & 3, sg = u % nl;
+        if (!(arrs >> a & 1)) continue;
+        const T* b = a == 0 ? R : (a == 1 ? st.e_n : st.acc);
+        const T* p = b + so + f * np + min(sg * (int)(128 / sizeof(T)), nk[k] - 1);
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
       }
     }
     cp_async_wait_all();
@@ -285,7 +498,7 @@ __global__ void __launch_bounds__(kWarps * 32, xpass_min_blocks(sizeof(T), N1)) 
       for (int t = lane; t < nk[k]; t += 32) {
         if (CH) {
           const T* v = E + k * 4 * nmax + t;
-          E[(k * 4 + 3) * nmax + t] = pressure<T>(v[0], v[nmax], v[2 * nmax], v[3 * nmax], gm1_of<T>(c)) / v[0];
+          E[(k * 4 + 3) * nmax + t] = pressure<T>(v[0], v[nmax], v[2 * nmax], v[3 * nmax], gm1) / v[0];
         }
         if (mu) any_mu |= M[k * nmax + t] != T(0);
       }
@@ -294,8 +507,8 @@ __global__ void __launch_bounds__(kWarps * 32, xpass_min_blocks(sizeof(T), N1)) 
       vrow[k] = __any_sync(0xffffffffu, any_mu);
     }
     __syncwarp();
-    const bool visc_any = vrow[0] || vrow[1];
-    for (int phase = visc_any ? 0 : 1; phase < 2; ++phase) {
+    const bool p0 = (vrow[0] && cart[0]) || (vrow[1] && cart[1]);
+    for (int phase = p0 ? 0 : 1; phase < 2; ++phase) {
       if (phase == 1 && !CH) {
 #pragma unroll
         for (int k = 0; k < RW; ++k) {
@@ -334,244 +547,73 @@ __global__ void __launch_bounds__(kWarps * 32, xpass_min_blocks(sizeof(T), N1)) 
         bool active = job < 2 * RW && (kk ? has[1] : has[0]);
         const PatchDev& P = c.patches[pidk];
         const PlanDev& pl = c.plans[line_plan(P, 0, rowk)];
-        if (phase == 0 && !(kk ? vrow[1] : vrow[0])) active = false;
+        if (phase == 0 && !(kk ? (vrow[1] && cart[1]) : (vrow[0] && cart[0]))) active = false;
         const long long np = (long long)P.n1 * P.n2;
         T* src = E + (kk * 4 + 2 * pr) * nmax;
         const long long orow = inst * c.sstride + P.soff + (long long)rowk * P.n1 + line_start(P, 0, rowk) +
                                (2 * pr) * np;
-        // chain-rule form: w_q1 in place of w (a pair's values are all read
-        // before any is written)
-        T* oa = CH ? src : (phase == 0 ? G1 : R) + orow;
-        const long long ob_off = CH ? (long long)nmax : np;
-        line_deriv_pair<T, N1>(src, 1, src + nmax, 1, oa, 1, oa + ob_off, 1, (phase == 0 || CH) ? T(1) : T(-1), c, pl,
-                               T(P.hx), 1, lane, aux, aux + nfmax, tile, active);
-      }
-      __syncwarp();
-    }
-    if (CH) {   // R = -(ca A + cb B) w_q1 at every point of the rows
-      const T gm1 = gm1_of<T>(c), gg = T(c.gamma) / gm1;
-#pragma unroll
-      for (int k = 0; k < RW; ++k) {
-        if (!has[k]) continue;
-        const PatchDev& P = c.patches[pid[k]];
-        const int a0 = line_start(P, 0, row[k]), N = P.n1 - a0;
-        const long long np = (long long)P.n1 * P.n2;
-        const long long s0 = inst * c.sstride + P.soff + (long long)row[k] * P.n1 + a0;
-        const long long q0 = P.qoff + (long long)row[k] * P.n1 + a0;
-        const T* Mt = metrics<T>(c);
-        for (int t = lane; t < N; t += 32) {
-          T v[4], dw[4], out[4];
-#pragma unroll
-          for (int f = 0; f < 4; ++f) {
-            v[f] = e[s0 + f * np + t];
-            dw[f] = E[(k * 4 + f) * nmax + t];
-          }
-          const T ca = P.cart ? T(1) : Mt[3 * c.qstride + q0 + t];
-          const T cb = P.cart ? T(0) : -Mt[c.qstride + q0 + t];
-          chain_contract<T>(v, dw, ca, cb, gm1, gg, out);
-#pragma unroll
-          for (int f = 0; f < 4; ++f) R[s0 + f * np + t] = -out[f];
-        }
-      }
-      __syncwarp();
-    }
-  }
-}
-
-// Pass along q2 on a tile of tw adjacent columns of one patch (coalesced row
-// segments staged in shared memory; blocks of 8 warps per SM: 4 for n = 64
-// (64 registers, a few spilled; measured faster than 3), 3 for n = 96, 2
-// above, where the line registers of the FFT would spill at 80 registers per
-// thread): L = (R - d/dq2 F2)/J, then either L
-// (MODE_RHS) or the Runge-Kutta stage with boundary conditions (MODE_RK).
-// The tile stages 5 values per point (state, then flux in its place, and mu).
-// Viscous columns take e_q2 from G2: on curvilinear patches from the e_q2
-// pass before the row pass, on Cartesian ones from this pass's phase 0;
-// curvilinear viscous columns also read e_q1 from G1 (left by the row pass;
-// rows without viscosity leave stale values there, which only meet mu = 0).
-// MODE_CHAIN (or-ed into MODE): chain-rule form (inviscid): w is staged and
-// differentiated in place, and the epilogue forms (ca A + cb B) w_q2.
-template <typename T, int MODE, int N1>
-__global__ void __launch_bounds__(kYWarps * 32, ypass_min_blocks(sizeof(T), N1)) k_ypass(CtxDev c, const int2* __restrict__ tiles, int ntiles,
-                                                         const T* __restrict__ e, const T* __restrict__ mu,
-                                                         const T* __restrict__ R, const T* __restrict__ G1,
-                                                         T* __restrict__ G2, StageArgs<T> st) {
-  constexpr int JPR = jobs_per_round(N1);
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int tw = c.tw, ld = c.tw + 1, n2m = c.gnmax[1][N1], nfmax = c.gnfmax[1][N1];
-  T* E = reinterpret_cast<T*>(smem_raw);           // [4][n2m][ld]: state, flux, d flux/dq2
-  T* M = E + 4 * n2m * ld;                         // [n2m][ld]
-  Cx<T>* aux = reinterpret_cast<Cx<T>*>(smem_raw + align16((size_t)5 * n2m * ld * sizeof(T))) +
-               (size_t)warp * aux_cx(N1, nfmax);
-  const int g = JPR == 4 ? (lane >> 3) : 0;
-  Cx<T>* tile = aux + (size_t)g * 8 * (4 * N1 + 1);
-  constexpr bool CH = (MODE & MODE_CHAIN) != 0;
-  const T gm1 = gm1_of<T>(c);
-  const long long total = (long long)c.instances * ntiles;
-  for (long long wk = blockIdx.x; wk < total; wk += gridDim.x) {
-    const int inst = (int)(wk / ntiles);
-    const int2 tl = tiles[wk % ntiles];
-    const PatchDev P = c.patches[tl.x];
-    const int c0 = tl.y;
-    // all columns of a tile share their segment (tiles never straddle i = m1)
-    const int j0 = line_start(P, 1, c0), N = P.n2 - j0;
-    const PlanDev pl = c.plans[line_plan(P, 1, c0)];
-    const int code_lo = j0 ? 1 : P.bc[2];
-    const int width = min(tw, (c0 < P.m1 ? P.m1 : P.n1) - c0);
-    const long long np = (long long)P.n1 * P.n2;
-    const long long sbase = inst * c.sstride + P.soff + (long long)j0 * P.n1 + c0;   // row j0 of the tile
-    const long long qbase = P.qoff + (long long)j0 * P.n1 + c0;
-    const bool visc = mu != nullptr;
-    // each thread keeps one column cc of the tile and strides over rows
-    const int cc = threadIdx.x % tw, jr = threadIdx.x / tw, js = blockDim.x / tw;
-    const bool colok = cc < width && jr < js;
-    __shared__ int colv[32];   // column has mu != 0 somewhere (tw <= 32)
-    __shared__ int act[32];    // compacted list of such columns
-    __shared__ int nact;
-    if (threadIdx.x < 32) colv[threadIdx.x] = 0;
-    // the epilogue's operands (R, and e_n, acc of a stage update) are read
-    // after the transforms: start moving the tile's rows of them into L2 now
-    // (one prefetch per row segment and field, spread over the threads)
-    {
-      const int narr = (MODE & 3) == MODE_RK ? 3 : 1;
-      const int nseg = N * 4 * narr;
-      for (int k = threadIdx.x; k < nseg; k += blockDim.x) {
-        const int j = k % N, f = (k / N) & 3, a = k / (4 * N);
-        const T* base = a == 0 ? R : (a == 1 ? st.e_n : st.acc);
-        if (base) {
-          const T* row = base + sbase + f * np + (long long)j * P.n1;
-          asm volatile("prefetch.global.L2 [%0];" ::"l"(row));
-          asm volatile("prefetch.global.L2 [%0];" ::"l"(row + width - 1));
-        }
-      }
-    }
-    __syncthreads();
-    if (colok)
-      for (int j = jr; j < N; j += js) {
-#pragma unroll
-        for (int f = 0; f < 4; ++f)
-          cp_async_elem(&E[(f * n2m + j) * ld + cc], e + sbase + f * np + (long long)j * P.n1 + cc);
-        if (visc) cp_async_elem(&M[j * ld + cc], mu + inst * c.qstride + qbase + (long long)j * P.n1 + cc);
-      }
-    cp_async_wait_all();
-    if (colok) {   // the thread's own staged points
-      bool any_mu = false;
-      for (int j = jr; j < N; j += js) {
-        if (CH) {
-          const T* v = E + j * ld + cc;
-          const int fs = n2m * ld;
-          E[(3 * n2m + j) * ld + cc] = pressure<T>(v[0], v[fs], v[2 * fs], v[3 * fs], gm1) / v[0];
-        }
-        if (visc) any_mu |= M[j * ld + cc] != T(0);
-      }
-      if (any_mu) atomicOr(&colv[cc], 1);
-    }
-    __syncthreads();
-    if (threadIdx.x < 32) {   // warp 0 compacts the viscous columns
-      const bool v = threadIdx.x < width && colv[threadIdx.x];
-      const unsigned bal = __ballot_sync(0xffffffffu, v);
-      if (v) act[__popc(bal & ((1u << threadIdx.x) - 1u))] = threadIdx.x;
-      if (threadIdx.x == 0) nact = __popc(bal);
-    }
-    __syncthreads();
-    const T h = T(P.hy);
-    // phase 0 (viscous columns of Cartesian patches only): G2 = d e/dq2; phase
-    // 1: F2 formed in place of the state, then E = d F2/dq2 in place
-    for (int phase = (visc && nact > 0 && P.cart) ? 0 : 1; phase < 2; ++phase) {
-      if (phase == 1 && !CH) {
-        for (int j = jr; colok && j < N; j += js) {
-          T v[4], dv[4], dvo[4], F[4];
-          const bool vc = visc && colv[cc];
-          const bool curv = vc && !P.cart;
-#pragma unroll
-          for (int f = 0; f < 4; ++f) {
-            v[f] = E[(f * n2m + j) * ld + cc];
-            dv[f] = vc ? G2[sbase + f * np + (long long)j * P.n1 + cc] : T(0);
-            dvo[f] = curv ? G1[sbase + f * np + (long long)j * P.n1 + cc] : T(0);
-          }
-          point_flux<T, 1>(c, P, qbase + (long long)j * P.n1 + cc, v, dv, dvo, vc ? M[j * ld + cc] : T(0), vc, F, j, N,
-                           code_lo);
-#pragma unroll
-          for (int f = 0; f < 4; ++f) E[(f * n2m + j) * ld + cc] = F[f];
-        }
-        __syncthreads();
-      }
-      // jobs (column, field pair): phase 0 over the viscous columns only (a
-      // line pair's values are all read before any is written, so phase 1
-      // differentiates in place)
-      const int ncol = phase == 0 ? nact : width;
-      for (int u0 = warp * JPR; u0 < 2 * ncol; u0 += kYWarps * JPR) {
-        const int u = u0 + g;
-        const bool active = u < 2 * ncol;
-        const int cc = active ? (phase == 0 ? act[u >> 1] : (u >> 1)) : 0, pr = u & 1;
-        T* src = E + (2 * pr) * n2m * ld + cc;
-        T* oa = phase == 0 ? G2 + sbase + (2 * pr) * np + cc : src;
-        const int so = phase == 0 ? P.n1 : ld;
-        const long long fo = phase == 0 ? np : (long long)n2m * ld;
-        line_deriv_pair<T, N1>(src, ld, src + n2m * ld, ld, oa, so, oa + fo, so, T(1), c, pl, h, 1, lane, aux,
+        // phase 1 in place (a pair's values are all read before any is written)
+        T* oa = phase == 0 ? G1 + orow : src;
+        const long long ob_off = phase == 0 ? np : (long long)nmax;
+        line_deriv_pair<T, N1>(src, 1, src + nmax, 1, oa, 1, oa + ob_off, 1, T(1), c, pl, T(P.hx), 1, lane, aux,
                                aux + nfmax, tile, active);
       }
-      __syncthreads();
+      __syncwarp();
     }
+    // epilogue: L = (R - d/dq1 F1)/J (chain-rule form: (R - (ca A + cb B) w_q1)/J),
+    // U points of a lane at a time, whose global loads are all issued before
+    // the first of them is used
+    constexpr int U = (sizeof(T) == 4 && N1 != 3 && N1 != 5) ? 4 : 2;   // N1 = 3, 5: 80, 96 registers
     const T dtv = st.dt_dev ? T(st.dt_dev[inst]) : st.dt;
-    for (int j = jr; colok && j < N; j += js) {
-      const long long off = sbase + (long long)j * P.n1 + cc;
-      const long long q = qbase + (long long)j * P.n1 + cc;
-      const T invJ = P.cart ? T(1) : T(1) / metrics<T>(c)[4 * c.qstride + q];
-      T kv[4];
-      if (CH) {   // (ca A + cb B) w_q2 at the stage's input state
-        T v[4], dw[4], out[4];
+    const T* Mt = metrics<T>(c);
+    const bool ld_en = rk && st.stage < 3, ld_ac = rk && st.stage > 0;
 #pragma unroll
-        for (int f = 0; f < 4; ++f) {
-          v[f] = e[off + f * np];
-          dw[f] = E[(f * n2m + j) * ld + cc];
+    for (int k = 0; k < RW; ++k) {
+      if (!has[k]) continue;
+      const PatchDev& P = c.patches[pid[k]];
+      const int a0 = line_start(P, 0, row[k]), N = P.n1 - a0;
+      const long long np = (long long)P.n1 * P.n2;
+      const long long s0 = inst * c.sstride + P.soff + (long long)row[k] * P.n1 + a0;
+      const long long q0 = P.qoff + (long long)row[k] * P.n1 + a0;
+      for (int t0 = lane; t0 < N; t0 += 32 * U) {
+        T r[U][4], en[U][4], ac[U][4], ev[U][4], ij[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int t = t0 + 32 * u;
+          const long long off = s0 + t;
+#pragma unroll
+          for (int f = 0; f < 4; ++f) {
+            r[u][f] = t < N ? R[off + f * np] : T(0);
+            en[u][f] = ld_en && t < N ? st.e_n[off + f * np] : T(0);
+            ac[u][f] = ld_ac && t < N ? st.acc[off + f * np] : T(0);
+            ev[u][f] = CH && t < N ? e[off + f * np] : T(0);
+          }
+          ij[u] = P.cart || t >= N ? T(1) : T(1) / Mt[4 * c.qstride + q0 + t];
         }
-        const T* Mt = metrics<T>(c);
-        const T ca = P.cart ? T(0) : -Mt[2 * c.qstride + q];
-        const T cb = P.cart ? T(1) : Mt[q];
-        chain_contract<T>(v, dw, ca, cb, gm1, T(c.gamma) / gm1, out);
 #pragma unroll
-        for (int f = 0; f < 4; ++f) kv[f] = (R[off + f * np] - out[f]) * invJ;
-      } else {
+        for (int u = 0; u < U; ++u) {
+          const int t = t0 + 32 * u;
+          if (t >= N) continue;
+          const long long off = s0 + t, q = q0 + t;
+          T kv[4];
+          if (CH) {
+            T dw[4], out[4];
 #pragma unroll
-        for (int f = 0; f < 4; ++f) kv[f] = (R[off + f * np] - E[(f * n2m + j) * ld + cc]) * invJ;
-      }
-      if ((MODE & 3) == MODE_RHS) {
+            for (int f = 0; f < 4; ++f) dw[f] = E[(k * 4 + f) * nmax + t];
+            const T ca = P.cart ? T(1) : Mt[3 * c.qstride + q];
+            const T cb = P.cart ? T(0) : -Mt[c.qstride + q];
+            chain_contract<T>(ev[u], dw, ca, cb, gm1, T(c.gamma) / gm1, out);
 #pragma unroll
-        for (int f = 0; f < 4; ++f) st.out[off + f * np] = kv[f];
-        continue;
-      }
-      T v[4];
-      const int s = st.stage;
-      if (s == 0) {
+            for (int f = 0; f < 4; ++f) kv[f] = (r[u][f] - out[f]) * ij[u];
+          } else {
 #pragma unroll
-        for (int f = 0; f < 4; ++f) {
-          const T en = st.e_n[off + f * np];
-          st.acc[off + f * np] = en + (dtv / T(6)) * kv[f];
-          v[f] = en + (dtv / T(2)) * kv[f];
+            for (int f = 0; f < 4; ++f) kv[f] = (r[u][f] - E[(k * 4 + f) * nmax + t]) * ij[u];
+          }
+          stage_point<T, MODE>(c, P, st, dtv, off, np, q, a0 + t, row[k], kv, en[u], ac[u]);
         }
-      } else if (s < 3) {
-        const T a = s == 1 ? dtv / T(2) : dtv;
-#pragma unroll
-        for (int f = 0; f < 4; ++f) {
-          st.acc[off + f * np] = st.acc[off + f * np] + (dtv / T(3)) * kv[f];
-          v[f] = st.e_n[off + f * np] + a * kv[f];
-        }
-      } else {
-#pragma unroll
-        for (int f = 0; f < 4; ++f) v[f] = st.acc[off + f * np] + (dtv / T(6)) * kv[f];
       }
-      apply_bc<T>(c, P, c0 + cc, j0 + j, q, v);
-      const T pr_ = pressure<T>(v[0], v[1], v[2], v[3], gm1);
-      int flag = 0;
-      if (!(isfinite(v[0]) && isfinite(v[1]) && isfinite(v[2]) && isfinite(v[3]))) flag |= 1;
-      else if (!(v[0] > T(0)) || !(pr_ > T(0))) flag |= 2;
-      if (flag) atomicOr(c.status, flag);
-#pragma unroll
-      for (int f = 0; f < 4; ++f) st.out[off + f * np] = v[f];
     }
-    __syncthreads();
+    __syncwarp();
   }
 }
 
