@@ -771,6 +771,208 @@ __device__ __forceinline__ void reg_deriv_pair(const T* a, int sa, const T* b, i
   }
 }
 
+// ------------------------------------------------------------ paired FP32 FFT
+// Two line pairs of one plan per warp (four real lines: the fields of one row
+// or column), in the paired FP32 instructions of sm_100+ (add/mul/fma.f32x2:
+// one instruction for both pairs).  C2 holds one complex value of each pair:
+// re = (pair 0, pair 1), im likewise.  The 32-lane four-step FFT of
+// reg_fft, with the radix-2 stages across lanes in the form
+// out = partner's (w' x) + sg (w' x): every lane first multiplies its own
+// value by w' (1 below, the stage twiddle above), so neither direction needs a
+// select on the lane's half.
+struct C2 {
+  float2 re, im;
+};
+__device__ __forceinline__ float2 bc2(float s) { return make_float2(s, s); }
+// a times the complex scalar w (the same for both pairs)
+__device__ __forceinline__ C2 c2mul(C2 a, float wr, float wi) {
+  return {__ffma2_rn(a.im, bc2(-wi), __fmul2_rn(a.re, bc2(wr))), __ffma2_rn(a.re, bc2(wi), __fmul2_rn(a.im, bc2(wr)))};
+}
+__device__ __forceinline__ C2 c2add(C2 a, C2 b) { return {__fadd2_rn(a.re, b.re), __fadd2_rn(a.im, b.im)}; }
+__device__ __forceinline__ C2 shfl_xor_c2(C2 v, int m) {
+  return {make_float2(__shfl_xor_sync(0xffffffffu, v.re.x, m), __shfl_xor_sync(0xffffffffu, v.re.y, m)),
+          make_float2(__shfl_xor_sync(0xffffffffu, v.im.x, m), __shfl_xor_sync(0xffffffffu, v.im.y, m))};
+}
+
+template <int N1>
+__device__ __forceinline__ void lane_dft2(C2* x, const Cx<float>* tw, bool inv) {
+  Cx<float> W[N1];
+#pragma unroll
+  for (int m = 0; m < N1; ++m) {
+    W[m] = ldtw(tw, 32 * m);
+    if (inv) W[m].y = -W[m].y;
+  }
+  C2 o[N1];
+#pragma unroll
+  for (int k = 0; k < N1; ++k) {
+    C2 acc = x[0];
+#pragma unroll
+    for (int j = 1; j < N1; ++j) acc = c2add(acc, c2mul(x[j], W[(j * k) % N1].x, W[(j * k) % N1].y));
+    o[k] = acc;
+  }
+#pragma unroll
+  for (int k = 0; k < N1; ++k) x[k] = o[k];
+}
+
+template <int N1>
+__device__ __forceinline__ void reg_fft2(C2* x, const Cx<float>* tw, bool inv, int lane) {
+  if (!inv) {
+    lane_dft2<N1>(x, tw, false);
+#pragma unroll
+    for (int k = 1; k < N1; ++k) {
+      const Cx<float> w = ldtw(tw, lane * k);
+      x[k] = c2mul(x[k], w.x, w.y);
+    }
+    // decimation in frequency: lower lane x + p, upper lane (p - x) w
+#pragma unroll
+    for (int s = 16; s >= 1; s >>= 1) {
+      const bool hi = lane & s;
+      const Cx<float> w0 = ldtw(tw, (lane & (s - 1)) * (16 / s) * N1);
+      const float wr = hi ? w0.x : 1.f, wi = hi ? w0.y : 0.f;
+      const float2 sg = bc2(hi ? -1.f : 1.f);
+#pragma unroll
+      for (int k = 0; k < N1; ++k) {
+        const C2 p = shfl_xor_c2(x[k], s);
+        x[k] = c2mul({__ffma2_rn(sg, x[k].re, p.re), __ffma2_rn(sg, x[k].im, p.im)}, wr, wi);
+      }
+    }
+  } else {
+    // decimation in time: lower lane x + conj(w0) p, upper lane p - conj(w0) x
+#pragma unroll
+    for (int s = 1; s <= 16; s <<= 1) {
+      const bool hi = lane & s;
+      const Cx<float> w0 = ldtw(tw, (lane & (s - 1)) * (16 / s) * N1);
+      const float wr = hi ? w0.x : 1.f, wi = hi ? -w0.y : 0.f;
+      const float2 sg = bc2(hi ? -1.f : 1.f);
+#pragma unroll
+      for (int k = 0; k < N1; ++k) {
+        const C2 v = c2mul(x[k], wr, wi);
+        const C2 p = shfl_xor_c2(v, s);
+        x[k] = {__ffma2_rn(sg, v.re, p.re), __ffma2_rn(sg, v.im, p.im)};
+      }
+    }
+#pragma unroll
+    for (int k = 1; k < N1; ++k) {
+      const Cx<float> w = ldtw(tw, lane * k);
+      x[k] = c2mul(x[k], w.x, -w.y);
+    }
+    lane_dft2<N1>(x, tw, true);
+  }
+}
+
+// FC derivative of the line pairs (a, b) and (c, e) of one plan (b, c, e may
+// be null), the FP32 form of reg_deriv_pair for two pairs at once: the same
+// continuation (Gram coefficients of the end values relative to each end's own
+// value, blend table, continuation of the constant part), FFT, (i k)^order
+// and inverse FFT; results times `scale` go to oa[t*soa] ... oe[t*soe].
+template <int N1>
+__device__ __forceinline__ void reg_deriv_quad(const float* a, int sa, const float* b, int sb, const float* c, int sc_,
+                                               const float* e, int se, float* oa, int soa, float* ob, int sob,
+                                               float* oc, int soc, float* oe, int soe, float scale,
+                                               const LineOp<float>& op, int order, int lane) {
+  const int N = op.N, n = 32 * N1, d = op.d;
+  float off[4] = {0.f, 0.f, 0.f, 0.f};
+  if (order != 0) {   // shift by the mean of the end values (Offset<float>)
+    off[0] = (a[0] + a[(N - 1) * sa]) * 0.5f;
+    if (b) off[1] = (b[0] + b[(N - 1) * sb]) * 0.5f;
+    if (c) off[2] = (c[0] + c[(N - 1) * sc_]) * 0.5f;
+    if (e) off[3] = (e[0] + e[(N - 1) * se]) * 0.5f;
+  }
+  const float* L[4] = {a, b, c, e};
+  const int S[4] = {sa, sb, sc_, se};
+  // lanes k < d: Gram coefficient k of every line at both ends, of the values
+  // relative to that end's own value
+  float gR[4] = {0.f, 0.f, 0.f, 0.f}, gL[4] = {0.f, 0.f, 0.f, 0.f};
+  if (lane < d) {
+#pragma unroll
+    for (int l = 0; l < 4; ++l) {
+      if (!L[l]) continue;
+      const float cR = L[l][(N - 1) * S[l]], cL = L[l][0];
+      for (int m = 0; m < d; ++m) {
+        const float q = __ldg(op.gQ32 + m * d + lane);
+        gR[l] = fmaf(q, L[l][(N - d + m) * S[l]] - cR, gR[l]);
+        gL[l] = fmaf(q, L[l][(d - 1 - m) * S[l]] - cL, gL[l]);
+      }
+    }
+  }
+  // the ends' values relative to the line offsets, continued as constants
+  float eR[4] = {0.f, 0.f, 0.f, 0.f}, eL[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+  for (int l = 0; l < 4; ++l)
+    if (L[l]) {
+      eR[l] = L[l][(N - 1) * S[l]] - off[l];
+      eL[l] = L[l][0] - off[l];
+    }
+  C2 x[N1];
+#pragma unroll
+  for (int j1 = 0; j1 < N1; ++j1) {
+    const int j = lane + 32 * j1;
+    float v[4] = {0.f, 0.f, 0.f, 0.f};
+    if (j < N) {
+#pragma unroll
+      for (int l = 0; l < 4; ++l)
+        if (L[l]) v[l] = L[l][j * S[l]] - off[l];
+    }
+    if (32 * j1 + 31 >= N) {   // this register row holds gap points (uniform over the warp)
+      const int q = j - N;
+      float2 sre = bc2(0.f), sim = bc2(0.f);   // (a, c) and (b, e) gap values
+      for (int k = 0; k < d; ++k) {
+        const float2 rRe = make_float2(__shfl_sync(0xffffffffu, gR[0], k), __shfl_sync(0xffffffffu, gR[2], k));
+        const float2 rIm = make_float2(__shfl_sync(0xffffffffu, gR[1], k), __shfl_sync(0xffffffffu, gR[3], k));
+        const float2 lRe = make_float2(__shfl_sync(0xffffffffu, gL[0], k), __shfl_sync(0xffffffffu, gL[2], k));
+        const float2 lIm = make_float2(__shfl_sync(0xffffffffu, gL[1], k), __shfl_sync(0xffffffffu, gL[3], k));
+        if (q >= 0) {
+          const float2 tr = bc2(__ldg(op.gT32 + q * d + k)), tl = bc2(__ldg(op.gT32 + (op.C - 1 - q) * d + k));
+          sre = __ffma2_rn(tr, rRe, __ffma2_rn(tl, lRe, sre));
+          sim = __ffma2_rn(tr, rIm, __ffma2_rn(tl, lIm, sim));
+        }
+      }
+      if (q >= 0) {
+        const float2 rr = bc2(__ldg(op.gR32 + q)), rl = bc2(__ldg(op.gR32 + op.C - 1 - q));
+        sre = __ffma2_rn(make_float2(eR[0], eR[2]), rr, __ffma2_rn(make_float2(eL[0], eL[2]), rl, sre));
+        sim = __ffma2_rn(make_float2(eR[1], eR[3]), rr, __ffma2_rn(make_float2(eL[1], eL[3]), rl, sim));
+        v[0] = sre.x;
+        v[2] = c ? sre.y : 0.f;
+        v[1] = b ? sim.x : 0.f;
+        v[3] = e ? sim.y : 0.f;
+      }
+    }
+    x[j1] = {make_float2(v[0], v[2]), make_float2(v[1], v[3])};
+  }
+  reg_fft2<N1>(x, op.tw, false, lane);
+  const float sc = 6.283185307179586476925286766559f / (float(n) * op.h);
+  const float inv_n = scale / float(n);
+  const int k2 = bitrev5(lane);
+#pragma unroll
+  for (int k1 = 0; k1 < N1; ++k1) {
+    const int k = k1 + N1 * k2;
+    const int km = (2 * k <= n) ? k : k - n;
+    const C2 z = x[k1];
+    if (order == 1) {
+      const float kk = (2 * k == n) ? 0.f : float(km) * sc * inv_n;
+      x[k1] = {__fmul2_rn(bc2(-kk), z.im), __fmul2_rn(bc2(kk), z.re)};
+    } else if (order == 2) {
+      const float kk = float(km) * sc;
+      const float f = -kk * kk * inv_n;
+      x[k1] = {__fmul2_rn(bc2(f), z.re), __fmul2_rn(bc2(f), z.im)};
+    } else {
+      const float f = __ldg(op.flt + k) * inv_n;
+      x[k1] = {__fmul2_rn(bc2(f), z.re), __fmul2_rn(bc2(f), z.im)};
+    }
+  }
+  reg_fft2<N1>(x, op.tw, true, lane);
+#pragma unroll
+  for (int j1 = 0; j1 < N1; ++j1) {
+    const int j = lane + 32 * j1;
+    if (j < N) {
+      oa[j * soa] = x[j1].re.x;
+      if (ob) ob[j * sob] = x[j1].im.x;
+      if (oc) oc[j * soc] = x[j1].re.y;
+      if (oe) oe[j * soe] = x[j1].im.y;
+    }
+  }
+}
+
 // Shared-memory Stockham path for lengths that are not 32 * N1.
 template <typename T>
 __device__ void stk_deriv_pair(const T* a, int sa, const T* b, int sb, T* oa, int soa, T* ob, int sob, T scale,
@@ -1146,6 +1348,25 @@ __device__ __forceinline__ void line_deriv_pair(const T* a, int sa, const T* b, 
     const GramOp<T> gop{c.gramQ, c.gramT + pl.tg_off, c.gramQ64h, c.gramQ64l, c.gramT64 + pl.tg_off,
                         c.gramR + pl.rs_off};
     tl_deriv_pair<T, 4 * N1>(a, sa, b, sb, oa, soa, ob, sob, scale, op, gop, order, lane & 7, tile, active);
+  }
+}
+
+// FP32 lines of the 32-lane shuffle FFT with n1 = 3, 5 go two pairs per warp
+// in paired FP32 arithmetic (reg_deriv_quad): the pass kernels give it the
+// four fields of one row or column, or four adjacent columns, which share a
+// plan.  (n1 = 7, 9 would spill at 128 registers.)
+template <typename T, int N1>
+__host__ __device__ constexpr bool quad_path() {
+  return sizeof(T) == 4 && (N1 == 3 || N1 == 5);
+}
+template <typename T, int N1>
+__device__ __forceinline__ void line_deriv_quad(const T* a, int sa, const T* b, int sb, const T* c, int sc, const T* e,
+                                                int se, T* oa, int soa, T* ob, int sob, T* oc, int soc, T* oe, int soe,
+                                                T scale, const CtxDev& ctx, const PlanDev& pl, T h, int order, int lane,
+                                                bool active) {
+  if constexpr (quad_path<T, N1>()) {
+    const LineOp<float> op = make_op<float>(ctx, pl, h);
+    if (active) reg_deriv_quad<N1>(a, sa, b, sb, c, sc, e, se, oa, soa, ob, sob, oc, soc, oe, soe, scale, op, order, lane);
   }
 }
 

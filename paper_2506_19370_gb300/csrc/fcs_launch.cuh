@@ -49,15 +49,16 @@ __host__ __device__ inline size_t ypass_bytes(int n2max, int tw, int nfmax, int 
 constexpr int kYWarps = 8;
 
 // Blocks per SM the flux passes are compiled for (register budget 65536 /
-// (threads x blocks)).  The 32-lane shuffle FFT (odd n1) keeps only 2 n1
-// values of a line pair per lane, so the FP32 passes of n1 = 3 and 5 take
-// more blocks than the two-level FFT (even n1: 2 x 4 n1 values per lane);
-// n1 = 7 and 9 spill at the lower budgets (ptxas).
+// (threads x blocks)).  FP32 lines of n1 = 3, 5 take the paired-FP32 shuffle
+// FFT (two line pairs per warp: twice the line registers of the pair path),
+// so they get the budgets of the two-level FFT (even n1: 2 x 4 n1 values per
+// lane); n1 = 3 rows take 96 registers; n1 = 7 and 9 (pair path) spill at
+// lower budgets (ptxas).
 __host__ __device__ constexpr int ypass_min_blocks(size_t tsize, int N1) {
-  return (N1 >= 1 && N1 <= 2) ? 4 : (N1 == 3 || (tsize == 4 && N1 == 5)) ? 3 : 2;
+  return (N1 >= 1 && N1 <= 2) ? 4 : (N1 == 3 && tsize == 8) ? 3 : 2;
 }
 __host__ __device__ constexpr int xpass_min_blocks(size_t tsize, int N1) {
-  return (tsize == 4 && N1 == 3) ? 6 : (tsize == 4 && N1 == 5) ? 5 : 4;
+  return (tsize == 4 && N1 == 3) ? 5 : 4;
 }
 
 struct LaunchCfg {

@@ -124,6 +124,19 @@ __global__ void __launch_bounds__(kYWarps * 32, ypass_min_blocks(sizeof(T), N1))
     __syncthreads();
     const int njobs = nf == 1 ? (width + 1) / 2 : 2 * width;
     const T h = T(1) / T(P.n2 - 1);
+    if constexpr (quad_path<T, N1>()) {   // a warp per column (4 fields) or per 4 adjacent columns
+      const int nq = nf == 1 ? (width + 3) / 4 : width;
+#pragma unroll 1
+      for (int u = warp; u < nq; u += kYWarps) {
+        T* l[4];
+#pragma unroll
+        for (int f = 0; f < 4; ++f)
+          l[f] = nf == 1 ? (4 * u + f < width ? E + 4 * u + f : nullptr) : E + f * n2m * ld + u;
+        line_deriv_quad<T, N1>(l[0], ld, l[1], ld, l[2], ld, l[3], ld, l[0], ld, l[1], ld, l[2], ld, l[3], ld, T(1), c,
+                               pl, h, order, lane, true);
+      }
+    } else
+#pragma unroll 1
     for (int u0 = warp * JPR; u0 < njobs; u0 += kYWarps * JPR) {
       const int u = u0 + g;
       const bool active = u < njobs;
@@ -233,9 +246,7 @@ __device__ __forceinline__ void chain_contract(const T* v, const T* dw, T ca, T 
 
 // Pass along q2, the first of the operator: a tile of tw adjacent columns of
 // one patch (coalesced row segments staged in shared memory; blocks of 8
-// warps per SM: 4 for n = 64 (64 registers, a few spilled; measured faster
-// than 3), 3 for n = 96, 2 above, where the line registers of the FFT would
-// spill at 80 registers per thread) writes the partial operator
+// warps, ypass_min_blocks of them per SM) writes the partial operator
 // R = -d/dq2 F2 that the pass along q1 completes.
 // The tile stages 5 values per point (state, then flux in its place, and mu).
 // Viscous columns (mu != 0 somewhere on them) first take e_q2 into G2 (phase
@@ -336,6 +347,22 @@ __global__ void __launch_bounds__(kYWarps * 32, ypass_min_blocks(sizeof(T), N1))
       // line pair's values are all read before any is written, so phase 1
       // differentiates in place)
       const int ncol = phase == 0 ? nact : width;
+      if constexpr (quad_path<T, N1>()) {   // a warp per column: its four fields at once
+#pragma unroll 1
+        for (int u = warp; u < ncol; u += kYWarps) {
+          const int cc = phase == 0 ? act[u] : u;
+          T* src = E + cc;
+          const long long fo = (long long)n2m * ld;
+          // one call for both phases (one inlined copy of the transform)
+          T* o = phase == 0 ? G2 + sbase + cc : src;
+          const long long of = phase == 0 ? np : fo;
+          const int so = phase == 0 ? P.n1 : ld;
+          line_deriv_quad<T, N1>(src, ld, src + fo, ld, src + 2 * fo, ld, src + 3 * fo, ld, o, so, o + of, so,
+                                 o + 2 * of, so, o + 3 * of, so, (phase == 0 || CH) ? T(1) : T(-1), c, pl, h, 1,
+                                 lane, true);
+        }
+      } else
+#pragma unroll 1
       for (int u0 = warp * JPR; u0 < 2 * ncol; u0 += kYWarps * JPR) {
         const int u = u0 + g;
         const bool active = u < 2 * ncol;
@@ -510,17 +537,18 @@ __global__ void __launch_bounds__(kWarps * 32, xpass_min_blocks(sizeof(T), N1))
     const bool p0 = (vrow[0] && cart[0]) || (vrow[1] && cart[1]);
     for (int phase = p0 ? 0 : 1; phase < 2; ++phase) {
       if (phase == 1 && !CH) {
-#pragma unroll
-        for (int k = 0; k < RW; ++k) {
-          if (!has[k]) continue;
-          const PatchDev& P = c.patches[pid[k]];
-          const bool visc = vrow[k];
+#pragma unroll 1
+        for (int k = 0; k < RW; ++k) {   // rolled (one copy of the flux); row data by selects
+          if (!(k ? has[1] : has[0])) continue;
+          const int rowk = k ? row[1] : row[0];
+          const PatchDev& P = c.patches[k ? pid[1] : pid[0]];
+          const bool visc = k ? vrow[1] : vrow[0];
           const bool curv = visc && !P.cart;
-          const int a0 = line_start(P, 0, row[k]), N = P.n1 - a0;
+          const int a0 = line_start(P, 0, rowk), N = P.n1 - a0;
           const int code_lo = a0 ? 1 : P.bc[0];
-          const long long q0 = P.qoff + (long long)row[k] * P.n1 + a0;
+          const long long q0 = P.qoff + (long long)rowk * P.n1 + a0;
           const long long np = (long long)P.n1 * P.n2;
-          const long long s0 = inst * c.sstride + P.soff + (long long)row[k] * P.n1 + a0;
+          const long long s0 = inst * c.sstride + P.soff + (long long)rowk * P.n1 + a0;
           for (int t = lane; t < N; t += 32) {
             T v[4], dv[4], dvo[4], F[4];
 #pragma unroll
@@ -539,6 +567,24 @@ __global__ void __launch_bounds__(kWarps * 32, xpass_min_blocks(sizeof(T), N1))
       // jobs: (row k, field pair pr), 2 RW of them (row data chosen by
       // selects, not by indexing, so the small per-row arrays stay in registers)
       static_assert(RW == 2, "row selection below assumes two rows per warp");
+      if constexpr (quad_path<T, N1>()) {   // a row's four fields at once
+#pragma unroll 1
+        for (int kk = 0; kk < RW; ++kk) {
+          const int pidk = kk ? pid[1] : pid[0], rowk = kk ? row[1] : row[0];
+          bool active = kk ? has[1] : has[0];
+          if (phase == 0 && !(kk ? (vrow[1] && cart[1]) : (vrow[0] && cart[0]))) active = false;
+          const PatchDev& P = c.patches[pidk];
+          const PlanDev& pl = c.plans[line_plan(P, 0, rowk)];
+          const long long np = (long long)P.n1 * P.n2;
+          T* src = E + kk * 4 * nmax;
+          // one call for both phases (one inlined copy of the transform)
+          T* o = phase == 0 ? G1 + inst * c.sstride + P.soff + (long long)rowk * P.n1 + line_start(P, 0, rowk) : src;
+          const long long of = phase == 0 ? np : (long long)nmax;
+          line_deriv_quad<T, N1>(src, 1, src + nmax, 1, src + 2 * nmax, 1, src + 3 * nmax, 1, o, 1, o + of, 1,
+                                 o + 2 * of, 1, o + 3 * of, 1, T(1), c, pl, T(P.hx), 1, lane, active);
+        }
+      } else
+#pragma unroll 1
       for (int r0 = 0; r0 < 2 * RW; r0 += JPR) {
         const int job = r0 + g;
         const int k = job >> 1, pr = job & 1;
@@ -563,18 +609,19 @@ __global__ void __launch_bounds__(kWarps * 32, xpass_min_blocks(sizeof(T), N1))
     // epilogue: L = (R - d/dq1 F1)/J (chain-rule form: (R - (ca A + cb B) w_q1)/J),
     // U points of a lane at a time, whose global loads are all issued before
     // the first of them is used
-    constexpr int U = (sizeof(T) == 4 && N1 != 3 && N1 != 5) ? 4 : 2;   // N1 = 3, 5: 80, 96 registers
+    constexpr int U = (sizeof(T) == 4 && !quad_path<T, N1>()) ? 4 : 2;   // the paired FFT keeps more registers
     const T dtv = st.dt_dev ? T(st.dt_dev[inst]) : st.dt;
     const T* Mt = metrics<T>(c);
     const bool ld_en = rk && st.stage < 3, ld_ac = rk && st.stage > 0;
-#pragma unroll
-    for (int k = 0; k < RW; ++k) {
-      if (!has[k]) continue;
-      const PatchDev& P = c.patches[pid[k]];
-      const int a0 = line_start(P, 0, row[k]), N = P.n1 - a0;
+#pragma unroll 1
+    for (int k = 0; k < RW; ++k) {   // rolled (one copy of the update); row data by selects
+      if (!(k ? has[1] : has[0])) continue;
+      const int rowk = k ? row[1] : row[0];
+      const PatchDev& P = c.patches[k ? pid[1] : pid[0]];
+      const int a0 = line_start(P, 0, rowk), N = P.n1 - a0;
       const long long np = (long long)P.n1 * P.n2;
-      const long long s0 = inst * c.sstride + P.soff + (long long)row[k] * P.n1 + a0;
-      const long long q0 = P.qoff + (long long)row[k] * P.n1 + a0;
+      const long long s0 = inst * c.sstride + P.soff + (long long)rowk * P.n1 + a0;
+      const long long q0 = P.qoff + (long long)rowk * P.n1 + a0;
       for (int t0 = lane; t0 < N; t0 += 32 * U) {
         T r[U][4], en[U][4], ac[U][4], ev[U][4], ij[U];
 #pragma unroll
@@ -609,7 +656,7 @@ __global__ void __launch_bounds__(kWarps * 32, xpass_min_blocks(sizeof(T), N1))
 #pragma unroll
             for (int f = 0; f < 4; ++f) kv[f] = (r[u][f] - E[(k * 4 + f) * nmax + t]) * ij[u];
           }
-          stage_point<T, MODE>(c, P, st, dtv, off, np, q, a0 + t, row[k], kv, en[u], ac[u]);
+          stage_point<T, MODE>(c, P, st, dtv, off, np, q, a0 + t, rowk, kv, en[u], ac[u]);
         }
       }
     }
