@@ -43,6 +43,13 @@ struct Group {
 }  // namespace
 
 struct fcs_ctx {
+  // side streams of the pass launches: the FFT-size classes of one pass are
+  // independent, so the smaller ones run next to the largest (forked from and
+  // joined back into the caller's stream by events; captured graphs get
+  // parallel branches)
+  static constexpr int kSide = 3;
+  cudaStream_t side[kSide] = {};
+  cudaEvent_t ev_fork = nullptr, ev_join[kSide] = {};
   fcs_options opt{};
   int d = 0, C = 0, npatch = 0;
   size_t tsize = 4;  // sizeof(T)
@@ -311,6 +318,42 @@ int set_smem_attrs(const fcs_ctx* c) {
   return FCS_OK;
 }
 
+// Launch order of the FFT-size groups of a pass (dir 0: rows, 1: column
+// tiles): ascending by points, so the largest group comes last, on the
+// caller's stream, and the others on the side streams.
+std::vector<int> pass_order(const fcs_ctx* c, int dir) {
+  const std::vector<Group>& g = dir == 0 ? c->g_rows : c->g_tiles;
+  std::vector<std::pair<long long, int>> w;
+  for (size_t k = 0; k < g.size(); ++k)
+    w.push_back({(long long)g[k].count * (dir == 0 ? 1 : c->tw) * c->gnmax[dir][g[k].n1], (int)k});
+  std::sort(w.begin(), w.end());
+  std::vector<int> o;
+  for (const auto& x : w) o.push_back(x.second);
+  return o;
+}
+// Stream of the k-th of n launches of a pass: the last (largest) on s, the
+// others round-robin on the side streams.
+cudaStream_t side_of(const fcs_ctx* c, cudaStream_t s, int k, int n) {
+  return k == n - 1 ? s : c->side[k % fcs_ctx::kSide];
+}
+// Make the side streams (the first min(nside, kSide)) wait for the work
+// issued so far on s, and s for everything issued on them.
+cudaError_t fork_side(fcs_ctx* c, cudaStream_t s, int nside) {
+  if (nside <= 0) return cudaSuccess;
+  cudaError_t e = cudaEventRecord(c->ev_fork, s);
+  for (int k = 0; k < std::min(nside, fcs_ctx::kSide) && e == cudaSuccess; ++k)
+    e = cudaStreamWaitEvent(c->side[k], c->ev_fork, 0);
+  return e;
+}
+cudaError_t join_side(fcs_ctx* c, cudaStream_t s, int nside) {
+  cudaError_t e = cudaSuccess;
+  for (int k = 0; k < std::min(nside, fcs_ctx::kSide) && e == cudaSuccess; ++k) {
+    e = cudaEventRecord(c->ev_join[k], c->side[k]);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, c->ev_join[k], 0);
+  }
+  return e;
+}
+
 // FC derivative of a scalar field: one launch per FFT-size group of line pairs
 // (rows or columns; the column-tile kernel leaves most of its warps idle on a
 // single field, whose adjacent columns share one transform).
@@ -337,25 +380,36 @@ int launch_flux(fcs_ctx* c, const void* e, const void* mu, int mode, StageArgs<T
   T* R = static_cast<T*>(c->R);
   T* G1 = static_cast<T*>(c->G1);
   T* G2 = static_cast<T*>(c->G2);
-  if (mu) {  // viscous fluxes of curvilinear patches need e_q1 before the column pass
+  if (mu) {  // viscous fluxes of curvilinear patches need e_q1 before the column pass (rows with mu != 0)
     for (const Group& gr : c->g_vpairs) {
       const long long work =
           ((long long)c->dev.instances * gr.count + jobs_per_round(gr.n1) - 1) / jobs_per_round(gr.n1);
       const LaunchCfg g{(unsigned)grid_for(work, kWarps), kWarps * 32, deriv_smem<T>(c, gr.n1), s};
-      FCS_N1_SWITCH(gr.n1, FCS_CUDA((run_fc_deriv<T, K>(c->dev, 0, 1, c->vpairs + gr.begin, gr.count, ep, G1, g)));
+      FCS_N1_SWITCH(gr.n1, FCS_CUDA((run_fc_deriv<T, K>(c->dev, 0, 1, c->vpairs + gr.begin, gr.count, ep, G1, g, mp)));
                     break)
     }
   }
   const bool ch = c->opt.op_form == 1;
-  for (const Group& gr : c->g_tiles) {
+  // columns (all classes), then rows (all classes): each pass forks its
+  // smaller classes onto the side streams, launched first so their few long
+  // blocks start next to the largest class, and joins them back
+  const std::vector<int> ocol = pass_order(c, 1), orow = pass_order(c, 0);
+  FCS_CUDA(fork_side(c, s, (int)ocol.size() - 1));
+  for (size_t k = 0; k < ocol.size(); ++k) {
+    const Group& gr = c->g_tiles[ocol[k]];
+    const cudaStream_t sk = side_of(c, s, (int)k, (int)ocol.size());
     const long long w1 = (long long)c->opt.instances * gr.count;
-    const LaunchCfg gy{(unsigned)grid_for(w1, 1), kYWarps * 32, ypass_smem<T>(c, c->tw, gr.n1), s};
+    const LaunchCfg gy{(unsigned)grid_for(w1, 1), kYWarps * 32, ypass_smem<T>(c, c->tw, gr.n1), sk};
     FCS_N1_SWITCH(gr.n1, FCS_CUDA((run_ypass<T, K>(c->dev, c->tiles + gr.begin, gr.count, ep, mp, R, G1, G2, ch, gy)));
                   break)
   }
-  for (const Group& gr : c->g_rows) {
+  FCS_CUDA(join_side(c, s, (int)ocol.size() - 1));
+  FCS_CUDA(fork_side(c, s, (int)orow.size() - 1));
+  for (size_t k = 0; k < orow.size(); ++k) {
+    const Group& gr = c->g_rows[orow[k]];
+    const cudaStream_t sk = side_of(c, s, (int)k, (int)orow.size());
     const long long w0 = (long long)c->opt.instances * ((gr.count + kRowsPerWarp - 1) / kRowsPerWarp);
-    const LaunchCfg gx{(unsigned)grid_for(w0, kWarps), kWarps * 32, xpass_smem<T>(c, gr.n1), s};
+    const LaunchCfg gx{(unsigned)grid_for(w0, kWarps), kWarps * 32, xpass_smem<T>(c, gr.n1), sk};
     const int b = gr.begin, n = gr.count;
     if (mode == MODE_RHS && !ch) {
       FCS_N1_SWITCH(gr.n1, FCS_CUDA((run_xpass<T, MODE_RHS, K>(c->dev, b, n, ep, mp, R, G1, G2, st, gx))); break)
@@ -369,6 +423,7 @@ int launch_flux(fcs_ctx* c, const void* e, const void* mu, int mode, StageArgs<T
                     break)
     }
   }
+  FCS_CUDA(join_side(c, s, (int)orow.size() - 1));
   if (mode == MODE_RK && c->dev.n_nsw > 0) {  // no-slip walls: temperature after every point's stage
     k_noslip_temperature<T><<<dim3((c->dev.n_nsw + 127) / 128, c->opt.instances), 128, 0, s>>>(c->dev, st.out);
     FCS_CUDA(cudaGetLastError());
@@ -603,6 +658,11 @@ void fc_destroy(fcs_ctx* c) {
   if (!c) return;
   if (c->gexec) cudaGraphExecDestroy(c->gexec);
   if (c->graph) cudaGraphDestroy(c->graph);
+  for (int k = 0; k < fcs_ctx::kSide; ++k) {
+    if (c->side[k]) cudaStreamDestroy(c->side[k]);
+    if (c->ev_join[k]) cudaEventDestroy(c->ev_join[k]);
+  }
+  if (c->ev_fork) cudaEventDestroy(c->ev_fork);
   for (void* p : c->allocs) cudaFree(p);
   delete c;
 }
@@ -1135,6 +1195,11 @@ int fc_setup(fcs_ctx** out, int d, int C, const fcs_patch_desc* pd, int npatch, 
   D.tw = c->tw;
   D.n2max = c->n2max;
   if ((rc = (o.dtype == FCS_F64 ? set_smem_attrs<double>(c) : set_smem_attrs<float>(c)))) return fail(rc);
+  if (cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess) return fail(FCS_ECUDA);
+  for (int k = 0; k < fcs_ctx::kSide; ++k)
+    if (cudaStreamCreateWithFlags(&c->side[k], cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_join[k], cudaEventDisableTiming) != cudaSuccess)
+      return fail(FCS_ECUDA);
   if (o.dtype != FCS_F64) {  // the metrics use FP64 derivatives
     for (int dir = 0; dir < 2; ++dir)
       for (int n1 : c->n1_dir[dir]) {
