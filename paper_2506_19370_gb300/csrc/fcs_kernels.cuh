@@ -55,16 +55,21 @@ __global__ void k_interp(CtxDev c, const int4* __restrict__ ent, const T* __rest
   const long long total = (long long)c.instances * nent;
   const long long istride = nfields == 4 ? c.sstride : c.qstride;
   const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
-  for (long long base = ((long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 4; base < total;
-       base += nwarps * 4) {
+  // the entry record of the group's next iteration is loaded one iteration
+  // ahead, so an iteration waits on one round trip (the donor values), not two
+  long long base = ((long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 4;
+  int4 xnext = base + grp < total ? ent[(base + grp) % nent] : make_int4(0, 0, 0, 0);
+  for (; base < total; base += nwarps * 4) {
     const long long t = base + grp;
     const bool ok = t < total;
+    const int4 x = xnext;
+    const long long tn = t + nwarps * 4;
+    if (tn < total) xnext = ent[tn % nent];
     T acc[4] = {T(0), T(0), T(0), T(0)};
     long long dbase = 0, fd = 0;
     if (ok) {
       const int inst = (int)(t / nent);
       const int k = (int)(t % nent);
-      const int4 x = ent[k];
       const T* wk = w + (size_t)k * 2 * S;   // independent of the entry record: both loads in flight together
       const long long fs = x.w;
       fd = ent_dnp(x);

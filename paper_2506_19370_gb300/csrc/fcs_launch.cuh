@@ -80,7 +80,7 @@ cudaError_t prep_fc_cols(size_t smem);
 
 template <typename T, int N1>
 cudaError_t run_fc_deriv(const CtxDev& c, int dir, int order, const int4* pairs, int npairs, const T* in, T* out,
-                         LaunchCfg g);
+                         LaunchCfg g, const T* mu = nullptr);
 template <typename T, int N1>
 cudaError_t run_fc_cols(const CtxDev& c, int order, const int2* tiles, int ntiles, int nf, const T* in, T* out,
                         LaunchCfg g);

@@ -39,8 +39,8 @@ cudaError_t run_fc_cols(const CtxDev& c, int order, const int2* tiles, int ntile
 }
 template <typename T, int N1>
 cudaError_t run_fc_deriv(const CtxDev& c, int dir, int order, const int4* pairs, int npairs, const T* in, T* out,
-                         LaunchCfg g) {
-  k_fc_deriv<T, N1><<<g.grid, g.block, g.smem, g.stream>>>(c, dir, order, pairs, npairs, in, out);
+                         LaunchCfg g, const T* mu) {
+  k_fc_deriv<T, N1><<<g.grid, g.block, g.smem, g.stream>>>(c, dir, order, pairs, npairs, in, out, mu);
   return cudaGetLastError();
 }
 template <typename T, int MODE, int N1>
@@ -67,7 +67,7 @@ cudaError_t run_ypass(const CtxDev& c, const int2* tiles, int ntiles, const T* e
   template cudaError_t fcs::run_fc_cols<T, N1>(const CtxDev&, int, const int2*, int, int, const T*, T*,        \
                                                LaunchCfg);                                                    \
   template cudaError_t fcs::run_fc_deriv<T, N1>(const CtxDev&, int, int, const int4*, int, const T*, T*,     \
-                                                LaunchCfg);                                                   \
+                                                LaunchCfg, const T*);                                         \
   template cudaError_t fcs::run_ypass<T, N1>(const CtxDev&, const int2*, int, const T*, const T*, T*, const T*, \
                                              T*, int, LaunchCfg);                                             \
   template cudaError_t fcs::run_xpass<T, fcs::MODE_RHS, N1>(const CtxDev&, int, int, const T*, const T*,     \

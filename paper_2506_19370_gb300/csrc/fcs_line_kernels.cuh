@@ -25,9 +25,12 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // each warp takes jobs_per_round(N1) line pairs at a time (two real lines ->
 // one complex FFT).  A pair (patch, line a,
 // line b, w) reads the scalar layout if w < 0, else field w of the state layout.
+// mu (scalar layout, may be null): transform only the pairs with mu != 0
+// somewhere on their lines (the viscous gradients, which only ever meet mu).
 template <typename T, int N1>
 __global__ void __launch_bounds__(kWarps * 32) k_fc_deriv(CtxDev c, int dir, int order, const int4* __restrict__ pairs,
-                                                           int npairs, const T* __restrict__ in, T* __restrict__ out) {
+                                                           int npairs, const T* __restrict__ in, T* __restrict__ out,
+                                                           const T* __restrict__ mu) {
   constexpr int JPR = jobs_per_round(N1);
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -40,11 +43,32 @@ __global__ void __launch_bounds__(kWarps * 32) k_fc_deriv(CtxDev c, int dir, int
   const long long total = (long long)c.instances * npairs;
   const long long rounds = (total + JPR - 1) / JPR;
   for (long long r = (long long)blockIdx.x * kWarps + warp; r < rounds; r += (long long)gridDim.x * kWarps) {
+    unsigned vis = 0xffffffffu;   // bit k: pair k of the round is transformed
+    if (mu) {
+      vis = 0u;
+      for (int k = 0; k < JPR; ++k) {
+        const long long w = r * JPR + k;
+        if (w >= total) break;
+        const int inst = (int)(w / npairs);
+        const int4 pr = pairs[w % npairs];
+        const PatchDev& P = c.patches[pr.x];
+        const int N = c.plans[line_plan(P, dir, pr.y)].N;
+        const long long stride = dir == 0 ? 1 : P.n1;
+        const long long s0 = (long long)line_start(P, dir, pr.y) * stride;
+        const long long la = (dir == 0 ? (long long)pr.y * P.n1 : pr.y) + s0;
+        const long long lb = pr.z < 0 ? -1 : (dir == 0 ? (long long)pr.z * P.n1 : pr.z) + s0;
+        const T* m = mu + inst * c.qstride + P.qoff;
+        bool any = false;
+        for (int t = lane; t < N; t += 32) any |= m[la + t * stride] != T(0) || (lb >= 0 && m[lb + t * stride] != T(0));
+        if (__any_sync(0xffffffffu, any)) vis |= 1u << k;
+      }
+    }
     // stage the JPR line pairs of this round (asynchronous copies: all of a
     // lane's loads are in flight together)
     for (int k = 0; k < JPR; ++k) {
       const long long w = r * JPR + k;
       if (w >= total) break;
+      if (!(vis >> k & 1u)) continue;
       const int inst = (int)(w / npairs);
       const int4 pr = pairs[w % npairs];
       const PatchDev& P = c.patches[pr.x];
@@ -63,8 +87,8 @@ __global__ void __launch_bounds__(kWarps * 32) k_fc_deriv(CtxDev c, int dir, int
     cp_async_wait_all();
     __syncwarp();
     const long long w = r * JPR + g;
-    const bool active = w < total;
-    const long long wc = active ? w : r * JPR;
+    const bool active = w < total && (vis >> g & 1u);
+    const long long wc = w < total ? w : r * JPR;
     const int inst = (int)(wc / npairs);
     const int4 pr = pairs[wc % npairs];
     const PatchDev& P = c.patches[pr.x];
