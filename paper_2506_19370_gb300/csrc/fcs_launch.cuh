@@ -53,9 +53,10 @@ constexpr int kYWarps = 8;
 // FFT (two line pairs per warp: twice the line registers of the pair path),
 // so they get the budgets of the two-level FFT (even n1: 2 x 4 n1 values per
 // lane); n1 = 3 rows take 96 registers; n1 = 7 and 9 (pair path) spill at
-// lower budgets (ptxas).
+// lower budgets (ptxas).  Column passes of n1 <= 2 run 3 blocks of 8 warps
+// (85 registers; 4 blocks spilled and measured 6 % slower on the Sod batch).
 __host__ __device__ constexpr int ypass_min_blocks(size_t tsize, int N1) {
-  return (N1 >= 1 && N1 <= 2) ? 4 : (N1 == 3 && tsize == 8) ? 3 : 2;
+  return ((N1 >= 1 && N1 <= 2) || (N1 == 3 && tsize == 8)) ? 3 : 2;
 }
 __host__ __device__ constexpr int xpass_min_blocks(size_t tsize, int N1) {
   return (tsize == 4 && N1 == 3) ? 5 : 4;

@@ -633,7 +633,7 @@ __global__ void __launch_bounds__(kWarps * 32, xpass_min_blocks(sizeof(T), N1))
     // epilogue: L = (R - d/dq1 F1)/J (chain-rule form: (R - (ca A + cb B) w_q1)/J),
     // U points of a lane at a time, whose global loads are all issued before
     // the first of them is used
-    constexpr int U = (sizeof(T) == 4 && !quad_path<T, N1>()) ? 4 : 2;   // the paired FFT keeps more registers
+    constexpr int U = 2;   // measured faster than 4 points per batch (registers)
     const T dtv = st.dt_dev ? T(st.dt_dev[inst]) : st.dt;
     const T* Mt = metrics<T>(c);
     const bool ld_en = rk && st.stage < 3, ld_ac = rk && st.stage > 0;
