@@ -151,7 +151,8 @@ void fcs_default_options(fcs_options* opt);
  * receiver itself), FCS_EUNSUPPORTED (FFT length with a prime factor above
  * 7; a line class whose buffers exceed a block's shared memory, possible
  * for FP64 lines near 512 points; no-slip walls on an L-shaped patch or on
- * two adjacent sides), FCS_ENOMEM, FCS_ECUDA.  *out is NULL on error. */
+ * two adjacent sides; more than 2^31 - 1 state elements per instance),
+ * FCS_ENOMEM, FCS_ECUDA.  *out is NULL on error. */
 int fc_setup(fcs_ctx** out, int d, int C, const fcs_patch_desc* patches, int npatch,
              const fcs_options* opt);
 
