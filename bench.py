@@ -638,8 +638,8 @@ def run_ours(args):
                 "achieved": gbs if bound == "hbm" else tfl, "peak": hbm_peak if bound == "hbm" else alu32,
                 "unit": "GB/s" if bound == "hbm" else "TFLOP/s",
                 "frac": gbs / hbm_peak if bound == "hbm" else tfl / alu32, "traffic": traffic,
-                "kernel": "rk_stage: flux pass along q1 (k_xpass) + flux pass along q2 with the stage update "
-                          "(k_ypass), every FFT-size group",
+                "kernel": "rk_stage: flux pass along q2 (k_ypass, partial operator R) + flux pass along q1 with "
+                          "the stage update (k_xpass), every FFT-size group (the groups of a pass concurrent)",
                 "stage_ms": stage_avg_ms, "alg_bytes_per_point_stage": alg_b,
                 "hbm": {"achieved_gbs": gbs, "peak_gbs": hbm_peak, "frac": gbs / hbm_peak, "peak_source": hbm_src},
                 "alu": {"executed_flops_per_point_stage": alg_f, "viscous_line_fraction": vfrac,
